@@ -1,0 +1,188 @@
+/*
+ * kitc.h -- C ABI of libkitc, a GB300 (sm_103a) implementation of the
+ * kernel-independent treecode (KITC) of Wang, Krasny & Tlupova, "A
+ * kernel-independent treecode based on barycentric Lagrange interpolation"
+ * (arXiv 1902.02250).
+ *
+ * The library evaluates the sum of Eq. N-body,
+ *     u(x_i) = sum_j k(x_i, y_j) f_j,
+ * for the regularized Stokes kernels of Sec. 7, either directly or with the
+ * treecode of Algorithm 2: a tree of clusters (Sec. 6), modified weights at
+ * the (n+1)^3 Chebyshev points of each cluster (Eq. modified_weights,
+ * Algorithm 1), and a MAC-driven traversal (Eq. MAC) that sums far clusters
+ * through Eq. pc_approximation_3D and near leaves through Eq.
+ * pc_interaction_3D.
+ *
+ * Conventions shared by every call:
+ *   - Arrays are row-major.  Coordinates are n x 3 doubles; weights are
+ *     n x w_in doubles; outputs are n x w_out doubles (w_in, w_out per
+ *     kernel below).  Inputs and outputs are in the caller's order.
+ *   - A pointer documented as "device" must point to memory of the current
+ *     CUDA device; "host" pointers are ordinary process memory.  The caller
+ *     owns every buffer it passes and keeps it alive until the work queued on
+ *     `stream` is complete.  The library owns what a kitc_tree holds.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     queued on it in order; only the calls that say so synchronize it.
+ *   - Every call returns a kitc_status; nothing is thrown across the ABI.
+ *     Argument errors are reported before any GPU work is queued.  After
+ *     KITC_ERR_CUDA the handle must only be freed.
+ *   - There is no CPU fallback: without a usable CUDA device the calls fail
+ *     with KITC_ERR_CUDA.
+ */
+#ifndef KITC_H
+#define KITC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KITC_OK = 0,
+    KITC_ERR_INVALID_ARG = 1, /* a null pointer, a size or parameter out of range */
+    KITC_ERR_CUDA = 2,        /* a CUDA runtime call failed                       */
+    KITC_ERR_OOM = 3,         /* device memory could not be allocated             */
+    KITC_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out               */
+    KITC_ERR_STATE = 5        /* call out of order (e.g. evaluate before weights) */
+} kitc_status;
+
+/* Kernels of Sec. 7.  d = x - y, r = |d|, H1, H2, Q, D1, D2 of Eq. MRS_kernels. */
+typedef enum {
+    KITC_STOKESLET = 0,        /* Eq. Velocity_1; w_in 3 (force f), w_out 3 (u)          */
+    KITC_ROTLET = 1,           /* torque terms of Eq. MRS_2; w_in 3 (torque n), w_out 6 (u, w) */
+    KITC_STOKESLET_ROTLET = 2, /* Eq. MRS_2; w_in 6 (f then n), w_out 6 (u then w)       */
+    KITC_TEST_POLY = 99        /* test kernel prod_l (1 + x_l y_l / 2)^3 times f; 3 -> 3  */
+} kitc_kernel;
+
+/* Arithmetic of the evaluation.  KITC_FP64: everything in FP64.
+ * KITC_MIXED: kernel evaluations in FP32 (coordinate differences formed
+ * from hi/lo FP32 pairs, far-field points taken relative to the target
+ * batch's centre), FP32 partial sums over short runs, FP64 accumulation
+ * of the per-leaf and per-cluster sums.  The tree, the MAC decisions, the
+ * barycentric denominators and the modified-weight sums are FP64 in both. */
+typedef enum { KITC_FP64 = 0, KITC_MIXED = 1 } kitc_precision;
+
+/* Traversal.  KITC_MAC_PARTICLE takes Algorithm 2's decision for every
+ * target: cluster C is used through its grid points iff r_C <= theta * R
+ * with R = |x - y_C| (Eq. MAC), and the target then skips C's subtree.
+ * KITC_MAC_BATCH takes one decision per target batch: C is accepted iff
+ * r_C <= theta * dist(box_B, y_C), box_B the smallest box enclosing the
+ * batch; every accepted C then also passes Eq. MAC for each target. */
+typedef enum { KITC_MAC_PARTICLE = 0, KITC_MAC_BATCH = 1 } kitc_mac;
+
+typedef struct {
+    double theta;      /* MAC parameter of Eq. MAC, >= 0 (0: direct sum through the tree) */
+    int degree;        /* interpolation degree n, 1..16; (n+1)^3 grid points per cluster  */
+    int leaf_size;     /* N0: a cluster with <= N0 particles is a leaf (Sec. 6), >= 1     */
+    double eps;        /* MRS regularization epsilon (Sec. 7), >= 0; with eps = 0 a pair
+                          at r = 0 contributes nothing (Sec. 1)                          */
+    int kernel;        /* kitc_kernel                                                     */
+    int precision;     /* kitc_precision                                                  */
+    int mac;           /* kitc_mac                                                        */
+    int target_batch;  /* targets per batch, 1..64 (0 = 64).  Targets are ordered by the
+                          Sec. 6 tree built on them with leaf size target_batch; batch b
+                          is the slots [b*B, (b+1)*B) of that order                      */
+} kitc_params;
+
+typedef struct kitc_tree_s *kitc_tree; /* opaque; owned by the library */
+
+typedef struct {
+    int64_t n_sources, n_clusters, n_leaves;
+    int32_t depth, degree;
+    int64_t n_targets, n_batches;          /* of the last kitc_evaluate                */
+    int64_t far_entries, near_entries;     /* interaction-list entries (batch, cluster) */
+    int64_t near_pairs, far_points;        /* (target, source) and (target, grid point)
+                                              kernel evaluations that count toward u   */
+    int64_t device_bytes;                  /* device memory held by the handle         */
+    float ms_tree, ms_weights, ms_lists, ms_evaluate; /* device time of the last calls */
+} kitc_stats;
+
+/* Sec. 6 tree build.  src_xyz: device, n_src x 3.  Copies the sources into
+ * tree order inside the handle, so src_xyz may be reused once the stream has
+ * passed this call.  Synchronizes `stream` once per tree level (the cluster
+ * count of the next level is read back).  On success *out holds a new
+ * handle; free it with kitc_free_tree. */
+kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
+                            void *stream, kitc_tree *out);
+
+/* Eq. modified_weights (Algorithm 1) for every cluster of the tree, in
+ * FP64.  w: device, n_src x w_in, in the order of src_xyz.  Replaces any
+ * weights set before; stream-ordered, no synchronization. */
+kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream);
+
+/* Algorithm 2: u at n_tgt targets.  tgt_xyz: device, n_tgt x 3; out: device,
+ * n_tgt x w_out, overwritten.  Builds the target order, the interaction
+ * lists and runs the fused near/far evaluator.  Synchronizes `stream` once
+ * per level of the target tree and once to size the lists.
+ * KITC_ERR_STATE if kitc_modified_weights was not called. */
+kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
+                          void *stream);
+
+/* Eq. N-body by direct summation over all sources (self term included;
+ * with eps = 0 a pair at r = 0 is skipped).  All pointers device.  Uses
+ * p->kernel, p->eps, p->precision and p->target_batch; the tree
+ * parameters are ignored.  Allocates and frees its own scratch. */
+kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,
+                        const double *w, int64_t n_src, const kitc_params *p, double *out,
+                        void *stream);
+
+/* End to end from host memory: copies the sources, weights and targets to
+ * the device, builds the tree, computes the modified weights, evaluates,
+ * and copies u back.  All pointers host; tgt_xyz = NULL means the targets
+ * are the sources (n_tgt ignored).  Synchronizes `stream` before returning. */
+kitc_status kitc_solve_host(const double *src_xyz, const double *w, int64_t n_src,
+                            const double *tgt_xyz, int64_t n_tgt, const kitc_params *p,
+                            double *out, void *stream);
+
+/* Statistics of the handle; waits for the handle's timing events. */
+kitc_status kitc_get_stats(kitc_tree t, kitc_stats *s);
+
+/* Copies the tree to host arrays (any pointer may be NULL; sizes from
+ * kitc_get_stats): perm[n_sources] (perm[slot] = caller index), lo/hi
+ * [n_clusters][3], begin/end [n_clusters], first_child, n_child, level,
+ * parent [n_clusters].  Clusters are numbered breadth first; the children
+ * of a cluster are contiguous and ordered by octant code (bit 0 = upper x,
+ * bit 1 = upper y, bit 2 = upper z).  Synchronizes `stream`. */
+kitc_status kitc_tree_download(kitc_tree t, int64_t *perm, double *lo, double *hi,
+                               int64_t *begin, int64_t *end, int32_t *first_child,
+                               int32_t *n_child, int32_t *level, int32_t *parent,
+                               void *stream);
+
+/* Copies the FP64 modified weights to a host array
+ * fhat[n_clusters][n+1][n+1][n+1][w_in].  Synchronizes `stream`. */
+kitc_status kitc_weights_download(kitc_tree t, double *fhat, void *stream);
+
+/* Copies the interaction lists of the last kitc_evaluate to host arrays
+ * (any may be NULL): tperm[n_targets] (target order), nfar/nnear
+ * [n_batches], far/near [far_entries / near_entries] cluster ids in
+ * traversal order, far_mask/near_mask (bit k = the batch's k-th target
+ * uses the entry).  Synchronizes `stream`. */
+kitc_status kitc_lists_download(kitc_tree t, int64_t *tperm, int64_t *nfar, int64_t *nnear,
+                                int32_t *far, uint64_t *far_mask, int32_t *near,
+                                uint64_t *near_mask, void *stream);
+
+void kitc_free_tree(kitc_tree t);
+
+const char *kitc_status_string(kitc_status s);
+
+/* Number of w_in / w_out components of a kernel, or -1 if unknown. */
+int kitc_kernel_win(int kernel);
+int kitc_kernel_wout(int kernel);
+
+/* Device-side wait limit in milliseconds for the evaluator's pipeline
+ * barriers (default 2000).  A wait that runs out makes the call return
+ * KITC_ERR_TIMEOUT.  Returns the previous value. */
+int kitc_set_wait_limit_ms(int ms);
+
+/* Failure-detection self test: launches one CTA whose thread waits, with the
+ * same bounded wait the evaluator uses, on a shared-memory barrier that
+ * nothing completes.  Returns KITC_ERR_TIMEOUT once limit_ms (1..10000) has
+ * passed -- the path a stuck evaluator pipeline takes -- and leaves the CUDA
+ * context usable.  Synchronizes `stream`. */
+kitc_status kitc_watchdog_selftest(int limit_ms, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KITC_H */

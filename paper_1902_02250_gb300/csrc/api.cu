@@ -1,0 +1,539 @@
+// C ABI of libkitc: argument checks, handle life cycle, stage timing.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+int g_wait_limit_ms = 2000;
+
+struct kitc_tree_s {
+    kitc_params p{};
+    int win = 3, wout = 3, device = 0;
+    TreeDev src, tgt;
+    WeightsDev wts;
+    ListsDev lists;
+    DevBuf flags;            // int [4]: work counter, error flag
+    bool has_weights = false, evaluated = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[8] = {};
+    bool ev_ok = false;
+    bool stage_done[4] = {false, false, false, false};
+};
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+kitc_status kitc_from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return KITC_OK;
+    cudaGetLastError();  // clear a non-sticky error so later calls start clean
+    return e == cudaErrorMemoryAllocation ? KITC_ERR_OOM : KITC_ERR_CUDA;
+}
+
+kitc_status host_readback_buffer(void **p)
+{
+    static std::mutex mu;
+    static void *buf = nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!buf) KITC_CUDA(cudaHostAlloc(&buf, 64, cudaHostAllocPortable));
+    *p = buf;
+    return KITC_OK;
+}
+
+kitc_status dev_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    static bool pool_set[64] = {false};
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !pool_set[dev]) {
+        // keep freed blocks in this process's pool between calls
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        pool_set[dev] = true;
+    }
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    KITC_CUDA(cudaMallocAsync(p, bytes, s));
+    return KITC_OK;
+}
+
+void dev_free(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+kitc_status DevBuf::reserve(size_t b, cudaStream_t s, bool keep)
+{
+    if (b <= bytes && ptr) return KITC_OK;
+    void *np_ = nullptr;
+    KITC_TRY(dev_alloc(&np_, b, s));
+    if (keep && ptr && bytes) {
+        cudaError_t e = cudaMemcpyAsync(np_, ptr, bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            dev_free(np_, s);
+            return kitc_from_cuda(e);
+        }
+    }
+    dev_free(ptr, s);
+    ptr = np_;
+    bytes = b;
+    return KITC_OK;
+}
+
+void DevBuf::release(cudaStream_t s)
+{
+    dev_free(ptr, s);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+void cheb_cos_table(int n, double *t)
+{
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k <= KITC_MAX_DEGREE; ++k) t[k] = k <= n ? cos((double)k * pi / (double)n) : 0.0;
+}
+
+namespace {
+
+bool valid_params(const kitc_params *p)
+{
+    if (!p) return false;
+    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return false;
+    if (p->degree < 1 || p->degree > KITC_MAX_DEGREE) return false;
+    if (p->leaf_size < 1) return false;
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
+    if (kitc_kernel_win(p->kernel) < 0) return false;
+    if (p->precision != KITC_FP64 && p->precision != KITC_MIXED) return false;
+    if (p->mac != KITC_MAC_PARTICLE && p->mac != KITC_MAC_BATCH) return false;
+    if (p->target_batch < 0 || p->target_batch > KITC_MAX_BATCH) return false;
+    if (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED) return false;
+    return true;
+}
+
+bool valid_count(int64_t n) { return n >= 1 && n <= (int64_t)INT32_MAX - 1024; }
+
+// A pointer the kernels may read or write: device, managed or registered host memory.
+bool device_accessible(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+           at.type == cudaMemoryTypeHost;
+}
+
+int batch_of(const kitc_params &p) { return p.target_batch == 0 ? KITC_MAX_BATCH : p.target_batch; }
+
+void record(kitc_tree t, int i, cudaStream_t s)
+{
+    if (t->ev_ok) cudaEventRecord(t->ev[i], s);
+}
+
+kitc_status read_error_flag(int *d_err, cudaStream_t s)
+{
+    int *h = nullptr;
+    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h)));
+    KITC_CUDA(cudaMemcpyAsync(h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return h[0] ? KITC_ERR_TIMEOUT : KITC_OK;
+}
+
+void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
+{
+    a.degree = p.degree;
+    cheb_cos_table(p.degree, a.cheb);
+    a.eps = p.eps;
+    a.queue = flags;
+    a.err = flags + 1;
+    a.wait_ns = (unsigned long long)g_wait_limit_ms * 1000000ull;
+}
+
+void free_handle(kitc_tree t)
+{
+    cudaStream_t s = t->stream;
+    t->src.release(s);
+    t->tgt.release(s);
+    t->wts.release(s);
+    t->lists.release(s);
+    t->flags.release(s);
+    if (t->ev_ok)
+        for (auto &e : t->ev) cudaEventDestroy(e);
+    delete t;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int kitc_kernel_win(int kernel)
+{
+    switch (kernel) {
+    case KITC_STOKESLET: case KITC_ROTLET: case KITC_TEST_POLY: return 3;
+    case KITC_STOKESLET_ROTLET: return 6;
+    default: return -1;
+    }
+}
+
+int kitc_kernel_wout(int kernel)
+{
+    switch (kernel) {
+    case KITC_STOKESLET: case KITC_TEST_POLY: return 3;
+    case KITC_ROTLET: case KITC_STOKESLET_ROTLET: return 6;
+    default: return -1;
+    }
+}
+
+const char *kitc_status_string(kitc_status s)
+{
+    switch (s) {
+    case KITC_OK: return "ok";
+    case KITC_ERR_INVALID_ARG: return "invalid argument";
+    case KITC_ERR_CUDA: return "CUDA error";
+    case KITC_ERR_OOM: return "out of device memory";
+    case KITC_ERR_TIMEOUT: return "device-side wait timed out";
+    case KITC_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int kitc_set_wait_limit_ms(int ms)
+{
+    int old = g_wait_limit_ms;
+    if (ms > 0) g_wait_limit_ms = ms;
+    return old;
+}
+
+kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
+                            void *stream, kitc_tree *out)
+{
+    if (!out) return KITC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid_params(p) || !valid_count(n_src) || !device_accessible(src_xyz))
+        return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    kitc_tree t = new kitc_tree_s();
+    t->p = *p;
+    t->p.target_batch = batch_of(*p);
+    t->win = kitc_kernel_win(p->kernel);
+    t->wout = kitc_kernel_wout(p->kernel);
+    t->stream = s;
+    cudaGetDevice(&t->device);
+    t->ev_ok = true;
+    for (auto &e : t->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) t->ev_ok = false;
+    record(t, 0, s);
+    kitc_status st = tree_build(src_xyz, n_src, p->leaf_size, s, t->src);
+    if (st == KITC_OK) st = t->flags.reserve(4 * sizeof(int), s);
+    record(t, 1, s);
+    if (st != KITC_OK) {
+        free_handle(t);
+        return st;
+    }
+    t->stage_done[0] = true;
+    *out = t;
+    return KITC_OK;
+}
+
+kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
+{
+    if (!t || !device_accessible(w)) return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t->stream = s;
+    bool mixed = t->p.precision == KITC_MIXED;
+    t->has_weights = false;
+    record(t, 2, s);
+    KITC_TRY(weights_compute(t->src, w, t->win, t->p.degree, s, t->wts));
+    KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
+    KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
+    record(t, 3, s);
+    t->has_weights = true;
+    t->stage_done[1] = true;
+    return KITC_OK;
+}
+
+kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
+                          void *stream)
+{
+    if (!t || !valid_count(n_tgt) || !device_accessible(tgt_xyz) || !device_accessible(out))
+        return KITC_ERR_INVALID_ARG;
+    if (!t->has_weights) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t->stream = s;
+    const kitc_params &p = t->p;
+    int B = p.target_batch;
+    t->evaluated = false;
+    record(t, 4, s);
+    KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt));
+    KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, p.mac, s, t->lists));
+    record(t, 5, s);
+    EvalArgs a{};
+    a.tx = t->tgt.xs.as<double>();
+    a.ty = a.tx + n_tgt;
+    a.tz = a.tx + 2 * n_tgt;
+    a.tstride = 1;
+    a.tperm = t->tgt.perm.as<int32_t>();
+    a.nt = n_tgt;
+    a.batch = B;
+    a.nb = t->lists.nb;
+    a.bctr = t->lists.bctr.as<dvec4>();
+    a.far_off = t->lists.far_off.as<int64_t>();
+    a.near_off = t->lists.near_off.as<int64_t>();
+    a.far_id = t->lists.far_id.as<int32_t>();
+    a.near_id = t->lists.near_id.as<int32_t>();
+    a.far_mask = t->lists.far_mask.as<uint64_t>();
+    a.near_mask = t->lists.near_mask.as<uint64_t>();
+    a.src = t->wts.src.ptr;
+    a.proxy = t->wts.proxy.ptr;
+    a.clo = t->src.lo.as<dvec4>();
+    a.chi = t->src.hi.as<dvec4>();
+    a.cbegin = t->src.begin.as<int32_t>();
+    a.cend = t->src.end.as<int32_t>();
+    a.out = out;
+    fill_eval_common(a, p, t->flags.as<int>());
+    KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
+    KITC_TRY(evaluate_launch(p.kernel, p.precision == KITC_MIXED, a, s));
+    record(t, 6, s);
+    KITC_TRY(read_error_flag(t->flags.as<int>() + 1, s));
+    t->evaluated = true;
+    t->stage_done[2] = t->stage_done[3] = true;
+    return KITC_OK;
+}
+
+kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,
+                        const double *w, int64_t n_src, const kitc_params *p, double *out,
+                        void *stream)
+{
+    if (!p || kitc_kernel_win(p->kernel) < 0 || !(p->eps >= 0.0) || !isfinite(p->eps) ||
+        (p->precision != KITC_FP64 && p->precision != KITC_MIXED) || p->target_batch < 0 ||
+        p->target_batch > KITC_MAX_BATCH ||
+        (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED))
+        return KITC_ERR_INVALID_ARG;
+    if (!valid_count(n_tgt) || !valid_count(n_src) || !device_accessible(tgt_xyz) ||
+        !device_accessible(src_xyz) || !device_accessible(w) || !device_accessible(out))
+        return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    bool mixed = p->precision == KITC_MIXED;
+    int win = kitc_kernel_win(p->kernel);
+    int B = batch_of(*p);
+    DevBuf rec, flags;
+    kitc_status st = pack_sources(nullptr, src_xyz, w, n_src, win, mixed, s, rec);
+    if (st == KITC_OK) st = flags.reserve(4 * sizeof(int), s);
+    if (st == KITC_OK) {
+        EvalArgs a{};
+        a.tx = tgt_xyz;
+        a.ty = tgt_xyz + 1;
+        a.tz = tgt_xyz + 2;
+        a.tstride = 3;
+        a.tperm = nullptr;
+        a.nt = n_tgt;
+        a.batch = B;
+        a.nb = (n_tgt + B - 1) / B;
+        a.direct_ns = n_src;
+        a.src = rec.ptr;
+        kitc_params q = *p;
+        q.degree = 1;
+        a.out = out;
+        fill_eval_common(a, q, flags.as<int>());
+        cudaError_t e = cudaMemsetAsync(flags.ptr, 0, 4 * sizeof(int), s);
+        st = e == cudaSuccess ? evaluate_launch(p->kernel, mixed, a, s) : kitc_from_cuda(e);
+        if (st == KITC_OK) st = read_error_flag(flags.as<int>() + 1, s);
+    }
+    rec.release(s);
+    flags.release(s);
+    return st;
+}
+
+kitc_status kitc_solve_host(const double *src_xyz, const double *w, int64_t n_src,
+                            const double *tgt_xyz, int64_t n_tgt, const kitc_params *p,
+                            double *out, void *stream)
+{
+    if (!src_xyz || !w || !out || !valid_params(p) || !valid_count(n_src)) return KITC_ERR_INVALID_ARG;
+    if (tgt_xyz && !valid_count(n_tgt)) return KITC_ERR_INVALID_ARG;
+    if (!tgt_xyz) n_tgt = n_src;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int win = kitc_kernel_win(p->kernel), wout = kitc_kernel_wout(p->kernel);
+    DevBuf dx, dw, dt, dout;
+    kitc_tree t = nullptr;
+    kitc_status st = dx.reserve(sizeof(double) * 3 * n_src, s);
+    if (st == KITC_OK) st = dw.reserve(sizeof(double) * win * n_src, s);
+    if (st == KITC_OK && tgt_xyz) st = dt.reserve(sizeof(double) * 3 * n_tgt, s);
+    if (st == KITC_OK) st = dout.reserve(sizeof(double) * wout * n_tgt, s);
+    if (st == KITC_OK)
+        st = kitc_from_cuda(cudaMemcpyAsync(dx.ptr, src_xyz, sizeof(double) * 3 * n_src,
+                                            cudaMemcpyHostToDevice, s));
+    if (st == KITC_OK)
+        st = kitc_from_cuda(cudaMemcpyAsync(dw.ptr, w, sizeof(double) * win * n_src,
+                                            cudaMemcpyHostToDevice, s));
+    if (st == KITC_OK && tgt_xyz)
+        st = kitc_from_cuda(cudaMemcpyAsync(dt.ptr, tgt_xyz, sizeof(double) * 3 * n_tgt,
+                                            cudaMemcpyHostToDevice, s));
+    if (st == KITC_OK) st = kitc_build_tree(dx.as<double>(), n_src, p, stream, &t);
+    if (st == KITC_OK) st = kitc_modified_weights(t, dw.as<double>(), stream);
+    if (st == KITC_OK)
+        st = kitc_evaluate(t, tgt_xyz ? dt.as<double>() : dx.as<double>(), n_tgt,
+                           dout.as<double>(), stream);
+    if (st == KITC_OK)
+        st = kitc_from_cuda(cudaMemcpyAsync(out, dout.ptr, sizeof(double) * wout * n_tgt,
+                                            cudaMemcpyDeviceToHost, s));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamSynchronize(s));
+    if (t) kitc_free_tree(t);
+    for (DevBuf *b : {&dx, &dw, &dt, &dout}) b->release(s);
+    return st;
+}
+
+kitc_status kitc_get_stats(kitc_tree t, kitc_stats *s)
+{
+    if (!t || !s) return KITC_ERR_INVALID_ARG;
+    memset(s, 0, sizeof(*s));
+    s->n_sources = t->src.n;
+    s->n_clusters = t->src.nclus;
+    s->n_leaves = t->src.nleaves;
+    s->depth = t->src.depth;
+    s->degree = t->p.degree;
+    if (t->evaluated) {
+        s->n_targets = t->lists.nt;
+        s->n_batches = t->lists.nb;
+        s->far_entries = t->lists.nfar;
+        s->near_entries = t->lists.nnear;
+        s->near_pairs = t->lists.near_pairs;
+        s->far_points = t->lists.far_points;
+    }
+    s->device_bytes = (int64_t)(t->src.bytes() + t->tgt.bytes() + t->wts.bytes() +
+                                t->lists.bytes() + t->flags.bytes);
+    if (t->ev_ok) {
+        float *ms[4] = {&s->ms_tree, &s->ms_weights, &s->ms_lists, &s->ms_evaluate};
+        int pairs[4][2] = {{0, 1}, {2, 3}, {4, 5}, {5, 6}};
+        for (int i = 0; i < 4; ++i) {
+            if (!t->stage_done[i]) continue;
+            KITC_CUDA(cudaEventSynchronize(t->ev[pairs[i][1]]));
+            KITC_CUDA(cudaEventElapsedTime(ms[i], t->ev[pairs[i][0]], t->ev[pairs[i][1]]));
+        }
+    }
+    return KITC_OK;
+}
+
+kitc_status kitc_tree_download(kitc_tree t, int64_t *perm, double *lo, double *hi,
+                               int64_t *begin, int64_t *end, int32_t *first_child,
+                               int32_t *n_child, int32_t *level, int32_t *parent, void *stream)
+{
+    if (!t) return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int m = t->src.nclus;
+    int64_t n = t->src.n;
+    std::vector<int32_t> tmp((size_t)std::max<int64_t>(n, m));
+    if (perm) {
+        KITC_CUDA(cudaMemcpyAsync(tmp.data(), t->src.perm.ptr, sizeof(int32_t) * n,
+                                  cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < n; ++i) perm[i] = tmp[i];
+    }
+    std::vector<dvec4> b4(m);
+    for (int side = 0; side < 2; ++side) {
+        double *dst = side ? hi : lo;
+        if (!dst) continue;
+        KITC_CUDA(cudaMemcpyAsync(b4.data(), (side ? t->src.hi : t->src.lo).ptr,
+                                  sizeof(dvec4) * m, cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < m; ++c) {
+            dst[3 * c] = b4[c].x;
+            dst[3 * c + 1] = b4[c].y;
+            dst[3 * c + 2] = b4[c].z;
+        }
+    }
+    const DevBuf *src64[2] = {&t->src.begin, &t->src.end};
+    int64_t *dst64[2] = {begin, end};
+    for (int i = 0; i < 2; ++i) {
+        if (!dst64[i]) continue;
+        KITC_CUDA(cudaMemcpyAsync(tmp.data(), src64[i]->ptr, sizeof(int32_t) * m,
+                                  cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < m; ++c) dst64[i][c] = tmp[c];
+    }
+    const DevBuf *src32[4] = {&t->src.first_child, &t->src.n_child, &t->src.level, &t->src.parent};
+    int32_t *dst32[4] = {first_child, n_child, level, parent};
+    for (int i = 0; i < 4; ++i)
+        if (dst32[i])
+            KITC_CUDA(cudaMemcpyAsync(dst32[i], src32[i]->ptr, sizeof(int32_t) * m,
+                                      cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return KITC_OK;
+}
+
+kitc_status kitc_weights_download(kitc_tree t, double *fhat, void *stream)
+{
+    if (!t || !fhat) return KITC_ERR_INVALID_ARG;
+    if (!t->has_weights) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int np = t->p.degree + 1;
+    size_t bytes = sizeof(double) * (size_t)t->src.nclus * np * np * np * t->win;
+    KITC_CUDA(cudaMemcpyAsync(fhat, t->wts.fhat.ptr, bytes, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return KITC_OK;
+}
+
+kitc_status kitc_lists_download(kitc_tree t, int64_t *tperm, int64_t *nfar, int64_t *nnear,
+                                int32_t *far, uint64_t *far_mask, int32_t *near,
+                                uint64_t *near_mask, void *stream)
+{
+    if (!t) return KITC_ERR_INVALID_ARG;
+    if (!t->evaluated) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const ListsDev &L = t->lists;
+    if (tperm) {
+        std::vector<int32_t> tmp(L.nt);
+        KITC_CUDA(cudaMemcpyAsync(tmp.data(), t->tgt.perm.ptr, sizeof(int32_t) * L.nt,
+                                  cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < L.nt; ++i) tperm[i] = tmp[i];
+    }
+    std::vector<int64_t> off(L.nb + 1);
+    for (int k = 0; k < 2; ++k) {
+        int64_t *dst = k ? nnear : nfar;
+        if (!dst) continue;
+        KITC_CUDA(cudaMemcpyAsync(off.data(), (k ? L.near_off : L.far_off).ptr,
+                                  sizeof(int64_t) * (L.nb + 1), cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int64_t b = 0; b < L.nb; ++b) dst[b] = off[b + 1] - off[b];
+    }
+    if (far) KITC_CUDA(cudaMemcpyAsync(far, L.far_id.ptr, sizeof(int32_t) * L.nfar, cudaMemcpyDeviceToHost, s));
+    if (far_mask)
+        KITC_CUDA(cudaMemcpyAsync(far_mask, L.far_mask.ptr, sizeof(uint64_t) * L.nfar, cudaMemcpyDeviceToHost, s));
+    if (near) KITC_CUDA(cudaMemcpyAsync(near, L.near_id.ptr, sizeof(int32_t) * L.nnear, cudaMemcpyDeviceToHost, s));
+    if (near_mask)
+        KITC_CUDA(cudaMemcpyAsync(near_mask, L.near_mask.ptr, sizeof(uint64_t) * L.nnear, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return KITC_OK;
+}
+
+void kitc_free_tree(kitc_tree t)
+{
+    if (t) free_handle(t);
+}
+
+kitc_status kitc_watchdog_selftest(int limit_ms, void *stream)
+{
+    if (limit_ms < 1 || limit_ms > 10000) return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    DevBuf flag;
+    KITC_TRY(flag.reserve(sizeof(int), s));
+    kitc_status st = kitc_from_cuda(cudaMemsetAsync(flag.ptr, 0, sizeof(int), s));
+    if (st == KITC_OK) st = watchdog_launch((unsigned long long)limit_ms * 1000000ull, flag.as<int>(), s);
+    if (st == KITC_OK) st = read_error_flag(flag.as<int>(), s);
+    flag.release(s);
+    return st;
+}
+
+}  // extern "C"

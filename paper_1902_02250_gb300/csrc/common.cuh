@@ -1,0 +1,176 @@
+// Internal declarations of libkitc (GB300 / sm_103a).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "kitc.h"
+
+// Four doubles, 32-byte aligned (box corners, centre + radius).
+struct alignas(32) dvec4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline dvec4 make_dvec4(double x, double y, double z, double w)
+{
+    dvec4 v;
+    v.x = x;
+    v.y = y;
+    v.z = z;
+    v.w = w;
+    return v;
+}
+
+#define KITC_MAX_DEGREE 16
+#define KITC_MAX_LEVEL 40      // splitting stops at this depth (degenerate inputs only)
+#define KITC_MAX_BATCH 64      // targets per batch: two per lane of a warp
+
+// ---------------------------------------------------------------------------
+// Status plumbing: every CUDA call goes through KITC_CUDA, which turns an error
+// into a kitc_status returned by the enclosing function.
+// ---------------------------------------------------------------------------
+kitc_status kitc_from_cuda(cudaError_t e);
+
+#define KITC_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) return kitc_from_cuda(_e); \
+    } while (0)
+
+#define KITC_TRY(call)                      \
+    do {                                    \
+        kitc_status _s = (call);            \
+        if (_s != KITC_OK) return _s;       \
+    } while (0)
+
+// A small pinned host buffer (64 bytes, per device and process) for
+// read-backs of counts; callers synchronize the stream before reading it.
+kitc_status host_readback_buffer(void **p);
+
+// Stream-ordered device allocation from the device's default pool.
+kitc_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+template <typename T>
+inline kitc_status dev_alloc_t(T **p, size_t count, cudaStream_t s)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), count * sizeof(T), s);
+}
+
+// Device buffer owned by a handle; grows on demand, freed in the destructor
+// of the owner through release().
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    kitc_status reserve(size_t b, cudaStream_t s, bool keep = false);
+    void release(cudaStream_t s);
+    template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+// ---------------------------------------------------------------------------
+// Sec. 6 tree on the device.  Clusters are numbered breadth first; the
+// children of a cluster are contiguous and ordered by octant code.
+// ---------------------------------------------------------------------------
+struct TreeDev {
+    int64_t n = 0;          // particles
+    int leaf = 0;           // N0
+    int32_t nclus = 0, cap = 0, depth = 0, nleaves = 0;
+    DevBuf perm;            // int32 [n]: perm[slot] = caller index
+    DevBuf xs;              // double [3][n]: coordinates in tree order (SoA)
+    DevBuf lo, hi;          // dvec4 [cap]: box corners (w unused)
+    DevBuf ctr;             // dvec4 [cap]: centre xyz, radius in w (Fig. 1)
+    DevBuf begin, end;      // int32 [cap]: slot range
+    DevBuf first_child, n_child, level, parent;  // int32 [cap]
+    std::vector<int32_t> level_start;            // host: first cluster of each level
+    void release(cudaStream_t s);
+    size_t bytes() const;
+};
+
+// Builds the tree of the n points xyz (device, n x 3 row-major).  Reads
+// back the child count of every level (one synchronization per level).
+kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t);
+
+// ---------------------------------------------------------------------------
+// Modified weights (Eq. modified_weights / Algorithm 1) and the packed
+// records the evaluator streams.
+// ---------------------------------------------------------------------------
+struct WeightsDev {
+    int degree = 0, win = 0;
+    DevBuf fhat;      // double [nclus][P][win]
+    DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
+    DevBuf src;       // evaluator records of the sources in tree order
+    DevBuf partial;   // scratch of the weights pass
+    DevBuf items;     // scratch: work items of the weights pass
+    void release(cudaStream_t s);
+    size_t bytes() const;
+};
+
+int proxy_record_bytes(int win, bool mixed);
+int source_record_bytes(int win, bool mixed);
+
+// cos(k pi / n), k = 0..n (Eq. Chebyshev_points), computed on the host.
+void cheb_cos_table(int n, double *t);
+
+kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree,
+                            cudaStream_t s, WeightsDev &wd);
+kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
+                         int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out);
+kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Interaction lists of target batches (Algorithm 2 traversal).
+// ---------------------------------------------------------------------------
+struct ListsDev {
+    int64_t nb = 0, nt = 0;
+    int batch = 0;
+    int64_t nfar = 0, nnear = 0;
+    DevBuf bctr;                 // dvec4 [nb]: batch box centre
+    DevBuf far_off, near_off;    // int64 [nb+1]
+    DevBuf far_id, near_id;      // int32 [entries]
+    DevBuf far_mask, near_mask;  // uint64 [entries]
+    DevBuf counts;               // int64 scratch [nb*2] + totals
+    DevBuf totals;               // int64 [8]
+    int64_t near_pairs = 0, far_points = 0;
+    void release(cudaStream_t s);
+    size_t bytes() const;
+};
+
+kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
+                        int degree, int mac, cudaStream_t s, ListsDev &L);
+
+// ---------------------------------------------------------------------------
+// Fused near/far evaluator.
+// ---------------------------------------------------------------------------
+struct EvalArgs {
+    // targets: slot -> coordinates (x[slot*stride], y[..], z[..]) and caller index
+    const double *tx, *ty, *tz;
+    int64_t tstride;
+    const int32_t *tperm;        // NULL: slot == caller index
+    int64_t nt;
+    int batch;                   // targets per batch
+    int64_t nb;
+    const dvec4 *bctr;         // batch centres (mixed far field frame); may be NULL if no far
+    // lists (NULL near_off = direct mode: one near range [0, direct_ns) per batch)
+    const int64_t *far_off, *near_off;
+    const int32_t *far_id, *near_id;
+    const uint64_t *far_mask, *near_mask;
+    int64_t direct_ns;
+    // sources / clusters
+    const void *src;             // source records (tree order, or caller order in direct mode)
+    const void *proxy;           // proxy records [cluster][P]
+    const dvec4 *clo, *chi;    // cluster boxes (far field grid points)
+    const int32_t *cbegin, *cend;
+    int degree;
+    double cheb[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
+    double eps;
+    double *out;                 // caller order, n x wout
+    int *queue;                  // work counter, zero at launch
+    int *err;                    // error flag (nonzero on a timed-out wait)
+    unsigned long long wait_ns;  // bound of every barrier wait
+};
+
+kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s);
+
+kitc_status watchdog_launch(unsigned long long limit_ns, int *err, cudaStream_t s);
+
+extern int g_wait_limit_ms;

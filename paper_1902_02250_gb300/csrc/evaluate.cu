@@ -1,0 +1,640 @@
+// Fused near/far evaluator of Algorithm 2 (and of the direct sum), for the
+// regularized Stokes kernels of Sec. 7 (Eqs. MRS_kernels, Velocity_1, MRS_2).
+//
+// Design (GB300, sm_103a):
+//  * Persistent CTAs take target batches from an atomic work counter.
+//  * A producer warp streams the batch's interaction list as tiles -- source
+//    records of a near leaf (Eq. pc_interaction_3D) or modified-weight records
+//    of a far cluster (Eq. pc_approximation_3D) -- global -> shared memory with
+//    TMA bulk copies (cp.async.bulk) into a ring of stages guarded by
+//    mbarriers (full: bytes landed; empty: all consumer warps done).
+//  * Eight consumer warps hold the batch's <= 64 targets (two per lane) and
+//    split every tile between them: near tiles by blocks of 8 sources, far
+//    tiles by grid rows (k1, k2) of (n+1) points.  The (n+1)^3 grid of a
+//    cluster is a tensor product, so only 3 (n+1) coordinates per cluster are
+//    formed; the per-point work is one rsqrt and a few FMAs.
+//  * KITC_MIXED: coordinate differences of near pairs come from hi/lo FP32
+//    pairs (d = (xh - yh) + (xl - yl), relative error ~1e-7 at any distance);
+//    far-field points are taken relative to the batch centre in FP64 and then
+//    rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
+//    terms, those runs summed over at most 8, and so on one more level; the
+//    per-leaf / per-cluster sums are accumulated in FP64.
+//  * Every barrier wait is bounded (globaltimer); a wait that runs out sets an
+//    error flag, the CTA drains its own copies in flight and returns.
+#include <type_traits>
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int NCW = 8;                 // consumer warps
+constexpr int NTH = (NCW + 1) * 32;    // plus one producer warp
+constexpr int STAGES = 4;
+constexpr int TILE = 16384;            // bytes per stage
+constexpr double INV8PI = 0.039788735772973836;
+
+enum { K_FAR = 0, K_NEAR = 1, K_EXIT = 2 };
+enum { F_FIRST_BATCH = 1, F_LAST_BATCH = 2, F_FIRST_ENTRY = 4, F_LAST_ENTRY = 8 };
+
+struct TileMeta {
+    int kind, flags, batch, id;
+    int a, b;        // far: k1 planes [a, b); near: source slots [a, b)
+    uint64_t mask;   // targets of the batch that use this entry
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            bar),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `parity` to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns)
+{
+    if (mbar_try(bar, parity)) return true;
+    unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (gtimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Kernel math.  d = x - y, rho^2 = r^2 + eps^2, ri = 1/rho.  With
+// r^2 = rho^2 - eps^2 the MRS functions of Eq. MRS_kernels become (times 8 pi):
+//   H1 = ri + eps^2 ri^3,  H2 = ri^3,  Q = 2 ri^3 + 3 eps^2 ri^5,
+//   D1 = -2 ri^3 - 3 eps^2 ri^5 + 15 eps^4 ri^7,  D2 = 6 ri^5 + 15 eps^2 ri^7.
+// The common factor 1/(8 pi) is applied once per target at the end.
+// A pair with rho = 0 (eps = 0, x = y) contributes nothing (Sec. 1).
+// ---------------------------------------------------------------------------
+template <int K> struct KT;
+template <> struct KT<KITC_STOKESLET> { static constexpr int WIN = 3, WOUT = 3; };
+template <> struct KT<KITC_ROTLET> { static constexpr int WIN = 3, WOUT = 6; };
+template <> struct KT<KITC_STOKESLET_ROTLET> { static constexpr int WIN = 6, WOUT = 6; };
+template <> struct KT<KITC_TEST_POLY> { static constexpr int WIN = 3, WOUT = 3; };
+
+template <typename R> __device__ __forceinline__ R rsq(R v);
+template <> __device__ __forceinline__ float rsq<float>(float v) { return v > 0.f ? rsqrtf(v) : 0.f; }
+template <> __device__ __forceinline__ double rsq<double>(double v) { return v > 0.0 ? rsqrt(v) : 0.0; }
+
+// u += k(x, y) f for one pair, given d = x - y and r2 = |d|^2 + eps^2
+// (Eqs. Velocity_1, MRS_2).
+template <int K, typename R>
+__device__ __forceinline__ void pair(R dx, R dy, R dz, const R *f, R e2, R e4, R *u, R r2)
+{
+    R ri = rsq<R>(r2);
+    R ri2 = ri * ri;
+    R ri3 = ri2 * ri;
+    if (K == KITC_STOKESLET || K == KITC_STOKESLET_ROTLET) {
+        R H1 = fma(e2, ri3, ri);
+        R fd = fma(f[0], dx, fma(f[1], dy, f[2] * dz));
+        R s = fd * ri3;
+        u[0] = fma(f[0], H1, fma(dx, s, u[0]));
+        u[1] = fma(f[1], H1, fma(dy, s, u[1]));
+        u[2] = fma(f[2], H1, fma(dz, s, u[2]));
+    }
+    if (K == KITC_ROTLET || K == KITC_STOKESLET_ROTLET) {
+        const R *n = (K == KITC_ROTLET) ? f : f + 3;
+        R ri5 = ri3 * ri2;
+        R ri7 = ri5 * ri2;
+        R hQ = fma(R(1.5) * e2, ri5, ri3);                              // Q / 2
+        R qD1 = fma(R(3.75) * e4, ri7, fma(R(-0.75) * e2, ri5, R(-0.5) * ri3));  // D1 / 4
+        R qD2 = fma(R(3.75) * e2, ri7, R(1.5) * ri5);                   // D2 / 4
+        R nd = fma(n[0], dx, fma(n[1], dy, n[2] * dz));
+        R t = nd * qD2;
+        u[0] = fma(hQ, n[1] * dz - n[2] * dy, u[0]);
+        u[1] = fma(hQ, n[2] * dx - n[0] * dz, u[1]);
+        u[2] = fma(hQ, n[0] * dy - n[1] * dx, u[2]);
+        u[3] = fma(n[0], qD1, fma(dx, t, u[3]));
+        u[4] = fma(n[1], qD1, fma(dy, t, u[4]));
+        u[5] = fma(n[2], qD1, fma(dz, t, u[5]));
+        if (K == KITC_STOKESLET_ROTLET) {
+            u[3] = fma(hQ, f[1] * dz - f[2] * dy, u[3]);
+            u[4] = fma(hQ, f[2] * dx - f[0] * dz, u[4]);
+            u[5] = fma(hQ, f[0] * dy - f[1] * dx, u[5]);
+        }
+    }
+}
+
+// The test kernel prod_l (1 + x_l y_l / 2)^3 f (FP64 only).
+__device__ __forceinline__ void pair_poly(const double *x, double y0, double y1, double y2,
+                                          const double *f, double *u)
+{
+    double q0 = 1.0 + 0.5 * x[0] * y0, q1 = 1.0 + 0.5 * x[1] * y1, q2 = 1.0 + 0.5 * x[2] * y2;
+    double p = (q0 * q0 * q0) * (q1 * q1 * q1) * (q2 * q2 * q2);
+    u[0] = fma(p, f[0], u[0]);
+    u[1] = fma(p, f[1], u[1]);
+    u[2] = fma(p, f[2], u[2]);
+}
+
+}  // namespace
+
+namespace {
+
+template <bool MIXED, int WIN> struct Rec {
+    static constexpr int SRC = MIXED ? 48 : (WIN == 3 ? 48 : 80);
+    static constexpr int PROXY = MIXED ? (WIN == 3 ? 16 : 32) : (WIN == 3 ? 32 : 48);
+};
+
+template <int K, bool MIXED> struct Smem {
+    static constexpr int WOUT = KT<K>::WOUT;
+    static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
+    static constexpr size_t META = STAGES * sizeof(TileMeta);
+    static constexpr size_t BARS = (2 * STAGES + 2) * sizeof(uint64_t);
+    static constexpr size_t GRID = (size_t)NCW * 3 * (KITC_MAX_DEGREE + 1) * sizeof(double);
+    static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID;
+};
+
+// Weight components of a record as R values.
+template <bool MIXED, int WIN, typename R>
+__device__ __forceinline__ void load_proxy(const unsigned char *p, R *f)
+{
+    if constexpr (MIXED) {
+        float4 v = *reinterpret_cast<const float4 *>(p);
+        f[0] = v.x; f[1] = v.y; f[2] = v.z;
+        if constexpr (WIN == 6) {
+            float4 u = *reinterpret_cast<const float4 *>(p + 16);
+            f[3] = u.x; f[4] = u.y; f[5] = u.z;
+        }
+    } else {
+        const double *d = reinterpret_cast<const double *>(p);
+#pragma unroll
+        for (int q = 0; q < WIN; ++q) f[q] = d[q];
+    }
+}
+
+// CTAs per SM the register budget targets: two for the FP32 Stokeslet (no
+// spills at 96 registers), one for the wider FP64 and rotlet variants.
+template <int K, bool MIXED> struct MinBlocks {
+    static constexpr int value = (MIXED && K == KITC_STOKESLET) ? 2 : 1;
+};
+
+template <int K, bool MIXED>
+__global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
+{
+    constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
+    constexpr int SREC = Rec<MIXED, WIN>::SRC, PREC = Rec<MIXED, WIN>::PROXY;
+    using R = typename std::conditional<MIXED, float, double>::type;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *tiles = smem;
+    double *red = reinterpret_cast<double *>(smem + (size_t)STAGES * TILE);
+    TileMeta *meta = reinterpret_cast<TileMeta *>(smem + (size_t)STAGES * TILE + Smem<K, MIXED>::RED);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(meta) +
+                                                  Smem<K, MIXED>::META);
+    double *gridc = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bars) +
+                                               Smem<K, MIXED>::BARS);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+    const uint32_t rbw = smem_u32(bars + 2 * STAGES), rbr = smem_u32(bars + 2 * STAGES + 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, NCW);
+        }
+        mbar_init(rbw, NCW);
+        mbar_init(rbr, NCW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int np = a.degree + 1, np2 = np * np;
+    const int near_max = (TILE / SREC) / 8 * 8;
+    const int planes_max = TILE / (np2 * PREC);
+    const unsigned long long wait_ns = a.wait_ns;
+
+    // ---------------------------------------------------------------- producer
+    if (warp == NCW) {
+        if (lane != 0) return;
+        uint32_t it = 0;
+        bool ok = true;
+        auto emit = [&](const TileMeta &m, const unsigned char *src, uint32_t bytes) -> bool {
+            int s = it % STAGES;
+            uint32_t ph = (it / STAGES) & 1u;
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, wait_ns)) return false;
+            meta[s] = m;
+            if (bytes) {
+                mbar_arrive_tx(full0 + 8 * s, bytes);
+                bulk_g2s(smem_u32(tiles + (size_t)s * TILE), src, bytes, full0 + 8 * s);
+            } else {
+                mbar_arrive(full0 + 8 * s);
+            }
+            ++it;
+            return true;
+        };
+        const unsigned char *srcb = reinterpret_cast<const unsigned char *>(a.src);
+        const unsigned char *pxb = reinterpret_cast<const unsigned char *>(a.proxy);
+        for (;;) {
+            int b = atomicAdd(a.queue, 1);
+            if (b >= a.nb) break;
+            bool have = false, first = true;
+            TileMeta pend{};
+            const unsigned char *psrc = nullptr;
+            uint32_t pbytes = 0;
+            auto push = [&](const TileMeta &m, const unsigned char *src, uint32_t bytes) -> bool {
+                if (have) {
+                    if (first) pend.flags |= F_FIRST_BATCH;
+                    first = false;
+                    if (!emit(pend, psrc, pbytes)) return false;
+                }
+                pend = m;
+                psrc = src;
+                pbytes = bytes;
+                have = true;
+                return true;
+            };
+            if (a.near_off) {
+                int64_t f0 = a.far_off[b], f1 = a.far_off[b + 1];
+                for (int64_t e = f0; e < f1 && ok; ++e) {
+                    int c = a.far_id[e];
+                    uint64_t mk = a.far_mask[e];
+                    for (int k1 = 0; k1 < np && ok; k1 += planes_max) {
+                        int k2 = min(np, k1 + planes_max);
+                        TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
+                                   b, c, k1, k2, mk};
+                        ok = push(m, pxb + ((size_t)c * np2 * np + (size_t)k1 * np2) * PREC,
+                                  (uint32_t)((k2 - k1) * np2 * PREC));
+                    }
+                }
+                int64_t n0 = a.near_off[b], n1 = a.near_off[b + 1];
+                for (int64_t e = n0; e < n1 && ok; ++e) {
+                    int c = a.near_id[e];
+                    uint64_t mk = a.near_mask[e];
+                    int p0 = a.cbegin[c], p1 = a.cend[c];
+                    for (int q = p0; q < p1 && ok; q += near_max) {
+                        int q1 = min(p1, q + near_max);
+                        TileMeta m{K_NEAR, (q == p0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
+                                   b, c, q, q1, mk};
+                        ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
+                    }
+                }
+            } else {
+                int64_t p1 = a.direct_ns;
+                for (int64_t q = 0; q < p1 && ok; q += near_max) {
+                    int64_t q1 = min(p1, q + (int64_t)near_max);
+                    TileMeta m{K_NEAR, (q == 0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
+                               b, -1, (int)q, (int)q1, ~0ull};
+                    ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
+                }
+            }
+            if (!ok) break;
+            if (!have) {  // no entries: one empty tile closes the batch
+                pend = TileMeta{K_NEAR, F_FIRST_ENTRY | F_LAST_ENTRY, b, -1, 0, 0, 0ull};
+                psrc = nullptr;
+                pbytes = 0;
+            }
+            pend.flags |= F_LAST_BATCH | (first ? F_FIRST_BATCH : 0);
+            if (!(ok = emit(pend, psrc, pbytes))) break;
+        }
+        if (ok) ok = emit(TileMeta{K_EXIT, 0, -1, -1, 0, 0, 0ull}, nullptr, 0);
+        if (!ok) atomicExch(a.err, 1);
+        // drain: the last phase of every stage this thread armed must complete
+        uint32_t last = it;
+        for (uint32_t j = (last > STAGES ? last - STAGES : 0); j < last; ++j)
+            if (!mbar_wait(full0 + 8 * (j % STAGES), (j / STAGES) & 1u, wait_ns)) atomicExch(a.err, 1);
+        return;
+    }
+
+    // --------------------------------------------------------------- consumers
+    const R e2 = (R)(a.eps * a.eps), e4 = (R)(a.eps * a.eps * a.eps * a.eps);
+    R X[2][3], XL[2][3], XO[2][3];
+    double acc[2][WOUT];
+    R a1[2][WOUT], a2[2][WOUT], a3[2][WOUT];
+    int c2 = 0, c3 = 0;
+    dvec4 cB = make_dvec4(0, 0, 0, 0);
+    double xd[2][3];
+    R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
+    uint32_t it = 0, nbd = 0;
+    bool t_ok[2] = {false, false};
+    int64_t bslot = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0, a1[t][c] = a2[t][c] = a3[t][c] = R(0);
+
+    auto flush3 = [&](uint64_t mask) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            bool use = (mask >> (lane + 32 * t)) & 1ull;
+#pragma unroll
+            for (int c = 0; c < WOUT; ++c) {
+                acc[t][c] += use ? (double)a3[t][c] : 0.0;
+                a3[t][c] = R(0);
+            }
+        }
+    };
+    auto step = [&](uint64_t mask) {  // end of a run of <= 8 (near) or n+1 (far) terms
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int c = 0; c < WOUT; ++c) a2[t][c] += a1[t][c], a1[t][c] = R(0);
+        if (++c2 == 8) {
+            c2 = 0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
+            if (++c3 == 8) {
+                c3 = 0;
+                flush3(mask);
+            }
+        }
+    };
+
+    for (;;) {
+        const int s = it % STAGES;
+        if (!mbar_wait(full0 + 8 * s, (it / STAGES) & 1u, wait_ns)) {
+            atomicExch(a.err, 1);
+            break;
+        }
+        const TileMeta m = meta[s];
+        if (m.kind == K_EXIT) break;
+        const unsigned char *tile = tiles + (size_t)s * TILE;
+        if (m.flags & F_FIRST_BATCH) {
+            bslot = (int64_t)m.batch * a.batch;
+            if (MIXED && a.bctr) cB = a.bctr[m.batch];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                int i = lane + 32 * t;
+                int64_t slot = bslot + i;
+                t_ok[t] = i < a.batch && slot < a.nt;
+                int64_t sl = t_ok[t] ? slot : bslot;
+                xd[t][0] = a.tx[sl * a.tstride];
+                xd[t][1] = a.ty[sl * a.tstride];
+                xd[t][2] = a.tz[sl * a.tstride];
+                const double cb[3] = {cB.x, cB.y, cB.z};
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    if constexpr (MIXED) {
+                        float h = __double2float_rn(xd[t][l]);
+                        X[t][l] = h;
+                        XL[t][l] = __double2float_rn(xd[t][l] - (double)h);
+                        XO[t][l] = __double2float_rn(xd[t][l] - cb[l]);
+                    } else {
+                        X[t][l] = xd[t][l];
+                        XL[t][l] = 0.0;
+                        XO[t][l] = xd[t][l];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0;
+            }
+        }
+        if (m.flags & F_FIRST_ENTRY) {
+            c2 = c3 = 0;
+            if (m.kind == K_FAR) {
+                for (int q = lane; q < 3 * np; q += 32) {
+                    int l = q / np, k = q % np;
+                    dvec4 lo = a.clo[m.id], hi = a.chi[m.id];
+                    double lo_l = l == 0 ? lo.x : (l == 1 ? lo.y : lo.z);
+                    double hi_l = l == 0 ? hi.x : (l == 1 ? hi.y : hi.z);
+                    double sk = 0.5 * ((lo_l + hi_l) + a.cheb[k] * (hi_l - lo_l));
+                    double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
+                    gs[l * (KITC_MAX_DEGREE + 1) + k] = MIXED ? (R)(sk - cb_l) : (R)sk;
+                }
+                __syncwarp();
+            }
+        }
+        if (m.kind == K_FAR) {
+            const R *gx = gs, *gy = gs + (KITC_MAX_DEGREE + 1), *gz = gs + 2 * (KITC_MAX_DEGREE + 1);
+            const int rows = (m.b - m.a) * np;
+            for (int r = warp; r < rows; r += NCW) {
+                const int k1 = m.a + r / np, k2 = r % np;
+                const unsigned char *row = tile + (size_t)r * np * PREC;
+                R dx[2], dy[2], rxy[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    dx[t] = XO[t][0] - gx[k1];
+                    dy[t] = XO[t][1] - gy[k2];
+                    rxy[t] = fma(dx[t], dx[t], fma(dy[t], dy[t], e2));
+                }
+                for (int k3 = 0; k3 < np; ++k3) {
+                    R f[WIN];
+                    load_proxy<MIXED, WIN, R>(row + (size_t)k3 * PREC, f);
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        R dz = XO[t][2] - gz[k3];
+                        R r2 = fma(dz, dz, rxy[t]);
+                        if constexpr (K == KITC_TEST_POLY) {
+                            pair_poly(xd[t], (double)gx[k1], (double)gy[k2], (double)gz[k3],
+                                      reinterpret_cast<const double *>(f), reinterpret_cast<double *>(a1[t]));
+                        } else {
+                            pair<K, R>(dx[t], dy[t], dz, f, e2, e4, a1[t], r2);
+                        }
+                    }
+                }
+                step(m.mask);
+            }
+        } else {
+            const int cnt = m.b - m.a;
+            const int nb8 = (cnt + 7) >> 3;
+            for (int blk = warp; blk < nb8; blk += NCW) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int idx = blk * 8 + j;
+                    if (idx < cnt) {
+                        const unsigned char *rec = tile + (size_t)idx * SREC;
+                        R f[WIN];
+                        R yh[3], yl[3];
+                        if constexpr (MIXED) {
+                            float4 r0 = *reinterpret_cast<const float4 *>(rec);
+                            float4 r1 = *reinterpret_cast<const float4 *>(rec + 16);
+                            float4 r2 = *reinterpret_cast<const float4 *>(rec + 32);
+                            yh[0] = r0.x; yh[1] = r0.y; yh[2] = r0.z;
+                            yl[0] = r0.w; yl[1] = r1.x; yl[2] = r1.y;
+                            f[0] = r1.z; f[1] = r1.w; f[2] = r2.x;
+                            if constexpr (WIN == 6) { f[3] = r2.y; f[4] = r2.z; f[5] = r2.w; }
+                        } else {
+                            const double *d = reinterpret_cast<const double *>(rec);
+                            yh[0] = d[0]; yh[1] = d[1]; yh[2] = d[2];
+                            yl[0] = yl[1] = yl[2] = 0.0;
+#pragma unroll
+                            for (int q = 0; q < WIN; ++q) f[q] = d[3 + q];
+                        }
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            if constexpr (K == KITC_TEST_POLY) {
+                                pair_poly(xd[t], (double)yh[0], (double)yh[1], (double)yh[2],
+                                          reinterpret_cast<const double *>(f),
+                                          reinterpret_cast<double *>(a1[t]));
+                            } else {
+                                R dx, dy, dz;
+                                if constexpr (MIXED) {
+                                    dx = (X[t][0] - yh[0]) + (XL[t][0] - yl[0]);
+                                    dy = (X[t][1] - yh[1]) + (XL[t][1] - yl[1]);
+                                    dz = (X[t][2] - yh[2]) + (XL[t][2] - yl[2]);
+                                } else {
+                                    dx = X[t][0] - yh[0];
+                                    dy = X[t][1] - yh[1];
+                                    dz = X[t][2] - yh[2];
+                                }
+                                R r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
+                                pair<K, R>(dx, dy, dz, f, e2, e4, a1[t], r2);
+                            }
+                        }
+                    }
+                }
+                step(m.mask);
+            }
+        }
+        if (m.flags & F_LAST_ENTRY) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
+            flush3(m.mask);
+            c2 = c3 = 0;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+        ++it;
+        if (m.flags & F_LAST_BATCH) {
+            // cross-warp sum: write partials, wait for all warps, add, write out
+            if (!mbar_wait(rbr, (nbd & 1u) ^ 1u, wait_ns)) { atomicExch(a.err, 1); break; }
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c)
+                    red[((size_t)warp * KITC_MAX_BATCH + lane + 32 * t) * WOUT + c] = acc[t][c];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(rbw);
+            if (!mbar_wait(rbw, nbd & 1u, wait_ns)) { atomicExch(a.err, 1); break; }
+            const double scale = (K == KITC_TEST_POLY) ? 1.0 : INV8PI;
+            const int ne = a.batch * WOUT;
+            for (int e = warp * 32 + lane; e < ne; e += NCW * 32) {
+                int i = e / WOUT, c = e % WOUT;
+                int64_t slot = bslot + i;
+                if (slot >= a.nt) continue;
+                double v = 0.0;
+#pragma unroll
+                for (int q = 0; q < NCW; ++q) v += red[((size_t)q * KITC_MAX_BATCH + i) * WOUT + c];
+                int64_t j = a.tperm ? (int64_t)a.tperm[slot] : slot;
+                a.out[j * WOUT + c] = v * scale;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(rbr);
+            ++nbd;
+        }
+    }
+}
+
+template <int K, bool MIXED>
+kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
+{
+    constexpr int WIN = KT<K>::WIN;
+    int np = a.degree + 1;
+    if ((size_t)np * np * Rec<MIXED, WIN>::PROXY > (size_t)TILE) return KITC_ERR_INVALID_ARG;
+    // bulk copies need 16-byte aligned sources; records are multiples of 16 bytes
+    if ((reinterpret_cast<uintptr_t>(a.src) & 15u) || (reinterpret_cast<uintptr_t>(a.proxy) & 15u))
+        return KITC_ERR_INVALID_ARG;
+    if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
+        return KITC_ERR_INVALID_ARG;
+    size_t smem = Smem<K, MIXED>::TOTAL;
+    static int configured[64] = {0};
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !configured[dev]) {
+        KITC_CUDA(cudaFuncSetAttribute(k_eval<K, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        configured[dev] = 1;
+    }
+    int sms = 0, occ = 0;
+    KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    KITC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<K, MIXED>, NTH, smem));
+    if (occ < 1) return KITC_ERR_CUDA;
+    int64_t grid = std::min<int64_t>(a.nb, (int64_t)sms * occ);
+    if (grid < 1) return KITC_OK;
+    k_eval<K, MIXED><<<(unsigned)grid, NTH, smem, s>>>(a);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+// One thread waits on a barrier that is never completed; the bounded wait
+// gives up after limit_ns and records the time-out.
+__global__ void k_watchdog(unsigned long long limit_ns, int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(b, 0, limit_ns)) atomicExch(err, 1);
+}
+
+}  // namespace
+
+kitc_status watchdog_launch(unsigned long long limit_ns, int *err, cudaStream_t s)
+{
+    k_watchdog<<<1, 32, 0, s>>>(limit_ns, err);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s)
+{
+    switch (kernel) {
+    case KITC_STOKESLET:
+        return mixed ? launch_k<KITC_STOKESLET, true>(a, s) : launch_k<KITC_STOKESLET, false>(a, s);
+    case KITC_ROTLET:
+        return mixed ? launch_k<KITC_ROTLET, true>(a, s) : launch_k<KITC_ROTLET, false>(a, s);
+    case KITC_STOKESLET_ROTLET:
+        return mixed ? launch_k<KITC_STOKESLET_ROTLET, true>(a, s)
+                     : launch_k<KITC_STOKESLET_ROTLET, false>(a, s);
+    case KITC_TEST_POLY:
+        if (mixed) return KITC_ERR_INVALID_ARG;
+        return launch_k<KITC_TEST_POLY, false>(a, s);
+    default:
+        return KITC_ERR_INVALID_ARG;
+    }
+}

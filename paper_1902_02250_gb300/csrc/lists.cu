@@ -1,0 +1,235 @@
+// Interaction lists of target batches: the traversal of Algorithm 2.
+//
+// One warp walks the source tree for one batch of up to 64 targets (two per
+// lane), depth first from the root, children in octant order.  Each stack
+// entry carries the mask of the batch's targets still descending.  At a
+// cluster C with mask M:
+//   KITC_MAC_PARTICLE: A = {targets of M with r_C <= theta |x - y_C|} (Eq. MAC,
+//     decided per target, so every target sees exactly Algorithm 2);
+//   KITC_MAC_BATCH:    A = M if r_C <= theta dist(box_B, y_C), else empty.
+// A non-empty A is a far entry (C, A); the rest R = M \ A becomes a near
+// entry (C, R) if C is a leaf, else R descends into C's children.
+// The MAC expressions round exactly as written (no contraction), so they
+// agree bit for bit with any IEEE implementation of the same formulas.
+// A first pass counts entries per batch, a scan sizes the arrays, a second
+// pass writes them.
+#include "common.cuh"
+
+namespace {
+
+constexpr int LW = 8;                          // warps per block
+constexpr int STK = 8 * KITC_MAX_LEVEL + 16;   // stack entries per warp
+
+__device__ __forceinline__ double norm3_rn(double a, double b, double c)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c)));
+}
+
+__device__ __forceinline__ double box_gap(double y, double lo, double hi)
+{
+    return y < lo ? __dsub_rn(lo, y) : (y > hi ? __dsub_rn(y, hi) : 0.0);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(LW * 32) k_lists(
+    int64_t nt, int batch, int64_t nb, const double *__restrict__ txs,
+    const dvec4 *__restrict__ ctr, const int32_t *__restrict__ cbegin,
+    const int32_t *__restrict__ cend, const int32_t *__restrict__ first_child,
+    const int32_t *__restrict__ n_child, double theta, int np3, int mac,
+    int64_t *__restrict__ counts, dvec4 *__restrict__ bctr, int64_t *__restrict__ totals,
+    const int64_t *__restrict__ far_off, const int64_t *__restrict__ near_off,
+    int32_t *__restrict__ far_id, uint64_t *__restrict__ far_mask, int32_t *__restrict__ near_id,
+    uint64_t *__restrict__ near_mask, int *__restrict__ err)
+{
+    __shared__ int32_t sid[LW][STK];
+    __shared__ uint64_t smask[LW][STK];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t b = (int64_t)blockIdx.x * LW + w;
+    if (b >= nb) return;
+    int64_t s0 = b * batch, s1 = min(nt, s0 + batch);
+    int64_t sa = s0 + lane, sb = s0 + 32 + lane;
+    bool va = sa < s1, vb = sb < s1;
+    double xa[3], xb[3], lo[3], hi[3];
+    for (int l = 0; l < 3; ++l) {
+        xa[l] = va ? txs[l * nt + sa] : txs[l * nt + s0];
+        xb[l] = vb ? txs[l * nt + sb] : xa[l];
+        lo[l] = fmin(xa[l], xb[l]);
+        hi[l] = fmax(xa[l], xb[l]);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[l] = fmin(lo[l], __shfl_xor_sync(0xffffffffu, lo[l], o));
+            hi[l] = fmax(hi[l], __shfl_xor_sync(0xffffffffu, hi[l], o));
+        }
+    }
+    uint64_t m0 = (uint64_t)__ballot_sync(0xffffffffu, va) |
+                  ((uint64_t)__ballot_sync(0xffffffffu, vb) << 32);
+    if (PASS == 0 && lane == 0)
+        bctr[b] = make_dvec4(__dmul_rn(0.5, __dadd_rn(lo[0], hi[0])),
+                               __dmul_rn(0.5, __dadd_rn(lo[1], hi[1])),
+                               __dmul_rn(0.5, __dadd_rn(lo[2], hi[2])), 0.0);
+    int64_t nfar = 0, nnear = 0, pairs = 0, points = 0;
+    int64_t fo = PASS ? far_off[b] : 0, no = PASS ? near_off[b] : 0;
+    int sp = 0;
+    if (lane == 0) {
+        sid[w][0] = 0;
+        smask[w][0] = m0;
+    }
+    sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+        --sp;
+        int c = sid[w][sp];
+        uint64_t M = smask[w][sp];
+        __syncwarp();
+        dvec4 g = ctr[c];  // centre, radius in w
+        uint64_t A;
+        if (mac == KITC_MAC_PARTICLE) {
+            double Ra = norm3_rn(__dsub_rn(xa[0], g.x), __dsub_rn(xa[1], g.y), __dsub_rn(xa[2], g.z));
+            double Rb = norm3_rn(__dsub_rn(xb[0], g.x), __dsub_rn(xb[1], g.y), __dsub_rn(xb[2], g.z));
+            bool aa = g.w <= __dmul_rn(theta, Ra), ab = g.w <= __dmul_rn(theta, Rb);
+            A = ((uint64_t)__ballot_sync(0xffffffffu, aa) |
+                 ((uint64_t)__ballot_sync(0xffffffffu, ab) << 32)) & M;
+        } else {
+            double d = norm3_rn(box_gap(g.x, lo[0], hi[0]), box_gap(g.y, lo[1], hi[1]),
+                                box_gap(g.z, lo[2], hi[2]));
+            A = (g.w <= __dmul_rn(theta, d)) ? M : 0;
+        }
+        uint64_t R = M & ~A;
+        if (A) {
+            if (PASS == 1 && lane == 0) {
+                far_id[fo + nfar] = c;
+                far_mask[fo + nfar] = A;
+            }
+            nfar++;
+            points += (int64_t)__popcll(A) * np3;
+        }
+        if (R) {
+            int nch = n_child[c];
+            if (nch == 0) {
+                if (PASS == 1 && lane == 0) {
+                    near_id[no + nnear] = c;
+                    near_mask[no + nnear] = R;
+                }
+                nnear++;
+                pairs += (int64_t)__popcll(R) * (cend[c] - cbegin[c]);
+            } else {
+                if (sp + nch > STK) {
+                    if (lane == 0) atomicExch(err, 1);
+                    break;
+                }
+                int fc = first_child[c];
+                if (lane < nch) {  // pushed in reverse so that they pop in octant order
+                    sid[w][sp + nch - 1 - lane] = fc + lane;
+                    smask[w][sp + nch - 1 - lane] = R;
+                }
+                sp += nch;
+                __syncwarp();
+            }
+        }
+    }
+    if (PASS == 0 && lane == 0) {
+        counts[b] = nfar;
+        counts[nb + b] = nnear;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&totals[0]), (unsigned long long)pairs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&totals[1]), (unsigned long long)points);
+    }
+}
+
+// Exclusive scan of in[0..m) into out[0..m] (out[m] = total); one block.
+__global__ void k_scan64(const int64_t *__restrict__ in, int64_t m, int64_t *__restrict__ out,
+                         int64_t *__restrict__ total)
+{
+    __shared__ int64_t sums[1024];
+    int64_t per = (m + blockDim.x - 1) / blockDim.x;
+    int64_t b = threadIdx.x * per, e = min(m, b + per);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += in[i];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int64_t v = sums[i];
+            sums[i] = run;
+            run += v;
+        }
+        out[m] = run;
+        *total = run;
+    }
+    __syncthreads();
+    int64_t run = sums[threadIdx.x];
+    for (int64_t i = b; i < e; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+}
+
+}  // namespace
+
+void ListsDev::release(cudaStream_t s)
+{
+    for (DevBuf *b : {&bctr, &far_off, &near_off, &far_id, &near_id, &far_mask, &near_mask,
+                      &counts, &totals})
+        b->release(s);
+    nb = nt = nfar = nnear = 0;
+}
+
+size_t ListsDev::bytes() const
+{
+    size_t b = 0;
+    for (const DevBuf *d : {&bctr, &far_off, &near_off, &far_id, &near_id, &far_mask, &near_mask,
+                            &counts, &totals})
+        b += d->bytes;
+    return b;
+}
+
+kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
+                        int degree, int mac, cudaStream_t s, ListsDev &L)
+{
+    int64_t nt = tgt.n;
+    int64_t nb = (nt + batch - 1) / batch;
+    L.nt = nt;
+    L.nb = nb;
+    L.batch = batch;
+    int np = degree + 1, np3 = np * np * np;
+    KITC_TRY(L.bctr.reserve(sizeof(dvec4) * nb, s));
+    KITC_TRY(L.counts.reserve(sizeof(int64_t) * 2 * nb, s));
+    KITC_TRY(L.far_off.reserve(sizeof(int64_t) * (nb + 1), s));
+    KITC_TRY(L.near_off.reserve(sizeof(int64_t) * (nb + 1), s));
+    KITC_TRY(L.totals.reserve(sizeof(int64_t) * 8, s));
+    int64_t *tot = L.totals.as<int64_t>();
+    KITC_CUDA(cudaMemsetAsync(tot, 0, sizeof(int64_t) * 8, s));
+    int *err = reinterpret_cast<int *>(tot + 6);
+    unsigned grid = (unsigned)((nb + LW - 1) / LW);
+    k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+                                        src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
+                                        theta, np3, mac, L.counts.as<int64_t>(),
+                                        L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
+                                        nullptr, nullptr, nullptr, err);
+    KITC_CUDA(cudaGetLastError());
+    k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>(), nb, L.far_off.as<int64_t>(), tot + 2);
+    k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>() + nb, nb, L.near_off.as<int64_t>(), tot + 3);
+    KITC_CUDA(cudaGetLastError());
+    int64_t *h = nullptr;
+    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h)));
+    KITC_CUDA(cudaMemcpyAsync(h, tot, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    if (reinterpret_cast<int *>(h + 6)[0] != 0) return KITC_ERR_INVALID_ARG;
+    L.near_pairs = h[0];
+    L.far_points = h[1];
+    L.nfar = h[2];
+    L.nnear = h[3];
+    KITC_TRY(L.far_id.reserve(sizeof(int32_t) * (L.nfar + 1), s));
+    KITC_TRY(L.far_mask.reserve(sizeof(uint64_t) * (L.nfar + 1), s));
+    KITC_TRY(L.near_id.reserve(sizeof(int32_t) * (L.nnear + 1), s));
+    KITC_TRY(L.near_mask.reserve(sizeof(uint64_t) * (L.nnear + 1), s));
+    k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+                                        src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
+                                        theta, np3, mac, nullptr, nullptr, nullptr,
+                                        L.far_off.as<int64_t>(), L.near_off.as<int64_t>(),
+                                        L.far_id.as<int32_t>(), L.far_mask.as<uint64_t>(),
+                                        L.near_id.as<int32_t>(), L.near_mask.as<uint64_t>(), err);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}

@@ -1,0 +1,459 @@
+// Sec. 6 tree of particle clusters, built level by level on the GPU.
+//
+// The root is the smallest box enclosing the particles.  A cluster holding
+// more than N0 particles is bisected at the midpoint of every side longer than
+// l_max / sqrt(2) (l_max = its longest side), into 8, 4 or 2 boxes; the
+// non-empty ones become its children, ordered by octant code (bit 0 = upper x,
+// bit 1 = upper y, bit 2 = upper z; a particle on the midpoint goes up).  Each
+// split is a stable partition of the cluster's slot range, so the final order
+// is unique and integer-exact.  Every floating-point decision (side, l_max /
+// sqrt(2), midpoint, x >= mid) uses round-to-nearest operations with no
+// contraction, so any IEEE implementation of the same expressions takes the
+// same decisions.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int BT = 1024;      // threads of the per-slot kernels
+constexpr int RPB = 4;        // rounds of BT consecutive slots per block
+constexpr int SPB = BT * RPB; // slots per block
+
+struct SplitInfo {
+    double mid[3];
+    int mask;   // bit l set: axis l is bisected; 0: the cluster is a leaf
+    int pad;
+};
+
+__device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
+__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
+
+// Gathers the caller's n x 3 coordinates into SoA, sets the identity order and
+// reduces each block's bounding box.
+__global__ void k_init(const double *__restrict__ xyz, int64_t n, double *__restrict__ xs,
+                       int32_t *__restrict__ perm, int32_t *__restrict__ node,
+                       double *__restrict__ part)
+{
+    __shared__ double red[6][BT / 32];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int64_t base = (int64_t)blockIdx.x * SPB;
+    for (int r = 0; r < RPB; ++r) {
+        int64_t i = base + r * BT + threadIdx.x;
+        if (i < n) {
+            for (int l = 0; l < 3; ++l) {
+                double v = xyz[3 * i + l];
+                xs[l * n + i] = v;
+                lo[l] = dmin(lo[l], v);
+                hi[l] = dmax(hi[l], v);
+            }
+            perm[i] = (int32_t)i;
+            node[i] = 0;
+        }
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int l = 0; l < 3; ++l) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[l] = dmin(lo[l], __shfl_xor_sync(0xffffffffu, lo[l], o));
+            hi[l] = dmax(hi[l], __shfl_xor_sync(0xffffffffu, hi[l], o));
+        }
+        if (lane == 0) {
+            red[l][w] = lo[l];
+            red[3 + l][w] = hi[l];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int q = threadIdx.x;
+        double v = red[q][0];
+        for (int k = 1; k < BT / 32; ++k) v = q < 3 ? dmin(v, red[q][k]) : dmax(v, red[q][k]);
+        part[blockIdx.x * 6 + q] = v;
+    }
+}
+
+// Root cluster: the exact bounding box over all blocks.
+__global__ void k_root(const double *__restrict__ part, int nblk, int64_t n, dvec4 *lo,
+                       dvec4 *hi, int32_t *begin, int32_t *end, int32_t *first_child,
+                       int32_t *n_child, int32_t *level, int32_t *parent)
+{
+    if (threadIdx.x != 0) return;
+    double b[6];
+    for (int q = 0; q < 6; ++q) b[q] = part[q];
+    for (int k = 1; k < nblk; ++k)
+        for (int q = 0; q < 6; ++q)
+            b[q] = q < 3 ? dmin(b[q], part[6 * k + q]) : dmax(b[q], part[6 * k + q]);
+    lo[0] = make_dvec4(b[0], b[1], b[2], 0.0);
+    hi[0] = make_dvec4(b[3], b[4], b[5], 0.0);
+    begin[0] = 0;
+    end[0] = (int32_t)n;
+    first_child[0] = -1;
+    n_child[0] = 0;
+    level[0] = 0;
+    parent[0] = -1;
+}
+
+// Split decision of each cluster of the level [lb, lb + nl).
+__global__ void k_split(int lb, int nl, int leaf, const dvec4 *__restrict__ lo,
+                        const dvec4 *__restrict__ hi, const int32_t *__restrict__ begin,
+                        const int32_t *__restrict__ end, const int32_t *__restrict__ level,
+                        SplitInfo *__restrict__ info)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    int c = lb + i;
+    SplitInfo s;
+    s.mask = 0;
+    s.pad = 0;
+    double l[3] = {lo[c].x, lo[c].y, lo[c].z}, h[3] = {hi[c].x, hi[c].y, hi[c].z};
+    double side[3], lmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        side[a] = __dsub_rn(h[a], l[a]);
+        if (side[a] > lmax) lmax = side[a];
+        s.mid[a] = __dmul_rn(0.5, __dadd_rn(l[a], h[a]));
+    }
+    if (end[c] - begin[c] > leaf && level[c] < KITC_MAX_LEVEL && lmax > 0.0) {
+        const double sqrt2 = 1.4142135623730951;  // correctly rounded sqrt(2)
+        double thr = __ddiv_rn(lmax, sqrt2);
+        for (int a = 0; a < 3; ++a)
+            if (side[a] > thr) s.mask |= 1 << a;
+    }
+    info[i] = s;
+}
+
+__device__ __forceinline__ int slot_key(int64_t p, int64_t n, int lb, int nl,
+                                        const double *__restrict__ xs,
+                                        const int32_t *__restrict__ node,
+                                        const SplitInfo *__restrict__ info, int *cl)
+{
+    int c = node[p] - lb;
+    *cl = c;
+    if (c < 0 || c >= nl) return 8;
+    int m = info[c].mask;
+    if (m == 0) return 8;
+    int k = 0;
+    for (int a = 0; a < 3; ++a)
+        if (((m >> a) & 1) && xs[a * n + p] >= info[c].mid[a]) k |= 1 << a;
+    return k;
+}
+
+// Per (cluster, code) counts and per (code, block) counts of the level.
+__global__ void k_count(int64_t n, int lb, int nl, const double *__restrict__ xs,
+                        const int32_t *__restrict__ node, const SplitInfo *__restrict__ info,
+                        int32_t *__restrict__ ccount, int32_t *__restrict__ bcount, int nblk)
+{
+    __shared__ int sb[8];
+    __shared__ int sc[8];
+    __shared__ int c0s;
+    if (threadIdx.x < 8) {
+        sb[threadIdx.x] = 0;
+        sc[threadIdx.x] = 0;
+    }
+    int64_t base = (int64_t)blockIdx.x * SPB;
+    if (threadIdx.x == 0) c0s = (base < n) ? node[base] - lb : -1;
+    __syncthreads();
+    int c0 = c0s;
+    for (int r = 0; r < RPB; ++r) {
+        int64_t p = base + r * BT + threadIdx.x;
+        int c = -1, k = 8;
+        if (p < n) k = slot_key(p, n, lb, nl, xs, node, info, &c);
+        unsigned key = 0xffffffffu;  // slots counted through global atomics
+        if (k < 8) {
+            atomicAdd(&sb[k], 1);
+            if (c == c0) atomicAdd(&sc[k], 1);
+            else key = (unsigned)c * 8u + (unsigned)k;
+        }
+        unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (key != 0xffffffffu && (threadIdx.x & 31) == __ffs(grp) - 1)
+            atomicAdd(&ccount[key], __popc(grp));
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        bcount[threadIdx.x * nblk + blockIdx.x] = sb[threadIdx.x];
+        if (c0 >= 0 && c0 < nl && sc[threadIdx.x] > 0)
+            atomicAdd(&ccount[c0 * 8 + threadIdx.x], sc[threadIdx.x]);
+    }
+}
+
+// In-place exclusive scan of a[0], a[stride], ... a[(m-1)*stride] by one block.
+__device__ void block_scan_strided(int32_t *a, int m, int stride, int *tot_out)
+{
+    __shared__ int32_t sums[BT];
+    int per = (m + blockDim.x - 1) / blockDim.x;
+    int b = threadIdx.x * per, e = min(m, b + per);
+    int32_t s = 0;
+    for (int i = b; i < e; ++i) s += a[(int64_t)i * stride];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int32_t v = sums[i];
+            sums[i] = run;
+            run += v;
+        }
+        if (tot_out) *tot_out = run;
+    }
+    __syncthreads();
+    int32_t run = sums[threadIdx.x];
+    for (int i = b; i < e; ++i) {
+        int32_t v = a[(int64_t)i * stride];
+        a[(int64_t)i * stride] = run;
+        run += v;
+    }
+    __syncthreads();
+}
+
+// Scans of the level and creation of the children clusters.  Single block.
+__global__ void __launch_bounds__(BT) k_children(
+    int lb, int nl, int nclus, const SplitInfo *__restrict__ info, int32_t *ccount,
+    int32_t *cprefix, int32_t *childoff, int32_t *childidx, int32_t *bcount, int nblk,
+    int32_t *nchild_scan, dvec4 *lo, dvec4 *hi, int32_t *begin, int32_t *end,
+    int32_t *first_child, int32_t *n_child, int32_t *level, int32_t *parent, int32_t *out2)
+{
+    // per code: exclusive scan of the block counts, and of the cluster counts
+    for (int k = 0; k < 8; ++k) block_scan_strided(bcount + k * nblk, nblk, 1, nullptr);
+    for (int i = threadIdx.x; i < nl * 8; i += blockDim.x) cprefix[i] = ccount[i];
+    __syncthreads();
+    for (int k = 0; k < 8; ++k) block_scan_strided(cprefix + k, nl, 8, nullptr);
+    // children per cluster and offsets of each code inside the cluster
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+        int nch = 0, off = 0;
+        for (int k = 0; k < 8; ++k) {
+            int v = ccount[i * 8 + k];
+            childoff[i * 8 + k] = off;
+            off += v;
+            if (info[i].mask != 0 && v > 0) nch++;
+        }
+        nchild_scan[i] = nch;
+    }
+    __syncthreads();
+    __shared__ int total;
+    block_scan_strided(nchild_scan, nl, 1, &total);
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+        int c = lb + i;
+        int m = info[i].mask;
+        int fc = nclus + nchild_scan[i];
+        int j = 0;
+        for (int k = 0; k < 8; ++k) {
+            int v = ccount[i * 8 + k];
+            childidx[i * 8 + k] = -1;
+            if (m == 0 || v == 0) continue;
+            int id = fc + j++;
+            childidx[i * 8 + k] = id;
+            double l[3] = {lo[c].x, lo[c].y, lo[c].z}, h[3] = {hi[c].x, hi[c].y, hi[c].z};
+            for (int a = 0; a < 3; ++a)
+                if ((m >> a) & 1) {
+                    if ((k >> a) & 1) l[a] = info[i].mid[a];
+                    else h[a] = info[i].mid[a];
+                }
+            lo[id] = make_dvec4(l[0], l[1], l[2], 0.0);
+            hi[id] = make_dvec4(h[0], h[1], h[2], 0.0);
+            begin[id] = begin[c] + childoff[i * 8 + k];
+            end[id] = begin[id] + v;
+            first_child[id] = -1;
+            n_child[id] = 0;
+            level[id] = level[c] + 1;
+            parent[id] = c;
+        }
+        first_child[c] = j > 0 ? fc : -1;
+        n_child[c] = j;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nsplit = 0;
+        for (int i = 0; i < nl; ++i) nsplit += info[i].mask != 0 && n_child[lb + i] > 0;
+        out2[0] = total;
+        out2[1] = nsplit;
+    }
+}
+
+// Stable scatter of the level's participating slots into their children.
+__global__ void __launch_bounds__(BT) k_scatter(
+    int64_t n, int lb, int nl, const double *__restrict__ xs, const int32_t *__restrict__ perm,
+    const int32_t *__restrict__ node, const SplitInfo *__restrict__ info,
+    const int32_t *__restrict__ begin, const int32_t *__restrict__ cprefix,
+    const int32_t *__restrict__ childoff, const int32_t *__restrict__ childidx,
+    const int32_t *__restrict__ bprefix, int nblk, double *__restrict__ xs2,
+    int32_t *__restrict__ perm2, int32_t *__restrict__ node2)
+{
+    __shared__ int wcnt[BT / 32][8];
+    __shared__ int run[8];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 8) run[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * SPB;
+    for (int r = 0; r < RPB; ++r) {
+        int64_t p = base + r * BT + threadIdx.x;
+        int c = -1, k = 8;
+        if (p < n) k = slot_key(p, n, lb, nl, xs, node, info, &c);
+        unsigned grp = __match_any_sync(0xffffffffu, k);
+        int rank = __popc(grp & ((1u << lane) - 1u));
+        if (lane < 8) wcnt[w][lane] = 0;
+        __syncwarp();
+        if (k < 8 && rank == 0) wcnt[w][k] = __popc(grp);
+        __syncthreads();
+        if (threadIdx.x < 8) {  // exclusive prefix over warps, per code
+            int s = run[threadIdx.x];
+            for (int q = 0; q < BT / 32; ++q) {
+                int v = wcnt[q][threadIdx.x];
+                wcnt[q][threadIdx.x] = s;
+                s += v;
+            }
+            run[threadIdx.x] = s;
+        }
+        __syncthreads();
+        if (p < n) {
+            if (k < 8) {
+                int g = bprefix[k * nblk + blockIdx.x] + wcnt[w][k] + rank;
+                int64_t np_ = (int64_t)begin[lb + c] + childoff[c * 8 + k] + g - cprefix[c * 8 + k];
+                perm2[np_] = perm[p];
+                node2[np_] = childidx[c * 8 + k];
+                for (int a = 0; a < 3; ++a) xs2[a * n + np_] = xs[a * n + p];
+            } else {
+                perm2[p] = perm[p];
+                node2[p] = node[p];
+                for (int a = 0; a < 3; ++a) xs2[a * n + p] = xs[a * n + p];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Cluster centre (box midpoint) and radius (half the diagonal), Fig. 1.
+__global__ void k_geometry(int m, const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi,
+                           dvec4 *__restrict__ ctr)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    dvec4 a = lo[c], b = hi[c];
+    double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    ctr[c] = make_dvec4(__dmul_rn(0.5, __dadd_rn(a.x, b.x)), __dmul_rn(0.5, __dadd_rn(a.y, b.y)),
+                          __dmul_rn(0.5, __dadd_rn(a.z, b.z)), __dmul_rn(0.5, __dsqrt_rn(s)));
+}
+
+kitc_status grow_clusters(TreeDev &t, int need, cudaStream_t s)
+{
+    if (need <= t.cap) return KITC_OK;
+    int cap = std::max(need, std::max(64, 2 * t.cap));
+    KITC_TRY(t.lo.reserve(sizeof(dvec4) * cap, s, true));
+    KITC_TRY(t.hi.reserve(sizeof(dvec4) * cap, s, true));
+    KITC_TRY(t.begin.reserve(sizeof(int32_t) * cap, s, true));
+    KITC_TRY(t.end.reserve(sizeof(int32_t) * cap, s, true));
+    KITC_TRY(t.first_child.reserve(sizeof(int32_t) * cap, s, true));
+    KITC_TRY(t.n_child.reserve(sizeof(int32_t) * cap, s, true));
+    KITC_TRY(t.level.reserve(sizeof(int32_t) * cap, s, true));
+    KITC_TRY(t.parent.reserve(sizeof(int32_t) * cap, s, true));
+    t.cap = cap;
+    return KITC_OK;
+}
+
+}  // namespace
+
+void TreeDev::release(cudaStream_t s)
+{
+    for (DevBuf *b : {&perm, &xs, &lo, &hi, &ctr, &begin, &end, &first_child, &n_child, &level,
+                      &parent})
+        b->release(s);
+    nclus = cap = depth = nleaves = 0;
+    level_start.clear();
+}
+
+size_t TreeDev::bytes() const
+{
+    size_t b = 0;
+    for (const DevBuf *d : {&perm, &xs, &lo, &hi, &ctr, &begin, &end, &first_child, &n_child,
+                            &level, &parent})
+        b += d->bytes;
+    return b;
+}
+
+kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t)
+{
+    t.release(s);
+    t.n = n;
+    t.leaf = leaf;
+    int nblk = (int)((n + SPB - 1) / SPB);
+    DevBuf perm2, xs2, node, node2, part, bcount, lvl;
+    KITC_TRY(t.perm.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(perm2.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(t.xs.reserve(sizeof(double) * 3 * n, s));
+    KITC_TRY(xs2.reserve(sizeof(double) * 3 * n, s));
+    KITC_TRY(node.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(node2.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(part.reserve(sizeof(double) * 6 * nblk, s));
+    KITC_TRY(bcount.reserve(sizeof(int32_t) * 8 * nblk, s));
+    KITC_TRY(grow_clusters(t, 64, s));
+    k_init<<<nblk, BT, 0, s>>>(xyz, n, t.xs.as<double>(), t.perm.as<int32_t>(),
+                               node.as<int32_t>(), part.as<double>());
+    KITC_CUDA(cudaGetLastError());
+    k_root<<<1, 32, 0, s>>>(part.as<double>(), nblk, n, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                            t.begin.as<int32_t>(), t.end.as<int32_t>(),
+                            t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                            t.level.as<int32_t>(), t.parent.as<int32_t>());
+    KITC_CUDA(cudaGetLastError());
+    int32_t *h2 = nullptr;
+    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h2)));
+    int lb = 0, nl = 1, nclus = 1, depth = 0, nleaves = 0;
+    t.level_start.assign(1, 0);
+    kitc_status st = KITC_OK;
+    while (nl > 0) {
+        if ((st = grow_clusters(t, nclus + 8 * nl, s)) != KITC_OK) break;
+        size_t per = (size_t)nl * 8;
+        // level scratch: info | ccount | cprefix | childoff | childidx | nchild_scan | out2
+        size_t need = sizeof(SplitInfo) * nl + sizeof(int32_t) * (4 * per + nl + 2) + 256;
+        if ((st = lvl.reserve(need, s)) != KITC_OK) break;
+        char *q = lvl.as<char>();
+        SplitInfo *info = reinterpret_cast<SplitInfo *>(q);
+        int32_t *ccount = reinterpret_cast<int32_t *>(q + sizeof(SplitInfo) * nl);
+        int32_t *cprefix = ccount + per, *childoff = cprefix + per, *childidx = childoff + per;
+        int32_t *nchs = childidx + per, *out2 = nchs + nl;
+        if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * per, s) != cudaSuccess) {
+            st = KITC_ERR_CUDA;
+            break;
+        }
+        k_split<<<(nl + 255) / 256, 256, 0, s>>>(lb, nl, leaf, t.lo.as<dvec4>(),
+                                                t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                                                t.end.as<int32_t>(), t.level.as<int32_t>(), info);
+        k_count<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), node.as<int32_t>(), info, ccount,
+                                    bcount.as<int32_t>(), nblk);
+        k_children<<<1, BT, 0, s>>>(lb, nl, nclus, info, ccount, cprefix, childoff, childidx,
+                                    bcount.as<int32_t>(), nblk, nchs, t.lo.as<dvec4>(),
+                                    t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                                    t.end.as<int32_t>(), t.first_child.as<int32_t>(),
+                                    t.n_child.as<int32_t>(), t.level.as<int32_t>(),
+                                    t.parent.as<int32_t>(), out2);
+        k_scatter<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), t.perm.as<int32_t>(),
+                                      node.as<int32_t>(), info, t.begin.as<int32_t>(), cprefix,
+                                      childoff, childidx, bcount.as<int32_t>(), nblk,
+                                      xs2.as<double>(), perm2.as<int32_t>(), node2.as<int32_t>());
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h2, out2, 2 * sizeof(int32_t),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = kitc_from_cuda(e);
+            break;
+        }
+        std::swap(t.xs, xs2);
+        std::swap(t.perm, perm2);
+        std::swap(node, node2);
+        int nch = h2[0], nsplit = h2[1];
+        nleaves += nl - nsplit;
+        depth++;
+        lb = nclus;
+        nclus += nch;
+        nl = nch;
+        if (nl > 0) t.level_start.push_back(lb);
+    }
+    for (DevBuf *b : {&perm2, &xs2, &node, &node2, &part, &bcount, &lvl}) b->release(s);
+    if (st != KITC_OK) return st;
+    t.nclus = nclus;
+    t.depth = depth;
+    t.nleaves = nleaves;
+    KITC_TRY(t.ctr.reserve(sizeof(dvec4) * t.cap, s));
+    k_geometry<<<(nclus + 255) / 256, 256, 0, s>>>(nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                                   t.ctr.as<dvec4>());
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}

@@ -1,0 +1,319 @@
+// Modified weights of every cluster (Sec. 4-5, Eq. modified_weights,
+// Algorithm 1) in FP64, and the packed records the evaluator streams.
+//
+//   fhat[c][k1][k2][k3][q] = sum_{y_j in c} L_k1(y_j1) L_k2(y_j2) L_k3(y_j3) f_j[q]
+//
+// Each L is the barycentric form of Eq. Barycentric-1D with the simple
+// weights of Eq. barycentric_weights at the Chebyshev points of Eq.
+// Chebyshev_points mapped to the cluster's box (Sec. 3 interval map); a
+// coordinate within DBL_MIN of a point s_m takes L_k = delta_km (Sec. 3,
+// Algorithm 1).  The sum per axis is normalized before the product, which
+// equals Algorithm 1's division by sum1*sum2*sum3 and cannot overflow.
+//
+// GPU form: the contraction over j is a batched outer-product sum.  For a
+// chunk of particles a CTA stages h_j[k1,k2] = L_k1 L_k2 and g_j[k3,q] =
+// L_k3 f_j[q] in shared memory and every thread accumulates its outputs with
+// one FP64 FMA per particle.  Chunks of one cluster write partial sums that a
+// second kernel adds in a fixed order, so the result is deterministic.
+#include <float.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int WT = 256;     // threads of the weights kernel
+constexpr int ACC = 16;     // outputs per thread per pass
+constexpr int CHUNK = 2048; // particles per work item
+
+struct Cheb {
+    double t[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
+    double w[KITC_MAX_DEGREE + 1];  // (-1)^k delta_k
+    int n;
+};
+
+Cheb make_cheb(int n)
+{
+    Cheb c;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k <= KITC_MAX_DEGREE; ++k) {
+        c.t[k] = k <= n ? cos((double)k * pi / (double)n) : 0.0;
+        double d = (k == 0 || k == n) ? 0.5 : 1.0;
+        c.w[k] = k <= n ? ((k & 1) ? -d : d) : 0.0;
+    }
+    c.n = n;
+    return c;
+}
+
+struct Item {
+    int32_t c, p0, p1, pad;
+};
+
+// Barycentric basis of one coordinate on [a, b] (Eq. Barycentric-1D with the
+// coincident-point rule), written to L[0..n].
+__device__ void bary_basis(const Cheb &cb, double a, double b, double y, double *L)
+{
+    int n = cb.n;
+    int flag = -1;
+    double sum = 0.0;
+    double ab = __dadd_rn(a, b), ba = __dsub_rn(b, a);
+    for (int k = 0; k <= n; ++k) {
+        double s = __dmul_rn(0.5, __dadd_rn(ab, __dmul_rn(cb.t[k], ba)));
+        double diff = y - s;
+        if (fabs(diff) <= DBL_MIN) {
+            flag = k;
+            L[k] = 0.0;
+        } else {
+            L[k] = cb.w[k] / diff;
+            sum += L[k];
+        }
+    }
+    if (flag >= 0) {
+        for (int k = 0; k <= n; ++k) L[k] = (k == flag) ? 1.0 : 0.0;
+    } else {
+        double inv = 1.0 / sum;
+        for (int k = 0; k <= n; ++k) L[k] *= inv;
+    }
+}
+
+__global__ void __launch_bounds__(WT) k_weights_chunk(
+    Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
+    const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
+    const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi, int sb,
+    double *__restrict__ partial)
+{
+    extern __shared__ double sm[];
+    const int np = cb.n + 1;
+    const int np2 = np * np, nw = np * win;
+    const int pwin = np2 * np * win;
+    double *Ls = sm;                        // [sb][3][np]
+    double *hs = Ls + (size_t)sb * 3 * np;  // [sb][np2]
+    double *gs = hs + (size_t)sb * np2;     // [sb][nw]
+    Item it = items[blockIdx.x];
+    int obase = blockIdx.y * ACC * WT;
+    dvec4 blo = lo[it.c], bhi = hi[it.c];
+    double acc[ACC];
+#pragma unroll
+    for (int i = 0; i < ACC; ++i) acc[i] = 0.0;
+    int rowoff[ACC], coloff[ACC];
+#pragma unroll
+    for (int i = 0; i < ACC; ++i) {
+        int o = obase + i * WT + threadIdx.x;
+        rowoff[i] = o < pwin ? o / nw : 0;
+        coloff[i] = o < pwin ? o % nw : 0;
+    }
+    for (int j0 = it.p0; j0 < it.p1; j0 += sb) {
+        int cnt = min(sb, it.p1 - j0);
+        for (int q = threadIdx.x; q < cnt * 3; q += WT) {
+            int j = q / 3, l = q % 3;
+            double a = l == 0 ? blo.x : (l == 1 ? blo.y : blo.z);
+            double b = l == 0 ? bhi.x : (l == 1 ? bhi.y : bhi.z);
+            double L[KITC_MAX_DEGREE + 1];
+            bary_basis(cb, a, b, xs[l * n + j0 + j], L);
+            for (int k = 0; k < np; ++k) Ls[(j * 3 + l) * np + k] = L[k];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt * np2; q += WT) {
+            int j = q / np2, r = q % np2;
+            hs[j * np2 + r] = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
+        }
+        for (int q = threadIdx.x; q < cnt * nw; q += WT) {
+            int j = q / nw, r = q % nw;
+            gs[j * nw + r] = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const double *h = hs + j * np2, *g = gs + j * nw;
+#pragma unroll
+            for (int i = 0; i < ACC; ++i) acc[i] = fma(h[rowoff[i]], g[coloff[i]], acc[i]);
+        }
+        __syncthreads();
+    }
+    double *dst = partial + (size_t)blockIdx.x * pwin;
+#pragma unroll
+    for (int i = 0; i < ACC; ++i) {
+        int o = obase + i * WT + threadIdx.x;
+        if (o < pwin) dst[o] = acc[i];
+    }
+}
+
+// fhat[c] = sum of the partials of c's work items, in item order.
+__global__ void k_weights_reduce(const int32_t *__restrict__ first_item, int pwin,
+                                 const double *__restrict__ partial, double *__restrict__ fhat)
+{
+    int c = blockIdx.x;
+    int i0 = first_item[c], i1 = first_item[c + 1];
+    for (int o = threadIdx.x; o < pwin; o += blockDim.x) {
+        double s = 0.0;
+        for (int i = i0; i < i1; ++i) s += partial[(size_t)i * pwin + o];
+        fhat[(size_t)c * pwin + o] = s;
+    }
+}
+
+template <bool MIXED>
+__global__ void k_pack_proxies(int64_t nrec, int win, const double *__restrict__ fhat,
+                               void *__restrict__ out)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    const double *f = fhat + r * win;
+    if (MIXED) {
+        float4 *o = reinterpret_cast<float4 *>(out);
+        if (win == 3) {
+            o[r] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
+        } else {
+            o[2 * r] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
+            o[2 * r + 1] = make_float4((float)f[3], (float)f[4], (float)f[5], 0.f);
+        }
+    } else {
+        double *o = reinterpret_cast<double *>(out);
+        if (win == 3) {
+            o[4 * r + 0] = f[0];
+            o[4 * r + 1] = f[1];
+            o[4 * r + 2] = f[2];
+            o[4 * r + 3] = 0.0;
+        } else {
+            for (int q = 0; q < 6; ++q) o[6 * r + q] = f[q];
+        }
+    }
+}
+
+// Source records in slot order.  t == NULL: slots are the caller's order and
+// coordinates come from xyz (n x 3).
+template <bool MIXED>
+__global__ void k_pack_sources(int64_t n, int win, const double *__restrict__ xs,
+                               const int32_t *__restrict__ perm, const double *__restrict__ xyz,
+                               const double *__restrict__ w, void *__restrict__ out)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t j = perm ? perm[p] : p;
+    double x[3];
+    for (int l = 0; l < 3; ++l) x[l] = perm ? xs[l * n + p] : xyz[3 * p + l];
+    const double *f = w + j * win;
+    if (MIXED) {
+        float v[12];
+        for (int l = 0; l < 3; ++l) {
+            float h = __double2float_rn(x[l]);
+            v[l] = h;
+            v[3 + l] = __double2float_rn(x[l] - (double)h);
+        }
+        for (int q = 0; q < 6; ++q) v[6 + q] = q < win ? (float)f[q] : 0.f;
+        float4 *o = reinterpret_cast<float4 *>(out) + 3 * p;
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        o[2] = make_float4(v[8], v[9], v[10], v[11]);
+    } else {
+        int stride = win == 3 ? 6 : 10;
+        double *o = reinterpret_cast<double *>(out) + p * stride;
+        for (int l = 0; l < 3; ++l) o[l] = x[l];
+        for (int q = 0; q < win; ++q) o[3 + q] = f[q];
+        if (win == 6) o[9] = 0.0;
+    }
+}
+
+}  // namespace
+
+int proxy_record_bytes(int win, bool mixed)
+{
+    return mixed ? (win == 3 ? 16 : 32) : (win == 3 ? 32 : 48);
+}
+
+int source_record_bytes(int win, bool mixed)
+{
+    return mixed ? 48 : (win == 3 ? 48 : 80);
+}
+
+void WeightsDev::release(cudaStream_t s)
+{
+    for (DevBuf *b : {&fhat, &proxy, &src, &partial, &items}) b->release(s);
+}
+
+size_t WeightsDev::bytes() const
+{
+    return fhat.bytes + proxy.bytes + src.bytes + partial.bytes + items.bytes;
+}
+
+kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree,
+                            cudaStream_t s, WeightsDev &wd)
+{
+    const int np = degree + 1;
+    const int pwin = np * np * np * win;
+    // work items: chunks of every cluster's slot range, in cluster order
+    std::vector<int32_t> hb(t.nclus), he(t.nclus);
+    KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * t.nclus,
+                              cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * t.nclus,
+                              cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    std::vector<Item> items;
+    std::vector<int32_t> first(t.nclus + 1);
+    for (int c = 0; c < t.nclus; ++c) {
+        first[c] = (int32_t)items.size();
+        for (int32_t p = hb[c]; p < he[c]; p += CHUNK)
+            items.push_back(Item{c, p, std::min(he[c], p + CHUNK), 0});
+    }
+    first[t.nclus] = (int32_t)items.size();
+    size_t nitems = items.size();
+    size_t ibytes = sizeof(Item) * nitems + sizeof(int32_t) * (t.nclus + 1) + 64;
+    KITC_TRY(wd.items.reserve(ibytes, s));
+    Item *d_items = wd.items.as<Item>();
+    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + nitems);
+    KITC_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * nitems,
+                              cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (t.nclus + 1),
+                              cudaMemcpyHostToDevice, s));
+    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * nitems, s));
+    KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
+    // the host vectors must outlive the copies above
+    KITC_CUDA(cudaStreamSynchronize(s));
+    size_t per = sizeof(double) * (3 * np + np * np + np * win);
+    int sb = 64;
+    while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
+    size_t smem = per * sb;
+    KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    int npass = (pwin + ACC * WT - 1) / (ACC * WT);
+    dim3 grid((unsigned)nitems, (unsigned)npass);
+    k_weights_chunk<<<grid, WT, smem, s>>>(make_cheb(degree), d_items, t.n, t.xs.as<double>(),
+                                           t.perm.as<int32_t>(), w_user, win, t.lo.as<dvec4>(),
+                                           t.hi.as<dvec4>(), sb, wd.partial.as<double>());
+    KITC_CUDA(cudaGetLastError());
+    k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
+                                             wd.fhat.as<double>());
+    KITC_CUDA(cudaGetLastError());
+    wd.degree = degree;
+    wd.win = win;
+    return KITC_OK;
+}
+
+kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s)
+{
+    int np = wd.degree + 1;
+    int64_t nrec = (int64_t)t.nclus * np * np * np;
+    KITC_TRY(wd.proxy.reserve((size_t)proxy_record_bytes(wd.win, mixed) * nrec, s));
+    unsigned g = (unsigned)((nrec + 255) / 256);
+    if (mixed)
+        k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
+    else
+        k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
+                         int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out)
+{
+    KITC_TRY(out.reserve((size_t)source_record_bytes(win, mixed) * n, s));
+    unsigned g = (unsigned)((n + 255) / 256);
+    const double *xs = t ? t->xs.as<double>() : nullptr;
+    const int32_t *perm = t ? t->perm.as<int32_t>() : nullptr;
+    if (mixed)
+        k_pack_sources<true><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
+    else
+        k_pack_sources<false><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}

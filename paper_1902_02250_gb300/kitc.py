@@ -1,0 +1,291 @@
+"""Python binding of libkitc (include/kitc.h): argument marshalling only.
+
+Every step of the treecode runs in the CUDA library; this module passes
+pointers, sizes and the current torch stream, and turns status codes into
+exceptions.  There is no fallback: without the built library or a CUDA
+device the calls raise.
+"""
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+from . import build as _build
+
+STOKESLET, ROTLET, STOKESLET_ROTLET, TEST_POLY = 0, 1, 2, 99
+FP64, MIXED = 0, 1
+MAC_PARTICLE, MAC_BATCH = 0, 1
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
+           4: "device-side wait timed out", 5: "call out of order"}
+
+
+class KitcError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s: %s (status %d)" % (where, _STATUS.get(status, "?"), status))
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("degree", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("eps", ctypes.c_double), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("mac", ctypes.c_int), ("target_batch", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_sources", ctypes.c_int64), ("n_clusters", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("n_targets", ctypes.c_int64),
+                ("n_batches", ctypes.c_int64), ("far_entries", ctypes.c_int64),
+                ("near_entries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("far_points", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("ms_tree", ctypes.c_float), ("ms_weights", ctypes.c_float),
+                ("ms_lists", ctypes.c_float), ("ms_evaluate", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+@dataclasses.dataclass
+class Params:
+    """kitc_params: MAC theta (Eq. MAC), degree n, leaf size N0, MRS eps,
+    kernel, precision, MAC mode and targets per batch (<= 64)."""
+    theta: float = 0.7
+    degree: int = 8
+    leaf_size: int = 2000
+    eps: float = 0.001
+    kernel: int = STOKESLET
+    precision: int = FP64
+    mac: int = MAC_PARTICLE
+    target_batch: int = 64
+
+    def c(self):
+        return _Params(float(self.theta), int(self.degree), int(self.leaf_size), float(self.eps),
+                       int(self.kernel), int(self.precision), int(self.mac),
+                       int(self.target_batch))
+
+
+_lib = None
+SYMBOLS = ["kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
+           "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
+           "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
+           "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest"]
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads the in-tree libkitc.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libkitc.so is not built (%s); run __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        PP = ctypes.POINTER(_Params)
+        L.kitc_build_tree.argtypes = [P, I64, PP, P, ctypes.POINTER(P)]
+        L.kitc_modified_weights.argtypes = [P, P, P]
+        L.kitc_evaluate.argtypes = [P, P, I64, P, P]
+        L.kitc_direct.argtypes = [P, I64, P, P, I64, PP, P, P]
+        L.kitc_solve_host.argtypes = [P, P, I64, P, I64, PP, P, P]
+        L.kitc_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        L.kitc_tree_download.argtypes = [P] * 11
+        L.kitc_weights_download.argtypes = [P, P, P]
+        L.kitc_lists_download.argtypes = [P] * 9
+        L.kitc_free_tree.argtypes = [P]
+        L.kitc_free_tree.restype = None
+        L.kitc_status_string.argtypes = [I]
+        L.kitc_status_string.restype = ctypes.c_char_p
+        L.kitc_kernel_win.argtypes = [I]
+        L.kitc_kernel_wout.argtypes = [I]
+        L.kitc_set_wait_limit_ms.argtypes = [I]
+        L.kitc_watchdog_selftest.argtypes = [I, P]
+        for name in ("kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
+                     "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
+                     "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest"):
+            getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise KitcError(status, where)
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, cols, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.dim() == 2 and t.shape[1] == cols):
+        raise ValueError("%s must be a contiguous CUDA float64 tensor of shape (n, %d)" % (name, cols))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kernel_win(kernel):
+    return lib().kitc_kernel_win(kernel)
+
+
+def kernel_wout(kernel):
+    return lib().kitc_kernel_wout(kernel)
+
+
+def set_wait_limit_ms(ms):
+    return lib().kitc_set_wait_limit_ms(int(ms))
+
+
+def kitc_watchdog_selftest(limit_ms=50, stream=None):
+    """Status of a bounded device wait on a barrier nothing completes (4 = timed out)."""
+    return lib().kitc_watchdog_selftest(int(limit_ms), _stream(stream))
+
+
+class Tree:
+    """A kitc_tree handle (owned by the library, freed with free())."""
+
+    def __init__(self, handle, params, n):
+        self._h = handle
+        self.params = params
+        self.n = n
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("tree already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().kitc_free_tree(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self):
+        s = Stats()
+        _check(lib().kitc_get_stats(self.handle, ctypes.byref(s)), "kitc_get_stats")
+        return s.as_dict()
+
+    def download(self, stream=None):
+        st = self.stats()
+        m, n = st["n_clusters"], st["n_sources"]
+        out = dict(perm=np.empty(n, np.int64), lo=np.empty((m, 3)), hi=np.empty((m, 3)),
+                   begin=np.empty(m, np.int64), end=np.empty(m, np.int64),
+                   first_child=np.empty(m, np.int32), n_child=np.empty(m, np.int32),
+                   level=np.empty(m, np.int32), parent=np.empty(m, np.int32))
+        _check(lib().kitc_tree_download(self.handle, *[_np(out[k]) for k in (
+            "perm", "lo", "hi", "begin", "end", "first_child", "n_child", "level", "parent")],
+            _stream(stream)), "kitc_tree_download")
+        return out
+
+    def weights(self, stream=None):
+        st = self.stats()
+        np1 = st["degree"] + 1
+        f = np.empty((st["n_clusters"], np1, np1, np1, kernel_win(self.params.kernel)))
+        _check(lib().kitc_weights_download(self.handle, _np(f), _stream(stream)),
+               "kitc_weights_download")
+        return f
+
+    def lists(self, stream=None):
+        st = self.stats()
+        nb, nt = st["n_batches"], st["n_targets"]
+        r = dict(tperm=np.empty(nt, np.int64), nfar=np.empty(nb, np.int64),
+                 nnear=np.empty(nb, np.int64), far=np.empty(max(1, st["far_entries"]), np.int32),
+                 far_mask=np.empty(max(1, st["far_entries"]), np.uint64),
+                 near=np.empty(max(1, st["near_entries"]), np.int32),
+                 near_mask=np.empty(max(1, st["near_entries"]), np.uint64))
+        _check(lib().kitc_lists_download(self.handle, *[_np(r[k]) for k in (
+            "tperm", "nfar", "nnear", "far", "far_mask", "near", "near_mask")], _stream(stream)),
+            "kitc_lists_download")
+        r["far"] = r["far"][:st["far_entries"]]
+        r["far_mask"] = r["far_mask"][:st["far_entries"]]
+        r["near"] = r["near"][:st["near_entries"]]
+        r["near_mask"] = r["near_mask"][:st["near_entries"]]
+        return r
+
+
+def kitc_build_tree(src_xyz, params, stream=None):
+    """Sec. 6 tree of the sources (CUDA float64 tensor, n x 3)."""
+    h = ctypes.c_void_p()
+    p = params.c()
+    _check(lib().kitc_build_tree(_dptr(src_xyz, 3, "src_xyz"), src_xyz.shape[0], ctypes.byref(p),
+                                 _stream(stream), ctypes.byref(h)), "kitc_build_tree")
+    return Tree(h.value, params, src_xyz.shape[0])
+
+
+def kitc_modified_weights(tree, w, stream=None):
+    """Eq. modified_weights for every cluster; w is n x w_in (CUDA float64)."""
+    _check(lib().kitc_modified_weights(tree.handle, _dptr(w, kernel_win(tree.params.kernel), "w"),
+                                       _stream(stream)), "kitc_modified_weights")
+
+
+def kitc_evaluate(tree, tgt_xyz, out=None, stream=None):
+    """Algorithm 2 at the targets; returns out (n_tgt x w_out, CUDA float64)."""
+    import torch
+    wout = kernel_wout(tree.params.kernel)
+    if out is None:
+        out = torch.empty((tgt_xyz.shape[0], wout), dtype=torch.float64, device=tgt_xyz.device)
+    _check(lib().kitc_evaluate(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
+                               _dptr(out, wout, "out"), _stream(stream)), "kitc_evaluate")
+    return out
+
+
+def kitc_direct(tgt_xyz, src_xyz, w, params, out=None, stream=None):
+    """Eq. N-body by direct summation on the GPU."""
+    import torch
+    wout = kernel_wout(params.kernel)
+    if out is None:
+        out = torch.empty((tgt_xyz.shape[0], wout), dtype=torch.float64, device=tgt_xyz.device)
+    p = params.c()
+    _check(lib().kitc_direct(_dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
+                             _dptr(src_xyz, 3, "src_xyz"), _dptr(w, kernel_win(params.kernel), "w"),
+                             src_xyz.shape[0], ctypes.byref(p), _dptr(out, wout, "out"),
+                             _stream(stream)), "kitc_direct")
+    return out
+
+
+def kitc_solve_host(src_xyz, w, params, tgt_xyz=None, out=None, stream=None):
+    """End to end from host (numpy float64) arrays: copies in, treecode, copies out."""
+    src_xyz = np.ascontiguousarray(src_xyz, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    n = src_xyz.shape[0]
+    nt = n if tgt_xyz is None else tgt_xyz.shape[0]
+    wout = kernel_wout(params.kernel)
+    if out is None:
+        out = np.empty((nt, wout))
+    tp = None
+    if tgt_xyz is not None:
+        tgt_xyz = np.ascontiguousarray(tgt_xyz, np.float64)
+        tp = _np(tgt_xyz)
+    p = params.c()
+    _check(lib().kitc_solve_host(_np(src_xyz), _np(w), n, tp, nt, ctypes.byref(p), _np(out),
+                                 _stream(stream)), "kitc_solve_host")
+    return out
+
+
+def treecode(src_xyz, w, params, tgt_xyz=None, stream=None):
+    """build tree -> modified weights -> evaluate (device tensors)."""
+    t = kitc_build_tree(src_xyz, params, stream)
+    try:
+        kitc_modified_weights(t, w, stream)
+        out = kitc_evaluate(t, src_xyz if tgt_xyz is None else tgt_xyz, stream=stream)
+        return out, t.stats()
+    finally:
+        t.free()
