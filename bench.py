@@ -1,0 +1,334 @@
+"""Benchmark: Stokeslet targets/s of the GB300 treecode at E <= 1e-6, N = 1M.
+
+One step = the whole hot path on one synthetic system already resident in
+HBM: tree build (Sec. 6), modified weights (Algorithm 1), target order and
+interaction lists, fused near/far evaluation (Algorithm 2), output in caller
+order.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kitc|reference]
+
+With N > 1 (torchrun) every rank solves its own independent system (weak
+scaling; no data-path collective); timings are reduced with MAX over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Workload: uniform cube N = 1e6 (the paper's Stokeslet setting on a 1M system),
+# eps = 1e-3, N0 = 2000, n = 8.  theta = 0.6 is the largest theta in
+# {0.5, 0.6, 0.7} that keeps E <= 1e-6 at n = 8 (theta = 0.7 gives E ~ 5.5e-6).
+N = 1_000_000
+SEED = 2
+EPS = 1e-3
+THETA = 0.6
+DEGREE = 8
+LEAF = 2000
+BATCH = 64
+N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacement)
+SAMPLE_SEED = 102
+L2_FLUSH_BYTES = 256 << 20
+FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kitc", choices=["kitc", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--mac", default="particle", choices=["particle", "batch"])
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def reduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class Clocks:
+    """nvidia-smi sampler of SM clock and throttle reasons (200 ms period)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [v.strip() for v in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rel_l2(a, b):
+    return float(math.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
+
+
+METRIC = "Stokeslet targets/sec at 1e-6 rel. L2 error, N=1M, vs plain FP64 GPU treecode"
+
+
+def config(mac, precision):
+    return {"workload": "uniform cube [-1,1]^3, N=1,000,000 (seed 2 + rank), Stokeslet, f ~ U[-1,1]^3",
+            "eps": EPS, "theta": THETA, "degree": DEGREE, "leaf_size": LEAF, "target_batch": BATCH,
+            "mac": mac, "precision": precision,
+            "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def oracle_sample(x, f, n_eval, seed):
+    """The CPU oracle as it stands on this host: tree + modified weights over
+    all N sources, Algorithm 2 on n_eval sampled targets, time scaled to N."""
+    import oracle
+    from paper_1902_02250_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    t = oracle.Tree(x, LEAF)
+    t1 = time.perf_counter()
+    fh = t.modified_weights(f, DEGREE)
+    t2 = time.perf_counter()
+    idx = wl.sample_indices(len(x), n_eval, seed)
+    t.treecode(f, fh, DEGREE, oracle.STOKESLET, EPS, THETA, x[idx])
+    t3 = time.perf_counter()
+    total = (t1 - t0) + (t2 - t1) + (t3 - t2) * len(x) / n_eval
+    return {"value": len(x) / total, "unit": "targets/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "tree + modified weights over all %d sources, Algorithm 2 on %d sampled "
+                      "targets, evaluation time scaled by N/%d; %.1f s of CPU work"
+                      % (len(x), n_eval, n_eval, t3 - t0),
+            "seconds": {"tree": t1 - t0, "weights": t2 - t1, "eval_sample": t3 - t2}}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1902_02250_gb300 import workloads as wl
+    import oracle
+    oracle.build()
+    x, f = wl.uniform_cube(N, SEED)
+    for i in range(args.warmup):
+        oracle_sample(x, f, 200, 900 + i)
+    vals = [oracle_sample(x, f, 1000, 1000 + i) for i in range(args.steps)]
+    v = float(np.mean([r["value"] for r in vals]))
+    ms = 1e3 * N / v
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "targets/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.mac, "fp64 (CPU oracle)"),
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_per_launch():
+    """DRAM bytes of one evaluator launch from the committed ncu capture, if it
+    was taken on the current evaluator source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "eval_traffic.json")
+    src = os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return rec["dram_bytes_per_launch"] if rec.get("evaluate_cu_sha256") == sha else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def run_kitc(args, ws, rank, local):
+    import torch
+    from paper_1902_02250_gb300 import kitc as K, workloads as wl
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mac = K.MAC_PARTICLE if args.mac == "particle" else K.MAC_BATCH
+    x, f = wl.uniform_cube(N, SEED + rank)
+    xd = torch.from_numpy(x).to(dev)
+    fd = torch.from_numpy(f).to(dev)
+    p = K.Params(theta=THETA, degree=DEGREE, leaf_size=LEAF, eps=EPS, kernel=K.STOKESLET,
+                 precision=K.MIXED, mac=mac, target_batch=BATCH)
+    out = torch.empty((N, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(params, o):
+        t = K.kitc_build_tree(xd, params)
+        try:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate(t, xd, o)
+            return t.stats()
+        finally:
+            t.free()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(p, out)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = K.kitc_launch_count()
+    step_ms, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(p, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = K.kitc_launch_count() - l0
+    clk = clocks.stop()
+    barrier(ws)
+    total_ms = reduce_max(sum(step_ms), ws)
+    value = ws * args.steps * N / (total_ms / 1e3)
+
+    # error of the timed result on sampled targets, against the FP64 direct sum on the GPU
+    idx = wl.sample_indices(N, N_SAMPLE, SAMPLE_SEED)
+    yd = xd[torch.from_numpy(idx).to(dev)].contiguous()
+    ref = K.kitc_direct(yd, xd, fd, K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
+    E = rel_l2(ref, out.cpu().numpy()[idx])
+
+    st = stats[-1]
+    ev_ms = float(np.mean([s["ms_evaluate"] for s in stats]))
+    flops = FLOPS_PER_INTERACTION * (st["near_pairs"] + st["far_points"])
+    achieved = flops / (ev_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
+            "config": config(args.mac, "mixed"), "E": E,
+            "stage_ms": {k: float(np.mean([s[k] for s in stats]))
+                         for k in ("ms_tree", "ms_weights", "ms_lists", "ms_evaluate")},
+            "interactions_per_target": {"near": st["near_pairs"] / N, "far": st["far_points"] / N},
+            "roofline": {"kernel": "k_eval<Stokeslet, mixed> (fused near/far evaluator)",
+                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz "
+                                        "(unit counts and maximum SM clock; no measured FP32 peak)",
+                         "flops_per_interaction": FLOPS_PER_INTERACTION,
+                         "launch_ms": ev_ms, "traffic": traffic_per_launch()},
+            "gpu_launches": int(launches), "clocks": clk}
+
+    if rank == 0 and ws == 1 and not args.no_fp64:
+        pf = K.Params(theta=THETA, degree=DEGREE, leaf_size=LEAF, eps=EPS, precision=K.FP64,
+                      mac=mac, target_batch=BATCH)
+        out64 = torch.empty_like(out)
+        step(pf, out64)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(pf, out64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        line["plain_fp64"] = {"value": N / (ms64 / 1e3), "unit": "targets/s", "ms_per_step": ms64,
+                              "E": rel_l2(ref, out64.cpu().numpy()[idx])}
+        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+
+    # end to end through the host API: pinned host inputs in, result out, every step
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    fh = torch.from_numpy(f).pin_memory().numpy()
+    oh = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+    K.kitc_solve_host(xh, fh, p, out=oh)
+    ke = max(1, min(args.steps, 3))
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        K.kitc_solve_host(xh, fh, p, out=oh)
+    e2e_s = reduce_max(time.perf_counter() - t0, ws)
+    line["e2e"] = {"value": ws * ke * N / e2e_s, "unit": "targets/s",
+                   "h2d_bytes_per_step": int(x.nbytes + f.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(x, f, 2000, 1234)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_kitc(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

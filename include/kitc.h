@@ -175,6 +175,9 @@ int kitc_kernel_wout(int kernel);
  * KITC_ERR_TIMEOUT.  Returns the previous value. */
 int kitc_set_wait_limit_ms(int ms);
 
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t kitc_launch_count(void);
+
 /* Failure-detection self test: launches one CTA whose thread waits, with the
  * same bounded wait the evaluator uses, on a shared-memory barrier that
  * nothing completes.  Returns KITC_ERR_TIMEOUT once limit_ms (1..10000) has

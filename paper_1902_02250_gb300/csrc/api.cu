@@ -8,7 +8,13 @@
 
 #include "common.cuh"
 
+#include <atomic>
+
 int g_wait_limit_ms = 2000;
+
+static std::atomic<int64_t> g_launches{0};
+
+void kitc_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct kitc_tree_s {
     kitc_params p{};
@@ -522,6 +528,8 @@ void kitc_free_tree(kitc_tree t)
 {
     if (t) free_handle(t);
 }
+
+int64_t kitc_launch_count(void) { return g_launches.load(); }
 
 kitc_status kitc_watchdog_selftest(int limit_ms, void *stream)
 {

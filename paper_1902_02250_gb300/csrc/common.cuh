@@ -171,6 +171,9 @@ struct EvalArgs {
 
 kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s);
 
+// Counts one kernel launch of this library (see kitc_launch_count).
+void kitc_count_launch();
+
 kitc_status watchdog_launch(unsigned long long limit_ns, int *err, cudaStream_t s);
 
 extern int g_wait_limit_ms;

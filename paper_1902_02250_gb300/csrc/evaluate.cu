@@ -595,6 +595,7 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
     if (occ < 1) return KITC_ERR_CUDA;
     int64_t grid = std::min<int64_t>(a.nb, (int64_t)sms * occ);
     if (grid < 1) return KITC_OK;
+    kitc_count_launch();
     k_eval<K, MIXED><<<(unsigned)grid, NTH, smem, s>>>(a);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
@@ -616,6 +617,7 @@ __global__ void k_watchdog(unsigned long long limit_ns, int *err)
 
 kitc_status watchdog_launch(unsigned long long limit_ns, int *err, cudaStream_t s)
 {
+    kitc_count_launch();
     k_watchdog<<<1, 32, 0, s>>>(limit_ns, err);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;

@@ -200,6 +200,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     KITC_CUDA(cudaMemsetAsync(tot, 0, sizeof(int64_t) * 8, s));
     int *err = reinterpret_cast<int *>(tot + 6);
     unsigned grid = (unsigned)((nb + LW - 1) / LW);
+    kitc_count_launch();
     k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
@@ -207,7 +208,9 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
                                         L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
                                         nullptr, nullptr, nullptr, err);
     KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
     k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>(), nb, L.far_off.as<int64_t>(), tot + 2);
+    kitc_count_launch();
     k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>() + nb, nb, L.near_off.as<int64_t>(), tot + 3);
     KITC_CUDA(cudaGetLastError());
     int64_t *h = nullptr;
@@ -223,6 +226,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     KITC_TRY(L.far_mask.reserve(sizeof(uint64_t) * (L.nfar + 1), s));
     KITC_TRY(L.near_id.reserve(sizeof(int32_t) * (L.nnear + 1), s));
     KITC_TRY(L.near_mask.reserve(sizeof(uint64_t) * (L.nnear + 1), s));
+    kitc_count_launch();
     k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),

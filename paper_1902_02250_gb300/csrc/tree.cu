@@ -384,9 +384,11 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
     KITC_TRY(part.reserve(sizeof(double) * 6 * nblk, s));
     KITC_TRY(bcount.reserve(sizeof(int32_t) * 8 * nblk, s));
     KITC_TRY(grow_clusters(t, 64, s));
+    kitc_count_launch();
     k_init<<<nblk, BT, 0, s>>>(xyz, n, t.xs.as<double>(), t.perm.as<int32_t>(),
                                node.as<int32_t>(), part.as<double>());
     KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
     k_root<<<1, 32, 0, s>>>(part.as<double>(), nblk, n, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
                             t.begin.as<int32_t>(), t.end.as<int32_t>(),
                             t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
@@ -412,17 +414,21 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
             st = KITC_ERR_CUDA;
             break;
         }
+        kitc_count_launch();
         k_split<<<(nl + 255) / 256, 256, 0, s>>>(lb, nl, leaf, t.lo.as<dvec4>(),
                                                 t.hi.as<dvec4>(), t.begin.as<int32_t>(),
                                                 t.end.as<int32_t>(), t.level.as<int32_t>(), info);
+        kitc_count_launch();
         k_count<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), node.as<int32_t>(), info, ccount,
                                     bcount.as<int32_t>(), nblk);
+        kitc_count_launch();
         k_children<<<1, BT, 0, s>>>(lb, nl, nclus, info, ccount, cprefix, childoff, childidx,
                                     bcount.as<int32_t>(), nblk, nchs, t.lo.as<dvec4>(),
                                     t.hi.as<dvec4>(), t.begin.as<int32_t>(),
                                     t.end.as<int32_t>(), t.first_child.as<int32_t>(),
                                     t.n_child.as<int32_t>(), t.level.as<int32_t>(),
                                     t.parent.as<int32_t>(), out2);
+        kitc_count_launch();
         k_scatter<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), t.perm.as<int32_t>(),
                                       node.as<int32_t>(), info, t.begin.as<int32_t>(), cprefix,
                                       childoff, childidx, bcount.as<int32_t>(), nblk,
@@ -452,6 +458,7 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
     t.depth = depth;
     t.nleaves = nleaves;
     KITC_TRY(t.ctr.reserve(sizeof(dvec4) * t.cap, s));
+    kitc_count_launch();
     k_geometry<<<(nclus + 255) / 256, 256, 0, s>>>(nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
                                                    t.ctr.as<dvec4>());
     KITC_CUDA(cudaGetLastError());

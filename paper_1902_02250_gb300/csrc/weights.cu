@@ -277,10 +277,12 @@ kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int
                                    (int)smem));
     int npass = (pwin + ACC * WT - 1) / (ACC * WT);
     dim3 grid((unsigned)nitems, (unsigned)npass);
+    kitc_count_launch();
     k_weights_chunk<<<grid, WT, smem, s>>>(make_cheb(degree), d_items, t.n, t.xs.as<double>(),
                                            t.perm.as<int32_t>(), w_user, win, t.lo.as<dvec4>(),
                                            t.hi.as<dvec4>(), sb, wd.partial.as<double>());
     KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
     k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
                                              wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
@@ -296,8 +298,10 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
     KITC_TRY(wd.proxy.reserve((size_t)proxy_record_bytes(wd.win, mixed) * nrec, s));
     unsigned g = (unsigned)((nrec + 255) / 256);
     if (mixed)
+        kitc_count_launch();
         k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
     else
+        kitc_count_launch();
         k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
@@ -311,8 +315,10 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
     const double *xs = t ? t->xs.as<double>() : nullptr;
     const int32_t *perm = t ? t->perm.as<int32_t>() : nullptr;
     if (mixed)
+        kitc_count_launch();
         k_pack_sources<true><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
     else
+        kitc_count_launch();
         k_pack_sources<false><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;

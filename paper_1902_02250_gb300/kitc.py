@@ -70,7 +70,8 @@ _lib = None
 SYMBOLS = ["kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
-           "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest"]
+           "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
+           "kitc_launch_count"]
 
 
 def library_path():
@@ -104,6 +105,8 @@ def lib():
         L.kitc_kernel_wout.argtypes = [I]
         L.kitc_set_wait_limit_ms.argtypes = [I]
         L.kitc_watchdog_selftest.argtypes = [I, P]
+        L.kitc_launch_count.argtypes = []
+        L.kitc_launch_count.restype = I64
         for name in ("kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest"):
@@ -146,6 +149,11 @@ def kernel_wout(kernel):
 
 def set_wait_limit_ms(ms):
     return lib().kitc_set_wait_limit_ms(int(ms))
+
+
+def kitc_launch_count():
+    """Kernels launched by libkitc in this process so far."""
+    return lib().kitc_launch_count()
 
 
 def kitc_watchdog_selftest(limit_ms=50, stream=None):
