@@ -297,11 +297,10 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
     int64_t nrec = (int64_t)t.nclus * np * np * np;
     KITC_TRY(wd.proxy.reserve((size_t)proxy_record_bytes(wd.win, mixed) * nrec, s));
     unsigned g = (unsigned)((nrec + 255) / 256);
+    kitc_count_launch();
     if (mixed)
-        kitc_count_launch();
         k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
     else
-        kitc_count_launch();
         k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
@@ -314,11 +313,10 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
     unsigned g = (unsigned)((n + 255) / 256);
     const double *xs = t ? t->xs.as<double>() : nullptr;
     const int32_t *perm = t ? t->perm.as<int32_t>() : nullptr;
+    kitc_count_launch();
     if (mixed)
-        kitc_count_launch();
         k_pack_sources<true><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
     else
-        kitc_count_launch();
         k_pack_sources<false><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
