@@ -71,6 +71,15 @@ typedef enum { KITC_FP64 = 0, KITC_MIXED = 1 } kitc_precision;
  * batch; every accepted C then also passes Eq. MAC for each target. */
 typedef enum { KITC_MAC_PARTICLE = 0, KITC_MAC_BATCH = 1 } kitc_mac;
 
+/* How the modified weights of Eq. modified_weights are formed.  Both give the
+ * same values up to rounding.  KITC_WEIGHTS_ALGORITHM1 runs Algorithm 1 on
+ * every cluster from its particles.  KITC_WEIGHTS_UPWARD runs Algorithm 1 on
+ * the leaves only and forms each parent from its children's weights through
+ * the parent's barycentric basis at the children's Chebyshev points (exact,
+ * Sec. 2: the parent's Lagrange polynomials have degree n); it falls back to
+ * Algorithm 1 when (n+1)^3 w_in is too large for its shared-memory buffers. */
+typedef enum { KITC_WEIGHTS_UPWARD = 0, KITC_WEIGHTS_ALGORITHM1 = 1 } kitc_weights_mode;
+
 typedef struct {
     double theta;      /* MAC parameter of Eq. MAC, >= 0 (0: direct sum through the tree) */
     int degree;        /* interpolation degree n, 1..16; (n+1)^3 grid points per cluster  */
@@ -83,6 +92,7 @@ typedef struct {
     int target_batch;  /* targets per batch, 1..64 (0 = 64).  Targets are ordered by the
                           Sec. 6 tree built on them with leaf size target_batch; batch b
                           is the slots [b*B, (b+1)*B) of that order                      */
+    int weights;       /* kitc_weights_mode                                               */
 } kitc_params;
 
 typedef struct kitc_tree_s *kitc_tree; /* opaque; owned by the library */

@@ -183,6 +183,7 @@ void or_kernel_apply(int kernel, double eps, const double *x, const double *y,
         return;
     }
     double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 + eps * eps == 0.0) return; /* eps = 0, x = y: singular, omitted (Sec. 1) */
     double H[5];
     or_mrs_functions(r2, eps, H);
     if (kernel == OR_STOKESLET || kernel == OR_STOKESLET_ROTLET) {
@@ -612,7 +613,9 @@ int64_t or_num_batches(int64_t nt, int batch)
 }
 
 /* Batch-MAC treecode.  Outputs (each may be NULL):
- *   out        nt x wout, user order (skipped when lists_only != 0);
+ *   out        nt x wout, user order (skipped when lists_only != 0); when sel
+ *              is not NULL only the targets i with sel[i] != 0 are summed
+ *              and the other rows are set to zero;
  *   counts[5]  as in or_treecode;
  *   tperm      nt, the target order (tperm[slot] = user index);
  *   nfar, nnear  per batch list lengths;
@@ -622,7 +625,8 @@ int64_t or_num_batches(int64_t nt, int batch)
 void or_treecode_batch(const or_tree *t, const double *x, const double *w,
                        const double *fhat, int n, int kernel, double eps, double theta,
                        const double *tgt, int64_t nt, int batch, int tgt_leaf,
-                       int lists_only, double *out, int64_t *counts, int64_t *tperm,
+                       int lists_only, const unsigned char *sel, double *out,
+                       int64_t *counts, int64_t *tperm,
                        int64_t *nfar, int64_t *nnear, int64_t *far_list, int64_t far_cap,
                        int64_t *near_list, int64_t near_cap)
 {
@@ -668,6 +672,10 @@ void or_treecode_batch(const or_tree *t, const double *x, const double *w,
             for (int64_t p = s0; p < s1; ++p) {
                 int64_t i = tt->perm[p];
                 double u[6] = {0, 0, 0, 0, 0, 0};
+                if (sel && !sel[i]) {
+                    for (int c = 0; c < q.wout; ++c) out[q.wout * i + c] = 0.0;
+                    continue;
+                }
                 for (int64_t m = 0; m < L->nfar; ++m) far_field(&q, L->far[m], tgt + 3 * i, u);
                 for (int64_t m = 0; m < L->nnear; ++m) near_field(&q, L->near[m], tgt + 3 * i, u);
                 for (int c = 0; c < q.wout; ++c) out[q.wout * i + c] = u[c];

@@ -64,7 +64,7 @@ def lib():
         L.or_treecode.argtypes = [P, P, P, P, I, I, D, D, P, I64, P, P]
         L.or_num_batches.argtypes = [I64, I]
         L.or_num_batches.restype = I64
-        L.or_treecode_batch.argtypes = [P, P, P, P, I, I, D, D, P, I64, I, I, I, P, P, P,
+        L.or_treecode_batch.argtypes = [P, P, P, P, I, I, D, D, P, I64, I, I, I, P, P, P, P,
                                         P, P, P, I64, P, I64]
         _lib = L
     return _lib
@@ -214,10 +214,11 @@ class Tree:
         return out, cnt
 
     def treecode_batch(self, w, fhat, n, kernel, eps, theta, tgt, batch, tgt_leaf,
-                       lists=False, evaluate=True):
+                       lists=False, evaluate=True, select=None):
         """Batch-MAC variant (targets grouped by the tree on the targets).
         Returns a dict with out, counts, tperm, nfar, nnear and, when lists,
-        far_list / near_list (concatenated per batch, traversal order)."""
+        far_list / near_list (concatenated per batch, traversal order).
+        select: optional target indices; only those rows of out are summed."""
         w = _f64(w, (self.n, kernel_win(kernel)))
         fhat = _f64(fhat)
         tgt = _f64(tgt, (-1, 3))
@@ -229,16 +230,21 @@ class Tree:
         nfar = np.empty(nb, np.int64)
         nnear = np.empty(nb, np.int64)
         L = lib()
+        sel = None
+        if select is not None:
+            sel = np.zeros(nt, np.uint8)
+            sel[np.asarray(select)] = 1
         L.or_treecode_batch(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
                             float(theta), _p(tgt), nt, batch, tgt_leaf, 0 if evaluate else 1,
-                            _p(out), _p(cnt), _p(tperm), _p(nfar), _p(nnear), None, 0, None, 0)
+                            _p(sel), _p(out), _p(cnt), _p(tperm), _p(nfar), _p(nnear), None, 0,
+                            None, 0)
         res = dict(out=out, counts=cnt, tperm=tperm, nfar=nfar, nnear=nnear)
         if lists:
             fl = np.empty(max(1, int(nfar.sum())), np.int64)
             nl = np.empty(max(1, int(nnear.sum())), np.int64)
             L.or_treecode_batch(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
                                 float(theta), _p(tgt), nt, batch, tgt_leaf, 1, None, None, None,
-                                None, None, _p(fl), len(fl), _p(nl), len(nl))
+                                None, None, None, _p(fl), len(fl), _p(nl), len(nl))
             res["far_list"] = fl[:int(nfar.sum())]
             res["near_list"] = nl[:int(nnear.sum())]
         return res

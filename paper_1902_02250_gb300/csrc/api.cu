@@ -120,6 +120,7 @@ bool valid_params(const kitc_params *p)
     if (p->mac != KITC_MAC_PARTICLE && p->mac != KITC_MAC_BATCH) return false;
     if (p->target_batch < 0 || p->target_batch > KITC_MAX_BATCH) return false;
     if (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED) return false;
+    if (p->weights != KITC_WEIGHTS_UPWARD && p->weights != KITC_WEIGHTS_ALGORITHM1) return false;
     return true;
 }
 
@@ -261,7 +262,7 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
     bool mixed = t->p.precision == KITC_MIXED;
     t->has_weights = false;
     record(t, 2, s);
-    KITC_TRY(weights_compute(t->src, w, t->win, t->p.degree, s, t->wts));
+    KITC_TRY(weights_compute(t->src, w, t->win, t->p.degree, t->p.weights, s, t->wts));
     KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
     KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
     record(t, 3, s);

@@ -111,7 +111,7 @@ int source_record_bytes(int win, bool mixed);
 // cos(k pi / n), k = 0..n (Eq. Chebyshev_points), computed on the host.
 void cheb_cos_table(int n, double *t);
 
-kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree,
+kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree, int mode,
                             cudaStream_t s, WeightsDev &wd);
 kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
                          int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out);

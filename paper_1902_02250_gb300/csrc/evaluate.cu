@@ -41,6 +41,7 @@ struct TileMeta {
     int kind, flags, batch, id;
     int a, b;        // far: k1 planes [a, b); near: source slots [a, b)
     uint64_t mask;   // targets of the batch that use this entry
+    dvec4 lo, hi;    // far: the cluster's box (read ahead by the producer)
 };
 
 // ---------------------------------------------------------------------------
@@ -126,16 +127,25 @@ template <> struct KT<KITC_ROTLET> { static constexpr int WIN = 3, WOUT = 6; };
 template <> struct KT<KITC_STOKESLET_ROTLET> { static constexpr int WIN = 6, WOUT = 6; };
 template <> struct KT<KITC_TEST_POLY> { static constexpr int WIN = 3, WOUT = 3; };
 
-template <typename R> __device__ __forceinline__ R rsq(R v);
-template <> __device__ __forceinline__ float rsq<float>(float v) { return v > 0.f ? rsqrtf(v) : 0.f; }
-template <> __device__ __forceinline__ double rsq<double>(double v) { return v > 0.0 ? rsqrt(v) : 0.0; }
+// 1/sqrt(v); with EPS0 (eps = 0) a coincident pair (v = 0) gives 0, otherwise
+// v >= eps^2 > 0 and no guard is needed.
+template <bool EPS0> __device__ __forceinline__ float rsq(float v)
+{
+    if constexpr (EPS0) return v > 0.f ? rsqrtf(v) : 0.f;
+    else return rsqrtf(v);
+}
+template <bool EPS0> __device__ __forceinline__ double rsq(double v)
+{
+    if constexpr (EPS0) return v > 0.0 ? rsqrt(v) : 0.0;
+    else return rsqrt(v);
+}
 
 // u += k(x, y) f for one pair, given d = x - y and r2 = |d|^2 + eps^2
 // (Eqs. Velocity_1, MRS_2).
-template <int K, typename R>
+template <int K, bool EPS0, typename R>
 __device__ __forceinline__ void pair(R dx, R dy, R dz, const R *f, R e2, R e4, R *u, R r2)
 {
-    R ri = rsq<R>(r2);
+    R ri = rsq<EPS0>(r2);
     R ri2 = ri * ri;
     R ri3 = ri2 * ri;
     if (K == KITC_STOKESLET || K == KITC_STOKESLET_ROTLET) {
@@ -189,7 +199,7 @@ template <bool MIXED, int WIN> struct Rec {
     static constexpr int PROXY = MIXED ? (WIN == 3 ? 16 : 32) : (WIN == 3 ? 32 : 48);
 };
 
-template <int K, bool MIXED> struct Smem {
+template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
     static constexpr size_t META = STAGES * sizeof(TileMeta);
@@ -216,13 +226,33 @@ __device__ __forceinline__ void load_proxy(const unsigned char *p, R *f)
     }
 }
 
+template <bool MIXED, int WIN, typename R>
+__device__ __forceinline__ void load_source(const unsigned char *rec, R *yh, R *yl, R *f)
+{
+    if constexpr (MIXED) {
+        float4 r0 = *reinterpret_cast<const float4 *>(rec);
+        float4 r1 = *reinterpret_cast<const float4 *>(rec + 16);
+        float4 r2 = *reinterpret_cast<const float4 *>(rec + 32);
+        yh[0] = r0.x; yh[1] = r0.y; yh[2] = r0.z;
+        yl[0] = r0.w; yl[1] = r1.x; yl[2] = r1.y;
+        f[0] = r1.z; f[1] = r1.w; f[2] = r2.x;
+        if constexpr (WIN == 6) { f[3] = r2.y; f[4] = r2.z; f[5] = r2.w; }
+    } else {
+        const double *d = reinterpret_cast<const double *>(rec);
+        yh[0] = d[0]; yh[1] = d[1]; yh[2] = d[2];
+        yl[0] = yl[1] = yl[2] = 0.0;
+#pragma unroll
+        for (int q = 0; q < WIN; ++q) f[q] = d[3 + q];
+    }
+}
+
 // CTAs per SM the register budget targets: two for the FP32 Stokeslet (no
 // spills at 96 registers), one for the wider FP64 and rotlet variants.
 template <int K, bool MIXED> struct MinBlocks {
     static constexpr int value = (MIXED && K == KITC_STOKESLET) ? 2 : 1;
 };
 
-template <int K, bool MIXED>
+template <int K, bool MIXED, bool EPS0>
 __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
 {
     constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
@@ -231,11 +261,11 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tiles = smem;
     double *red = reinterpret_cast<double *>(smem + (size_t)STAGES * TILE);
-    TileMeta *meta = reinterpret_cast<TileMeta *>(smem + (size_t)STAGES * TILE + Smem<K, MIXED>::RED);
+    TileMeta *meta = reinterpret_cast<TileMeta *>(smem + (size_t)STAGES * TILE + Smem<K>::RED);
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(meta) +
-                                                  Smem<K, MIXED>::META);
+                                                  Smem<K>::META);
     double *gridc = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bars) +
-                                               Smem<K, MIXED>::BARS);
+                                               Smem<K>::BARS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
     const uint32_t rbw = smem_u32(bars + 2 * STAGES), rbr = smem_u32(bars + 2 * STAGES + 1);
@@ -275,6 +305,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
         };
         const unsigned char *srcb = reinterpret_cast<const unsigned char *>(a.src);
         const unsigned char *pxb = reinterpret_cast<const unsigned char *>(a.proxy);
+        const dvec4 zero4 = make_dvec4(0, 0, 0, 0);
         for (;;) {
             int b = atomicAdd(a.queue, 1);
             if (b >= a.nb) break;
@@ -299,10 +330,11 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                 for (int64_t e = f0; e < f1 && ok; ++e) {
                     int c = a.far_id[e];
                     uint64_t mk = a.far_mask[e];
+                    dvec4 lo = a.clo[c], hi = a.chi[c];
                     for (int k1 = 0; k1 < np && ok; k1 += planes_max) {
                         int k2 = min(np, k1 + planes_max);
                         TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
-                                   b, c, k1, k2, mk};
+                                   b, c, k1, k2, mk, lo, hi};
                         ok = push(m, pxb + ((size_t)c * np2 * np + (size_t)k1 * np2) * PREC,
                                   (uint32_t)((k2 - k1) * np2 * PREC));
                     }
@@ -315,7 +347,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     for (int q = p0; q < p1 && ok; q += near_max) {
                         int q1 = min(p1, q + near_max);
                         TileMeta m{K_NEAR, (q == p0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
-                                   b, c, q, q1, mk};
+                                   b, c, q, q1, mk, zero4, zero4};
                         ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
                     }
                 }
@@ -324,20 +356,20 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                 for (int64_t q = 0; q < p1 && ok; q += near_max) {
                     int64_t q1 = min(p1, q + (int64_t)near_max);
                     TileMeta m{K_NEAR, (q == 0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
-                               b, -1, (int)q, (int)q1, ~0ull};
+                               b, -1, (int)q, (int)q1, ~0ull, zero4, zero4};
                     ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
                 }
             }
             if (!ok) break;
             if (!have) {  // no entries: one empty tile closes the batch
-                pend = TileMeta{K_NEAR, F_FIRST_ENTRY | F_LAST_ENTRY, b, -1, 0, 0, 0ull};
+                pend = TileMeta{K_NEAR, F_FIRST_ENTRY | F_LAST_ENTRY, b, -1, 0, 0, 0ull, zero4, zero4};
                 psrc = nullptr;
                 pbytes = 0;
             }
             pend.flags |= F_LAST_BATCH | (first ? F_FIRST_BATCH : 0);
             if (!(ok = emit(pend, psrc, pbytes))) break;
         }
-        if (ok) ok = emit(TileMeta{K_EXIT, 0, -1, -1, 0, 0, 0ull}, nullptr, 0);
+        if (ok) ok = emit(TileMeta{K_EXIT, 0, -1, -1, 0, 0, 0ull, zero4, zero4}, nullptr, 0);
         if (!ok) atomicExch(a.err, 1);
         // drain: the last phase of every stage this thread armed must complete
         uint32_t last = it;
@@ -347,6 +379,9 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     }
 
     // --------------------------------------------------------------- consumers
+    // Per target: a1 sums one run (a grid row of n+1 points or a block of <= 8
+    // sources) and is added to a2 only if the target uses the entry; a2 holds
+    // <= 8 runs, a3 <= 8 a2's, and every 64 runs a3 goes into the FP64 sum.
     const R e2 = (R)(a.eps * a.eps), e4 = (R)(a.eps * a.eps * a.eps * a.eps);
     R X[2][3], XL[2][3], XO[2][3];
     double acc[2][WOUT];
@@ -356,38 +391,44 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     double xd[2][3];
     R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
     uint32_t it = 0, nbd = 0;
-    bool t_ok[2] = {false, false};
     int64_t bslot = 0;
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0, a1[t][c] = a2[t][c] = a3[t][c] = R(0);
 
-    auto flush3 = [&](uint64_t mask) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            bool use = (mask >> (lane + 32 * t)) & 1ull;
-#pragma unroll
-            for (int c = 0; c < WOUT; ++c) {
-                acc[t][c] += use ? (double)a3[t][c] : 0.0;
-                a3[t][c] = R(0);
-            }
-        }
-    };
-    auto step = [&](uint64_t mask) {  // end of a run of <= 8 (near) or n+1 (far) terms
+    auto to_fp64 = [&]() {
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
-            for (int c = 0; c < WOUT; ++c) a2[t][c] += a1[t][c], a1[t][c] = R(0);
-        if (++c2 == 8) {
-            c2 = 0;
+            for (int c = 0; c < WOUT; ++c) {
+                acc[t][c] += (double)(a3[t][c] + a2[t][c]);
+                a2[t][c] = a3[t][c] = R(0);
+            }
+        c2 = c3 = 0;
+    };
+    auto step = [&](bool u0, bool u1) {
+        if constexpr (MIXED) {
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int c = 0; c < WOUT; ++c) {
+                a2[0][c] += u0 ? a1[0][c] : R(0);
+                a2[1][c] += u1 ? a1[1][c] : R(0);
+                a1[0][c] = a1[1][c] = R(0);
+            }
+            if (++c2 == 8) {
+                c2 = 0;
 #pragma unroll
-                for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
-            if (++c3 == 8) {
-                c3 = 0;
-                flush3(mask);
+                for (int t = 0; t < 2; ++t)
+#pragma unroll
+                    for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
+                if (++c3 == 8) to_fp64();
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < WOUT; ++c) {
+                acc[0][c] += u0 ? a1[0][c] : 0.0;
+                acc[1][c] += u1 ? a1[1][c] : 0.0;
+                a1[0][c] = a1[1][c] = 0.0;
             }
         }
     };
@@ -398,18 +439,20 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
             atomicExch(a.err, 1);
             break;
         }
-        const TileMeta m = meta[s];
-        if (m.kind == K_EXIT) break;
+        const TileMeta &mr = meta[s];
+        const int kind = mr.kind, flags = mr.flags, batch = mr.batch, ta = mr.a, tb = mr.b;
+        const uint64_t mask = mr.mask;
+        if (kind == K_EXIT) break;
         const unsigned char *tile = tiles + (size_t)s * TILE;
-        if (m.flags & F_FIRST_BATCH) {
-            bslot = (int64_t)m.batch * a.batch;
-            if (MIXED && a.bctr) cB = a.bctr[m.batch];
+        const bool u0 = (mask >> lane) & 1ull, u1 = (mask >> (lane + 32)) & 1ull;
+        if (flags & F_FIRST_BATCH) {
+            bslot = (int64_t)batch * a.batch;
+            if (MIXED && a.bctr) cB = a.bctr[batch];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 int i = lane + 32 * t;
                 int64_t slot = bslot + i;
-                t_ok[t] = i < a.batch && slot < a.nt;
-                int64_t sl = t_ok[t] ? slot : bslot;
+                int64_t sl = (i < a.batch && slot < a.nt) ? slot : bslot;
                 xd[t][0] = a.tx[sl * a.tstride];
                 xd[t][1] = a.ty[sl * a.tstride];
                 xd[t][2] = a.tz[sl * a.tstride];
@@ -431,26 +474,24 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                 for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0;
             }
         }
-        if (m.flags & F_FIRST_ENTRY) {
-            c2 = c3 = 0;
-            if (m.kind == K_FAR) {
+        if (kind == K_FAR) {
+            if (flags & F_FIRST_ENTRY) {
+                // mapped Chebyshev points of the cluster (Sec. 3 interval map);
+                // FP32 runs take them relative to the batch centre
                 for (int q = lane; q < 3 * np; q += 32) {
                     int l = q / np, k = q % np;
-                    dvec4 lo = a.clo[m.id], hi = a.chi[m.id];
-                    double lo_l = l == 0 ? lo.x : (l == 1 ? lo.y : lo.z);
-                    double hi_l = l == 0 ? hi.x : (l == 1 ? hi.y : hi.z);
+                    double lo_l = l == 0 ? mr.lo.x : (l == 1 ? mr.lo.y : mr.lo.z);
+                    double hi_l = l == 0 ? mr.hi.x : (l == 1 ? mr.hi.y : mr.hi.z);
                     double sk = 0.5 * ((lo_l + hi_l) + a.cheb[k] * (hi_l - lo_l));
                     double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
                     gs[l * (KITC_MAX_DEGREE + 1) + k] = MIXED ? (R)(sk - cb_l) : (R)sk;
                 }
                 __syncwarp();
             }
-        }
-        if (m.kind == K_FAR) {
             const R *gx = gs, *gy = gs + (KITC_MAX_DEGREE + 1), *gz = gs + 2 * (KITC_MAX_DEGREE + 1);
-            const int rows = (m.b - m.a) * np;
+            const int rows = (tb - ta) * np;
             for (int r = warp; r < rows; r += NCW) {
-                const int k1 = m.a + r / np, k2 = r % np;
+                const int k1 = ta + r / np, k2 = r % np;
                 const unsigned char *row = tile + (size_t)r * np * PREC;
                 R dx[2], dy[2], rxy[2];
 #pragma unroll
@@ -459,87 +500,69 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     dy[t] = XO[t][1] - gy[k2];
                     rxy[t] = fma(dx[t], dx[t], fma(dy[t], dy[t], e2));
                 }
+#pragma unroll 3
                 for (int k3 = 0; k3 < np; ++k3) {
                     R f[WIN];
                     load_proxy<MIXED, WIN, R>(row + (size_t)k3 * PREC, f);
+                    const R gzk = gz[k3];
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
-                        R dz = XO[t][2] - gz[k3];
-                        R r2 = fma(dz, dz, rxy[t]);
                         if constexpr (K == KITC_TEST_POLY) {
-                            pair_poly(xd[t], (double)gx[k1], (double)gy[k2], (double)gz[k3],
-                                      reinterpret_cast<const double *>(f), reinterpret_cast<double *>(a1[t]));
+                            pair_poly(xd[t], (double)gx[k1], (double)gy[k2], (double)gzk,
+                                      reinterpret_cast<const double *>(f),
+                                      reinterpret_cast<double *>(a1[t]));
                         } else {
-                            pair<K, R>(dx[t], dy[t], dz, f, e2, e4, a1[t], r2);
+                            R dz = XO[t][2] - gzk;
+                            R r2 = fma(dz, dz, rxy[t]);
+                            pair<K, EPS0, R>(dx[t], dy[t], dz, f, e2, e4, a1[t], r2);
                         }
                     }
                 }
-                step(m.mask);
+                step(u0, u1);
             }
         } else {
-            const int cnt = m.b - m.a;
-            const int nb8 = (cnt + 7) >> 3;
-            for (int blk = warp; blk < nb8; blk += NCW) {
+            const int cnt = tb - ta;
+            const int nb8 = (cnt + 7) >> 3, nfull = cnt >> 3;
+            auto body = [&](int idx) {
+                R f[WIN], yh[3], yl[3];
+                load_source<MIXED, WIN, R>(tile + (size_t)idx * SREC, yh, yl, f);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    int idx = blk * 8 + j;
-                    if (idx < cnt) {
-                        const unsigned char *rec = tile + (size_t)idx * SREC;
-                        R f[WIN];
-                        R yh[3], yl[3];
+                for (int t = 0; t < 2; ++t) {
+                    if constexpr (K == KITC_TEST_POLY) {
+                        pair_poly(xd[t], (double)yh[0], (double)yh[1], (double)yh[2],
+                                  reinterpret_cast<const double *>(f),
+                                  reinterpret_cast<double *>(a1[t]));
+                    } else {
+                        R dx, dy, dz;
                         if constexpr (MIXED) {
-                            float4 r0 = *reinterpret_cast<const float4 *>(rec);
-                            float4 r1 = *reinterpret_cast<const float4 *>(rec + 16);
-                            float4 r2 = *reinterpret_cast<const float4 *>(rec + 32);
-                            yh[0] = r0.x; yh[1] = r0.y; yh[2] = r0.z;
-                            yl[0] = r0.w; yl[1] = r1.x; yl[2] = r1.y;
-                            f[0] = r1.z; f[1] = r1.w; f[2] = r2.x;
-                            if constexpr (WIN == 6) { f[3] = r2.y; f[4] = r2.z; f[5] = r2.w; }
+                            dx = (X[t][0] - yh[0]) + (XL[t][0] - yl[0]);
+                            dy = (X[t][1] - yh[1]) + (XL[t][1] - yl[1]);
+                            dz = (X[t][2] - yh[2]) + (XL[t][2] - yl[2]);
                         } else {
-                            const double *d = reinterpret_cast<const double *>(rec);
-                            yh[0] = d[0]; yh[1] = d[1]; yh[2] = d[2];
-                            yl[0] = yl[1] = yl[2] = 0.0;
-#pragma unroll
-                            for (int q = 0; q < WIN; ++q) f[q] = d[3 + q];
+                            dx = X[t][0] - yh[0];
+                            dy = X[t][1] - yh[1];
+                            dz = X[t][2] - yh[2];
                         }
-#pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            if constexpr (K == KITC_TEST_POLY) {
-                                pair_poly(xd[t], (double)yh[0], (double)yh[1], (double)yh[2],
-                                          reinterpret_cast<const double *>(f),
-                                          reinterpret_cast<double *>(a1[t]));
-                            } else {
-                                R dx, dy, dz;
-                                if constexpr (MIXED) {
-                                    dx = (X[t][0] - yh[0]) + (XL[t][0] - yl[0]);
-                                    dy = (X[t][1] - yh[1]) + (XL[t][1] - yl[1]);
-                                    dz = (X[t][2] - yh[2]) + (XL[t][2] - yl[2]);
-                                } else {
-                                    dx = X[t][0] - yh[0];
-                                    dy = X[t][1] - yh[1];
-                                    dz = X[t][2] - yh[2];
-                                }
-                                R r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
-                                pair<K, R>(dx, dy, dz, f, e2, e4, a1[t], r2);
-                            }
-                        }
+                        R r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
+                        pair<K, EPS0, R>(dx, dy, dz, f, e2, e4, a1[t], r2);
                     }
                 }
-                step(m.mask);
+            };
+            for (int blk = warp; blk < nb8; blk += NCW) {
+                if (blk < nfull) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) body(blk * 8 + j);
+                } else {
+                    for (int idx = blk * 8; idx < cnt; ++idx) body(idx);
+                }
+                step(u0, u1);
             }
-        }
-        if (m.flags & F_LAST_ENTRY) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-#pragma unroll
-                for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
-            flush3(m.mask);
-            c2 = c3 = 0;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty0 + 8 * s);
         ++it;
-        if (m.flags & F_LAST_BATCH) {
+        if (flags & F_LAST_BATCH) {
+            if constexpr (MIXED) to_fp64();
             // cross-warp sum: write partials, wait for all warps, add, write out
             if (!mbar_wait(rbr, (nbd & 1u) ^ 1u, wait_ns)) { atomicExch(a.err, 1); break; }
 #pragma unroll
@@ -569,38 +592,6 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     }
 }
 
-template <int K, bool MIXED>
-kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
-{
-    constexpr int WIN = KT<K>::WIN;
-    int np = a.degree + 1;
-    if ((size_t)np * np * Rec<MIXED, WIN>::PROXY > (size_t)TILE) return KITC_ERR_INVALID_ARG;
-    // bulk copies need 16-byte aligned sources; records are multiples of 16 bytes
-    if ((reinterpret_cast<uintptr_t>(a.src) & 15u) || (reinterpret_cast<uintptr_t>(a.proxy) & 15u))
-        return KITC_ERR_INVALID_ARG;
-    if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
-        return KITC_ERR_INVALID_ARG;
-    size_t smem = Smem<K, MIXED>::TOTAL;
-    static int configured[64] = {0};
-    int dev = 0;
-    KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !configured[dev]) {
-        KITC_CUDA(cudaFuncSetAttribute(k_eval<K, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-        configured[dev] = 1;
-    }
-    int sms = 0, occ = 0;
-    KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    KITC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<K, MIXED>, NTH, smem));
-    if (occ < 1) return KITC_ERR_CUDA;
-    int64_t grid = std::min<int64_t>(a.nb, (int64_t)sms * occ);
-    if (grid < 1) return KITC_OK;
-    kitc_count_launch();
-    k_eval<K, MIXED><<<(unsigned)grid, NTH, smem, s>>>(a);
-    KITC_CUDA(cudaGetLastError());
-    return KITC_OK;
-}
-
 // One thread waits on a barrier that is never completed; the bounded wait
 // gives up after limit_ns and records the time-out.
 __global__ void k_watchdog(unsigned long long limit_ns, int *err)
@@ -611,6 +602,44 @@ __global__ void k_watchdog(unsigned long long limit_ns, int *err)
     mbar_init(b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!mbar_wait(b, 0, limit_ns)) atomicExch(err, 1);
+}
+
+template <int K, bool MIXED, bool EPS0>
+kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
+{
+    constexpr int WIN = KT<K>::WIN;
+    int np = a.degree + 1;
+    if ((size_t)np * np * Rec<MIXED, WIN>::PROXY > (size_t)TILE) return KITC_ERR_INVALID_ARG;
+    // bulk copies need 16-byte aligned sources; records are multiples of 16 bytes
+    if ((reinterpret_cast<uintptr_t>(a.src) & 15u) || (reinterpret_cast<uintptr_t>(a.proxy) & 15u))
+        return KITC_ERR_INVALID_ARG;
+    if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
+        return KITC_ERR_INVALID_ARG;
+    size_t smem = Smem<K>::TOTAL;
+    static int configured[64] = {0};
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !configured[dev]) {
+        KITC_CUDA(cudaFuncSetAttribute(k_eval<K, MIXED, EPS0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured[dev] = 1;
+    }
+    int sms = 0, occ = 0;
+    KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    KITC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<K, MIXED, EPS0>, NTH, smem));
+    if (occ < 1) return KITC_ERR_CUDA;
+    int64_t grid = std::min<int64_t>(a.nb, (int64_t)sms * occ);
+    if (grid < 1) return KITC_OK;
+    kitc_count_launch();
+    k_eval<K, MIXED, EPS0><<<(unsigned)grid, NTH, smem, s>>>(a);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+template <int K, bool MIXED>
+kitc_status launch_eps(const EvalArgs &a, cudaStream_t s)
+{
+    return a.eps == 0.0 ? launch_k<K, MIXED, true>(a, s) : launch_k<K, MIXED, false>(a, s);
 }
 
 }  // namespace
@@ -627,15 +656,15 @@ kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStrea
 {
     switch (kernel) {
     case KITC_STOKESLET:
-        return mixed ? launch_k<KITC_STOKESLET, true>(a, s) : launch_k<KITC_STOKESLET, false>(a, s);
+        return mixed ? launch_eps<KITC_STOKESLET, true>(a, s) : launch_eps<KITC_STOKESLET, false>(a, s);
     case KITC_ROTLET:
-        return mixed ? launch_k<KITC_ROTLET, true>(a, s) : launch_k<KITC_ROTLET, false>(a, s);
+        return mixed ? launch_eps<KITC_ROTLET, true>(a, s) : launch_eps<KITC_ROTLET, false>(a, s);
     case KITC_STOKESLET_ROTLET:
-        return mixed ? launch_k<KITC_STOKESLET_ROTLET, true>(a, s)
-                     : launch_k<KITC_STOKESLET_ROTLET, false>(a, s);
+        return mixed ? launch_eps<KITC_STOKESLET_ROTLET, true>(a, s)
+                     : launch_eps<KITC_STOKESLET_ROTLET, false>(a, s);
     case KITC_TEST_POLY:
         if (mixed) return KITC_ERR_INVALID_ARG;
-        return launch_k<KITC_TEST_POLY, false>(a, s);
+        return launch_k<KITC_TEST_POLY, false, false>(a, s);
     default:
         return KITC_ERR_INVALID_ARG;
     }

@@ -174,27 +174,35 @@ __global__ void k_count(int64_t n, int lb, int nl, const double *__restrict__ xs
     }
 }
 
-// In-place exclusive scan of a[0], a[stride], ... a[(m-1)*stride] by one block.
+// In-place exclusive scan of a[0], a[stride], ... a[(m-1)*stride] by one block
+// (each thread scans a contiguous segment; the segment sums are scanned with
+// warp shuffles).
 __device__ void block_scan_strided(int32_t *a, int m, int stride, int *tot_out)
 {
-    __shared__ int32_t sums[BT];
+    __shared__ int32_t wsum[BT / 32];
     int per = (m + blockDim.x - 1) / blockDim.x;
     int b = threadIdx.x * per, e = min(m, b + per);
     int32_t s = 0;
     for (int i = b; i < e; ++i) s += a[(int64_t)i * stride];
-    sums[threadIdx.x] = s;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t run = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i) {
-            int32_t v = sums[i];
-            sums[i] = run;
-            run += v;
+    if (w == 0) {
+        int32_t v = lane < (int)(blockDim.x / 32) ? wsum[lane] : 0, x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
         }
-        if (tot_out) *tot_out = run;
+        if (lane < (int)(blockDim.x / 32)) wsum[lane] = x - v;
+        if (lane == 31 && tot_out) *tot_out = x;
     }
     __syncthreads();
-    int32_t run = sums[threadIdx.x];
+    int32_t run = wsum[w] + incl - s;
     for (int i = b; i < e; ++i) {
         int32_t v = a[(int64_t)i * stride];
         a[(int64_t)i * stride] = run;
@@ -227,7 +235,8 @@ __global__ void __launch_bounds__(BT) k_children(
         nchild_scan[i] = nch;
     }
     __syncthreads();
-    __shared__ int total;
+    __shared__ int total, nsplit;
+    if (threadIdx.x == 0) nsplit = 0;
     block_scan_strided(nchild_scan, nl, 1, &total);
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
         int c = lb + i;
@@ -257,11 +266,10 @@ __global__ void __launch_bounds__(BT) k_children(
         }
         first_child[c] = j > 0 ? fc : -1;
         n_child[c] = j;
+        if (j > 0) atomicAdd(&nsplit, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int nsplit = 0;
-        for (int i = 0; i < nl; ++i) nsplit += info[i].mask != 0 && n_child[lb + i] > 0;
         out2[0] = total;
         out2[1] = nsplit;
     }

@@ -24,9 +24,10 @@
 
 namespace {
 
-constexpr int WT = 256;     // threads of the weights kernel
-constexpr int ACC = 16;     // outputs per thread per pass
-constexpr int CHUNK = 2048; // particles per work item
+constexpr int WT = 256;       // threads of the weights kernels
+constexpr int ACC_MAX = 16;   // outputs per thread per pass, at most
+constexpr int CHUNK = 2048;   // particles per work item
+constexpr size_t UP_SMEM_MAX = 200 * 1024;
 
 struct Cheb {
     double t[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
@@ -78,6 +79,7 @@ __device__ void bary_basis(const Cheb &cb, double a, double b, double y, double 
     }
 }
 
+template <int ACC>
 __global__ void __launch_bounds__(WT) k_weights_chunk(
     Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
     const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
@@ -139,12 +141,78 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
     }
 }
 
+// Modified weights of a parent from those of its children.  For a child c the
+// parent's Lagrange polynomials L^P_k, restricted to c's box, are polynomials
+// of degree n in each variable, so interpolating them at c's Chebyshev points
+// reproduces them exactly (Sec. 2).  Summing Eq. modified_weights over the
+// children therefore gives
+//   fhat_P[k1,k2,k3] = sum_c sum_k' L^P_k1(s^c_k1') L^P_k2(s^c_k2') L^P_k3(s^c_k3') fhat_c[k'],
+// three 1D contractions per child instead of (n+1)^3 work per particle.
+__global__ void __launch_bounds__(WT) k_upward(Cheb cb, int lb, const dvec4 *__restrict__ lo,
+                                               const dvec4 *__restrict__ hi,
+                                               const int32_t *__restrict__ first_child,
+                                               const int32_t *__restrict__ n_child, int win,
+                                               double *__restrict__ fhat)
+{
+    extern __shared__ double sm[];
+    const int p = lb + blockIdx.x;
+    const int nch = n_child[p];
+    if (nch == 0) return;
+    const int np = cb.n + 1, np2 = np * np, pw = np2 * np * win;
+    double *T1 = sm, *T2 = T1 + pw, *A = T2 + pw, *M = A + pw;  // M[l][k'][k] = L^P_k(s^c_k')
+    for (int i = threadIdx.x; i < pw; i += WT) A[i] = 0.0;
+    const dvec4 plo = lo[p], phi = hi[p];
+    for (int ci = 0; ci < nch; ++ci) {
+        const int c = first_child[p] + ci;
+        const dvec4 clo = lo[c], chi = hi[c];
+        __syncthreads();
+        for (int q = threadIdx.x; q < 3 * np; q += WT) {
+            int l = q / np, kp = q % np;
+            double ca = l == 0 ? clo.x : (l == 1 ? clo.y : clo.z);
+            double cb_ = l == 0 ? chi.x : (l == 1 ? chi.y : chi.z);
+            double pa = l == 0 ? plo.x : (l == 1 ? plo.y : plo.z);
+            double pb = l == 0 ? phi.x : (l == 1 ? phi.y : phi.z);
+            double y = __dmul_rn(0.5, __dadd_rn(__dadd_rn(ca, cb_), __dmul_rn(cb.t[kp], __dsub_rn(cb_, ca))));
+            double L[KITC_MAX_DEGREE + 1];
+            bary_basis(cb, pa, pb, y, L);
+            for (int k = 0; k < np; ++k) M[(l * np + kp) * np + k] = L[k];
+        }
+        __syncthreads();
+        const double *F = fhat + (size_t)c * pw;
+        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k3
+            int q = o % win, k3 = (o / win) % np, r = o / (win * np);
+            double v = 0.0;
+            for (int kp = 0; kp < np; ++kp) v = fma(M[(2 * np + kp) * np + k3], F[(r * np + kp) * win + q], v);
+            T1[o] = v;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k2
+            int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
+            double v = 0.0;
+            for (int kp = 0; kp < np; ++kp)
+                v = fma(M[(np + kp) * np + k2], T1[((k1 * np + kp) * np + k3) * win + q], v);
+            T2[o] = v;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k1, accumulate over children
+            int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
+            double v = 0.0;
+            for (int kp = 0; kp < np; ++kp)
+                v = fma(M[kp * np + k1], T2[((kp * np + k2) * np + k3) * win + q], v);
+            A[o] += v;
+        }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < pw; o += WT) fhat[(size_t)p * pw + o] = A[o];
+}
+
 // fhat[c] = sum of the partials of c's work items, in item order.
 __global__ void k_weights_reduce(const int32_t *__restrict__ first_item, int pwin,
                                  const double *__restrict__ partial, double *__restrict__ fhat)
 {
     int c = blockIdx.x;
     int i0 = first_item[c], i1 = first_item[c + 1];
+    if (i0 == i1) return;  // computed by the upward pass
     for (int o = threadIdx.x; o < pwin; o += blockDim.x) {
         double s = 0.0;
         for (int i = i0; i < i1; ++i) s += partial[(size_t)i * pwin + o];
@@ -236,22 +304,50 @@ size_t WeightsDev::bytes() const
     return fhat.bytes + proxy.bytes + src.bytes + partial.bytes + items.bytes;
 }
 
-kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree,
+template <int ACC>
+kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
+                          const TreeDev &t, const double *w, int win, int sb, double *partial)
+{
+    KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    kitc_count_launch();
+    k_weights_chunk<ACC><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
+                                                t.perm.as<int32_t>(), w, win, t.lo.as<dvec4>(),
+                                                t.hi.as<dvec4>(), sb, partial);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+using ChunkLauncher = kitc_status (*)(dim3, size_t, cudaStream_t, const Cheb &, const Item *,
+                                      const TreeDev &, const double *, int, int, double *);
+
+size_t upward_smem(int np, int win)
+{
+    size_t pw = (size_t)np * np * np * win;
+    return sizeof(double) * (3 * pw + 3 * (size_t)np * np);
+}
+
+kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree, int mode,
                             cudaStream_t s, WeightsDev &wd)
 {
     const int np = degree + 1;
     const int pwin = np * np * np * win;
-    // work items: chunks of every cluster's slot range, in cluster order
-    std::vector<int32_t> hb(t.nclus), he(t.nclus);
+    const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_smem(np, win) <= UP_SMEM_MAX;
+    // work items: chunks of the slot range of every cluster (of every leaf only,
+    // when the parents come from the upward pass), in cluster order
+    std::vector<int32_t> hb(t.nclus), he(t.nclus), hn(t.nclus);
     KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * t.nclus,
                               cudaMemcpyDeviceToHost, s));
     KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * t.nclus,
+                              cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(hn.data(), t.n_child.ptr, sizeof(int32_t) * t.nclus,
                               cudaMemcpyDeviceToHost, s));
     KITC_CUDA(cudaStreamSynchronize(s));
     std::vector<Item> items;
     std::vector<int32_t> first(t.nclus + 1);
     for (int c = 0; c < t.nclus; ++c) {
         first[c] = (int32_t)items.size();
+        if (upward && hn[c] > 0) continue;
         for (int32_t p = hb[c]; p < he[c]; p += CHUNK)
             items.push_back(Item{c, p, std::min(he[c], p + CHUNK), 0});
     }
@@ -273,19 +369,35 @@ kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int
     int sb = 64;
     while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
     size_t smem = per * sb;
-    KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    int npass = (pwin + ACC * WT - 1) / (ACC * WT);
+    // the fewest accumulators per thread that cover the outputs in one pass
+    int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
+    int npass = (pwin + acc * WT - 1) / (acc * WT);
     dim3 grid((unsigned)nitems, (unsigned)npass);
-    kitc_count_launch();
-    k_weights_chunk<<<grid, WT, smem, s>>>(make_cheb(degree), d_items, t.n, t.xs.as<double>(),
-                                           t.perm.as<int32_t>(), w_user, win, t.lo.as<dvec4>(),
-                                           t.hi.as<dvec4>(), sb, wd.partial.as<double>());
-    KITC_CUDA(cudaGetLastError());
+    const Cheb cb = make_cheb(degree);
+    static constexpr ChunkLauncher table[ACC_MAX] = {
+        &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
+        &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
+        &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
+        &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
+    if (nitems > 0)
+        KITC_TRY(table[acc - 1](grid, smem, s, cb, d_items, t, w_user, win, sb, wd.partial.as<double>()));
     kitc_count_launch();
     k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
                                              wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
+    if (upward) {
+        size_t us = upward_smem(np, win);
+        KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)us));
+        // deepest parents first: level L needs every child at level L + 1
+        for (int L = (int)t.level_start.size() - 2; L >= 0; --L) {
+            int lb = t.level_start[L], le = t.level_start[L + 1];
+            kitc_count_launch();
+            k_upward<<<le - lb, WT, us, s>>>(cb, lb, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                             t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                                             win, wd.fhat.as<double>());
+            KITC_CUDA(cudaGetLastError());
+        }
+    }
     wd.degree = degree;
     wd.win = win;
     return KITC_OK;

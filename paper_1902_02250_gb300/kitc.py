@@ -16,6 +16,7 @@ from . import build as _build
 STOKESLET, ROTLET, STOKESLET_ROTLET, TEST_POLY = 0, 1, 2, 99
 FP64, MIXED = 0, 1
 MAC_PARTICLE, MAC_BATCH = 0, 1
+WEIGHTS_UPWARD, WEIGHTS_ALGORITHM1 = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
            4: "device-side wait timed out", 5: "call out of order"}
@@ -30,7 +31,7 @@ class KitcError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("degree", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("eps", ctypes.c_double), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
-                ("mac", ctypes.c_int), ("target_batch", ctypes.c_int)]
+                ("mac", ctypes.c_int), ("target_batch", ctypes.c_int), ("weights", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
 @dataclasses.dataclass
 class Params:
     """kitc_params: MAC theta (Eq. MAC), degree n, leaf size N0, MRS eps,
-    kernel, precision, MAC mode and targets per batch (<= 64)."""
+    kernel, precision, MAC mode, targets per batch (<= 64) and how the
+    modified weights are formed (upward pass or Algorithm 1 everywhere)."""
     theta: float = 0.7
     degree: int = 8
     leaf_size: int = 2000
@@ -59,11 +61,12 @@ class Params:
     precision: int = FP64
     mac: int = MAC_PARTICLE
     target_batch: int = 64
+    weights: int = WEIGHTS_UPWARD
 
     def c(self):
         return _Params(float(self.theta), int(self.degree), int(self.leaf_size), float(self.eps),
                        int(self.kernel), int(self.precision), int(self.mac),
-                       int(self.target_batch))
+                       int(self.target_batch), int(self.weights))
 
 
 _lib = None

@@ -74,16 +74,21 @@ def test_tree_is_identical(K, orc, case):
 
 
 # ------------------------------------------------------------------ weights
-@pytest.mark.parametrize("n,kernel", [(1, ST), (4, SR), (8, ST), (12, RO)])
-def test_modified_weights_match(K, orc, n, kernel):
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n,kernel", [(1, ST), (4, SR), (8, ST), (12, RO), (16, ST)])
+def test_modified_weights_match(K, orc, n, kernel, mode):
+    # mode 1: Algorithm 1 on every cluster; mode 0: leaves by Algorithm 1,
+    # parents from their children (exact by Sec. 2, so equal up to rounding)
     win = 6 if kernel == SR else 3
     x, f = wl.uniform_cube(12000, 36, win=win)
-    t = K.kitc_build_tree(dev(x), K.Params(leaf_size=300, degree=n, kernel=kernel))
+    t = K.kitc_build_tree(dev(x), K.Params(leaf_size=300, degree=n, kernel=kernel, weights=mode))
     K.kitc_modified_weights(t, dev(f))
     g = t.weights()
     o = orc.Tree(x, 300).modified_weights(f, n)
     scale = np.abs(o).max()
-    assert np.abs(g - o).max() <= 1e-13 * scale
+    err = np.abs(g - o).max() / scale
+    print("weights n=%d mode=%d max rel err %.2e" % (n, mode, err))
+    assert err <= 1e-13
     t.free()
 
 
