@@ -106,6 +106,9 @@ typedef struct {
                                               kernel evaluations that count toward u   */
     int64_t device_bytes;                  /* device memory held by the handle         */
     float ms_tree, ms_weights, ms_lists, ms_evaluate; /* device time of the last calls */
+    int64_t near_exec, far_exec;           /* evaluations the GPU performs: every entry
+                                              is computed for all targets of its batch;
+                                              near_pairs / near_exec is the lane use   */
 } kitc_stats;
 
 /* Sec. 6 tree build.  src_xyz: device, n_src x 3.  Copies the sources into

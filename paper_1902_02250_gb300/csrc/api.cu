@@ -263,8 +263,13 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
     t->has_weights = false;
     record(t, 2, s);
     KITC_TRY(weights_compute(t->src, w, t->win, t->p.degree, t->p.weights, s, t->wts));
-    KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
-    KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
+    if (mixed && t->p.kernel == KITC_STOKESLET) {  // FP32x2 evaluator records
+        KITC_TRY(pack_proxy_pairs(t->src, t->wts, s));
+        KITC_TRY(pack_pairs(&t->src, nullptr, w, t->src.n, s, t->wts.src, t->wts.pbegin));
+    } else {
+        KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
+        KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
+    }
     record(t, 3, s);
     t->has_weights = true;
     t->stage_done[1] = true;
@@ -308,6 +313,7 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
     a.chi = t->src.hi.as<dvec4>();
     a.cbegin = t->src.begin.as<int32_t>();
     a.cend = t->src.end.as<int32_t>();
+    a.pbegin = t->wts.pbegin.as<int32_t>();
     a.out = out;
     fill_eval_common(a, p, t->flags.as<int>());
     KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
@@ -335,8 +341,10 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
     bool mixed = p->precision == KITC_MIXED;
     int win = kitc_kernel_win(p->kernel);
     int B = batch_of(*p);
-    DevBuf rec, flags;
-    kitc_status st = pack_sources(nullptr, src_xyz, w, n_src, win, mixed, s, rec);
+    DevBuf rec, flags, pb;
+    kitc_status st = (mixed && p->kernel == KITC_STOKESLET)
+                         ? pack_pairs(nullptr, src_xyz, w, n_src, s, rec, pb)
+                         : pack_sources(nullptr, src_xyz, w, n_src, win, mixed, s, rec);
     if (st == KITC_OK) st = flags.reserve(4 * sizeof(int), s);
     if (st == KITC_OK) {
         EvalArgs a{};
@@ -360,6 +368,7 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
     }
     rec.release(s);
     flags.release(s);
+    pb.release(s);
     return st;
 }
 
@@ -417,6 +426,8 @@ kitc_status kitc_get_stats(kitc_tree t, kitc_stats *s)
         s->near_entries = t->lists.nnear;
         s->near_pairs = t->lists.near_pairs;
         s->far_points = t->lists.far_points;
+        s->near_exec = t->lists.near_exec;
+        s->far_exec = t->lists.far_exec;
     }
     s->device_bytes = (int64_t)(t->src.bytes() + t->tgt.bytes() + t->wts.bytes() +
                                 t->lists.bytes() + t->flags.bytes);

@@ -99,6 +99,7 @@ struct WeightsDev {
     DevBuf fhat;      // double [nclus][P][win]
     DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
     DevBuf src;       // evaluator records of the sources in tree order
+    DevBuf pbegin;    // int32 [nclus]: first source pair of each leaf (paired records)
     DevBuf partial;   // scratch of the weights pass
     DevBuf items;     // scratch: work items of the weights pass
     void release(cudaStream_t s);
@@ -116,6 +117,11 @@ kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int
 kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
                          int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out);
 kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s);
+// Paired FP32 records of the FP32x2 Stokeslet evaluator; pbegin receives the
+// first pair of every leaf (-1 for other clusters), followed by scratch.
+kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
+                       cudaStream_t s, DevBuf &out, DevBuf &pbegin);
+kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Interaction lists of target batches (Algorithm 2 traversal).
@@ -130,7 +136,7 @@ struct ListsDev {
     DevBuf far_mask, near_mask;  // uint64 [entries]
     DevBuf counts;               // int64 scratch [nb*2] + totals
     DevBuf totals;               // int64 [8]
-    int64_t near_pairs = 0, far_points = 0;
+    int64_t near_pairs = 0, far_points = 0, near_exec = 0, far_exec = 0;
     void release(cudaStream_t s);
     size_t bytes() const;
 };
@@ -160,6 +166,7 @@ struct EvalArgs {
     const void *proxy;           // proxy records [cluster][P]
     const dvec4 *clo, *chi;    // cluster boxes (far field grid points)
     const int32_t *cbegin, *cend;
+    const int32_t *pbegin;       // paired records: first pair of each leaf
     int degree;
     double cheb[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
     double eps;

@@ -28,7 +28,10 @@
 
 namespace {
 
-constexpr int NCW = 8;                 // consumer warps
+#ifndef KITC_NCW
+#define KITC_NCW 8
+#endif
+constexpr int NCW = KITC_NCW;          // consumer warps
 constexpr int NTH = (NCW + 1) * 32;    // plus one producer warp
 constexpr int STAGES = 4;
 constexpr int TILE = 16384;            // bytes per stage
@@ -127,12 +130,19 @@ template <> struct KT<KITC_ROTLET> { static constexpr int WIN = 3, WOUT = 6; };
 template <> struct KT<KITC_STOKESLET_ROTLET> { static constexpr int WIN = 6, WOUT = 6; };
 template <> struct KT<KITC_TEST_POLY> { static constexpr int WIN = 3, WOUT = 3; };
 
-// 1/sqrt(v); with EPS0 (eps = 0) a coincident pair (v = 0) gives 0, otherwise
-// v >= eps^2 > 0 and no guard is needed.
+// 1/sqrt(v) on the MUFU in one instruction (approximate, <= 2 ulp; inputs are
+// never subnormal: v >= eps^2 or a squared distance).  With EPS0 (eps = 0) a
+// coincident pair (v = 0) gives 0, otherwise v > 0 and no guard is needed.
+__device__ __forceinline__ float rsqrt_mufu(float v)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 template <bool EPS0> __device__ __forceinline__ float rsq(float v)
 {
-    if constexpr (EPS0) return v > 0.f ? rsqrtf(v) : 0.f;
-    else return rsqrtf(v);
+    if constexpr (EPS0) return v > 0.f ? rsqrt_mufu(v) : 0.f;
+    else return rsqrt_mufu(v);
 }
 template <bool EPS0> __device__ __forceinline__ double rsq(double v)
 {
@@ -178,6 +188,12 @@ __device__ __forceinline__ void pair(R dx, R dy, R dz, const R *f, R e2, R e4, R
         }
     }
 }
+
+// Packed FP32x2 arithmetic of sm_100+ (one instruction, two FP32 lanes).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 // The test kernel prod_l (1 + x_l y_l / 2)^3 f (FP64 only).
 __device__ __forceinline__ void pair_poly(const double *x, double y0, double y1, double y2,
@@ -248,8 +264,11 @@ __device__ __forceinline__ void load_source(const unsigned char *rec, R *yh, R *
 
 // CTAs per SM the register budget targets: two for the FP32 Stokeslet (no
 // spills at 96 registers), one for the wider FP64 and rotlet variants.
+#ifndef KITC_PAIR_MINB
+#define KITC_PAIR_MINB 2
+#endif
 template <int K, bool MIXED> struct MinBlocks {
-    static constexpr int value = (MIXED && K == KITC_STOKESLET) ? 2 : 1;
+    static constexpr int value = (MIXED && K == KITC_STOKESLET) ? KITC_PAIR_MINB : 1;
 };
 
 template <int K, bool MIXED, bool EPS0>
@@ -257,6 +276,9 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
 {
     constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
     constexpr int SREC = Rec<MIXED, WIN>::SRC, PREC = Rec<MIXED, WIN>::PROXY;
+    // FP32x2 path: paired source records and paired grid points (see pack_pairs)
+    constexpr bool PAIR = MIXED && K == KITC_STOKESLET;
+    constexpr int PAIR_REC = 80;
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tiles = smem;
@@ -280,8 +302,12 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     }
     __syncthreads();
     const int np = a.degree + 1, np2 = np * np;
-    const int near_max = (TILE / SREC) / 8 * 8;
-    const int planes_max = TILE / (np2 * PREC);
+    const int npair = (np + 1) / 2;
+    const int row_bytes = PAIR ? npair * 32 : np * PREC;          // one grid row (k1, k2)
+    const int plane_bytes = np * row_bytes;                       // one k1 plane
+    const int near_unit = PAIR ? PAIR_REC : SREC;                 // one near item
+    const int near_max = PAIR ? (TILE / PAIR_REC) / 4 * 4 : (TILE / SREC) / 8 * 8;
+    const int planes_max = TILE / plane_bytes;
     const unsigned long long wait_ns = a.wait_ns;
 
     // ---------------------------------------------------------------- producer
@@ -335,8 +361,8 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                         int k2 = min(np, k1 + planes_max);
                         TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
                                    b, c, k1, k2, mk, lo, hi};
-                        ok = push(m, pxb + ((size_t)c * np2 * np + (size_t)k1 * np2) * PREC,
-                                  (uint32_t)((k2 - k1) * np2 * PREC));
+                        ok = push(m, pxb + (size_t)c * np * plane_bytes + (size_t)k1 * plane_bytes,
+                                  (uint32_t)((k2 - k1) * plane_bytes));
                     }
                 }
                 int64_t n0 = a.near_off[b], n1 = a.near_off[b + 1];
@@ -344,20 +370,25 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     int c = a.near_id[e];
                     uint64_t mk = a.near_mask[e];
                     int p0 = a.cbegin[c], p1 = a.cend[c];
+                    if (PAIR) {  // items are source pairs
+                        int pc = (p1 - p0 + 1) / 2;
+                        p0 = a.pbegin[c];
+                        p1 = p0 + pc;
+                    }
                     for (int q = p0; q < p1 && ok; q += near_max) {
                         int q1 = min(p1, q + near_max);
                         TileMeta m{K_NEAR, (q == p0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
                                    b, c, q, q1, mk, zero4, zero4};
-                        ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
+                        ok = push(m, srcb + (size_t)q * near_unit, (uint32_t)((q1 - q) * near_unit));
                     }
                 }
             } else {
-                int64_t p1 = a.direct_ns;
+                int64_t p1 = PAIR ? (a.direct_ns + 1) / 2 : a.direct_ns;
                 for (int64_t q = 0; q < p1 && ok; q += near_max) {
                     int64_t q1 = min(p1, q + (int64_t)near_max);
                     TileMeta m{K_NEAR, (q == 0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
                                b, -1, (int)q, (int)q1, ~0ull, zero4, zero4};
-                    ok = push(m, srcb + (size_t)q * SREC, (uint32_t)((q1 - q) * SREC));
+                    ok = push(m, srcb + (size_t)q * near_unit, (uint32_t)((q1 - q) * near_unit));
                 }
             }
             if (!ok) break;
@@ -390,6 +421,9 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     dvec4 cB = make_dvec4(0, 0, 0, 0);
     double xd[2][3];
     R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
+    float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
+    float2 Xh2[2][3], Xl2[2][3];
+    const float2 e22 = bc2((float)(a.eps * a.eps));
     uint32_t it = 0, nbd = 0;
     int64_t bslot = 0;
 #pragma unroll
@@ -472,9 +506,154 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                 }
 #pragma unroll
                 for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0;
+                if constexpr (PAIR) {
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        Xh2[t][l] = bc2(X[t][l]);
+                        Xl2[t][l] = bc2(XL[t][l]);
+                    }
+                }
             }
         }
-        if (kind == K_FAR) {
+        if constexpr (PAIR) {
+            if (kind == K_FAR) {
+                if (flags & F_FIRST_ENTRY) {
+                    // grid points relative to the batch centre: x at gsf[0..], y at
+                    // gsf[18..], -z at gsf[36..] (a missing odd point lies far away)
+                    for (int q = lane; q < 3 * np; q += 32) {
+                        int l = q / np, k = q % np;
+                        double lo_l = l == 0 ? mr.lo.x : (l == 1 ? mr.lo.y : mr.lo.z);
+                        double hi_l = l == 0 ? mr.hi.x : (l == 1 ? mr.hi.y : mr.hi.z);
+                        double sk = 0.5 * ((lo_l + hi_l) + a.cheb[k] * (hi_l - lo_l));
+                        double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
+                        float v = (float)(sk - cb_l);
+                        gsf[18 * l + k] = l == 2 ? -v : v;
+                    }
+                    if (lane == 0 && (np & 1)) gsf[36 + np] = -1e18f;
+                    __syncwarp();
+                }
+                const int rows = (tb - ta) * np;
+                // rows of the tile, split over the warps; the loop over the point
+                // pairs of a row is unrolled for each (n+1)/2 so that the pairs'
+                // z coordinates stay in registers for the whole tile
+                auto far_rows = [&](auto npc) {
+                    constexpr int NPAIR = decltype(npc)::value;
+                    float2 ngz[NPAIR];
+#pragma unroll
+                    for (int q = 0; q < NPAIR; ++q) ngz[q] = *reinterpret_cast<const float2 *>(gsf + 36 + 2 * q);
+                    int r = (warp + it) % NCW;
+                    int k1 = ta + r / np, k2 = r % np;  // advanced incrementally below
+                    for (; r < rows; r += NCW) {
+                        const unsigned char *row = tile + (size_t)r * row_bytes;
+                        float2 dx2[2], dy2[2], rxy2[2], z2[2], ux[2], uy[2], uz[2], S[2];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
+                            dx2[t] = bc2(dx);
+                            dy2[t] = bc2(dy);
+                            rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
+                            z2[t] = bc2(XO[t][2]);
+                            ux[t] = uy[t] = uz[t] = S[t] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NPAIR; ++q) {
+                            const float4 A = *reinterpret_cast<const float4 *>(row + q * 32);
+                            const float4 B = *reinterpret_cast<const float4 *>(row + q * 32 + 16);
+                            const float2 fx = make_float2(A.x, A.y), fy = make_float2(A.z, A.w);
+                            const float2 fz = make_float2(B.x, B.y);
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                float2 dz = add2(z2[t], ngz[q]);
+                                float2 r2 = fma2(dz, dz, rxy2[t]);
+                                float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
+                                float2 ri3 = mul2(mul2(ri, ri), ri);
+                                float2 H1 = fma2(e22, ri3, ri);
+                                float2 fd = fma2(fx, dx2[t], fma2(fy, dy2[t], mul2(fz, dz)));
+                                float2 sv = mul2(fd, ri3);
+                                ux[t] = fma2(fx, H1, ux[t]);
+                                uy[t] = fma2(fy, H1, uy[t]);
+                                uz[t] = fma2(fz, H1, fma2(dz, sv, uz[t]));
+                                S[t] = add2(S[t], sv);
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {  // the x and y parts of d s, summed over the row
+                            ux[t] = fma2(dx2[t], S[t], ux[t]);
+                            uy[t] = fma2(dy2[t], S[t], uy[t]);
+                            a1[t][0] += ux[t].x + ux[t].y;
+                            a1[t][1] += uy[t].x + uy[t].y;
+                            a1[t][2] += uz[t].x + uz[t].y;
+                        }
+                        step(u0, u1);
+                        k2 += NCW;
+                        while (k2 >= np) {
+                            k2 -= np;
+                            ++k1;
+                        }
+                    }
+                };
+                switch (npair) {
+                case 1: far_rows(std::integral_constant<int, 1>{}); break;
+                case 2: far_rows(std::integral_constant<int, 2>{}); break;
+                case 3: far_rows(std::integral_constant<int, 3>{}); break;
+                case 4: far_rows(std::integral_constant<int, 4>{}); break;
+                case 5: far_rows(std::integral_constant<int, 5>{}); break;
+                case 6: far_rows(std::integral_constant<int, 6>{}); break;
+                case 7: far_rows(std::integral_constant<int, 7>{}); break;
+                case 8: far_rows(std::integral_constant<int, 8>{}); break;
+                default: far_rows(std::integral_constant<int, 9>{}); break;
+                }
+            } else {
+                const int cnt = tb - ta;  // source pairs
+                const int nb4 = (cnt + 3) >> 2, nfull = cnt >> 2;
+                float2 ux[2], uy[2], uz[2];
+                auto body = [&](int idx) {
+                    const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
+                    const float4 A = *reinterpret_cast<const float4 *>(rec);
+                    const float4 B = *reinterpret_cast<const float4 *>(rec + 16);
+                    const float4 C = *reinterpret_cast<const float4 *>(rec + 32);
+                    const float4 D = *reinterpret_cast<const float4 *>(rec + 48);
+                    const float4 E = *reinterpret_cast<const float4 *>(rec + 64);
+                    const float2 hx = make_float2(A.x, A.y), hy = make_float2(A.z, A.w);
+                    const float2 hz = make_float2(B.x, B.y), lx = make_float2(B.z, B.w);
+                    const float2 ly = make_float2(C.x, C.y), lz = make_float2(C.z, C.w);
+                    const float2 fx = make_float2(D.x, D.y), fy = make_float2(D.z, D.w);
+                    const float2 fz = make_float2(E.x, E.y);
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
+                        float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
+                        float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
+                        float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e22)));
+                        float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
+                        float2 ri3 = mul2(mul2(ri, ri), ri);
+                        float2 H1 = fma2(e22, ri3, ri);
+                        float2 fd = fma2(fx, dx, fma2(fy, dy, mul2(fz, dz)));
+                        float2 sv = mul2(fd, ri3);
+                        ux[t] = fma2(fx, H1, fma2(dx, sv, ux[t]));
+                        uy[t] = fma2(fy, H1, fma2(dy, sv, uy[t]));
+                        uz[t] = fma2(fz, H1, fma2(dz, sv, uz[t]));
+                    }
+                };
+                for (int blk = (warp + it) % NCW; blk < nb4; blk += NCW) {
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
+                    if (blk < nfull) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) body(blk * 4 + j);
+                    } else {
+                        for (int idx = blk * 4; idx < cnt; ++idx) body(idx);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        a1[t][0] += ux[t].x + ux[t].y;
+                        a1[t][1] += uy[t].x + uy[t].y;
+                        a1[t][2] += uz[t].x + uz[t].y;
+                    }
+                    step(u0, u1);
+                }
+            }
+        } else if (kind == K_FAR) {
             if (flags & F_FIRST_ENTRY) {
                 // mapped Chebyshev points of the cluster (Sec. 3 interval map);
                 // FP32 runs take them relative to the batch centre
@@ -490,7 +669,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
             }
             const R *gx = gs, *gy = gs + (KITC_MAX_DEGREE + 1), *gz = gs + 2 * (KITC_MAX_DEGREE + 1);
             const int rows = (tb - ta) * np;
-            for (int r = warp; r < rows; r += NCW) {
+            for (int r = (warp + it) % NCW; r < rows; r += NCW) {
                 const int k1 = ta + r / np, k2 = r % np;
                 const unsigned char *row = tile + (size_t)r * np * PREC;
                 R dx[2], dy[2], rxy[2];
@@ -548,7 +727,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     }
                 }
             };
-            for (int blk = warp; blk < nb8; blk += NCW) {
+            for (int blk = (warp + it) % NCW; blk < nb8; blk += NCW) {
                 if (blk < nfull) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) body(blk * 8 + j);
@@ -609,7 +788,10 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
 {
     constexpr int WIN = KT<K>::WIN;
     int np = a.degree + 1;
-    if ((size_t)np * np * Rec<MIXED, WIN>::PROXY > (size_t)TILE) return KITC_ERR_INVALID_ARG;
+    constexpr bool PAIR = MIXED && K == KITC_STOKESLET;
+    size_t plane = PAIR ? (size_t)np * ((np + 1) / 2) * 32 : (size_t)np * np * Rec<MIXED, WIN>::PROXY;
+    if (plane > (size_t)TILE) return KITC_ERR_INVALID_ARG;
+    if (PAIR && a.near_off && !a.pbegin) return KITC_ERR_INVALID_ARG;
     // bulk copies need 16-byte aligned sources; records are multiples of 16 bytes
     if ((reinterpret_cast<uintptr_t>(a.src) & 15u) || (reinterpret_cast<uintptr_t>(a.proxy) & 15u))
         return KITC_ERR_INVALID_ARG;

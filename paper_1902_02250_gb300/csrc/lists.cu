@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
         bctr[b] = make_dvec4(__dmul_rn(0.5, __dadd_rn(lo[0], hi[0])),
                                __dmul_rn(0.5, __dadd_rn(lo[1], hi[1])),
                                __dmul_rn(0.5, __dadd_rn(lo[2], hi[2])), 0.0);
-    int64_t nfar = 0, nnear = 0, pairs = 0, points = 0;
+    int64_t nfar = 0, nnear = 0, pairs = 0, points = 0, xpairs = 0, xpoints = 0;
+    const int nvalid = __popcll(m0);
     int64_t fo = PASS ? far_off[b] : 0, no = PASS ? near_off[b] : 0;
     int sp = 0;
     if (lane == 0) {
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
             }
             nfar++;
             points += (int64_t)__popcll(A) * np3;
+            xpoints += (int64_t)nvalid * np3;
         }
         if (R) {
             int nch = n_child[c];
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
                 }
                 nnear++;
                 pairs += (int64_t)__popcll(R) * (cend[c] - cbegin[c]);
+                xpairs += (int64_t)nvalid * (cend[c] - cbegin[c]);
             } else {
                 if (sp + nch > STK) {
                     if (lane == 0) atomicExch(err, 1);
@@ -131,6 +134,8 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
         counts[nb + b] = nnear;
         atomicAdd(reinterpret_cast<unsigned long long *>(&totals[0]), (unsigned long long)pairs);
         atomicAdd(reinterpret_cast<unsigned long long *>(&totals[1]), (unsigned long long)points);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&totals[4]), (unsigned long long)xpairs);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&totals[5]), (unsigned long long)xpoints);
     }
 }
 
@@ -222,6 +227,8 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     L.far_points = h[1];
     L.nfar = h[2];
     L.nnear = h[3];
+    L.near_exec = h[4];
+    L.far_exec = h[5];
     KITC_TRY(L.far_id.reserve(sizeof(int32_t) * (L.nfar + 1), s));
     KITC_TRY(L.far_mask.reserve(sizeof(uint64_t) * (L.nfar + 1), s));
     KITC_TRY(L.near_id.reserve(sizeof(int32_t) * (L.nnear + 1), s));

@@ -282,6 +282,69 @@ __global__ void k_pack_sources(int64_t n, int win, const double *__restrict__ xs
     }
 }
 
+// Paired records for the FP32x2 Stokeslet evaluator: two consecutive sources
+// of one leaf share a 80-byte record (negated hi/lo coordinates, so that the
+// packed add forms x - y, then the weights):
+//   [-yh_x0 -yh_x1 -yh_y0 -yh_y1][-yh_z0 -yh_z1 -yl_x0 -yl_x1]
+//   [-yl_y0 -yl_y1 -yl_z0 -yl_z1][f_x0 f_x1 f_y0 f_y1][f_z0 f_z1 0 0]
+// A leaf of odd size is padded with a zero-weight point at 1e18, whose term is
+// exactly zero.  Block r packs the slot range [rb[r], re[r]) from pair pb[r].
+__global__ void k_pack_pairs(const int32_t *__restrict__ rb, const int32_t *__restrict__ re,
+                             const int32_t *__restrict__ pb, int64_t n,
+                             const double *__restrict__ xs, const int32_t *__restrict__ perm,
+                             const double *__restrict__ xyz, const double *__restrict__ w,
+                             float *__restrict__ out)
+{
+    const int r = blockIdx.x;
+    const int64_t b = rb[r], e = re[r];
+    const int64_t cnt2 = ((e - b + 1) / 2) * 2;
+    for (int64_t i = threadIdx.x; i < cnt2; i += blockDim.x) {
+        int64_t slot = b + i;
+        double x[3], f[3];
+        if (slot < e) {
+            int64_t j = perm ? perm[slot] : slot;
+            for (int l = 0; l < 3; ++l) {
+                x[l] = perm ? xs[l * n + slot] : xyz[3 * slot + l];
+                f[l] = w[3 * j + l];
+            }
+        } else {
+            for (int l = 0; l < 3; ++l) {
+                x[l] = 1e18;
+                f[l] = 0.0;
+            }
+        }
+        float *rec = out + ((int64_t)pb[r] + i / 2) * 20;
+        int h = (int)(i & 1);
+        for (int l = 0; l < 3; ++l) {
+            float hi = __double2float_rn(x[l]);
+            float lo = __double2float_rn(x[l] - (double)hi);
+            rec[2 * l + h] = -hi;
+            rec[6 + 2 * l + h] = -lo;
+            rec[12 + 2 * l + h] = (float)f[l];
+        }
+        rec[18 + h] = 0.f;
+    }
+}
+
+// Paired modified-weight records: each grid row (k1, k2) holds ceil((n+1)/2)
+// pairs of consecutive k3 points, [fx_k fx_k+1 fy_k fy_k+1][fz_k fz_k+1 0 0];
+// a missing last point has zero weight.
+__global__ void k_pack_proxy_pairs(int64_t nrows, int np, const double *__restrict__ fhat,
+                                   float4 *__restrict__ out)
+{
+    const int npair = (np + 1) / 2;
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nrows * npair) return;
+    int64_t r = q / npair;
+    int k = (int)(q % npair) * 2;
+    const double *f0 = fhat + (r * np + k) * 3;
+    double g[3] = {0.0, 0.0, 0.0};
+    if (k + 1 < np)
+        for (int l = 0; l < 3; ++l) g[l] = f0[3 + l];
+    out[2 * q] = make_float4((float)f0[0], (float)g[0], (float)f0[1], (float)g[1]);
+    out[2 * q + 1] = make_float4((float)f0[2], (float)g[2], 0.f, 0.f);
+}
+
 }  // namespace
 
 int proxy_record_bytes(int win, bool mixed)
@@ -296,12 +359,12 @@ int source_record_bytes(int win, bool mixed)
 
 void WeightsDev::release(cudaStream_t s)
 {
-    for (DevBuf *b : {&fhat, &proxy, &src, &partial, &items}) b->release(s);
+    for (DevBuf *b : {&fhat, &proxy, &src, &pbegin, &partial, &items}) b->release(s);
 }
 
 size_t WeightsDev::bytes() const
 {
-    return fhat.bytes + proxy.bytes + src.bytes + partial.bytes + items.bytes;
+    return fhat.bytes + proxy.bytes + src.bytes + pbegin.bytes + partial.bytes + items.bytes;
 }
 
 template <int ACC>
@@ -430,6 +493,67 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
         k_pack_sources<true><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
     else
         k_pack_sources<false><<<g, 256, 0, s>>>(n, win, xs, perm, xyz_user, w_user, out.ptr);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
+                       cudaStream_t s, DevBuf &out, DevBuf &pbegin)
+{
+    std::vector<int32_t> rb, re, pb;
+    int nclus = t ? t->nclus : 1;
+    std::vector<int32_t> cpb(nclus, -1);
+    if (t) {
+        std::vector<int32_t> hb(nclus), he(nclus), hn(nclus);
+        KITC_CUDA(cudaMemcpyAsync(hb.data(), t->begin.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaMemcpyAsync(he.data(), t->end.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaMemcpyAsync(hn.data(), t->n_child.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        int32_t next = 0;
+        for (int c = 0; c < nclus; ++c) {
+            if (hn[c] != 0) continue;
+            rb.push_back(hb[c]);
+            re.push_back(he[c]);
+            pb.push_back(next);
+            cpb[c] = next;
+            next += (he[c] - hb[c] + 1) / 2;
+        }
+    } else {
+        rb.push_back(0);
+        re.push_back((int32_t)n);
+        pb.push_back(0);
+        cpb[0] = 0;
+    }
+    int64_t npairs = 0;
+    for (size_t i = 0; i < rb.size(); ++i) npairs += (re[i] - rb[i] + 1) / 2;
+    size_t nr = rb.size();
+    KITC_TRY(out.reserve((size_t)80 * npairs + 16, s));
+    KITC_TRY(pbegin.reserve(sizeof(int32_t) * (3 * nr + nclus) + 16, s));
+    int32_t *d = pbegin.as<int32_t>();
+    std::vector<int32_t> all;
+    all.insert(all.end(), cpb.begin(), cpb.end());
+    all.insert(all.end(), rb.begin(), rb.end());
+    all.insert(all.end(), re.begin(), re.end());
+    all.insert(all.end(), pb.begin(), pb.end());
+    KITC_CUDA(cudaMemcpyAsync(d, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
+    kitc_count_launch();
+    k_pack_pairs<<<(unsigned)nr, 256, 0, s>>>(d + nclus, d + nclus + nr, d + nclus + 2 * nr, n,
+                                              t ? t->xs.as<double>() : nullptr,
+                                              t ? t->perm.as<int32_t>() : nullptr, xyz_user, w_user,
+                                              out.as<float>());
+    KITC_CUDA(cudaGetLastError());
+    KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copy
+    return KITC_OK;
+}
+
+kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)
+{
+    int np = wd.degree + 1, npair = (np + 1) / 2;
+    int64_t nrows = (int64_t)t.nclus * np * np;
+    KITC_TRY(wd.proxy.reserve((size_t)32 * nrows * npair, s));
+    unsigned g = (unsigned)((nrows * npair + 255) / 256);
+    kitc_count_launch();
+    k_pack_proxy_pairs<<<g, 256, 0, s>>>(nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }

@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
                 ("near_entries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
                 ("far_points", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("ms_tree", ctypes.c_float), ("ms_weights", ctypes.c_float),
-                ("ms_lists", ctypes.c_float), ("ms_evaluate", ctypes.c_float)]
+                ("ms_lists", ctypes.c_float), ("ms_evaluate", ctypes.c_float),
+                ("near_exec", ctypes.c_int64), ("far_exec", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
