@@ -79,6 +79,7 @@ struct TreeDev {
     DevBuf xs;              // double [3][n]: coordinates in tree order (SoA)
     DevBuf lo, hi;          // dvec4 [cap]: box corners (w unused)
     DevBuf ctr;             // dvec4 [cap]: centre xyz, radius in w (Fig. 1)
+    DevBuf ctrf;            // float4 [2 cap]: centre as FP32 hi (+ radius) and lo parts
     DevBuf begin, end;      // int32 [cap]: slot range
     DevBuf first_child, n_child, level, parent;  // int32 [cap]
     std::vector<int32_t> level_start;            // host: first cluster of each level

@@ -33,7 +33,7 @@ __device__ __forceinline__ double box_gap(double y, double lo, double hi)
 template <int PASS>
 __global__ void __launch_bounds__(LW * 32) k_lists(
     int64_t nt, int batch, int64_t nb, const double *__restrict__ txs,
-    const dvec4 *__restrict__ ctr, const int32_t *__restrict__ cbegin,
+    const dvec4 *__restrict__ ctr, const float4 *__restrict__ ctrf, const int32_t *__restrict__ cbegin,
     const int32_t *__restrict__ cend, const int32_t *__restrict__ first_child,
     const int32_t *__restrict__ n_child, double theta, int np3, int mac,
     int64_t *__restrict__ counts, dvec4 *__restrict__ bctr, int64_t *__restrict__ totals,
@@ -62,10 +62,25 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
     }
     uint64_t m0 = (uint64_t)__ballot_sync(0xffffffffu, va) |
                   ((uint64_t)__ballot_sync(0xffffffffu, vb) << 32);
-    if (PASS == 0 && lane == 0)
-        bctr[b] = make_dvec4(__dmul_rn(0.5, __dadd_rn(lo[0], hi[0])),
-                               __dmul_rn(0.5, __dadd_rn(lo[1], hi[1])),
-                               __dmul_rn(0.5, __dadd_rn(lo[2], hi[2])), 0.0);
+    double cb[3];
+    for (int l = 0; l < 3; ++l) cb[l] = __dmul_rn(0.5, __dadd_rn(lo[l], hi[l]));
+    if (PASS == 0 && lane == 0) bctr[b] = make_dvec4(cb[0], cb[1], cb[2], 0.0);
+    // FP32 frame of the pre-test: offsets from the batch centre cb, which is
+    // held as an FP32 hi/lo pair
+    float cbh[3], cbl[3], xoa[3], xob[3], bl[3], bh[3];
+    float sxa = 0.f, sxb = 0.f, sbx = 0.f;
+    for (int l = 0; l < 3; ++l) {
+        cbh[l] = __double2float_rn(cb[l]);
+        cbl[l] = __double2float_rn(cb[l] - (double)cbh[l]);
+        xoa[l] = __double2float_rn(xa[l] - cb[l]);
+        xob[l] = __double2float_rn(xb[l] - cb[l]);
+        bl[l] = __double2float_rn(lo[l] - cb[l]);
+        bh[l] = __double2float_rn(hi[l] - cb[l]);
+        sxa += fabsf(xoa[l]);
+        sxb += fabsf(xob[l]);
+        sbx += fmaxf(fabsf(bl[l]), fabsf(bh[l]));
+    }
+    const float thf = (float)theta;
     int64_t nfar = 0, nnear = 0, pairs = 0, points = 0, xpairs = 0, xpoints = 0;
     const int nvalid = __popcll(m0);
     int64_t fo = PASS ? far_off[b] : 0, no = PASS ? near_off[b] : 0;
@@ -81,18 +96,52 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
         int c = sid[w][sp];
         uint64_t M = smask[w][sp];
         __syncwarp();
-        dvec4 g = ctr[c];  // centre, radius in w
+        // MAC: an FP32 pre-test decides when the margin exceeds a bound on its
+        // rounding error; otherwise the exact FP64 expression decides.  The
+        // FP32 distance carries an absolute error <= 3u (|x - cb|_1 + |y_C - cb|_1)
+        // (u = 2^-24) plus relative errors far below the 1e-5 margin.
+        const float4 gh = ctrf[2 * c], gl = ctrf[2 * c + 1];
+        float cc[3] = {(gh.x - cbh[0]) + (gl.x - cbl[0]), (gh.y - cbh[1]) + (gl.y - cbl[1]),
+                       (gh.z - cbh[2]) + (gl.z - cbl[2])};
+        const float scc = fabsf(cc[0]) + fabsf(cc[1]) + fabsf(cc[2]);
+        const float rf = gh.w;
+        auto pretest = [&](float dist, float err) -> int {  // 1 accept, 0 reject, 2 undecided
+            if (rf < thf * (dist - err) * (1.f - 1e-5f)) return 1;
+            if (rf > thf * (dist + err) * (1.f + 1e-5f)) return 0;
+            return 2;
+        };
         uint64_t A;
         if (mac == KITC_MAC_PARTICLE) {
-            double Ra = norm3_rn(__dsub_rn(xa[0], g.x), __dsub_rn(xa[1], g.y), __dsub_rn(xa[2], g.z));
-            double Rb = norm3_rn(__dsub_rn(xb[0], g.x), __dsub_rn(xb[1], g.y), __dsub_rn(xb[2], g.z));
-            bool aa = g.w <= __dmul_rn(theta, Ra), ab = g.w <= __dmul_rn(theta, Rb);
-            A = ((uint64_t)__ballot_sync(0xffffffffu, aa) |
-                 ((uint64_t)__ballot_sync(0xffffffffu, ab) << 32)) & M;
+            float da0 = xoa[0] - cc[0], da1 = xoa[1] - cc[1], da2 = xoa[2] - cc[2];
+            float db0 = xob[0] - cc[0], db1 = xob[1] - cc[1], db2 = xob[2] - cc[2];
+            int pa = pretest(sqrtf(fmaf(da0, da0, fmaf(da1, da1, da2 * da2))), 2e-7f * (sxa + scc));
+            int pb = pretest(sqrtf(fmaf(db0, db0, fmaf(db1, db1, db2 * db2))), 2e-7f * (sxb + scc));
+            if (pa == 2 || pb == 2) {
+                const dvec4 g = ctr[c];  // centre, radius in w
+                if (pa == 2) {
+                    double Ra = norm3_rn(__dsub_rn(xa[0], g.x), __dsub_rn(xa[1], g.y), __dsub_rn(xa[2], g.z));
+                    pa = g.w <= __dmul_rn(theta, Ra);
+                }
+                if (pb == 2) {
+                    double Rb = norm3_rn(__dsub_rn(xb[0], g.x), __dsub_rn(xb[1], g.y), __dsub_rn(xb[2], g.z));
+                    pb = g.w <= __dmul_rn(theta, Rb);
+                }
+            }
+            A = ((uint64_t)__ballot_sync(0xffffffffu, pa == 1) |
+                 ((uint64_t)__ballot_sync(0xffffffffu, pb == 1) << 32)) & M;
         } else {
-            double d = norm3_rn(box_gap(g.x, lo[0], hi[0]), box_gap(g.y, lo[1], hi[1]),
-                                box_gap(g.z, lo[2], hi[2]));
-            A = (g.w <= __dmul_rn(theta, d)) ? M : 0;
+            float gap[3];
+            for (int l = 0; l < 3; ++l)
+                gap[l] = cc[l] < bl[l] ? bl[l] - cc[l] : (cc[l] > bh[l] ? cc[l] - bh[l] : 0.f);
+            int p = pretest(sqrtf(fmaf(gap[0], gap[0], fmaf(gap[1], gap[1], gap[2] * gap[2]))),
+                            2e-7f * (scc + sbx));
+            if (p == 2) {
+                const dvec4 g = ctr[c];
+                double d = norm3_rn(box_gap(g.x, lo[0], hi[0]), box_gap(g.y, lo[1], hi[1]),
+                                    box_gap(g.z, lo[2], hi[2]));
+                p = g.w <= __dmul_rn(theta, d);
+            }
+            A = p == 1 ? M : 0;
         }
         uint64_t R = M & ~A;
         if (A) {
@@ -207,7 +256,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     unsigned grid = (unsigned)((nb + LW - 1) / LW);
     kitc_count_launch();
     k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
-                                        src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
                                         theta, np3, mac, L.counts.as<int64_t>(),
                                         L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
@@ -235,7 +284,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     KITC_TRY(L.near_mask.reserve(sizeof(uint64_t) * (L.nnear + 1), s));
     kitc_count_launch();
     k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
-                                        src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
                                         theta, np3, mac, nullptr, nullptr, nullptr,
                                         L.far_off.as<int64_t>(), L.near_off.as<int64_t>(),

@@ -328,16 +328,24 @@ __global__ void __launch_bounds__(BT) k_scatter(
 }
 
 // Cluster centre (box midpoint) and radius (half the diagonal), Fig. 1.
+// Also writes the centre as FP32 hi/lo pairs and the radius in FP32
+// (ctrf[2c] = hi xyz + radius, ctrf[2c+1] = lo xyz) for the list builder's
+// FP32 pre-test of the MAC.
 __global__ void k_geometry(int m, const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi,
-                           dvec4 *__restrict__ ctr)
+                           dvec4 *__restrict__ ctr, float4 *__restrict__ ctrf)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     dvec4 a = lo[c], b = hi[c];
     double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
     double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    ctr[c] = make_dvec4(__dmul_rn(0.5, __dadd_rn(a.x, b.x)), __dmul_rn(0.5, __dadd_rn(a.y, b.y)),
-                          __dmul_rn(0.5, __dadd_rn(a.z, b.z)), __dmul_rn(0.5, __dsqrt_rn(s)));
+    dvec4 g = make_dvec4(__dmul_rn(0.5, __dadd_rn(a.x, b.x)), __dmul_rn(0.5, __dadd_rn(a.y, b.y)),
+                         __dmul_rn(0.5, __dadd_rn(a.z, b.z)), __dmul_rn(0.5, __dsqrt_rn(s)));
+    ctr[c] = g;
+    float hx = __double2float_rn(g.x), hy = __double2float_rn(g.y), hz = __double2float_rn(g.z);
+    ctrf[2 * c] = make_float4(hx, hy, hz, __double2float_rn(g.w));
+    ctrf[2 * c + 1] = make_float4(__double2float_rn(g.x - (double)hx), __double2float_rn(g.y - (double)hy),
+                                  __double2float_rn(g.z - (double)hz), 0.f);
 }
 
 kitc_status grow_clusters(TreeDev &t, int need, cudaStream_t s)
@@ -360,8 +368,8 @@ kitc_status grow_clusters(TreeDev &t, int need, cudaStream_t s)
 
 void TreeDev::release(cudaStream_t s)
 {
-    for (DevBuf *b : {&perm, &xs, &lo, &hi, &ctr, &begin, &end, &first_child, &n_child, &level,
-                      &parent})
+    for (DevBuf *b : {&perm, &xs, &lo, &hi, &ctr, &ctrf, &begin, &end, &first_child, &n_child,
+                      &level, &parent})
         b->release(s);
     nclus = cap = depth = nleaves = 0;
     level_start.clear();
@@ -370,8 +378,8 @@ void TreeDev::release(cudaStream_t s)
 size_t TreeDev::bytes() const
 {
     size_t b = 0;
-    for (const DevBuf *d : {&perm, &xs, &lo, &hi, &ctr, &begin, &end, &first_child, &n_child,
-                            &level, &parent})
+    for (const DevBuf *d : {&perm, &xs, &lo, &hi, &ctr, &ctrf, &begin, &end, &first_child,
+                            &n_child, &level, &parent})
         b += d->bytes;
     return b;
 }
@@ -466,9 +474,10 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
     t.depth = depth;
     t.nleaves = nleaves;
     KITC_TRY(t.ctr.reserve(sizeof(dvec4) * t.cap, s));
+    KITC_TRY(t.ctrf.reserve(2 * sizeof(float4) * t.cap, s));
     kitc_count_launch();
     k_geometry<<<(nclus + 255) / 256, 256, 0, s>>>(nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
-                                                   t.ctr.as<dvec4>());
+                                                   t.ctr.as<dvec4>(), t.ctrf.as<float4>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
