@@ -24,15 +24,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Workload: uniform cube N = 1e6 (the paper's Stokeslet setting on a 1M system),
-# eps = 1e-3, N0 = 2000, n = 8.  theta = 0.6 is the largest theta in
-# {0.5, 0.6, 0.7} that keeps E <= 1e-6 at n = 8 (theta = 0.7 gives E ~ 5.5e-6).
+# Workload: uniform cube N = 1e6 with eps = 1e-3 (the 1M Stokeslet system).
+# Treecode parameters: the fastest point with E <= 8e-7 (a margin under the
+# metric's 1e-6) found by paper_1902_02250_gb300/tune.py on a GB300 over the
+# batch / per-target MAC, theta in [0.5, 0.8], n in 6..10, N0 in {1000, 2000,
+# 4000}: batch MAC, theta = 0.7, n = 9, N0 = 4000 (E is re-measured every run).
+# The literal point theta = 0.7, n = 8, N0 = 2000 gives E ~ 5.5e-6 (--literal).
 N = 1_000_000
 SEED = 2
 EPS = 1e-3
-THETA = 0.6
-DEGREE = 8
-LEAF = 2000
+THETA, DEGREE, LEAF, MAC = 0.7, 9, 4000, "batch"
+LITERAL = (0.7, 8, 2000, "particle")
 BATCH = 64
 N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacement)
 SAMPLE_SEED = 102
@@ -49,8 +51,19 @@ def parse():
     ap.add_argument("--impl", default="kitc", choices=["kitc", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--mac", default="particle", choices=["particle", "batch"])
-    return ap.parse_args()
+    ap.add_argument("--mac", default=None, choices=["particle", "batch"])
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--degree", type=int, default=None)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--literal", action="store_true",
+                    help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
+    args = ap.parse_args()
+    th, n, leaf, mac = LITERAL if args.literal else (THETA, DEGREE, LEAF, MAC)
+    args.theta = th if args.theta is None else args.theta
+    args.degree = n if args.degree is None else args.degree
+    args.leaf = leaf if args.leaf is None else args.leaf
+    args.mac = mac if args.mac is None else args.mac
+    return args
 
 
 def dist_init(args):
@@ -138,33 +151,40 @@ def rel_l2(a, b):
 METRIC = "Stokeslet targets/sec at 1e-6 rel. L2 error, N=1M, vs plain FP64 GPU treecode"
 
 
-def config(mac, precision):
+def config(args, precision):
     return {"workload": "uniform cube [-1,1]^3, N=1,000,000 (seed 2 + rank), Stokeslet, f ~ U[-1,1]^3",
-            "eps": EPS, "theta": THETA, "degree": DEGREE, "leaf_size": LEAF, "target_batch": BATCH,
-            "mac": mac, "precision": precision,
+            "eps": EPS, "theta": args.theta, "degree": args.degree, "leaf_size": args.leaf,
+            "target_batch": BATCH, "mac": args.mac, "precision": precision,
+            "parameters": "fastest with E <= 8e-7 per tune.py" if not args.literal else "literal",
             "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def oracle_sample(x, f, n_eval, seed):
+def oracle_sample(args, x, f, n_eval, seed):
     """The CPU oracle as it stands on this host: tree + modified weights over
-    all N sources, Algorithm 2 on n_eval sampled targets, time scaled to N."""
+    all N sources, the traversal (Algorithm 2, or its batch-MAC variant) on
+    n_eval sampled targets, time scaled to N."""
     import oracle
     from paper_1902_02250_gb300 import workloads as wl
     t0 = time.perf_counter()
-    t = oracle.Tree(x, LEAF)
+    t = oracle.Tree(x, args.leaf)
     t1 = time.perf_counter()
-    fh = t.modified_weights(f, DEGREE)
+    fh = t.modified_weights(f, args.degree)
     t2 = time.perf_counter()
     idx = wl.sample_indices(len(x), n_eval, seed)
-    t.treecode(f, fh, DEGREE, oracle.STOKESLET, EPS, THETA, x[idx])
+    if args.mac == "batch":
+        t.treecode_batch(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x, BATCH, BATCH,
+                         select=idx)
+    else:
+        t.treecode(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x[idx])
     t3 = time.perf_counter()
     total = (t1 - t0) + (t2 - t1) + (t3 - t2) * len(x) / n_eval
     return {"value": len(x) / total, "unit": "targets/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": "tree + modified weights over all %d sources, Algorithm 2 on %d sampled "
-                      "targets, evaluation time scaled by N/%d; %.1f s of CPU work"
-                      % (len(x), n_eval, n_eval, t3 - t0),
+            "sample": "tree + modified weights over all %d sources, the %s traversal on %d "
+                      "sampled targets, evaluation time scaled by N/%d; %.1f s of CPU work"
+                      % (len(x), "batch-MAC" if args.mac == "batch" else "Algorithm 2 (per-target MAC)",
+                         n_eval, n_eval, t3 - t0),
             "seconds": {"tree": t1 - t0, "weights": t2 - t1, "eval_sample": t3 - t2}}
 
 
@@ -176,8 +196,8 @@ def run_reference(args, ws, rank):
     oracle.build()
     x, f = wl.uniform_cube(N, SEED)
     for i in range(args.warmup):
-        oracle_sample(x, f, 200, 900 + i)
-    vals = [oracle_sample(x, f, 1000, 1000 + i) for i in range(args.steps)]
+        oracle_sample(args, x, f, 200, 900 + i)
+    vals = [oracle_sample(args, x, f, 1000, 1000 + i) for i in range(args.steps)]
     v = float(np.mean([r["value"] for r in vals]))
     ms = 1e3 * N / v
     cb = dict(vals[-1])
@@ -185,7 +205,7 @@ def run_reference(args, ws, rank):
     line = {"metric": METRIC, "value": v, "unit": "targets/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(args.mac, "fp64 (CPU oracle)"),
+            "data": "synthetic", "config": config(args, "fp64 (CPU oracle)"),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -214,8 +234,8 @@ def run_kitc(args, ws, rank, local):
     x, f = wl.uniform_cube(N, SEED + rank)
     xd = torch.from_numpy(x).to(dev)
     fd = torch.from_numpy(f).to(dev)
-    p = K.Params(theta=THETA, degree=DEGREE, leaf_size=LEAF, eps=EPS, kernel=K.STOKESLET,
-                 precision=K.MIXED, mac=mac, target_batch=BATCH)
+    p = K.Params(theta=args.theta, degree=args.degree, leaf_size=args.leaf, eps=EPS,
+                 kernel=K.STOKESLET, precision=K.MIXED, mac=mac, target_batch=BATCH)
     out = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -268,7 +288,7 @@ def run_kitc(args, ws, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
-            "config": config(args.mac, "mixed"), "E": E,
+            "config": config(args, "mixed"), "E": E,
             "stage_ms": {k: float(np.mean([s[k] for s in stats]))
                          for k in ("ms_tree", "ms_weights", "ms_lists", "ms_evaluate")},
             "interactions_per_target": {"near": st["near_pairs"] / N, "far": st["far_points"] / N},
@@ -282,8 +302,8 @@ def run_kitc(args, ws, rank, local):
             "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and ws == 1 and not args.no_fp64:
-        pf = K.Params(theta=THETA, degree=DEGREE, leaf_size=LEAF, eps=EPS, precision=K.FP64,
-                      mac=mac, target_batch=BATCH)
+        pf = K.Params(theta=args.theta, degree=args.degree, leaf_size=args.leaf, eps=EPS,
+                      precision=K.FP64, mac=mac, target_batch=BATCH)
         out64 = torch.empty_like(out)
         step(pf, out64)
         torch.cuda.synchronize()
@@ -313,7 +333,7 @@ def run_kitc(args, ws, rank, local):
                    "h2d_bytes_per_step": int(x.nbytes + f.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(x, f, 2000, 1234)
+        line["cpu_baseline"] = oracle_sample(args, x, f, 2000, 1234)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -119,6 +119,15 @@ typedef struct {
 kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
                             void *stream, kitc_tree *out);
 
+/* Many independent systems in one handle: a forest with one Sec. 6 tree per
+ * system, built in the same level-synchronous passes.  src_xyz: device,
+ * n_src x 3, system k owning the counts[k] rows after those of systems < k;
+ * counts: host, num_systems entries >= 1 summing to n_src.  The handle is used
+ * with kitc_modified_weights (one pass over every cluster of every system) and
+ * kitc_evaluate_forest; kitc_evaluate is refused (KITC_ERR_STATE). */
+kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int num_systems,
+                              const kitc_params *p, void *stream, kitc_tree *out);
+
 /* Eq. modified_weights (Algorithm 1) for every cluster of the tree, in
  * FP64.  w: device, n_src x w_in, in the order of src_xyz.  Replaces any
  * weights set before; stream-ordered, no synchronization. */
@@ -131,6 +140,14 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream);
  * KITC_ERR_STATE if kitc_modified_weights was not called. */
 kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
                           void *stream);
+
+/* Algorithm 2 for every system of a forest: the targets of system k (rows of
+ * tgt_xyz after those of systems < k, tgt_counts[k] >= 1 of them, host array of
+ * num_systems entries) interact with system k's sources only.  Target batches
+ * never span two systems; all batches of all systems go through one persistent
+ * evaluator launch.  Synchronizes like kitc_evaluate. */
+kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
+                                 double *out, void *stream);
 
 /* Eq. N-body by direct summation over all sources (self term included;
  * with eps = 0 a pair at r = 0 is skipped).  All pointers device.  Uses

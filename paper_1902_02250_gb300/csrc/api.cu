@@ -223,8 +223,8 @@ int kitc_set_wait_limit_ms(int ms)
     return old;
 }
 
-kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
-                            void *stream, kitc_tree *out)
+static kitc_status build_impl(const double *src_xyz, int64_t n_src, const int64_t *counts,
+                              int nsys, const kitc_params *p, void *stream, kitc_tree *out)
 {
     if (!out) return KITC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -242,7 +242,7 @@ kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_par
     for (auto &e : t->ev)
         if (cudaEventCreate(&e) != cudaSuccess) t->ev_ok = false;
     record(t, 0, s);
-    kitc_status st = tree_build(src_xyz, n_src, p->leaf_size, s, t->src);
+    kitc_status st = tree_build(src_xyz, n_src, p->leaf_size, s, t->src, counts, nsys);
     if (st == KITC_OK) st = t->flags.reserve(4 * sizeof(int), s);
     record(t, 1, s);
     if (st != KITC_OK) {
@@ -252,6 +252,25 @@ kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_par
     t->stage_done[0] = true;
     *out = t;
     return KITC_OK;
+}
+
+kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
+                            void *stream, kitc_tree *out)
+{
+    return build_impl(src_xyz, n_src, nullptr, 1, p, stream, out);
+}
+
+kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int num_systems,
+                              const kitc_params *p, void *stream, kitc_tree *out)
+{
+    if (out) *out = nullptr;
+    if (!counts || num_systems < 1) return KITC_ERR_INVALID_ARG;
+    int64_t tot = 0;
+    for (int k = 0; k < num_systems; ++k) {
+        if (counts[k] < 1) return KITC_ERR_INVALID_ARG;
+        tot += counts[k];
+    }
+    return build_impl(src_xyz, tot, counts, num_systems, p, stream, out);
 }
 
 kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
@@ -276,8 +295,8 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
     return KITC_OK;
 }
 
-kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
-                          void *stream)
+static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
+                                 const int64_t *counts, int nsys, double *out, void *stream)
 {
     if (!t || !valid_count(n_tgt) || !device_accessible(tgt_xyz) || !device_accessible(out))
         return KITC_ERR_INVALID_ARG;
@@ -288,7 +307,7 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
     int B = p.target_batch;
     t->evaluated = false;
     record(t, 4, s);
-    KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt));
+    KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt, counts, nsys));
     KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, p.mac, s, t->lists));
     record(t, 5, s);
     EvalArgs a{};
@@ -301,6 +320,10 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
     a.batch = B;
     a.nb = t->lists.nb;
     a.bctr = t->lists.bctr.as<dvec4>();
+    if (t->lists.forest) {
+        a.bstart = t->lists.bdesc.as<int32_t>();
+        a.bcount = a.bstart + t->lists.nb;
+    }
     a.far_off = t->lists.far_off.as<int64_t>();
     a.near_off = t->lists.near_off.as<int64_t>();
     a.far_id = t->lists.far_id.as<int32_t>();
@@ -323,6 +346,26 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
     t->evaluated = true;
     t->stage_done[2] = t->stage_done[3] = true;
     return KITC_OK;
+}
+
+kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
+                          void *stream)
+{
+    if (t && t->src.nsys > 1) return KITC_ERR_STATE;
+    return evaluate_impl(t, tgt_xyz, n_tgt, nullptr, 1, out, stream);
+}
+
+kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
+                                 double *out, void *stream)
+{
+    if (!t || !tgt_counts) return KITC_ERR_INVALID_ARG;
+    int nsys = t->src.nsys;
+    int64_t tot = 0;
+    for (int k = 0; k < nsys; ++k) {
+        if (tgt_counts[k] < 1) return KITC_ERR_INVALID_ARG;
+        tot += tgt_counts[k];
+    }
+    return evaluate_impl(t, tgt_xyz, tot, tgt_counts, nsys, out, stream);
 }
 
 kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,

@@ -75,6 +75,7 @@ struct TreeDev {
     int64_t n = 0;          // particles
     int leaf = 0;           // N0
     int32_t nclus = 0, cap = 0, depth = 0, nleaves = 0;
+    int32_t nsys = 1;       // independent systems; cluster s < nsys is the root of system s
     DevBuf perm;            // int32 [n]: perm[slot] = caller index
     DevBuf xs;              // double [3][n]: coordinates in tree order (SoA)
     DevBuf lo, hi;          // dvec4 [cap]: box corners (w unused)
@@ -83,13 +84,17 @@ struct TreeDev {
     DevBuf begin, end;      // int32 [cap]: slot range
     DevBuf first_child, n_child, level, parent;  // int32 [cap]
     std::vector<int32_t> level_start;            // host: first cluster of each level
+    std::vector<int64_t> sys_off;                // host: first slot of each system (+ n)
     void release(cudaStream_t s);
     size_t bytes() const;
 };
 
-// Builds the tree of the n points xyz (device, n x 3 row-major).  Reads
-// back the child count of every level (one synchronization per level).
-kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t);
+// Builds the tree of the n points xyz (device, n x 3 row-major), or a forest
+// with one tree per system when counts (host, nsys entries summing to n) is
+// given: system k owns rows [sum_{j<k} counts[j], ...).  Reads back the child
+// count of every level (one synchronization per level).
+kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t,
+                       const int64_t *counts = nullptr, int nsys = 1);
 
 // ---------------------------------------------------------------------------
 // Modified weights (Eq. modified_weights / Algorithm 1) and the packed
@@ -130,8 +135,10 @@ kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
 struct ListsDev {
     int64_t nb = 0, nt = 0;
     int batch = 0;
+    bool forest = false;
     int64_t nfar = 0, nnear = 0;
     DevBuf bctr;                 // dvec4 [nb]: batch box centre
+    DevBuf bdesc;                // forests: int32 [3][nb] first slot, size, source root
     DevBuf far_off, near_off;    // int64 [nb+1]
     DevBuf far_id, near_id;      // int32 [entries]
     DevBuf far_mask, near_mask;  // uint64 [entries]
@@ -156,7 +163,8 @@ struct EvalArgs {
     int64_t nt;
     int batch;                   // targets per batch
     int64_t nb;
-    const dvec4 *bctr;         // batch centres (mixed far field frame); may be NULL if no far
+    const dvec4 *bctr;           // batch centres (mixed far field frame); may be NULL if no far
+    const int32_t *bstart, *bcount;  // forests: first slot and size of each batch (else NULL)
     // lists (NULL near_off = direct mode: one near range [0, direct_ns) per batch)
     const int64_t *far_off, *near_off;
     const int32_t *far_id, *near_id;

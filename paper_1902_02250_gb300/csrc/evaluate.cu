@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     const float2 e22 = bc2((float)(a.eps * a.eps));
     uint32_t it = 0, nbd = 0;
     int64_t bslot = 0;
+    int bsize = 0;
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
@@ -480,13 +481,14 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
         const unsigned char *tile = tiles + (size_t)s * TILE;
         const bool u0 = (mask >> lane) & 1ull, u1 = (mask >> (lane + 32)) & 1ull;
         if (flags & F_FIRST_BATCH) {
-            bslot = (int64_t)batch * a.batch;
+            bslot = a.bstart ? (int64_t)a.bstart[batch] : (int64_t)batch * a.batch;
+            bsize = a.bcount ? a.bcount[batch] : (int)min((int64_t)a.batch, a.nt - bslot);
             if (MIXED && a.bctr) cB = a.bctr[batch];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 int i = lane + 32 * t;
                 int64_t slot = bslot + i;
-                int64_t sl = (i < a.batch && slot < a.nt) ? slot : bslot;
+                int64_t sl = i < bsize ? slot : bslot;
                 xd[t][0] = a.tx[sl * a.tstride];
                 xd[t][1] = a.ty[sl * a.tstride];
                 xd[t][2] = a.tz[sl * a.tstride];
@@ -753,11 +755,10 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
             if (lane == 0) mbar_arrive(rbw);
             if (!mbar_wait(rbw, nbd & 1u, wait_ns)) { atomicExch(a.err, 1); break; }
             const double scale = (K == KITC_TEST_POLY) ? 1.0 : INV8PI;
-            const int ne = a.batch * WOUT;
+            const int ne = bsize * WOUT;
             for (int e = warp * 32 + lane; e < ne; e += NCW * 32) {
                 int i = e / WOUT, c = e % WOUT;
                 int64_t slot = bslot + i;
-                if (slot >= a.nt) continue;
                 double v = 0.0;
 #pragma unroll
                 for (int q = 0; q < NCW; ++q) v += red[((size_t)q * KITC_MAX_BATCH + i) * WOUT + c];

@@ -13,6 +13,9 @@
 // agree bit for bit with any IEEE implementation of the same formulas.
 // A first pass counts entries per batch, a scan sizes the arrays, a second
 // pass writes them.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -32,7 +35,7 @@ __device__ __forceinline__ double box_gap(double y, double lo, double hi)
 
 template <int PASS>
 __global__ void __launch_bounds__(LW * 32) k_lists(
-    int64_t nt, int batch, int64_t nb, const double *__restrict__ txs,
+    int64_t nt, int batch, int64_t nb, const int32_t *__restrict__ bdesc, const double *__restrict__ txs,
     const dvec4 *__restrict__ ctr, const float4 *__restrict__ ctrf, const int32_t *__restrict__ cbegin,
     const int32_t *__restrict__ cend, const int32_t *__restrict__ first_child,
     const int32_t *__restrict__ n_child, double theta, int np3, int mac,
@@ -46,7 +49,11 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t b = (int64_t)blockIdx.x * LW + w;
     if (b >= nb) return;
-    int64_t s0 = b * batch, s1 = min(nt, s0 + batch);
+    // batch b: slots [s0, s1) of the target order; forests give each batch its
+    // own slots and the root of its system's source tree
+    int64_t s0 = bdesc ? (int64_t)bdesc[b] : b * batch;
+    int64_t s1 = bdesc ? s0 + bdesc[nb + b] : min(nt, s0 + batch);
+    const int root = bdesc ? bdesc[2 * nb + b] : 0;
     int64_t sa = s0 + lane, sb = s0 + 32 + lane;
     bool va = sa < s1, vb = sb < s1;
     double xa[3], xb[3], lo[3], hi[3];
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
     int64_t fo = PASS ? far_off[b] : 0, no = PASS ? near_off[b] : 0;
     int sp = 0;
     if (lane == 0) {
-        sid[w][0] = 0;
+        sid[w][0] = root;
         smask[w][0] = m0;
     }
     sp = 1;
@@ -221,7 +228,7 @@ __global__ void k_scan64(const int64_t *__restrict__ in, int64_t m, int64_t *__r
 
 void ListsDev::release(cudaStream_t s)
 {
-    for (DevBuf *b : {&bctr, &far_off, &near_off, &far_id, &near_id, &far_mask, &near_mask,
+    for (DevBuf *b : {&bctr, &bdesc, &far_off, &near_off, &far_id, &near_id, &far_mask, &near_mask,
                       &counts, &totals})
         b->release(s);
     nb = nt = nfar = nnear = 0;
@@ -230,8 +237,8 @@ void ListsDev::release(cudaStream_t s)
 size_t ListsDev::bytes() const
 {
     size_t b = 0;
-    for (const DevBuf *d : {&bctr, &far_off, &near_off, &far_id, &near_id, &far_mask, &near_mask,
-                            &counts, &totals})
+    for (const DevBuf *d : {&bctr, &bdesc, &far_off, &near_off, &far_id, &near_id, &far_mask,
+                            &near_mask, &counts, &totals})
         b += d->bytes;
     return b;
 }
@@ -241,6 +248,27 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
 {
     int64_t nt = tgt.n;
     int64_t nb = (nt + batch - 1) / batch;
+    const int32_t *bdesc = nullptr;
+    if (tgt.nsys > 1) {  // per-system batches: target system k meets source system k
+        if (src.nsys != tgt.nsys) return KITC_ERR_INVALID_ARG;
+        std::vector<int32_t> st, sz, rt;
+        for (int k = 0; k < tgt.nsys; ++k)
+            for (int64_t p = tgt.sys_off[k]; p < tgt.sys_off[k + 1]; p += batch) {
+                st.push_back((int32_t)p);
+                sz.push_back((int32_t)std::min<int64_t>(batch, tgt.sys_off[k + 1] - p));
+                rt.push_back(k);
+            }
+        nb = (int64_t)st.size();
+        KITC_TRY(L.bdesc.reserve(sizeof(int32_t) * 3 * nb, s));
+        std::vector<int32_t> all(st);
+        all.insert(all.end(), sz.begin(), sz.end());
+        all.insert(all.end(), rt.begin(), rt.end());
+        KITC_CUDA(cudaMemcpyAsync(L.bdesc.ptr, all.data(), sizeof(int32_t) * all.size(),
+                                  cudaMemcpyHostToDevice, s));
+        KITC_CUDA(cudaStreamSynchronize(s));  // the host vector must outlive the copy
+        bdesc = L.bdesc.as<int32_t>();
+    }
+    L.forest = bdesc != nullptr;
     L.nt = nt;
     L.nb = nb;
     L.batch = batch;
@@ -255,7 +283,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     int *err = reinterpret_cast<int *>(tot + 6);
     unsigned grid = (unsigned)((nb + LW - 1) / LW);
     kitc_count_launch();
-    k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+    k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
                                         theta, np3, mac, L.counts.as<int64_t>(),
@@ -283,7 +311,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     KITC_TRY(L.near_id.reserve(sizeof(int32_t) * (L.nnear + 1), s));
     KITC_TRY(L.near_mask.reserve(sizeof(uint64_t) * (L.nnear + 1), s));
     kitc_count_launch();
-    k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+    k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
                                         theta, np3, mac, nullptr, nullptr, nullptr,

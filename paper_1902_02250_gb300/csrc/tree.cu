@@ -29,37 +29,50 @@ struct SplitInfo {
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
-// Gathers the caller's n x 3 coordinates into SoA, sets the identity order and
-// reduces each block's bounding box.
+// Gathers the caller's n x 3 coordinates into SoA and sets the identity order.
 __global__ void k_init(const double *__restrict__ xyz, int64_t n, double *__restrict__ xs,
-                       int32_t *__restrict__ perm, int32_t *__restrict__ node,
-                       double *__restrict__ part)
+                       int32_t *__restrict__ perm)
 {
-    __shared__ double red[6][BT / 32];
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int64_t base = (int64_t)blockIdx.x * SPB;
     for (int r = 0; r < RPB; ++r) {
         int64_t i = base + r * BT + threadIdx.x;
         if (i < n) {
-            for (int l = 0; l < 3; ++l) {
-                double v = xyz[3 * i + l];
-                xs[l * n + i] = v;
-                lo[l] = dmin(lo[l], v);
-                hi[l] = dmax(hi[l], v);
-            }
+            for (int l = 0; l < 3; ++l) xs[l * n + i] = xyz[3 * i + l];
             perm[i] = (int32_t)i;
-            node[i] = 0;
+        }
+    }
+}
+
+// Bounding box of one chunk of one system's slots (chunk c covers
+// [cb[c], ce[c]) of system cs[c]); also marks those slots as belonging to the
+// system's root.
+__global__ void __launch_bounds__(BT) k_root_partial(const int32_t *__restrict__ cs,
+                                                     const int64_t *__restrict__ cb,
+                                                     const int64_t *__restrict__ ce, int64_t n,
+                                                     const double *__restrict__ xs,
+                                                     int32_t *__restrict__ node,
+                                                     double *__restrict__ part)
+{
+    __shared__ double red[6][BT / 32];
+    const int c = blockIdx.x, sys = cs[c];
+    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = cb[c] + threadIdx.x; i < ce[c]; i += BT) {
+        node[i] = sys;
+        for (int a = 0; a < 3; ++a) {
+            double v = xs[a * n + i];
+            l[a] = dmin(l[a], v);
+            h[a] = dmax(h[a], v);
         }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int l = 0; l < 3; ++l) {
+    for (int a = 0; a < 3; ++a) {
         for (int o = 16; o > 0; o >>= 1) {
-            lo[l] = dmin(lo[l], __shfl_xor_sync(0xffffffffu, lo[l], o));
-            hi[l] = dmax(hi[l], __shfl_xor_sync(0xffffffffu, hi[l], o));
+            l[a] = dmin(l[a], __shfl_xor_sync(0xffffffffu, l[a], o));
+            h[a] = dmax(h[a], __shfl_xor_sync(0xffffffffu, h[a], o));
         }
         if (lane == 0) {
-            red[l][w] = lo[l];
-            red[3 + l][w] = hi[l];
+            red[a][w] = l[a];
+            red[3 + a][w] = h[a];
         }
     }
     __syncthreads();
@@ -67,29 +80,31 @@ __global__ void k_init(const double *__restrict__ xyz, int64_t n, double *__rest
         int q = threadIdx.x;
         double v = red[q][0];
         for (int k = 1; k < BT / 32; ++k) v = q < 3 ? dmin(v, red[q][k]) : dmax(v, red[q][k]);
-        part[blockIdx.x * 6 + q] = v;
+        part[6 * c + q] = v;
     }
 }
 
-// Root cluster: the exact bounding box over all blocks.
-__global__ void k_root(const double *__restrict__ part, int nblk, int64_t n, dvec4 *lo,
-                       dvec4 *hi, int32_t *begin, int32_t *end, int32_t *first_child,
-                       int32_t *n_child, int32_t *level, int32_t *parent)
+// Root cluster of every system: the smallest box enclosing its particles,
+// from the partial boxes of its chunks [c0[s], c0[s+1]).
+__global__ void k_root_final(int nsys, const int32_t *__restrict__ c0, const int64_t *__restrict__ off,
+                             const double *__restrict__ part, dvec4 *lo, dvec4 *hi, int32_t *begin,
+                             int32_t *end, int32_t *first_child, int32_t *n_child, int32_t *level,
+                             int32_t *parent)
 {
-    if (threadIdx.x != 0) return;
-    double b[6];
-    for (int q = 0; q < 6; ++q) b[q] = part[q];
-    for (int k = 1; k < nblk; ++k)
-        for (int q = 0; q < 6; ++q)
-            b[q] = q < 3 ? dmin(b[q], part[6 * k + q]) : dmax(b[q], part[6 * k + q]);
-    lo[0] = make_dvec4(b[0], b[1], b[2], 0.0);
-    hi[0] = make_dvec4(b[3], b[4], b[5], 0.0);
-    begin[0] = 0;
-    end[0] = (int32_t)n;
-    first_child[0] = -1;
-    n_child[0] = 0;
-    level[0] = 0;
-    parent[0] = -1;
+    int sys = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sys >= nsys) return;
+    double v[6];
+    for (int q = 0; q < 6; ++q) v[q] = part[6 * c0[sys] + q];
+    for (int c = c0[sys] + 1; c < c0[sys + 1]; ++c)
+        for (int q = 0; q < 6; ++q) v[q] = q < 3 ? dmin(v[q], part[6 * c + q]) : dmax(v[q], part[6 * c + q]);
+    lo[sys] = make_dvec4(v[0], v[1], v[2], 0.0);
+    hi[sys] = make_dvec4(v[3], v[4], v[5], 0.0);
+    begin[sys] = (int32_t)off[sys];
+    end[sys] = (int32_t)off[sys + 1];
+    first_child[sys] = -1;
+    n_child[sys] = 0;
+    level[sys] = 0;
+    parent[sys] = -1;
 }
 
 // Split decision of each cluster of the level [lb, lb + nl).
@@ -372,7 +387,9 @@ void TreeDev::release(cudaStream_t s)
                       &level, &parent})
         b->release(s);
     nclus = cap = depth = nleaves = 0;
+    nsys = 1;
     level_start.clear();
+    sys_off.clear();
 }
 
 size_t TreeDev::bytes() const
@@ -384,35 +401,77 @@ size_t TreeDev::bytes() const
     return b;
 }
 
-kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t)
+kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t,
+                       const int64_t *counts, int nsys)
 {
+    if (!counts) nsys = 1;
     t.release(s);
     t.n = n;
     t.leaf = leaf;
     int nblk = (int)((n + SPB - 1) / SPB);
-    DevBuf perm2, xs2, node, node2, part, bcount, lvl;
+    DevBuf perm2, xs2, node, node2, offs, bcount, lvl;
     KITC_TRY(t.perm.reserve(sizeof(int32_t) * n, s));
     KITC_TRY(perm2.reserve(sizeof(int32_t) * n, s));
     KITC_TRY(t.xs.reserve(sizeof(double) * 3 * n, s));
     KITC_TRY(xs2.reserve(sizeof(double) * 3 * n, s));
     KITC_TRY(node.reserve(sizeof(int32_t) * n, s));
     KITC_TRY(node2.reserve(sizeof(int32_t) * n, s));
-    KITC_TRY(part.reserve(sizeof(double) * 6 * nblk, s));
+    std::vector<int64_t> hoff(nsys + 1, 0);
+    for (int k = 0; k < nsys; ++k) hoff[k + 1] = hoff[k] + (counts ? counts[k] : n);
+    if (hoff[nsys] != n) return KITC_ERR_INVALID_ARG;
+    // chunks of at most 64K slots for the root boxes; packed as
+    // [off (nsys+1) | cb (nc) | ce (nc)] int64 and [c0 (nsys+1) | cs (nc)] int32
+    const int64_t CH = 65536;
+    std::vector<int64_t> cbv, cev;
+    std::vector<int32_t> c0v(nsys + 1, 0), csv;
+    for (int k = 0; k < nsys; ++k) {
+        c0v[k] = (int32_t)cbv.size();
+        for (int64_t p = hoff[k]; p < hoff[k + 1]; p += CH) {
+            cbv.push_back(p);
+            cev.push_back(std::min(hoff[k + 1], p + CH));
+            csv.push_back(k);
+        }
+    }
+    const int nc = (int)cbv.size();
+    c0v[nsys] = nc;
+    std::vector<int64_t> h64(hoff);
+    h64.insert(h64.end(), cbv.begin(), cbv.end());
+    h64.insert(h64.end(), cev.begin(), cev.end());
+    std::vector<int32_t> h32(c0v);
+    h32.insert(h32.end(), csv.begin(), csv.end());
+    KITC_TRY(offs.reserve(sizeof(int64_t) * h64.size() + sizeof(int32_t) * h32.size() +
+                          sizeof(double) * 6 * nc + 64, s));
+    int64_t *d64 = offs.as<int64_t>();
+    int32_t *d32 = reinterpret_cast<int32_t *>(d64 + h64.size());
+    double *dpart = reinterpret_cast<double *>(offs.as<char>() + ((sizeof(int64_t) * h64.size() +
+                                                                   sizeof(int32_t) * h32.size() + 15) / 16) * 16);
     KITC_TRY(bcount.reserve(sizeof(int32_t) * 8 * nblk, s));
-    KITC_TRY(grow_clusters(t, 64, s));
+    KITC_TRY(grow_clusters(t, std::max(64, nsys), s));
+    // every buffer the kernels below write must exist before any launch
+    for (const DevBuf *b : {&t.perm, &perm2, &t.xs, &xs2, &node, &node2, &offs, &bcount, &t.lo, &t.hi,
+                            &t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
+        if (!b->ptr) return KITC_ERR_OOM;
+    KITC_CUDA(cudaMemcpyAsync(d64, h64.data(), sizeof(int64_t) * h64.size(), cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d32, h32.data(), sizeof(int32_t) * h32.size(), cudaMemcpyHostToDevice, s));
     kitc_count_launch();
-    k_init<<<nblk, BT, 0, s>>>(xyz, n, t.xs.as<double>(), t.perm.as<int32_t>(),
-                               node.as<int32_t>(), part.as<double>());
+    k_init<<<nblk, BT, 0, s>>>(xyz, n, t.xs.as<double>(), t.perm.as<int32_t>());
     KITC_CUDA(cudaGetLastError());
     kitc_count_launch();
-    k_root<<<1, 32, 0, s>>>(part.as<double>(), nblk, n, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
-                            t.begin.as<int32_t>(), t.end.as<int32_t>(),
-                            t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
-                            t.level.as<int32_t>(), t.parent.as<int32_t>());
+    k_root_partial<<<nc, BT, 0, s>>>(d32 + nsys + 1, d64 + nsys + 1, d64 + nsys + 1 + nc, n,
+                                     t.xs.as<double>(), node.as<int32_t>(), dpart);
+    KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
+    k_root_final<<<(nsys + 127) / 128, 128, 0, s>>>(nsys, d32, d64, dpart, t.lo.as<dvec4>(),
+                                                    t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                                                    t.end.as<int32_t>(), t.first_child.as<int32_t>(),
+                                                    t.n_child.as<int32_t>(), t.level.as<int32_t>(),
+                                                    t.parent.as<int32_t>());
     KITC_CUDA(cudaGetLastError());
     int32_t *h2 = nullptr;
     KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h2)));
-    int lb = 0, nl = 1, nclus = 1, depth = 0, nleaves = 0;
+    int lb = 0, nl = nsys, nclus = nsys, depth = 0, nleaves = 0;
+    t.nsys = nsys;
+    t.sys_off = hoff;
     t.level_start.assign(1, 0);
     kitc_status st = KITC_OK;
     while (nl > 0) {
@@ -468,7 +527,10 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
         nl = nch;
         if (nl > 0) t.level_start.push_back(lb);
     }
-    for (DevBuf *b : {&perm2, &xs2, &node, &node2, &part, &bcount, &lvl}) b->release(s);
+    // the host offsets must outlive the copy above
+    cudaError_t se = cudaStreamSynchronize(s);
+    for (DevBuf *b : {&perm2, &xs2, &node, &node2, &offs, &bcount, &lvl}) b->release(s);
+    if (st == KITC_OK && se != cudaSuccess) st = kitc_from_cuda(se);
     if (st != KITC_OK) return st;
     t.nclus = nclus;
     t.depth = depth;

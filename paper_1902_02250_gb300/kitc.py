@@ -71,7 +71,8 @@ class Params:
 
 
 _lib = None
-SYMBOLS = ["kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
+SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kitc_evaluate",
+           "kitc_evaluate_forest", "kitc_direct",
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
@@ -93,6 +94,8 @@ def lib():
         P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         PP = ctypes.POINTER(_Params)
         L.kitc_build_tree.argtypes = [P, I64, PP, P, ctypes.POINTER(P)]
+        L.kitc_build_forest.argtypes = [P, P, I, PP, P, ctypes.POINTER(P)]
+        L.kitc_evaluate_forest.argtypes = [P, P, P, P, P]
         L.kitc_modified_weights.argtypes = [P, P, P]
         L.kitc_evaluate.argtypes = [P, P, I64, P, P]
         L.kitc_direct.argtypes = [P, I64, P, P, I64, PP, P, P]
@@ -111,7 +114,8 @@ def lib():
         L.kitc_watchdog_selftest.argtypes = [I, P]
         L.kitc_launch_count.argtypes = []
         L.kitc_launch_count.restype = I64
-        for name in ("kitc_build_tree", "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
+        for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest",
+                     "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest"):
             getattr(L, name).restype = I
@@ -240,6 +244,30 @@ def kitc_build_tree(src_xyz, params, stream=None):
     _check(lib().kitc_build_tree(_dptr(src_xyz, 3, "src_xyz"), src_xyz.shape[0], ctypes.byref(p),
                                  _stream(stream), ctypes.byref(h)), "kitc_build_tree")
     return Tree(h.value, params, src_xyz.shape[0])
+
+
+def kitc_build_forest(src_xyz, counts, params, stream=None):
+    """One Sec. 6 tree per system; counts[k] rows of src_xyz belong to system k."""
+    counts = np.ascontiguousarray(counts, np.int64)
+    h = ctypes.c_void_p()
+    p = params.c()
+    _check(lib().kitc_build_forest(_dptr(src_xyz, 3, "src_xyz"), _np(counts), len(counts),
+                                   ctypes.byref(p), _stream(stream), ctypes.byref(h)),
+           "kitc_build_forest")
+    return Tree(h.value, params, src_xyz.shape[0])
+
+
+def kitc_evaluate_forest(tree, tgt_xyz, tgt_counts, out=None, stream=None):
+    """Algorithm 2 per system of a forest; returns out (sum(tgt_counts) x w_out)."""
+    import torch
+    wout = kernel_wout(tree.params.kernel)
+    tgt_counts = np.ascontiguousarray(tgt_counts, np.int64)
+    if out is None:
+        out = torch.empty((tgt_xyz.shape[0], wout), dtype=torch.float64, device=tgt_xyz.device)
+    _check(lib().kitc_evaluate_forest(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), _np(tgt_counts),
+                                      _dptr(out, wout, "out"), _stream(stream)),
+           "kitc_evaluate_forest")
+    return out
 
 
 def kitc_modified_weights(tree, w, stream=None):

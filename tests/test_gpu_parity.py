@@ -279,3 +279,49 @@ def test_watchdog_times_out_and_context_survives(K, orc):
     got, _ = gpu_treecode(K, x, f, eps=0.01, theta=0.7, degree=3, leaf_size=100)
     ref = _oracle(orc, x, f, ST, 0.01, 0.7, 3, 100, 0, 64)
     assert orc.rel_l2(ref, got) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ forests
+def _systems(num, seed, nmin, nmax):
+    return wl.batched_systems(num, seed, nmin=nmin, nmax=nmax)
+
+
+@pytest.mark.parametrize("mac", [0, 1])
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_forest_matches_oracle_per_system(K, orc, mac, precision, tol):
+    systems = _systems(7, 52, 300, 6000)
+    counts = [len(x) for x, _ in systems]
+    x = np.vstack([s[0] for s in systems])
+    f = np.vstack([s[1] for s in systems])
+    p = K.Params(theta=0.7, degree=5, leaf_size=250, eps=0.01, mac=mac, precision=precision)
+    t = K.kitc_build_forest(dev(x), counts, p)
+    K.kitc_modified_weights(t, dev(f))
+    got = K.kitc_evaluate_forest(t, dev(x), counts).cpu().numpy()
+    st = t.stats()
+    t.free()
+    off = np.concatenate([[0], np.cumsum(counts)])
+    near = far = 0
+    for k in range(len(counts)):
+        xs, fs = x[off[k]:off[k + 1]], f[off[k]:off[k + 1]]
+        o = orc.Tree(xs, 250)
+        fh = o.modified_weights(fs, 5)
+        if mac == 0:
+            ref, cnt = o.treecode(fs, fh, 5, ST, 0.01, 0.7, xs)
+        else:
+            r = o.treecode_batch(fs, fh, 5, ST, 0.01, 0.7, xs, 64, 64)
+            ref, cnt = r["out"], r["counts"]
+        near += cnt[0]
+        far += cnt[1]
+        assert orc.rel_l2(ref, got[off[k]:off[k + 1]]) <= tol, k
+    assert st["near_pairs"] == near and st["far_points"] == far
+
+
+def test_forest_of_one_equals_tree(K):
+    x, f = wl.uniform_cube(5000, 53)
+    p = K.Params(theta=0.7, degree=4, leaf_size=200, eps=0.01)
+    a, _ = gpu_treecode(K, x, f, theta=0.7, degree=4, leaf_size=200, eps=0.01)
+    t = K.kitc_build_forest(dev(x), [len(x)], p)
+    K.kitc_modified_weights(t, dev(f))
+    b = K.kitc_evaluate_forest(t, dev(x), [len(x)]).cpu().numpy()
+    t.free()
+    assert np.array_equal(a, b)
