@@ -44,7 +44,8 @@ typedef enum {
     KITC_ERR_CUDA = 2,        /* a CUDA runtime call failed                       */
     KITC_ERR_OOM = 3,         /* device memory could not be allocated             */
     KITC_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out               */
-    KITC_ERR_STATE = 5        /* call out of order (e.g. evaluate before weights) */
+    KITC_ERR_STATE = 5,       /* call out of order (e.g. evaluate before weights) */
+    KITC_ERR_TOO_LARGE = 6    /* size beyond the fixed scratch of kitc_direct_noalloc */
 } kitc_status;
 
 /* Kernels of Sec. 7.  d = x - y, r = |d|, H1, H2, Q, D1, D2 of Eq. MRS_kernels. */
@@ -156,6 +157,24 @@ kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64
 kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,
                         const double *w, int64_t n_src, const kitc_params *p, double *out,
                         void *stream);
+
+/* kitc_direct without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory --
+ * latency-critical loops where an allocation may stall or fail, embeddings
+ * whose own allocator owns all of the device's memory, or error handling that
+ * runs when memory is already exhausted.  Arguments and results are those of
+ * kitc_direct; the caller still passes (device) inputs and outputs.
+ * Scratch is one file-scope device array of 8 MiB (held by every GPU that
+ * loads the library until the process exits); n_src is limited to 100000
+ * sources (KITC_ERR_TOO_LARGE beyond).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the array: each
+ * call clears the flags it needs and rewrites the records, and calls that
+ * overlap on the GPU (other streams, other threads) race on it.  Synchronizes
+ * `stream`. */
+kitc_status kitc_direct_noalloc(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,
+                                const double *w, int64_t n_src, const kitc_params *p, double *out,
+                                void *stream);
 
 /* End to end from host memory: copies the sources, weights and targets to
  * the device, builds the tree, computes the modified weights, evaluates,

@@ -212,6 +212,7 @@ const char *kitc_status_string(kitc_status s)
     case KITC_ERR_OOM: return "out of device memory";
     case KITC_ERR_TIMEOUT: return "device-side wait timed out";
     case KITC_ERR_STATE: return "call out of order";
+    case KITC_ERR_TOO_LARGE: return "size exceeds the fixed scratch of kitc_direct_noalloc";
     default: return "unknown status";
     }
 }

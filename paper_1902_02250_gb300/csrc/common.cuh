@@ -128,6 +128,12 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
 kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
                        cudaStream_t s, DevBuf &out, DevBuf &pbegin);
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
+// Direct-sum source records written to caller-provided device memory (no
+// allocation); pairs selects the paired FP32x2 format, range3 is 3 int32 of
+// device scratch used by that format.
+size_t direct_record_bytes(int64_t n, int win, bool mixed, bool pairs);
+kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, int win, bool mixed,
+                                bool pairs, int32_t *range3, void *out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Interaction lists of target batches (Algorithm 2 traversal).

@@ -557,3 +557,30 @@ kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
+
+size_t direct_record_bytes(int64_t n, int win, bool mixed, bool pairs)
+{
+    return pairs ? (size_t)80 * ((n + 1) / 2) : (size_t)source_record_bytes(win, mixed) * n;
+}
+
+kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, int win, bool mixed,
+                                bool pairs, int32_t *range3, void *out, cudaStream_t s)
+{
+    if (pairs) {
+        // one range [0, n) starting at pair 0, read by the pair-packing kernel
+        const int32_t h[3] = {0, (int32_t)n, 0};
+        KITC_CUDA(cudaMemcpyAsync(range3, h, sizeof(h), cudaMemcpyHostToDevice, s));
+        kitc_count_launch();
+        k_pack_pairs<<<1, 256, 0, s>>>(range3, range3 + 1, range3 + 2, n, nullptr, nullptr, xyz, w,
+                                      reinterpret_cast<float *>(out));
+    } else {
+        unsigned g = (unsigned)((n + 255) / 256);
+        kitc_count_launch();
+        if (mixed)
+            k_pack_sources<true><<<g, 256, 0, s>>>(n, win, nullptr, nullptr, xyz, w, out);
+        else
+            k_pack_sources<false><<<g, 256, 0, s>>>(n, win, nullptr, nullptr, xyz, w, out);
+    }
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}

@@ -19,7 +19,8 @@ MAC_PARTICLE, MAC_BATCH = 0, 1
 WEIGHTS_UPWARD, WEIGHTS_ALGORITHM1 = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
-           4: "device-side wait timed out", 5: "call out of order"}
+           4: "device-side wait timed out", 5: "call out of order",
+           6: "size exceeds the fixed scratch of kitc_direct_noalloc"}
 
 
 class KitcError(RuntimeError):
@@ -72,7 +73,7 @@ class Params:
 
 _lib = None
 SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kitc_evaluate",
-           "kitc_evaluate_forest", "kitc_direct",
+           "kitc_evaluate_forest", "kitc_direct", "kitc_direct_noalloc",
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
@@ -99,6 +100,7 @@ def lib():
         L.kitc_modified_weights.argtypes = [P, P, P]
         L.kitc_evaluate.argtypes = [P, P, I64, P, P]
         L.kitc_direct.argtypes = [P, I64, P, P, I64, PP, P, P]
+        L.kitc_direct_noalloc.argtypes = [P, I64, P, P, I64, PP, P, P]
         L.kitc_solve_host.argtypes = [P, P, I64, P, I64, PP, P, P]
         L.kitc_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
         L.kitc_tree_download.argtypes = [P] * 11
@@ -116,6 +118,7 @@ def lib():
         L.kitc_launch_count.restype = I64
         for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
+                     "kitc_direct_noalloc",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest"):
             getattr(L, name).restype = I
@@ -298,6 +301,20 @@ def kitc_direct(tgt_xyz, src_xyz, w, params, out=None, stream=None):
                              _dptr(src_xyz, 3, "src_xyz"), _dptr(w, kernel_win(params.kernel), "w"),
                              src_xyz.shape[0], ctypes.byref(p), _dptr(out, wout, "out"),
                              _stream(stream)), "kitc_direct")
+    return out
+
+
+def kitc_direct_noalloc(tgt_xyz, src_xyz, w, params, out, stream=None):
+    """kitc_direct for callers that must not allocate device memory: the
+    library's fixed 8 MiB device scratch array is used instead (at most 100000
+    sources; overlapping calls race on it).  out must be given."""
+    wout = kernel_wout(params.kernel)
+    p = params.c()
+    _check(lib().kitc_direct_noalloc(_dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
+                                     _dptr(src_xyz, 3, "src_xyz"),
+                                     _dptr(w, kernel_win(params.kernel), "w"), src_xyz.shape[0],
+                                     ctypes.byref(p), _dptr(out, wout, "out"), _stream(stream)),
+           "kitc_direct_noalloc")
     return out
 
 
