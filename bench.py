@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched"],
+                    help="batched: 256 independent systems (a parity/measurement case, not "
+                         "the headline line)")
     ap.add_argument("--literal", action="store_true",
                     help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
     args = ap.parse_args()
@@ -338,10 +341,124 @@ def run_kitc(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_batched(args, ws, rank, local):
+    """256 independent Stokeslet systems, N_s log-uniform in [1e3, 2e5], each
+    uniform in its own box: one forest, one persistent evaluator launch per
+    step; theta = 0.7, n = 6, mixed; N0 and the batch size from tune_forest."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K, tune, workloads as wl
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems = wl.batched_systems(256, 4 + rank)
+    counts = np.array([len(s[0]) for s in systems], np.int64)
+    x = np.vstack([s[0] for s in systems])
+    f = np.vstack([s[1] for s in systems])
+    ntot = len(x)
+    xd = torch.from_numpy(x).to(dev)
+    fd = torch.from_numpy(f).to(dev)
+    base = K.Params(theta=0.7, degree=6, eps=EPS, precision=K.MIXED, mac=K.MAC_PARTICLE)
+    tuned = tune.tune_forest(xd, fd, counts, base)[0]
+    out = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p, o):
+        t = K.kitc_build_forest(xd, counts, p)
+        try:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate_forest(t, xd, counts, o)
+            return t.stats()
+        finally:
+            t.free()
+
+    for _ in range(args.warmup):
+        step(tuned, out)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = K.kitc_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(tuned, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = K.kitc_launch_count() - l0
+    clk = clocks.stop()
+    total = reduce_max(sum(ms), ws)
+    value = ws * args.steps * ntot / (total / 1e3)
+    # repeated products with the same geometry: CUDA-graph replay of weights + evaluator
+    t = K.kitc_build_forest(xd, counts, tuned)
+    K.kitc_modified_weights(t, fd)
+    K.kitc_evaluate_forest(t, xd, counts, out)
+    side = torch.cuda.Stream()
+    out2 = torch.empty_like(out)
+    with torch.cuda.stream(side):
+        K.kitc_apply(t, fd, out2)
+        side.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(side)
+        for _ in range(args.steps):
+            K.kitc_apply(t, fd, out2)
+        a1.record(side)
+        side.synchronize()
+    apply_ms = a0.elapsed_time(a1) / args.steps
+    t.free()
+    # error per system on <= 1000 sampled targets against the FP64 direct sum
+    off = np.concatenate([[0], np.cumsum(counts)])
+    res = out.cpu().numpy()
+    num = den = 0.0
+    worst = 0.0
+    for k in range(len(counts)):
+        idx = wl.sample_indices(int(counts[k]), 1000, 4000 + k) + off[k]
+        xs = xd[off[k]:off[k + 1]]
+        ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xs, fd[off[k]:off[k + 1]],
+                            K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
+        d2 = float(((ref - res[idx]) ** 2).sum())
+        r2 = float((ref ** 2).sum())
+        num += d2
+        den += r2
+        worst = max(worst, math.sqrt(d2 / r2))
+    line = {"metric": "batched Stokeslet targets/sec, 256 systems", "value": value,
+            "unit": "targets/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
+            "config": {"workload": "256 systems, N_s = round(exp(U[ln 1e3, ln 2e5])), uniform in "
+                                   "boxes of side U[0.5, 2], total %d targets" % ntot,
+                       "eps": EPS, "theta": 0.7, "degree": 6, "mac": "particle",
+                       "leaf_size": tuned.leaf_size, "target_batch": tuned.target_batch,
+                       "tuning": "N0 in {250,500,1000,2000} x batch in {32,64}, fastest step",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "E_all": math.sqrt(num / den), "E_worst_system": worst,
+            "apply_graph": {"value": ntot / (apply_ms / 1e3), "unit": "targets/s",
+                            "ms": apply_ms,
+                            "what": "kitc_apply: new weights, same geometry, CUDA-graph replay"},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_fp64:
+        pf = K.Params(theta=0.7, degree=6, eps=EPS, precision=K.FP64, mac=K.MAC_PARTICLE,
+                      leaf_size=tuned.leaf_size, target_batch=tuned.target_batch)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(pf, torch.empty_like(out))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["plain_fp64"] = {"value": ntot / (e0.elapsed_time(e1) / 1e3), "unit": "targets/s",
+                              "ms_per_step": e0.elapsed_time(e1)}
+        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
-    if args.impl == "reference":
+    if args.workload == "batched" and args.impl != "reference":
+        run_batched(args, ws, rank, local)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_kitc(args, ws, rank, local)

@@ -150,6 +150,17 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
 kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
                                  double *out, void *stream);
 
+/* Applies the treecode again with new weights, for the same sources and the
+ * targets of the last kitc_evaluate / kitc_evaluate_forest (an iterative
+ * solver's repeated products with one geometry): modified weights of w, then
+ * the evaluator over the stored target order and interaction lists.  w: device,
+ * n_src x w_in; out: device, n_tgt x w_out.  On a non-default stream the launch
+ * sequence is captured into a CUDA graph at the first call for a given (w, out,
+ * stream) and replayed afterwards (the first call also runs it once without
+ * capture).  Synchronizes `stream` once to read the evaluator's error flag.
+ * KITC_ERR_STATE if no evaluation has been done on the handle. */
+kitc_status kitc_apply(kitc_tree t, const double *w, double *out, void *stream);
+
 /* Eq. N-body by direct summation over all sources (self term included;
  * with eps = 0 a pair at r = 0 is skipped).  All pointers device.  Uses
  * p->kernel, p->eps, p->precision and p->target_batch; the tree

@@ -23,7 +23,13 @@ struct kitc_tree_s {
     WeightsDev wts;
     ListsDev lists;
     DevBuf flags;            // int [4]: work counter, error flag
-    bool has_weights = false, evaluated = false;
+    bool has_weights = false, evaluated = false, pairs_planned = false;
+    EvalArgs last{};          // evaluator arguments of the last evaluate (reused by kitc_apply)
+    // CUDA graph of weights + packing + evaluator (kitc_apply)
+    cudaGraphExec_t graph = nullptr;
+    const void *graph_w = nullptr, *graph_out = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int64_t graph_launches = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[8] = {};
     bool ev_ok = false;
@@ -168,6 +174,7 @@ void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
 void free_handle(kitc_tree t)
 {
     cudaStream_t s = t->stream;
+    if (t->graph) cudaGraphExecDestroy(t->graph);
     t->src.release(s);
     t->tgt.release(s);
     t->wts.release(s);
@@ -274,22 +281,43 @@ kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int 
     return build_impl(src_xyz, tot, counts, num_systems, p, stream, out);
 }
 
+// Kernel launches of the weights pass and the evaluator records; the host-side
+// plans must exist (prepare_weights).
+static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
+{
+    const bool mixed = t->p.precision == KITC_MIXED;
+    KITC_TRY(weights_launch(t->src, w, t->wts, s));
+    if (mixed && t->p.kernel == KITC_STOKESLET) {  // FP32x2 evaluator records
+        KITC_TRY(pack_proxy_pairs(t->src, t->wts, s));
+        KITC_TRY(pack_pairs_launch(&t->src, nullptr, w, t->src.n, t->wts.pair_ranges, s,
+                                   t->wts.src, t->wts.pbegin));
+    } else {
+        KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
+        KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
+    }
+    return KITC_OK;
+}
+
+static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
+{
+    KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
+    if (t->p.precision == KITC_MIXED && t->p.kernel == KITC_STOKESLET && !t->pairs_planned) {
+        KITC_TRY(pack_pairs_plan(&t->src, t->src.n, s, t->wts.src, t->wts.pbegin,
+                                 &t->wts.pair_ranges));
+        t->pairs_planned = true;
+    }
+    return KITC_OK;
+}
+
 kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
 {
     if (!t || !device_accessible(w)) return KITC_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     t->stream = s;
-    bool mixed = t->p.precision == KITC_MIXED;
     t->has_weights = false;
     record(t, 2, s);
-    KITC_TRY(weights_compute(t->src, w, t->win, t->p.degree, t->p.weights, s, t->wts));
-    if (mixed && t->p.kernel == KITC_STOKESLET) {  // FP32x2 evaluator records
-        KITC_TRY(pack_proxy_pairs(t->src, t->wts, s));
-        KITC_TRY(pack_pairs(&t->src, nullptr, w, t->src.n, s, t->wts.src, t->wts.pbegin));
-    } else {
-        KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
-        KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
-    }
+    KITC_TRY(prepare_weights(t, s));
+    KITC_TRY(launch_weights(t, w, s));
     record(t, 3, s);
     t->has_weights = true;
     t->stage_done[1] = true;
@@ -343,6 +371,7 @@ static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_t
     KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
     KITC_TRY(evaluate_launch(p.kernel, p.precision == KITC_MIXED, a, s));
     record(t, 6, s);
+    t->last = a;
     KITC_TRY(read_error_flag(t->flags.as<int>() + 1, s));
     t->evaluated = true;
     t->stage_done[2] = t->stage_done[3] = true;
@@ -586,6 +615,58 @@ void kitc_free_tree(kitc_tree t)
 }
 
 int64_t kitc_launch_count(void) { return g_launches.load(); }
+
+kitc_status kitc_apply(kitc_tree t, const double *w, double *out, void *stream)
+{
+    if (!t || !device_accessible(w) || !device_accessible(out)) return KITC_ERR_INVALID_ARG;
+    if (!t->evaluated) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t->stream = s;
+    EvalArgs a = t->last;
+    a.out = out;
+    const bool mixed = t->p.precision == KITC_MIXED;
+    auto body = [&]() -> kitc_status {
+        KITC_TRY(launch_weights(t, w, s));
+        KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
+        return evaluate_launch(t->p.kernel, mixed, a, s);
+    };
+    KITC_TRY(prepare_weights(t, s));
+    if (!s) {  // the legacy default stream cannot be captured: launch directly
+        KITC_TRY(body());
+    } else {
+        if (!t->graph || t->graph_w != w || t->graph_out != out || t->graph_stream != s) {
+            if (t->graph) {
+                cudaGraphExecDestroy(t->graph);
+                t->graph = nullptr;
+            }
+            KITC_TRY(body());  // eager run: sets every kernel attribute before the capture
+            int64_t l0 = g_launches.load();
+            KITC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            kitc_status st = body();
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st != KITC_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return st != KITC_OK ? st : kitc_from_cuda(e);
+            }
+            e = cudaGraphInstantiate(&t->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                t->graph = nullptr;
+                return kitc_from_cuda(e);
+            }
+            t->graph_launches = g_launches.load() - l0;
+            t->graph_w = w;
+            t->graph_out = out;
+            t->graph_stream = s;
+        } else {
+            g_launches.fetch_add(t->graph_launches);
+        }
+        KITC_CUDA(cudaGraphLaunch(t->graph, s));
+    }
+    t->has_weights = true;
+    return read_error_flag(t->flags.as<int>() + 1, s);
+}
 
 kitc_status kitc_watchdog_selftest(int limit_ms, void *stream)
 {

@@ -101,7 +101,12 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
 // records the evaluator streams.
 // ---------------------------------------------------------------------------
 struct WeightsDev {
-    int degree = 0, win = 0;
+    int degree = 0, win = 0, mode = 0;
+    // plan of the weights pass (weights_plan), reused by weights_launch
+    bool planned = false, upward = false;
+    size_t nitems = 0, smem = 0;
+    int acc = 1, npass = 1, sb = 8;
+    int pair_ranges = 0;  // ranges of the paired records (pack_pairs_plan)
     DevBuf fhat;      // double [nclus][P][win]
     DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
     DevBuf src;       // evaluator records of the sources in tree order
@@ -120,6 +125,9 @@ void cheb_cos_table(int n, double *t);
 
 kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree, int mode,
                             cudaStream_t s, WeightsDev &wd);
+kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaStream_t s,
+                         WeightsDev &wd);
+kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &wd, cudaStream_t s);
 kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
                          int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out);
 kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s);
@@ -128,6 +136,10 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
 kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
                        cudaStream_t s, DevBuf &out, DevBuf &pbegin);
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
+kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
+                            DevBuf &pbegin, int *nranges);
+kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
+                              int64_t n, int nranges, cudaStream_t s, DevBuf &out, DevBuf &pbegin);
 // Direct-sum source records written to caller-provided device memory (no
 // allocation); pairs selects the paired FP32x2 format, range3 is 3 int32 of
 // device scratch used by that format.

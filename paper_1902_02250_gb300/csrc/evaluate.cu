@@ -43,6 +43,7 @@ enum { F_FIRST_BATCH = 1, F_LAST_BATCH = 2, F_FIRST_ENTRY = 4, F_LAST_ENTRY = 8 
 struct TileMeta {
     int kind, flags, batch, id;
     int a, b;        // far: k1 planes [a, b); near: source slots [a, b)
+    int seq, pad;    // position of the tile within its batch (fixes the work split)
     uint64_t mask;   // targets of the batch that use this entry
     dvec4 lo, hi;    // far: the cluster's box (read ahead by the producer)
 };
@@ -339,7 +340,10 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
             TileMeta pend{};
             const unsigned char *psrc = nullptr;
             uint32_t pbytes = 0;
-            auto push = [&](const TileMeta &m, const unsigned char *src, uint32_t bytes) -> bool {
+            int tseq = 0;
+            auto push = [&](const TileMeta &m0, const unsigned char *src, uint32_t bytes) -> bool {
+                TileMeta m = m0;
+                m.seq = tseq++;
                 if (have) {
                     if (first) pend.flags |= F_FIRST_BATCH;
                     first = false;
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     for (int k1 = 0; k1 < np && ok; k1 += planes_max) {
                         int k2 = min(np, k1 + planes_max);
                         TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
-                                   b, c, k1, k2, mk, lo, hi};
+                                   b, c, k1, k2, 0, 0, mk, lo, hi};
                         ok = push(m, pxb + (size_t)c * np * plane_bytes + (size_t)k1 * plane_bytes,
                                   (uint32_t)((k2 - k1) * plane_bytes));
                     }
@@ -378,7 +382,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     for (int q = p0; q < p1 && ok; q += near_max) {
                         int q1 = min(p1, q + near_max);
                         TileMeta m{K_NEAR, (q == p0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
-                                   b, c, q, q1, mk, zero4, zero4};
+                                   b, c, q, q1, 0, 0, mk, zero4, zero4};
                         ok = push(m, srcb + (size_t)q * near_unit, (uint32_t)((q1 - q) * near_unit));
                     }
                 }
@@ -387,20 +391,20 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                 for (int64_t q = 0; q < p1 && ok; q += near_max) {
                     int64_t q1 = min(p1, q + (int64_t)near_max);
                     TileMeta m{K_NEAR, (q == 0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
-                               b, -1, (int)q, (int)q1, ~0ull, zero4, zero4};
+                               b, -1, (int)q, (int)q1, 0, 0, ~0ull, zero4, zero4};
                     ok = push(m, srcb + (size_t)q * near_unit, (uint32_t)((q1 - q) * near_unit));
                 }
             }
             if (!ok) break;
             if (!have) {  // no entries: one empty tile closes the batch
-                pend = TileMeta{K_NEAR, F_FIRST_ENTRY | F_LAST_ENTRY, b, -1, 0, 0, 0ull, zero4, zero4};
+                pend = TileMeta{K_NEAR, F_FIRST_ENTRY | F_LAST_ENTRY, b, -1, 0, 0, 0, 0, 0ull, zero4, zero4};
                 psrc = nullptr;
                 pbytes = 0;
             }
             pend.flags |= F_LAST_BATCH | (first ? F_FIRST_BATCH : 0);
             if (!(ok = emit(pend, psrc, pbytes))) break;
         }
-        if (ok) ok = emit(TileMeta{K_EXIT, 0, -1, -1, 0, 0, 0ull, zero4, zero4}, nullptr, 0);
+        if (ok) ok = emit(TileMeta{K_EXIT, 0, -1, -1, 0, 0, 0, 0, 0ull, zero4, zero4}, nullptr, 0);
         if (!ok) atomicExch(a.err, 1);
         // drain: the last phase of every stage this thread armed must complete
         uint32_t last = it;
@@ -476,6 +480,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
         }
         const TileMeta &mr = meta[s];
         const int kind = mr.kind, flags = mr.flags, batch = mr.batch, ta = mr.a, tb = mr.b;
+        const int rot = mr.seq % NCW;  // depends on the batch only: results are deterministic
         const uint64_t mask = mr.mask;
         if (kind == K_EXIT) break;
         const unsigned char *tile = tiles + (size_t)s * TILE;
@@ -543,7 +548,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     float2 ngz[NPAIR];
 #pragma unroll
                     for (int q = 0; q < NPAIR; ++q) ngz[q] = *reinterpret_cast<const float2 *>(gsf + 36 + 2 * q);
-                    int r = (warp + it) % NCW;
+                    int r = (warp + rot) % NCW;
                     int k1 = ta + r / np, k2 = r % np;  // advanced incrementally below
                     for (; r < rows; r += NCW) {
                         const unsigned char *row = tile + (size_t)r * row_bytes;
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                         uz[t] = fma2(fz, H1, fma2(dz, sv, uz[t]));
                     }
                 };
-                for (int blk = (warp + it) % NCW; blk < nb4; blk += NCW) {
+                for (int blk = (warp + rot) % NCW; blk < nb4; blk += NCW) {
 #pragma unroll
                     for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
                     if (blk < nfull) {
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
             }
             const R *gx = gs, *gy = gs + (KITC_MAX_DEGREE + 1), *gz = gs + 2 * (KITC_MAX_DEGREE + 1);
             const int rows = (tb - ta) * np;
-            for (int r = (warp + it) % NCW; r < rows; r += NCW) {
+            for (int r = (warp + rot) % NCW; r < rows; r += NCW) {
                 const int k1 = ta + r / np, k2 = r % np;
                 const unsigned char *row = tile + (size_t)r * np * PREC;
                 R dx[2], dy[2], rxy[2];
@@ -729,7 +734,7 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     }
                 }
             };
-            for (int blk = (warp + it) % NCW; blk < nb8; blk += NCW) {
+            for (int blk = (warp + rot) % NCW; blk < nb8; blk += NCW) {
                 if (blk < nfull) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) body(blk * 8 + j);

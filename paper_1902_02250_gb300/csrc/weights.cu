@@ -371,8 +371,14 @@ template <int ACC>
 kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
                           const TreeDev &t, const double *w, int win, int sb, double *partial)
 {
-    KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+    static size_t configured[64] = {0};  // largest dynamic shared memory set, per device
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || smem > configured[dev]) {
+        KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (dev >= 0 && dev < 64) configured[dev] = smem;
+    }
     kitc_count_launch();
     k_weights_chunk<ACC><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
                                                 t.perm.as<int32_t>(), w, win, t.lo.as<dvec4>(),
@@ -390,9 +396,14 @@ size_t upward_smem(int np, int win)
     return sizeof(double) * (3 * pw + 3 * (size_t)np * np);
 }
 
-kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree, int mode,
-                            cudaStream_t s, WeightsDev &wd)
+// Host-side plan of the weights pass for one tree: work items, buffer sizes and
+// launch shapes.  Done once per tree; weights_launch then only launches kernels
+// (so that it can be captured in a CUDA graph).
+kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaStream_t s,
+                         WeightsDev &wd)
 {
+    if (wd.planned && wd.degree == degree && wd.win == win && wd.mode == mode) return KITC_OK;
+    wd.planned = false;
     const int np = degree + 1;
     const int pwin = np * np * np * win;
     const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_smem(np, win) <= UP_SMEM_MAX;
@@ -424,33 +435,52 @@ kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int
                               cudaMemcpyHostToDevice, s));
     KITC_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (t.nclus + 1),
                               cudaMemcpyHostToDevice, s));
-    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * nitems, s));
+    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * std::max<size_t>(nitems, 1), s));
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
     // the host vectors must outlive the copies above
     KITC_CUDA(cudaStreamSynchronize(s));
     size_t per = sizeof(double) * (3 * np + np * np + np * win);
     int sb = 64;
     while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
-    size_t smem = per * sb;
+    wd.sb = sb;
+    wd.smem = per * sb;
     // the fewest accumulators per thread that cover the outputs in one pass
-    int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
-    int npass = (pwin + acc * WT - 1) / (acc * WT);
-    dim3 grid((unsigned)nitems, (unsigned)npass);
-    const Cheb cb = make_cheb(degree);
+    wd.acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
+    wd.npass = (pwin + wd.acc * WT - 1) / (wd.acc * WT);
+    wd.nitems = nitems;
+    wd.upward = upward;
+    if (upward)
+        KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)upward_smem(np, win)));
+    wd.degree = degree;
+    wd.win = win;
+    wd.mode = mode;
+    wd.planned = true;
+    return KITC_OK;
+}
+
+kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &wd, cudaStream_t s)
+{
+    if (!wd.planned) return KITC_ERR_STATE;
+    const int np = wd.degree + 1, win = wd.win;
+    const int pwin = np * np * np * win;
+    Item *d_items = wd.items.as<Item>();
+    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + wd.nitems);
+    const Cheb cb = make_cheb(wd.degree);
     static constexpr ChunkLauncher table[ACC_MAX] = {
         &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
         &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
         &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
         &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
-    if (nitems > 0)
-        KITC_TRY(table[acc - 1](grid, smem, s, cb, d_items, t, w_user, win, sb, wd.partial.as<double>()));
+    if (wd.nitems > 0)
+        KITC_TRY(table[wd.acc - 1](dim3((unsigned)wd.nitems, (unsigned)wd.npass), wd.smem, s, cb,
+                                   d_items, t, w_user, win, wd.sb, wd.partial.as<double>()));
     kitc_count_launch();
     k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
                                              wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
-    if (upward) {
+    if (wd.upward) {
         size_t us = upward_smem(np, win);
-        KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)us));
         // deepest parents first: level L needs every child at level L + 1
         for (int L = (int)t.level_start.size() - 2; L >= 0; --L) {
             int lb = t.level_start[L], le = t.level_start[L + 1];
@@ -461,9 +491,14 @@ kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int
             KITC_CUDA(cudaGetLastError());
         }
     }
-    wd.degree = degree;
-    wd.win = win;
     return KITC_OK;
+}
+
+kitc_status weights_compute(const TreeDev &t, const double *w_user, int win, int degree, int mode,
+                            cudaStream_t s, WeightsDev &wd)
+{
+    KITC_TRY(weights_plan(t, win, degree, mode, s, wd));
+    return weights_launch(t, w_user, wd, s);
 }
 
 kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s)
@@ -497,8 +532,11 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
     return KITC_OK;
 }
 
-kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
-                       cudaStream_t s, DevBuf &out, DevBuf &pbegin)
+// Host-side plan of the paired records: one range per leaf (or one for a
+// direct sum), the first pair of each range, uploaded once into pbegin as
+// [cluster -> first pair (nclus) | range begin | range end | first pair].
+kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
+                            DevBuf &pbegin, int *nranges)
 {
     std::vector<int32_t> rb, re, pb;
     int nclus = t ? t->nclus : 1;
@@ -529,21 +567,39 @@ kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w
     size_t nr = rb.size();
     KITC_TRY(out.reserve((size_t)80 * npairs + 16, s));
     KITC_TRY(pbegin.reserve(sizeof(int32_t) * (3 * nr + nclus) + 16, s));
-    int32_t *d = pbegin.as<int32_t>();
     std::vector<int32_t> all;
     all.insert(all.end(), cpb.begin(), cpb.end());
     all.insert(all.end(), rb.begin(), rb.end());
     all.insert(all.end(), re.begin(), re.end());
     all.insert(all.end(), pb.begin(), pb.end());
-    KITC_CUDA(cudaMemcpyAsync(d, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
-    kitc_count_launch();
-    k_pack_pairs<<<(unsigned)nr, 256, 0, s>>>(d + nclus, d + nclus + nr, d + nclus + 2 * nr, n,
-                                              t ? t->xs.as<double>() : nullptr,
-                                              t ? t->perm.as<int32_t>() : nullptr, xyz_user, w_user,
-                                              out.as<float>());
-    KITC_CUDA(cudaGetLastError());
-    KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copy
+    KITC_CUDA(cudaMemcpyAsync(pbegin.ptr, all.data(), sizeof(int32_t) * all.size(),
+                              cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaStreamSynchronize(s));  // the host vector must outlive the copy
+    *nranges = (int)nr;
     return KITC_OK;
+}
+
+kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
+                              int64_t n, int nranges, cudaStream_t s, DevBuf &out, DevBuf &pbegin)
+{
+    int nclus = t ? t->nclus : 1;
+    int32_t *d = pbegin.as<int32_t>();
+    kitc_count_launch();
+    k_pack_pairs<<<(unsigned)nranges, 256, 0, s>>>(d + nclus, d + nclus + nranges,
+                                                   d + nclus + 2 * nranges, n,
+                                                   t ? t->xs.as<double>() : nullptr,
+                                                   t ? t->perm.as<int32_t>() : nullptr, xyz_user,
+                                                   w_user, out.as<float>());
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
+                       cudaStream_t s, DevBuf &out, DevBuf &pbegin)
+{
+    int nr = 0;
+    KITC_TRY(pack_pairs_plan(t, n, s, out, pbegin, &nr));
+    return pack_pairs_launch(t, xyz_user, w_user, n, nr, s, out, pbegin);
 }
 
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)

@@ -73,7 +73,7 @@ class Params:
 
 _lib = None
 SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kitc_evaluate",
-           "kitc_evaluate_forest", "kitc_direct", "kitc_direct_noalloc",
+           "kitc_evaluate_forest", "kitc_apply", "kitc_direct", "kitc_direct_noalloc",
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
@@ -97,6 +97,7 @@ def lib():
         L.kitc_build_tree.argtypes = [P, I64, PP, P, ctypes.POINTER(P)]
         L.kitc_build_forest.argtypes = [P, P, I, PP, P, ctypes.POINTER(P)]
         L.kitc_evaluate_forest.argtypes = [P, P, P, P, P]
+        L.kitc_apply.argtypes = [P, P, P, P]
         L.kitc_modified_weights.argtypes = [P, P, P]
         L.kitc_evaluate.argtypes = [P, P, I64, P, P]
         L.kitc_direct.argtypes = [P, I64, P, P, I64, PP, P, P]
@@ -116,7 +117,7 @@ def lib():
         L.kitc_watchdog_selftest.argtypes = [I, P]
         L.kitc_launch_count.argtypes = []
         L.kitc_launch_count.restype = I64
-        for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest",
+        for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest", "kitc_apply",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_direct_noalloc",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
@@ -287,6 +288,14 @@ def kitc_evaluate(tree, tgt_xyz, out=None, stream=None):
         out = torch.empty((tgt_xyz.shape[0], wout), dtype=torch.float64, device=tgt_xyz.device)
     _check(lib().kitc_evaluate(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
                                _dptr(out, wout, "out"), _stream(stream)), "kitc_evaluate")
+    return out
+
+
+def kitc_apply(tree, w, out, stream=None):
+    """New weights, same sources and targets as the last evaluate (CUDA-graph replay)."""
+    _check(lib().kitc_apply(tree.handle, _dptr(w, kernel_win(tree.params.kernel), "w"),
+                            _dptr(out, kernel_wout(tree.params.kernel), "out"), _stream(stream)),
+           "kitc_apply")
     return out
 
 

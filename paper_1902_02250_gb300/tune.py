@@ -78,6 +78,44 @@ def tune(xd, fd, base, budget, idx, ref, thetas=THETAS, degrees=DEGREES, leaves=
     return best, records
 
 
+def time_forest(xd, fd, counts, p, out, reps=2):
+    """Milliseconds of one forest build + weights + evaluate (best of reps after a warm-up)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    best = float("inf")
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t = K.kitc_build_forest(xd, counts, p)
+        try:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate_forest(t, xd, counts, out)
+        finally:
+            t.free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune_forest(xd, fd, counts, base, leaves=(250, 500, 1000, 2000), batches=(32, 64), log=None):
+    """Fastest leaf size N0 and target-batch size for a forest at fixed theta, n."""
+    import torch
+    out = torch.empty((xd.shape[0], K.kernel_wout(base.kernel)), dtype=torch.float64, device=xd.device)
+    best = None
+    for leaf, b in itertools.product(leaves, batches):
+        p = K.Params(theta=base.theta, degree=base.degree, leaf_size=leaf, eps=base.eps,
+                     kernel=base.kernel, precision=base.precision, mac=base.mac, target_batch=b,
+                     weights=base.weights)
+        ms = time_forest(xd, fd, counts, p, out)
+        if log:
+            log(dict(leaf_size=leaf, target_batch=b, ms=ms))
+        if best is None or ms < best[1]:
+            best = (p, ms)
+    return best
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()

@@ -325,3 +325,58 @@ def test_forest_of_one_equals_tree(K):
     b = K.kitc_evaluate_forest(t, dev(x), [len(x)]).cpu().numpy()
     t.free()
     assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------ kitc_apply
+@pytest.mark.parametrize("precision", [0, 1])
+def test_apply_replays_with_new_weights(K, precision):
+    import torch
+    x, f1 = wl.uniform_cube(20000, 54)
+    _, f2 = wl.uniform_cube(20000, 55)
+    p = K.Params(theta=0.7, degree=6, leaf_size=500, eps=0.005, precision=precision,
+                 mac=K.MAC_BATCH)
+    xd = dev(x)
+    t = K.kitc_build_tree(xd, p)
+    K.kitc_modified_weights(t, dev(f1))
+    K.kitc_evaluate(t, xd)
+    w = dev(f2)
+    out = torch.empty((len(x), 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        K.kitc_apply(t, w, out)           # eager run + capture + replay
+        a = out.cpu().numpy()
+        w.copy_(dev(f1))                 # same buffer, new contents: pure replay
+        K.kitc_apply(t, w, out)
+        b = out.cpu().numpy()
+    t.free()
+    ref2, _ = gpu_treecode(K, x, f2, theta=0.7, degree=6, leaf_size=500, eps=0.005,
+                           precision=precision, mac=K.MAC_BATCH)
+    ref1, _ = gpu_treecode(K, x, f1, theta=0.7, degree=6, leaf_size=500, eps=0.005,
+                           precision=precision, mac=K.MAC_BATCH)
+    assert np.array_equal(a, ref2) and np.array_equal(b, ref1)
+
+
+def test_apply_on_forest_and_before_evaluate(K):
+    import torch
+    systems = _systems(5, 56, 500, 5000)
+    counts = [len(s[0]) for s in systems]
+    x = np.vstack([s[0] for s in systems])
+    f = np.vstack([s[1] for s in systems])
+    p = K.Params(theta=0.7, degree=5, leaf_size=300, eps=0.01, precision=K.MIXED)
+    t = K.kitc_build_forest(dev(x), counts, p)
+    out = torch.empty((len(x), 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(K.KitcError) as e:
+        K.kitc_apply(t, dev(f), out)
+    assert e.value.status == 5
+    K.kitc_modified_weights(t, dev(np.zeros_like(f)))
+    K.kitc_evaluate_forest(t, dev(x), counts)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        K.kitc_apply(t, dev(f), out)
+        got = out.cpu().numpy()
+    t2 = K.kitc_build_forest(dev(x), counts, p)
+    K.kitc_modified_weights(t2, dev(f))
+    ref = K.kitc_evaluate_forest(t2, dev(x), counts).cpu().numpy()
+    t.free()
+    t2.free()
+    assert np.array_equal(got, ref)
