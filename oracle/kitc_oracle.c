@@ -460,31 +460,43 @@ void or_modified_weights(const or_tree *t, const double *x, const double *w,
 /* Sec. 6, Algorithm 2: the treecode.                                        */
 /* ------------------------------------------------------------------------ */
 
+#define OR_SMAX (3 * 17)  /* grid coordinates stored per cluster (n <= 16) */
+
 typedef struct {
     const or_tree *t;
-    const double *x, *w;   /* sources and weights, user order           */
-    const double *fhat;    /* modified weights, [cluster][P][win]       */
-    const double *s;       /* mapped Chebyshev points, [cluster][3][n+1] */
+    const double *x, *w;   /* sources and weights, user order                    */
+    const double *fhat;    /* modified weights, [cluster][P][win]                */
+    const double *s;       /* mapped Chebyshev points, [cluster][3][n_c+1]       */
     int n, kernel, win, wout;
     double eps, theta;
+    const int32_t *deg;    /* per-cluster degree n_c, or NULL for n everywhere   */
+    const int64_t *foff;   /* with deg: offset (doubles) of each cluster's fhat */
+    int64_t bad;           /* accepted clusters without weights (deg 0)          */
 } tc_ctx;
+
+static int cluster_degree(const tc_ctx *q, int64_t c)
+{
+    return q->deg ? q->deg[c] : q->n;
+}
 
 static void tc_points(tc_ctx *q, double **s_out)
 {
-    int np = q->n + 1;
-    double *s = malloc(sizeof(double) * 3 * np * (q->t->nclus > 0 ? q->t->nclus : 1));
-    for (int64_t c = 0; c < q->t->nclus; ++c) or_cluster_points(q->t, c, q->n, s + 3 * np * c);
+    double *s = malloc(sizeof(double) * OR_SMAX * (q->t->nclus > 0 ? q->t->nclus : 1));
+    for (int64_t c = 0; c < q->t->nclus; ++c) {
+        int n = cluster_degree(q, c);
+        if (n > 0) or_cluster_points(q->t, c, n, s + OR_SMAX * c);
+    }
     *s_out = s;
 }
 
-/* Eq. pc_approximation_3D: u += sum_k k(x, s_k) fhat_k over the (n+1)^3
+/* Eq. pc_approximation_3D: u += sum_k k(x, s_k) fhat_k over the (n_c+1)^3
  * grid points of cluster c. */
 static void far_field(const tc_ctx *q, int64_t c, const double *x, double *u)
 {
-    int np = q->n + 1;
+    int np = cluster_degree(q, c) + 1;
     int64_t P = (int64_t)np * np * np;
-    const double *s = q->s + 3 * np * c;
-    const double *fh = q->fhat + c * P * q->win;
+    const double *s = q->s + OR_SMAX * c;
+    const double *fh = q->fhat + (q->foff ? q->foff[c] : c * P * q->win);
     for (int k1 = 0; k1 < np; ++k1)
         for (int k2 = 0; k2 < np; ++k2)
             for (int k3 = 0; k3 < np; ++k3) {
@@ -507,7 +519,7 @@ static void near_field(const tc_ctx *q, int64_t c, const double *x, double *u)
  * cnt[1] += far grid points, cnt[2] += accepted clusters, cnt[3] += leaves
  * summed directly, cnt[4] += sources inside accepted clusters (so that
  * cnt[0] + cnt[4] counts every source once per target). */
-static void compute_velocity(const tc_ctx *q, const double *x, int64_t c, double *u,
+static void compute_velocity(tc_ctx *q, const double *x, int64_t c, double *u,
                              int64_t *cnt)
 {
     double yc[3], r;
@@ -515,8 +527,13 @@ static void compute_velocity(const tc_ctx *q, const double *x, int64_t c, double
     double d0 = x[0] - yc[0], d1 = x[1] - yc[1], d2 = x[2] - yc[2];
     double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     if (r <= q->theta * R) {                         /* Eq. MAC */
+        int np = cluster_degree(q, c) + 1;
+        if (np < 2) {  /* caller error: no modified weights for an accepted cluster */
+#pragma omp atomic
+            q->bad++;
+            return;
+        }
         far_field(q, c, x, u);
-        int np = q->n + 1;
         cnt[1] += (int64_t)np * np * np;
         cnt[2] += 1;
         cnt[4] += q->t->end[c] - q->t->begin[c];
@@ -534,12 +551,13 @@ static void compute_velocity(const tc_ctx *q, const double *x, int64_t c, double
  * for each target x_i, compute_velocity(x_i, root).  tgt: nt x 3, out:
  * nt x wout (user order, overwritten).  counts (may be NULL): five totals as
  * in compute_velocity. */
-void or_treecode(const or_tree *t, const double *x, const double *w, const double *fhat,
-                 int n, int kernel, double eps, double theta,
-                 const double *tgt, int64_t nt, double *out, int64_t *counts)
+static int64_t treecode_impl(const or_tree *t, const double *x, const double *w,
+                             const double *fhat, int n, const int32_t *deg, const int64_t *foff,
+                             int kernel, double eps, double theta, const double *tgt, int64_t nt,
+                             double *out, int64_t *counts)
 {
     tc_ctx q = {t, x, w, fhat, NULL, n, kernel, or_kernel_win(kernel),
-                or_kernel_wout(kernel), eps, theta};
+                or_kernel_wout(kernel), eps, theta, deg, foff, 0};
     double *s;
     tc_points(&q, &s);
     q.s = s;
@@ -559,6 +577,24 @@ void or_treecode(const or_tree *t, const double *x, const double *w, const doubl
     if (counts)
         for (int k = 0; k < 5; ++k) counts[k] = tot[k];
     free(s);
+    return q.bad;
+}
+
+void or_treecode(const or_tree *t, const double *x, const double *w, const double *fhat,
+                 int n, int kernel, double eps, double theta,
+                 const double *tgt, int64_t nt, double *out, int64_t *counts)
+{
+    treecode_impl(t, x, w, fhat, n, NULL, NULL, kernel, eps, theta, tgt, nt, out, counts);
+}
+
+/* Algorithm 2 with a degree n_c per cluster (deg[c]; the weights of cluster c
+ * start at fhat + foff[c]).  Returns the number of (target, cluster) far
+ * interactions that met a cluster with deg 0, which must be 0. */
+int64_t or_treecode_var(const or_tree *t, const double *x, const double *w, const double *fhat,
+                        const int32_t *deg, const int64_t *foff, int kernel, double eps,
+                        double theta, const double *tgt, int64_t nt, double *out, int64_t *counts)
+{
+    return treecode_impl(t, x, w, fhat, 0, deg, foff, kernel, eps, theta, tgt, nt, out, counts);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -622,16 +658,17 @@ int64_t or_num_batches(int64_t nt, int batch)
  *   far_list, near_list  concatenated per-batch lists in traversal order,
  *              written only when their capacity (far_cap, near_cap) holds
  *              the totals. */
-void or_treecode_batch(const or_tree *t, const double *x, const double *w,
-                       const double *fhat, int n, int kernel, double eps, double theta,
-                       const double *tgt, int64_t nt, int batch, int tgt_leaf,
-                       int lists_only, const unsigned char *sel, double *out,
-                       int64_t *counts, int64_t *tperm,
-                       int64_t *nfar, int64_t *nnear, int64_t *far_list, int64_t far_cap,
-                       int64_t *near_list, int64_t near_cap)
+static void treecode_batch_impl(const or_tree *t, const double *x, const double *w,
+                                const double *fhat, int n, const int32_t *deg,
+                                const int64_t *foff, int kernel, double eps, double theta,
+                                const double *tgt, int64_t nt, int batch, int tgt_leaf,
+                                int lists_only, const unsigned char *sel, double *out,
+                                int64_t *counts, int64_t *tperm, int64_t *nfar, int64_t *nnear,
+                                int64_t *far_list, int64_t far_cap, int64_t *near_list,
+                                int64_t near_cap)
 {
     tc_ctx q = {t, x, w, fhat, NULL, n, kernel, or_kernel_win(kernel),
-                or_kernel_wout(kernel), eps, theta};
+                or_kernel_wout(kernel), eps, theta, deg, foff, 0};
     double *s;
     tc_points(&q, &s);
     q.s = s;
@@ -656,12 +693,16 @@ void or_treecode_batch(const or_tree *t, const double *x, const double *w,
                 }
             blist *L = &lists[b];
             if (t->nclus > 0) batch_lists(&q, blo, bhi, 0, L);
-            int np = n + 1;
             int64_t npair = 0;
             for (int64_t m = 0; m < L->nnear; ++m)
                 npair += t->end[L->near[m]] - t->begin[L->near[m]];
             loc[0] += npair * (s1 - s0);
-            loc[1] += (int64_t)np * np * np * L->nfar * (s1 - s0);
+            int64_t pts = 0;
+            for (int64_t m = 0; m < L->nfar; ++m) {
+                int npc = cluster_degree(&q, L->far[m]) + 1;
+                pts += (int64_t)npc * npc * npc;
+            }
+            loc[1] += pts * (s1 - s0);
             int64_t nsrc = 0;
             for (int64_t m = 0; m < L->nfar; ++m)
                 nsrc += t->end[L->far[m]] - t->begin[L->far[m]];
@@ -709,4 +750,57 @@ void or_treecode_batch(const or_tree *t, const double *x, const double *w,
     free(lists);
     or_tree_free(tt);
     free(s);
+}
+
+void or_treecode_batch(const or_tree *t, const double *x, const double *w,
+                       const double *fhat, int n, int kernel, double eps, double theta,
+                       const double *tgt, int64_t nt, int batch, int tgt_leaf,
+                       int lists_only, const unsigned char *sel, double *out,
+                       int64_t *counts, int64_t *tperm,
+                       int64_t *nfar, int64_t *nnear, int64_t *far_list, int64_t far_cap,
+                       int64_t *near_list, int64_t near_cap)
+{
+    treecode_batch_impl(t, x, w, fhat, n, NULL, NULL, kernel, eps, theta, tgt, nt, batch,
+                        tgt_leaf, lists_only, sel, out, counts, tperm, nfar, nnear, far_list,
+                        far_cap, near_list, near_cap);
+}
+
+/* Batch-MAC variant with a degree per cluster (see or_treecode_var). */
+void or_treecode_batch_var(const or_tree *t, const double *x, const double *w,
+                           const double *fhat, const int32_t *deg, const int64_t *foff, int kernel,
+                           double eps, double theta, const double *tgt, int64_t nt, int batch,
+                           int tgt_leaf, const unsigned char *sel, double *out, int64_t *counts)
+{
+    treecode_batch_impl(t, x, w, fhat, 0, deg, foff, kernel, eps, theta, tgt, nt, batch, tgt_leaf,
+                        0, sel, out, counts, NULL, NULL, NULL, NULL, 0, NULL, 0);
+}
+
+/* Eq. modified_weights with a degree n_c per cluster: cluster c (deg[c] > 0)
+ * writes (n_c+1)^3 x win values at fhat + foff[c]; clusters with deg 0 get none. */
+void or_modified_weights_var(const or_tree *t, const double *x, const double *w, int win,
+                             const int32_t *deg, const int64_t *foff, double *fhat)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < t->nclus; ++c) {
+        int n = deg[c];
+        if (n <= 0) continue;
+        int np = n + 1;
+        int64_t P = (int64_t)np * np * np;
+        double s[3 * 17], wk[17], L[3][17];
+        or_cluster_points(t, c, n, s);
+        or_bary_weights(n, wk);
+        double *fh = fhat + foff[c];
+        for (int64_t q = 0; q < P * win; ++q) fh[q] = 0.0;
+        for (int64_t p = t->begin[c]; p < t->end[c]; ++p) {
+            int64_t j = t->perm[p];
+            for (int l = 0; l < 3; ++l) or_bary_basis(n, s + l * np, wk, x[3 * j + l], L[l]);
+            for (int k1 = 0; k1 < np; ++k1)
+                for (int k2 = 0; k2 < np; ++k2)
+                    for (int k3 = 0; k3 < np; ++k3) {
+                        double prod = L[0][k1] * L[1][k2] * L[2][k3];
+                        double *o = fh + ((int64_t)(k1 * np + k2) * np + k3) * win;
+                        for (int q = 0; q < win; ++q) o[q] += prod * w[win * j + q];
+                    }
+        }
+    }
 }

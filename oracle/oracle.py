@@ -62,6 +62,10 @@ def lib():
         L.or_cluster_points.argtypes = [P, I64, I, P]
         L.or_modified_weights.argtypes = [P, P, P, I, I, P]
         L.or_treecode.argtypes = [P, P, P, P, I, I, D, D, P, I64, P, P]
+        L.or_modified_weights_var.argtypes = [P, P, P, I, P, P, P]
+        L.or_treecode_var.argtypes = [P, P, P, P, P, P, I, D, D, P, I64, P, P]
+        L.or_treecode_var.restype = I64
+        L.or_treecode_batch_var.argtypes = [P, P, P, P, P, P, I, D, D, P, I64, I, I, P, P, P]
         L.or_num_batches.argtypes = [I64, I]
         L.or_num_batches.restype = I64
         L.or_treecode_batch.argtypes = [P, P, P, P, I, I, D, D, P, I64, I, I, I, P, P, P, P,
@@ -199,6 +203,56 @@ class Tree:
         fhat = np.empty((self.nclusters, np1, np1, np1, win))
         lib().or_modified_weights(self._h, _p(self.x), _p(w), win, n, _p(fhat))
         return fhat
+
+    def weight_offsets(self, deg, win):
+        """Offsets (in doubles) of each cluster's weights for per-cluster degrees."""
+        deg = np.asarray(deg, np.int64)
+        sizes = np.where(deg > 0, (deg + 1) ** 3 * win, 0)
+        return np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64), int(sizes.sum())
+
+    def modified_weights_var(self, w, deg):
+        """Eq. modified_weights with degree deg[c] per cluster (0: none).
+        Returns (flat fhat, offsets)."""
+        w = _f64(w, (self.n, -1))
+        win = w.shape[1]
+        deg = np.ascontiguousarray(deg, np.int32)
+        foff, tot = self.weight_offsets(deg, win)
+        fhat = np.zeros(max(tot, 1))
+        lib().or_modified_weights_var(self._h, _p(self.x), _p(w), win, _p(deg), _p(foff), _p(fhat))
+        return fhat, foff
+
+    def treecode_var(self, w, fhat, deg, foff, kernel, eps, theta, tgt):
+        """Algorithm 2 with a degree per cluster; returns (out, counts, bad) where
+        bad counts far interactions with clusters of degree 0 (must be 0)."""
+        w = _f64(w, (self.n, kernel_win(kernel)))
+        deg = np.ascontiguousarray(deg, np.int32)
+        foff = np.ascontiguousarray(foff, np.int64)
+        tgt = _f64(tgt, (-1, 3))
+        out = np.empty((len(tgt), kernel_wout(kernel)))
+        cnt = np.zeros(5, np.int64)
+        bad = lib().or_treecode_var(self._h, _p(self.x), _p(w), _p(_f64(fhat)), _p(deg), _p(foff),
+                                    kernel, float(eps), float(theta), _p(tgt), len(tgt), _p(out),
+                                    _p(cnt))
+        return out, cnt, bad
+
+    def treecode_batch_var(self, w, fhat, deg, foff, kernel, eps, theta, tgt, batch, tgt_leaf,
+                           select=None):
+        """Batch-MAC variant with a degree per cluster; returns (out, counts)."""
+        w = _f64(w, (self.n, kernel_win(kernel)))
+        deg = np.ascontiguousarray(deg, np.int32)
+        foff = np.ascontiguousarray(foff, np.int64)
+        tgt = _f64(tgt, (-1, 3))
+        nt = len(tgt)
+        out = np.empty((nt, kernel_wout(kernel)))
+        cnt = np.zeros(5, np.int64)
+        sel = None
+        if select is not None:
+            sel = np.zeros(nt, np.uint8)
+            sel[np.asarray(select)] = 1
+        lib().or_treecode_batch_var(self._h, _p(self.x), _p(w), _p(_f64(fhat)), _p(deg), _p(foff),
+                                    kernel, float(eps), float(theta), _p(tgt), nt, batch, tgt_leaf,
+                                    _p(sel), _p(out), _p(cnt))
+        return out, cnt
 
     def treecode(self, w, fhat, n, kernel, eps, theta, tgt):
         """Algorithm 2 (per-target MAC).  Returns (out, counts) with counts =

@@ -122,3 +122,45 @@ def test_batch_lists_are_valid(orc, batch):
     # is at least about as accurate
     up, _ = t.treecode(f, fh, 3, ST, 0.01, 0.7, x)
     assert orc.rel_l2(ud, r["out"]) < 1.05 * orc.rel_l2(ud, up)
+
+
+def test_variable_degree_uniform_equals_fixed(orc):
+    x, f = wl.uniform_cube(3000, 31)
+    t = orc.Tree(x, 100)
+    n = 4
+    fh = t.modified_weights(f, n)
+    deg = np.full(t.nclusters, n, np.int32)
+    fv, foff = t.modified_weights_var(f, deg)
+    assert np.array_equal(fv, fh.ravel())
+    u1, c1 = t.treecode(f, fh, n, ST, 0.01, 0.7, x)
+    u2, c2, bad = t.treecode_var(f, fv, deg, foff, ST, 0.01, 0.7, x)
+    assert bad == 0 and np.array_equal(u1, u2) and np.array_equal(c1, c2)
+
+
+def test_variable_degree_polynomial_kernel_exact(orc):
+    # every accepted cluster with n_c >= 3 reproduces the degree-3 test kernel
+    x, f = wl.uniform_cube(3000, 32)
+    t = orc.Tree(x, 60)
+    g = np.random.default_rng(3)
+    deg = g.integers(3, 7, t.nclusters).astype(np.int32)
+    fv, foff = t.modified_weights_var(f, deg)
+    u, cnt, bad = t.treecode_var(f, fv, deg, foff, POLY, 0.0, 0.9, x)
+    assert bad == 0 and cnt[2] > 0
+    # far grid points counted with each cluster's own degree
+    assert cnt[1] != 64 * cnt[2]
+    assert orc.rel_l2(orc.direct(POLY, 0.0, x, x, f), u) < 1e-12
+    deg2 = deg.copy()
+    deg2[deg2 == 3] = 2   # one degree too low somewhere: no longer exact
+    fv2, foff2 = t.modified_weights_var(f, deg2)
+    u2, _, _ = t.treecode_var(f, fv2, deg2, foff2, POLY, 0.0, 0.9, x)
+    assert orc.rel_l2(orc.direct(POLY, 0.0, x, x, f), u2) > 1e-8
+
+
+def test_variable_degree_batch_matches_per_target_form(orc):
+    x, f = wl.uniform_cube(2000, 33)
+    t = orc.Tree(x, 80)
+    deg = np.random.default_rng(4).integers(2, 9, t.nclusters).astype(np.int32)
+    fv, foff = t.modified_weights_var(f, deg)
+    u1, c1, _ = t.treecode_var(f, fv, deg, foff, ST, 0.01, 0.7, x)
+    u2, c2 = t.treecode_batch_var(f, fv, deg, foff, ST, 0.01, 0.7, x, 1, 1)
+    assert np.array_equal(c1, c2) and orc.rel_l2(u1, u2) < 1e-14
