@@ -161,6 +161,22 @@ kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64
  * KITC_ERR_STATE if no evaluation has been done on the handle. */
 kitc_status kitc_apply(kitc_tree t, const double *w, double *out, void *stream);
 
+/* Gives every cluster c its own interpolation degree n_c = degrees[c]
+ * (n_clusters int32 values in 0..16, host or device memory; NULL returns to
+ * the uniform degree of kitc_params).  The paper uses one n for all clusters
+ * (Sec. 3, Eq. pc_approximation_3D); the MAC of Eq. MAC does not involve n, so
+ * the same interaction lists serve any degree map, and cluster c's far field
+ * takes its own (n_c+1)^3 Chebyshev grid with the modified weights of
+ * Eq. modified_weights at that degree (Algorithm 1 per cluster; the upward
+ * pass is not used).  n_c = 0 means "no modified weights": a later
+ * kitc_evaluate returns KITC_ERR_INVALID_ARG if any target accepts such a
+ * cluster by the MAC.  Discards the weights, the lists and a captured graph
+ * of the handle (call kitc_modified_weights and kitc_evaluate again).
+ * kitc_weights_download then returns, cluster by cluster in cluster order,
+ * (n_c+1)^3 x w_in values for every cluster with n_c > 0.  Synchronizes
+ * `stream`.  KITC_ERR_INVALID_ARG for a degree outside 0..16. */
+kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream);
+
 /* Eq. N-body by direct summation over all sources (self term included;
  * with eps = 0 a pair at r = 0 is skipped).  All pointers device.  Uses
  * p->kernel, p->eps, p->precision and p->target_batch; the tree

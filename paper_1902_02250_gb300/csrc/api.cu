@@ -34,6 +34,11 @@ struct kitc_tree_s {
     cudaEvent_t ev[8] = {};
     bool ev_ok = false;
     bool stage_done[4] = {false, false, false, false};
+    // degree per cluster (kitc_set_degrees)
+    bool var = false;
+    std::vector<int32_t> hdeg;
+    DevBuf cdeg, roff, chebt;  // int32 [nclus], int64 [nclus] record offsets, double [17][17]
+    int64_t proxy_bytes = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -180,6 +185,7 @@ void free_handle(kitc_tree t)
     t->wts.release(s);
     t->lists.release(s);
     t->flags.release(s);
+    for (DevBuf *b : {&t->cdeg, &t->roff, &t->chebt}) b->release(s);
     if (t->ev_ok)
         for (auto &e : t->ev) cudaEventDestroy(e);
     delete t;
@@ -286,8 +292,20 @@ kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int 
 static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 {
     const bool mixed = t->p.precision == KITC_MIXED;
+    const bool pairs = mixed && t->p.kernel == KITC_STOKESLET;
+    if (t->var) {
+        KITC_TRY(weights_launch_var(t->src, w, t->cdeg.as<int32_t>(), t->wts, s));
+        KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
+                                  mixed, pairs, s));
+        if (pairs)
+            KITC_TRY(pack_pairs_launch(&t->src, nullptr, w, t->src.n, t->wts.pair_ranges, s,
+                                       t->wts.src, t->wts.pbegin));
+        else
+            KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
+        return KITC_OK;
+    }
     KITC_TRY(weights_launch(t->src, w, t->wts, s));
-    if (mixed && t->p.kernel == KITC_STOKESLET) {  // FP32x2 evaluator records
+    if (pairs) {  // FP32x2 evaluator records
         KITC_TRY(pack_proxy_pairs(t->src, t->wts, s));
         KITC_TRY(pack_pairs_launch(&t->src, nullptr, w, t->src.n, t->wts.pair_ranges, s,
                                    t->wts.src, t->wts.pbegin));
@@ -300,7 +318,14 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 
 static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
 {
-    KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
+    if (t->var) {
+        if (!t->wts.planned || !t->wts.var) {
+            KITC_TRY(weights_plan_var(t->src, t->win, t->hdeg, s, t->wts));
+            KITC_TRY(t->wts.proxy.reserve((size_t)std::max<int64_t>(t->proxy_bytes, 16), s));
+        }
+    } else {
+        KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
+    }
     if (t->p.precision == KITC_MIXED && t->p.kernel == KITC_STOKESLET && !t->pairs_planned) {
         KITC_TRY(pack_pairs_plan(&t->src, t->src.n, s, t->wts.src, t->wts.pbegin,
                                  &t->wts.pair_ranges));
@@ -337,7 +362,8 @@ static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_t
     t->evaluated = false;
     record(t, 4, s);
     KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt, counts, nsys));
-    KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, p.mac, s, t->lists));
+    KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, t->var ? t->cdeg.as<int32_t>() : nullptr,
+                          p.mac, s, t->lists));
     record(t, 5, s);
     EvalArgs a{};
     a.tx = t->tgt.xs.as<double>();
@@ -368,6 +394,11 @@ static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_t
     a.pbegin = t->wts.pbegin.as<int32_t>();
     a.out = out;
     fill_eval_common(a, p, t->flags.as<int>());
+    if (t->var) {
+        a.cdeg = t->cdeg.as<int32_t>();
+        a.roff = t->roff.as<int64_t>();
+        a.chebt = t->chebt.as<double>();
+    }
     KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
     KITC_TRY(evaluate_launch(p.kernel, p.precision == KITC_MIXED, a, s));
     record(t, 6, s);
@@ -569,7 +600,8 @@ kitc_status kitc_weights_download(kitc_tree t, double *fhat, void *stream)
     if (!t->has_weights) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int np = t->p.degree + 1;
-    size_t bytes = sizeof(double) * (size_t)t->src.nclus * np * np * np * t->win;
+    size_t bytes = t->var ? sizeof(double) * (size_t)t->wts.fhat_len
+                          : sizeof(double) * (size_t)t->src.nclus * np * np * np * t->win;
     KITC_CUDA(cudaMemcpyAsync(fhat, t->wts.fhat.ptr, bytes, cudaMemcpyDeviceToHost, s));
     KITC_CUDA(cudaStreamSynchronize(s));
     return KITC_OK;
@@ -679,6 +711,48 @@ kitc_status kitc_watchdog_selftest(int limit_ms, void *stream)
     if (st == KITC_OK) st = read_error_flag(flag.as<int>(), s);
     flag.release(s);
     return st;
+}
+
+
+kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream)
+{
+    if (!t) return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int m = t->src.nclus;
+    std::vector<int32_t> h;
+    if (degrees) {
+        h.resize(m);
+        KITC_CUDA(cudaMemcpyAsync(h.data(), degrees, sizeof(int32_t) * m, cudaMemcpyDefault, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < m; ++c)
+            if (h[c] < 0 || h[c] > KITC_MAX_DEGREE) return KITC_ERR_INVALID_ARG;
+    }
+    // a new degree map invalidates the weights, the lists and the captured graph
+    if (t->graph) {
+        cudaGraphExecDestroy(t->graph);
+        t->graph = nullptr;
+    }
+    t->has_weights = t->evaluated = false;
+    t->wts.planned = false;
+    t->var = false;
+    if (!degrees) return KITC_OK;
+    const bool mixed = t->p.precision == KITC_MIXED;
+    const bool pairs = mixed && t->p.kernel == KITC_STOKESLET;
+    std::vector<int64_t> ro;
+    t->proxy_bytes = proxy_offsets_var(h, t->win, mixed, pairs, ro);
+    std::vector<double> tab((KITC_MAX_DEGREE + 1) * (KITC_MAX_DEGREE + 1), 0.0);
+    for (int d = 1; d <= KITC_MAX_DEGREE; ++d) cheb_cos_table(d, &tab[(size_t)d * (KITC_MAX_DEGREE + 1)]);
+    KITC_TRY(t->cdeg.reserve(sizeof(int32_t) * m, s));
+    KITC_TRY(t->roff.reserve(sizeof(int64_t) * m, s));
+    KITC_TRY(t->chebt.reserve(sizeof(double) * tab.size(), s));
+    KITC_CUDA(cudaMemcpyAsync(t->cdeg.ptr, h.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(t->roff.ptr, ro.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(t->chebt.ptr, tab.data(), sizeof(double) * tab.size(),
+                              cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+    t->hdeg.swap(h);
+    t->var = true;
+    return KITC_OK;
 }
 
 }  // extern "C"

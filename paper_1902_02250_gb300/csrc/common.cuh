@@ -107,6 +107,15 @@ struct WeightsDev {
     size_t nitems = 0, smem = 0;
     int acc = 1, npass = 1, sb = 8;
     int pair_ranges = 0;  // ranges of the paired records (pack_pairs_plan)
+    // degree per cluster (weights_plan_var): one Algorithm 1 launch per degree
+    struct Group {
+        int degree = 0;
+        size_t item0 = 0, nitems = 0;
+        int64_t pofs = 0;
+    };
+    std::vector<Group> groups;
+    bool var = false;
+    int64_t fhat_len = 0;  // doubles of fhat in use
     DevBuf fhat;      // double [nclus][P][win]
     DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
     DevBuf src;       // evaluator records of the sources in tree order
@@ -136,6 +145,14 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
 kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
                        cudaStream_t s, DevBuf &out, DevBuf &pbegin);
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
+kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
+                             cudaStream_t s, WeightsDev &wd);
+kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int32_t *d_deg,
+                               WeightsDev &wd, cudaStream_t s);
+int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed, bool pairs,
+                          std::vector<int64_t> &roff);
+kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,
+                             const int64_t *d_roff, bool mixed, bool pairs, cudaStream_t s);
 kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
                             DevBuf &pbegin, int *nranges);
 kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
@@ -168,7 +185,7 @@ struct ListsDev {
 };
 
 kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
-                        int degree, int mac, cudaStream_t s, ListsDev &L);
+                        int degree, const int32_t *cdeg, int mac, cudaStream_t s, ListsDev &L);
 
 // ---------------------------------------------------------------------------
 // Fused near/far evaluator.
@@ -196,6 +213,11 @@ struct EvalArgs {
     const int32_t *pbegin;       // paired records: first pair of each leaf
     int degree;
     double cheb[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
+    // degree per cluster (NULL: degree everywhere); then cluster c's grid
+    // records start roff[c] bytes into proxy and chebt[n][k] = cos(k pi / n)
+    const int32_t *cdeg;
+    const int64_t *roff;
+    const double *chebt;
     double eps;
     double *out;                 // caller order, n x wout
     int *queue;                  // work counter, zero at launch

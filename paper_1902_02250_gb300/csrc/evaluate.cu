@@ -33,8 +33,14 @@ namespace {
 #endif
 constexpr int NCW = KITC_NCW;          // consumer warps
 constexpr int NTH = (NCW + 1) * 32;    // plus one producer warp
-constexpr int STAGES = 4;
-constexpr int TILE = 16384;            // bytes per stage
+#ifndef KITC_STAGES
+#define KITC_STAGES 4
+#endif
+#ifndef KITC_TILE
+#define KITC_TILE 16384
+#endif
+constexpr int STAGES = KITC_STAGES;    // ring of shared-memory stages
+constexpr int TILE = KITC_TILE;        // bytes per stage
 constexpr double INV8PI = 0.039788735772973836;
 
 enum { K_FAR = 0, K_NEAR = 1, K_EXIT = 2 };
@@ -43,7 +49,8 @@ enum { F_FIRST_BATCH = 1, F_LAST_BATCH = 2, F_FIRST_ENTRY = 4, F_LAST_ENTRY = 8 
 struct TileMeta {
     int kind, flags, batch, id;
     int a, b;        // far: k1 planes [a, b); near: source slots [a, b)
-    int seq, pad;    // position of the tile within its batch (fixes the work split)
+    int seq;         // position of the tile within its batch (fixes the work split)
+    int np;          // far: grid points per dimension of the cluster (n_c + 1)
     uint64_t mask;   // targets of the batch that use this entry
     dvec4 lo, hi;    // far: the cluster's box (read ahead by the producer)
 };
@@ -302,13 +309,9 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int np = a.degree + 1, np2 = np * np;
-    const int npair = (np + 1) / 2;
-    const int row_bytes = PAIR ? npair * 32 : np * PREC;          // one grid row (k1, k2)
-    const int plane_bytes = np * row_bytes;                       // one k1 plane
+    const int np0 = a.degree + 1;                                 // uniform degree
     const int near_unit = PAIR ? PAIR_REC : SREC;                 // one near item
     const int near_max = PAIR ? (TILE / PAIR_REC) / 4 * 4 : (TILE / SREC) / 8 * 8;
-    const int planes_max = TILE / plane_bytes;
     const unsigned long long wait_ns = a.wait_ns;
 
     // ---------------------------------------------------------------- producer
@@ -361,12 +364,19 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     int c = a.far_id[e];
                     uint64_t mk = a.far_mask[e];
                     dvec4 lo = a.clo[c], hi = a.chi[c];
+                    // grid of cluster c: (n_c+1)^3 records from its offset
+                    const int np = a.cdeg ? a.cdeg[c] + 1 : np0;
+                    if (np < 2 || np > KITC_MAX_DEGREE + 1) { ok = false; break; }
+                    const int row_bytes = PAIR ? (np + 1) / 2 * 32 : np * PREC;
+                    const int plane_bytes = np * row_bytes;
+                    const int planes_max = TILE / plane_bytes;
+                    const unsigned char *cb = pxb + (a.roff ? (size_t)a.roff[c]
+                                                            : (size_t)c * np * plane_bytes);
                     for (int k1 = 0; k1 < np && ok; k1 += planes_max) {
                         int k2 = min(np, k1 + planes_max);
                         TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
-                                   b, c, k1, k2, 0, 0, mk, lo, hi};
-                        ok = push(m, pxb + (size_t)c * np * plane_bytes + (size_t)k1 * plane_bytes,
-                                  (uint32_t)((k2 - k1) * plane_bytes));
+                                   b, c, k1, k2, 0, np, mk, lo, hi};
+                        ok = push(m, cb + (size_t)k1 * plane_bytes, (uint32_t)((k2 - k1) * plane_bytes));
                     }
                 }
                 int64_t n0 = a.near_off[b], n1 = a.near_off[b + 1];
@@ -483,6 +493,9 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
         const int rot = mr.seq % NCW;  // depends on the batch only: results are deterministic
         const uint64_t mask = mr.mask;
         if (kind == K_EXIT) break;
+        // far tiles: grid size of the tile's cluster
+        const int np = mr.np, npair = (np + 1) / 2;
+        const int row_bytes = PAIR ? npair * 32 : np * PREC;
         const unsigned char *tile = tiles + (size_t)s * TILE;
         const bool u0 = (mask >> lane) & 1ull, u1 = (mask >> (lane + 32)) & 1ull;
         if (flags & F_FIRST_BATCH) {
@@ -531,7 +544,8 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                         int l = q / np, k = q % np;
                         double lo_l = l == 0 ? mr.lo.x : (l == 1 ? mr.lo.y : mr.lo.z);
                         double hi_l = l == 0 ? mr.hi.x : (l == 1 ? mr.hi.y : mr.hi.z);
-                        double sk = 0.5 * ((lo_l + hi_l) + a.cheb[k] * (hi_l - lo_l));
+                        const double ck = a.chebt ? a.chebt[(np - 1) * (KITC_MAX_DEGREE + 1) + k] : a.cheb[k];
+                        double sk = 0.5 * ((lo_l + hi_l) + ck * (hi_l - lo_l));
                         double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
                         float v = (float)(sk - cb_l);
                         gsf[18 * l + k] = l == 2 ? -v : v;
@@ -668,7 +682,8 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
                     int l = q / np, k = q % np;
                     double lo_l = l == 0 ? mr.lo.x : (l == 1 ? mr.lo.y : mr.lo.z);
                     double hi_l = l == 0 ? mr.hi.x : (l == 1 ? mr.hi.y : mr.hi.z);
-                    double sk = 0.5 * ((lo_l + hi_l) + a.cheb[k] * (hi_l - lo_l));
+                    const double ck = a.chebt ? a.chebt[(np - 1) * (KITC_MAX_DEGREE + 1) + k] : a.cheb[k];
+                        double sk = 0.5 * ((lo_l + hi_l) + ck * (hi_l - lo_l));
                     double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
                     gs[l * (KITC_MAX_DEGREE + 1) + k] = MIXED ? (R)(sk - cb_l) : (R)sk;
                 }
@@ -793,8 +808,9 @@ template <int K, bool MIXED, bool EPS0>
 kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
 {
     constexpr int WIN = KT<K>::WIN;
-    int np = a.degree + 1;
+    int np = a.cdeg ? KITC_MAX_DEGREE + 1 : a.degree + 1;  // the largest grid of the launch
     constexpr bool PAIR = MIXED && K == KITC_STOKESLET;
+    if (a.cdeg && (!a.roff || !a.chebt)) return KITC_ERR_INVALID_ARG;
     size_t plane = PAIR ? (size_t)np * ((np + 1) / 2) * 32 : (size_t)np * np * Rec<MIXED, WIN>::PROXY;
     if (plane > (size_t)TILE) return KITC_ERR_INVALID_ARG;
     if (PAIR && a.near_off && !a.pbegin) return KITC_ERR_INVALID_ARG;

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
     int64_t nt, int batch, int64_t nb, const int32_t *__restrict__ bdesc, const double *__restrict__ txs,
     const dvec4 *__restrict__ ctr, const float4 *__restrict__ ctrf, const int32_t *__restrict__ cbegin,
     const int32_t *__restrict__ cend, const int32_t *__restrict__ first_child,
-    const int32_t *__restrict__ n_child, double theta, int np3, int mac,
+    const int32_t *__restrict__ n_child, double theta, int np3, const int32_t *__restrict__ cdeg, int mac,
     int64_t *__restrict__ counts, dvec4 *__restrict__ bctr, int64_t *__restrict__ totals,
     const int64_t *__restrict__ far_off, const int64_t *__restrict__ near_off,
     int32_t *__restrict__ far_id, uint64_t *__restrict__ far_mask, int32_t *__restrict__ near_id,
@@ -157,8 +157,14 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
                 far_mask[fo + nfar] = A;
             }
             nfar++;
-            points += (int64_t)__popcll(A) * np3;
-            xpoints += (int64_t)nvalid * np3;
+            int64_t g3 = np3;
+            if (cdeg) {  // degree of cluster c; an accepted cluster must have weights
+                int gn = cdeg[c] + 1;
+                if (gn < 2 && lane == 0) atomicExch(err, 2);
+                g3 = (int64_t)gn * gn * gn;
+            }
+            points += (int64_t)__popcll(A) * g3;
+            xpoints += (int64_t)nvalid * g3;
         }
         if (R) {
             int nch = n_child[c];
@@ -244,7 +250,7 @@ size_t ListsDev::bytes() const
 }
 
 kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
-                        int degree, int mac, cudaStream_t s, ListsDev &L)
+                        int degree, const int32_t *cdeg, int mac, cudaStream_t s, ListsDev &L)
 {
     int64_t nt = tgt.n;
     int64_t nb = (nt + batch - 1) / batch;
@@ -286,7 +292,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
-                                        theta, np3, mac, L.counts.as<int64_t>(),
+                                        theta, np3, cdeg, mac, L.counts.as<int64_t>(),
                                         L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
                                         nullptr, nullptr, nullptr, err);
     KITC_CUDA(cudaGetLastError());
@@ -314,7 +320,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
                                         src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
-                                        theta, np3, mac, nullptr, nullptr, nullptr,
+                                        theta, np3, cdeg, mac, nullptr, nullptr, nullptr,
                                         L.far_off.as<int64_t>(), L.near_off.as<int64_t>(),
                                         L.far_id.as<int32_t>(), L.far_mask.as<uint64_t>(),
                                         L.near_id.as<int32_t>(), L.near_mask.as<uint64_t>(), err);

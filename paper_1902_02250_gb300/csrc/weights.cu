@@ -402,7 +402,8 @@ size_t upward_smem(int np, int win)
 kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaStream_t s,
                          WeightsDev &wd)
 {
-    if (wd.planned && wd.degree == degree && wd.win == win && wd.mode == mode) return KITC_OK;
+    if (wd.planned && !wd.var && wd.degree == degree && wd.win == win && wd.mode == mode)
+        return KITC_OK;
     wd.planned = false;
     const int np = degree + 1;
     const int pwin = np * np * np * win;
@@ -455,6 +456,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     wd.degree = degree;
     wd.win = win;
     wd.mode = mode;
+    wd.var = false;
     wd.planned = true;
     return KITC_OK;
 }
@@ -637,6 +639,204 @@ kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, i
         else
             k_pack_sources<false><<<g, 256, 0, s>>>(n, win, nullptr, nullptr, xyz, w, out);
     }
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Degree per cluster (kitc_set_degrees).  Cluster c has degree deg[c] (0: no
+// modified weights); its FP64 weights start at fhat + foff[c] and its grid
+// records at proxy + roff[c] bytes.  Every cluster runs Algorithm 1 (one
+// launch per distinct degree); the upward pass is not used because a child of
+// lower degree does not reproduce its parent's Lagrange polynomials.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_weights_reduce_var(const int32_t *__restrict__ deg, int win,
+                                     const int64_t *__restrict__ pstart,
+                                     const int32_t *__restrict__ icount,
+                                     const int64_t *__restrict__ foff,
+                                     const double *__restrict__ partial, double *__restrict__ fhat)
+{
+    int c = blockIdx.x;
+    int d = deg[c];
+    if (d <= 0) return;
+    int np = d + 1, pw = np * np * np * win;
+    const double *src = partial + pstart[c];
+    for (int o = threadIdx.x; o < pw; o += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < icount[c]; ++i) s += src[(size_t)i * pw + o];
+        fhat[foff[c] + o] = s;
+    }
+}
+
+// Block per cluster: grid records of the cluster, paired (FP32x2 Stokeslet)
+// or one record per point (other forms), at proxy + roff[c].
+template <int FORM>  // 0: pairs, 1: FP32 float4 per point, 2: FP64 per point
+__global__ void k_pack_proxies_var(const int32_t *__restrict__ deg, int win,
+                                   const int64_t *__restrict__ foff,
+                                   const int64_t *__restrict__ roff, const double *__restrict__ fhat,
+                                   unsigned char *__restrict__ proxy)
+{
+    int c = blockIdx.x;
+    int d = deg[c];
+    if (d <= 0) return;
+    int np = d + 1;
+    const double *fh = fhat + foff[c];
+    unsigned char *out = proxy + roff[c];
+    if (FORM == 0) {
+        int npair = (np + 1) / 2;
+        for (int q = threadIdx.x; q < np * np * npair; q += blockDim.x) {
+            int r = q / npair, k = (q % npair) * 2;
+            const double *f0 = fh + ((size_t)r * np + k) * 3;
+            double g[3] = {0.0, 0.0, 0.0};
+            if (k + 1 < np)
+                for (int l = 0; l < 3; ++l) g[l] = f0[3 + l];
+            float4 *o = reinterpret_cast<float4 *>(out) + 2 * q;
+            o[0] = make_float4((float)f0[0], (float)g[0], (float)f0[1], (float)g[1]);
+            o[1] = make_float4((float)f0[2], (float)g[2], 0.f, 0.f);
+        }
+    } else {
+        int P = np * np * np;
+        for (int r = threadIdx.x; r < P; r += blockDim.x) {
+            const double *f = fh + (size_t)r * win;
+            if (FORM == 1) {
+                float4 *o = reinterpret_cast<float4 *>(out);
+                o[(win == 3 ? 1 : 2) * r] = make_float4((float)f[0], (float)f[1], (float)f[2], 0.f);
+                if (win == 6)
+                    o[2 * r + 1] = make_float4((float)f[3], (float)f[4], (float)f[5], 0.f);
+            } else {
+                double *o = reinterpret_cast<double *>(out) + (size_t)r * (win == 3 ? 4 : 6);
+                for (int q = 0; q < (win == 3 ? 4 : 6); ++q) o[q] = q < win ? f[q] : 0.0;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
+                             cudaStream_t s, WeightsDev &wd)
+{
+    wd.planned = false;
+    std::vector<int32_t> hb(t.nclus), he(t.nclus);
+    KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * t.nclus, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * t.nclus, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    // items grouped by degree; per cluster: offset of its partials and item count
+    std::vector<Item> items;
+    std::vector<int64_t> pstart(t.nclus, 0), foff(t.nclus, 0);
+    std::vector<int32_t> icount(t.nclus, 0);
+    wd.groups.clear();
+    int64_t pofs = 0, fofs = 0;
+    for (int d = 1; d <= KITC_MAX_DEGREE; ++d) {
+        WeightsDev::Group g;
+        g.degree = d;
+        g.item0 = items.size();
+        g.pofs = pofs;
+        int np = d + 1, pw = np * np * np * win;
+        for (int c = 0; c < t.nclus; ++c) {
+            if (hdeg[c] != d) continue;
+            pstart[c] = pofs;
+            for (int32_t p = hb[c]; p < he[c]; p += CHUNK) {
+                items.push_back(Item{c, p, std::min(he[c], p + CHUNK), 0});
+                pofs += pw;
+                icount[c]++;
+            }
+        }
+        g.nitems = items.size() - g.item0;
+        if (g.nitems) wd.groups.push_back(g);
+    }
+    for (int c = 0; c < t.nclus; ++c) {
+        foff[c] = fofs;
+        if (hdeg[c] > 0) fofs += (int64_t)(hdeg[c] + 1) * (hdeg[c] + 1) * (hdeg[c] + 1) * win;
+    }
+    size_t ni = items.size();
+    size_t bytes = sizeof(Item) * ni + sizeof(int64_t) * 2 * t.nclus + sizeof(int32_t) * t.nclus + 64;
+    KITC_TRY(wd.items.reserve(bytes, s));
+    Item *d_items = wd.items.as<Item>();
+    int64_t *d_p = reinterpret_cast<int64_t *>(d_items + ni);
+    int64_t *d_f = d_p + t.nclus;
+    int32_t *d_c = reinterpret_cast<int32_t *>(d_f + t.nclus);
+    KITC_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * ni, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_p, pstart.data(), sizeof(int64_t) * t.nclus, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_f, foff.data(), sizeof(int64_t) * t.nclus, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_c, icount.data(), sizeof(int32_t) * t.nclus, cudaMemcpyHostToDevice, s));
+    KITC_TRY(wd.partial.reserve(sizeof(double) * std::max<int64_t>(pofs, 1), s));
+    KITC_TRY(wd.fhat.reserve(sizeof(double) * std::max<int64_t>(fofs, 1), s));
+    KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+    wd.nitems = ni;
+    wd.fhat_len = fofs;
+    wd.win = win;
+    wd.degree = -1;
+    wd.var = true;
+    wd.planned = true;
+    return KITC_OK;
+}
+
+kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int32_t *d_deg,
+                               WeightsDev &wd, cudaStream_t s)
+{
+    if (!wd.planned || !wd.var) return KITC_ERR_STATE;
+    const int win = wd.win;
+    Item *d_items = wd.items.as<Item>();
+    int64_t *d_p = reinterpret_cast<int64_t *>(d_items + wd.nitems);
+    int64_t *d_f = d_p + t.nclus;
+    int32_t *d_c = reinterpret_cast<int32_t *>(d_f + t.nclus);
+    static constexpr ChunkLauncher table[ACC_MAX] = {
+        &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
+        &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
+        &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
+        &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
+    for (const auto &g : wd.groups) {
+        int np = g.degree + 1, pwin = np * np * np * win;
+        size_t per = sizeof(double) * (3 * np + np * np + np * win);
+        int sb = 64;
+        while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
+        int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
+        int npass = (pwin + acc * WT - 1) / (acc * WT);
+        KITC_TRY(table[acc - 1](dim3((unsigned)g.nitems, (unsigned)npass), per * sb, s,
+                                make_cheb(g.degree), d_items + g.item0, t, w_user, win, sb,
+                                wd.partial.as<double>() + g.pofs));
+    }
+    kitc_count_launch();
+    k_weights_reduce_var<<<t.nclus, 256, 0, s>>>(d_deg, win, d_p, d_c, d_f, wd.partial.as<double>(),
+                                                 wd.fhat.as<double>());
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+// Record offsets (bytes) of each cluster's grid records in the given form.
+int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed, bool pairs,
+                          std::vector<int64_t> &roff)
+{
+    roff.assign(hdeg.size(), 0);
+    int64_t o = 0;
+    for (size_t c = 0; c < hdeg.size(); ++c) {
+        roff[c] = o;
+        int d = hdeg[c];
+        if (d <= 0) continue;
+        int64_t np = d + 1;
+        o += pairs ? np * np * ((np + 1) / 2) * 32 : np * np * np * proxy_record_bytes(win, mixed);
+    }
+    return o;
+}
+
+kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,
+                             const int64_t *d_roff, bool mixed, bool pairs, cudaStream_t s)
+{
+    Item *d_items = wd.items.as<Item>();
+    const int64_t *d_f = reinterpret_cast<int64_t *>(d_items + wd.nitems) + t.nclus;
+    kitc_count_launch();
+    if (pairs)
+        k_pack_proxies_var<0><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
+                                                     wd.proxy.as<unsigned char>());
+    else if (mixed)
+        k_pack_proxies_var<1><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
+                                                     wd.proxy.as<unsigned char>());
+    else
+        k_pack_proxies_var<2><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
+                                                     wd.proxy.as<unsigned char>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }

@@ -77,7 +77,7 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
-           "kitc_launch_count"]
+           "kitc_launch_count", "kitc_set_degrees"]
 
 
 def library_path():
@@ -117,11 +117,13 @@ def lib():
         L.kitc_watchdog_selftest.argtypes = [I, P]
         L.kitc_launch_count.argtypes = []
         L.kitc_launch_count.restype = I64
+        L.kitc_set_degrees.argtypes = [P, P, P]
         for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest", "kitc_apply",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_direct_noalloc",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
-                     "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest"):
+                     "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest",
+                     "kitc_set_degrees"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -180,6 +182,7 @@ class Tree:
         self._h = handle
         self.params = params
         self.n = n
+        self.degrees = None  # host copy of a per-cluster degree map (kitc_set_degrees)
 
     @property
     def handle(self):
@@ -216,7 +219,16 @@ class Tree:
         return out
 
     def weights(self, stream=None):
+        """FP64 modified weights: [clusters, n+1, n+1, n+1, w_in], or with a
+        per-cluster degree map the flat concatenation over clusters with n_c > 0."""
         st = self.stats()
+        if self.degrees is not None:
+            g = self.degrees.astype(np.int64) + 1
+            tot = int((g ** 3 * (self.degrees > 0)).sum()) * kernel_win(self.params.kernel)
+            f = np.empty(max(tot, 1))
+            _check(lib().kitc_weights_download(self.handle, _np(f), _stream(stream)),
+                   "kitc_weights_download")
+            return f[:tot]
         np1 = st["degree"] + 1
         f = np.empty((st["n_clusters"], np1, np1, np1, kernel_win(self.params.kernel)))
         _check(lib().kitc_weights_download(self.handle, _np(f), _stream(stream)),
@@ -289,6 +301,27 @@ def kitc_evaluate(tree, tgt_xyz, out=None, stream=None):
     _check(lib().kitc_evaluate(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
                                _dptr(out, wout, "out"), _stream(stream)), "kitc_evaluate")
     return out
+
+
+def kitc_set_degrees(tree, degrees, stream=None):
+    """Degree n_c per cluster (int32, one per cluster: numpy or CUDA tensor), or
+    None for the uniform degree.  Weights and lists must be computed again."""
+    if degrees is None:
+        _check(lib().kitc_set_degrees(tree.handle, None, _stream(stream)), "kitc_set_degrees")
+        tree.degrees = None
+        return
+    if isinstance(degrees, np.ndarray):
+        h = np.ascontiguousarray(degrees, np.int32)
+        ptr = _np(h)
+    else:
+        if degrees.dtype.__str__() != "torch.int32" or not degrees.is_contiguous():
+            raise ValueError("degrees must be a contiguous int32 tensor")
+        h = degrees.cpu().numpy()
+        ptr = degrees.data_ptr()
+    if h.shape != (tree.stats()["n_clusters"],):
+        raise ValueError("degrees must hold one value per cluster")
+    _check(lib().kitc_set_degrees(tree.handle, ptr, _stream(stream)), "kitc_set_degrees")
+    tree.degrees = h.copy()
 
 
 def kitc_apply(tree, w, out, stream=None):

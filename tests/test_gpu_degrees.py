@@ -1,0 +1,188 @@
+"""Per-cluster interpolation degrees (kitc_set_degrees) against the FP64 CPU
+oracle: modified weights of Eq. modified_weights at each cluster's own degree,
+Algorithm 2 and its batch-MAC variant with (n_c+1)^3 grid points per accepted
+cluster, the interaction counts, and the error paths.
+
+Tolerances as in the fixed-degree parity tests: FP64 to 1e-12 relative L2,
+the mixed form to MIXED_TOL, counts exact.
+"""
+import numpy as np
+import pytest
+
+from paper_1902_02250_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-6
+ST, RO, SR = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def K():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_02250_gb300 import build, kitc
+    build.build()
+    torch.cuda.set_device(0)
+    return kitc
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def random_degrees(m, seed, lo=1, hi=12):
+    return np.random.default_rng(seed).integers(lo, hi + 1, m).astype(np.int32)
+
+
+def test_weights_per_cluster_degree(K, orc):
+    x, f = wl.plummer_with_background(12000, 61)
+    p = K.Params(theta=0.7, degree=6, leaf_size=150, eps=0.01)
+    t = K.kitc_build_tree(dev(x), p)
+    m = t.stats()["n_clusters"]
+    deg = random_degrees(m, 62, 0, 16)
+    deg[0] = 0
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = t.weights()
+    o = orc.Tree(x, 150)
+    ref, foff = o.modified_weights_var(f, deg)
+    assert got.shape == ref[:len(got)].shape and len(got) == int(
+        ((deg.astype(np.int64) + 1) ** 3 * (deg > 0)).sum() * 3)
+    for c in range(m):
+        if deg[c] == 0:
+            continue
+        k = (int(deg[c]) + 1) ** 3 * 3
+        a, b = got[foff[c]:foff[c] + k], ref[foff[c]:foff[c] + k]
+        assert np.linalg.norm(a - b) <= FP64_TOL * max(np.linalg.norm(b), 1e-300), c
+    t.free()
+
+
+@pytest.mark.parametrize("kernel", [ST, RO, SR])
+def test_fp64_particle_mac_per_cluster_degree(K, orc, kernel):
+    win = 6 if kernel == SR else 3
+    x, f = wl.uniform_cube(9001, 63, win=win)
+    tg = wl.uniform_cube(3001, 64)[0]
+    p = K.Params(theta=0.7, degree=5, leaf_size=120, eps=0.02, kernel=kernel, mac=K.MAC_PARTICLE)
+    t = K.kitc_build_tree(dev(x), p)
+    deg = random_degrees(t.stats()["n_clusters"], 65)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = K.kitc_evaluate(t, dev(tg)).cpu().numpy()
+    st = t.stats()
+    o = orc.Tree(x, 120)
+    fh, foff = o.modified_weights_var(f, deg)
+    ref, cnt, bad = o.treecode_var(f, fh, deg, foff, kernel, 0.02, 0.7, tg)
+    assert bad == 0
+    assert st["far_points"] == cnt[1] and st["near_pairs"] == cnt[0] and cnt[1] > 0
+    assert orc.rel_l2(ref, got) <= FP64_TOL
+    t.free()
+
+
+def test_fp64_batch_mac_per_cluster_degree_zero_where_unused(K, orc):
+    """Clusters that no batch accepts get degree 0 (no weights at all)."""
+    x, f = wl.plummer_with_background(10007, 66)
+    B = 64
+    o = orc.Tree(x, 100)
+    lists = o.treecode_batch(f, o.modified_weights(f, 1), 1, ST, 0.01, 0.7, x, B, B, lists=True,
+                             evaluate=False)
+    used = np.zeros(o.nclusters, bool)
+    used[lists["far_list"]] = True
+    deg = np.where(used, random_degrees(o.nclusters, 67, 2, 12), 0).astype(np.int32)
+    assert (deg == 0).sum() > 0 and used.sum() > 0
+    p = K.Params(theta=0.7, degree=4, leaf_size=100, eps=0.01, mac=K.MAC_BATCH, target_batch=B)
+    t = K.kitc_build_tree(dev(x), p)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = K.kitc_evaluate(t, dev(x)).cpu().numpy()
+    st = t.stats()
+    fh, foff = o.modified_weights_var(f, deg)
+    sel = wl.sample_indices(len(x), 2500, 68)
+    ref, cnt = o.treecode_batch_var(f, fh, deg, foff, ST, 0.01, 0.7, x, B, B, select=sel)
+    assert st["far_points"] == cnt[1] and st["near_pairs"] == cnt[0]
+    assert orc.rel_l2(ref[sel], got[sel]) <= FP64_TOL
+    t.free()
+
+
+@pytest.mark.parametrize("kernel", [ST, RO])
+@pytest.mark.parametrize("mac", [0, 1])
+def test_mixed_per_cluster_degree(K, orc, kernel, mac):
+    """FP32x2 paired records (Stokeslet) and per-point records (rotlet)."""
+    x, f = wl.uniform_cube(20000, 69)
+    p = K.Params(theta=0.6, degree=6, leaf_size=300, eps=0.005, kernel=kernel, mac=mac,
+                 precision=K.MIXED)
+    t = K.kitc_build_tree(dev(x), p)
+    deg = random_degrees(t.stats()["n_clusters"], 70, 2, 16)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = K.kitc_evaluate(t, dev(x)).cpu().numpy()
+    o = orc.Tree(x, 300)
+    fh, foff = o.modified_weights_var(f, deg)
+    sel = wl.sample_indices(len(x), 3000, 71)
+    if mac == 0:
+        ref, _, bad = o.treecode_var(f, fh, deg, foff, kernel, 0.005, 0.6, x[sel])
+        assert bad == 0
+    else:
+        ref = o.treecode_batch_var(f, fh, deg, foff, kernel, 0.005, 0.6, x, 64, 64,
+                                   select=sel)[0][sel]
+    e = orc.rel_l2(ref, got[sel])
+    print("mixed per-cluster degree kernel=%d mac=%d rel_l2=%.3e" % (kernel, mac, e))
+    assert e <= MIXED_TOL
+    t.free()
+
+
+def test_uniform_map_equals_fixed_degree(K):
+    """A map with n_c = n everywhere reproduces the fixed-degree path that uses
+    Algorithm 1 (same sums in the same order)."""
+    x, f = wl.uniform_cube(30000, 72)
+    for prec in (K.FP64, K.MIXED):
+        p = K.Params(theta=0.7, degree=7, leaf_size=400, eps=0.001, precision=prec,
+                     weights=K.WEIGHTS_ALGORITHM1, mac=K.MAC_BATCH)
+        t = K.kitc_build_tree(dev(x), p)
+        K.kitc_modified_weights(t, dev(f))
+        a = K.kitc_evaluate(t, dev(x)).cpu().numpy()
+        fa = t.weights().ravel()
+        K.kitc_set_degrees(t, np.full(t.stats()["n_clusters"], 7, np.int32))
+        K.kitc_modified_weights(t, dev(f))
+        b = K.kitc_evaluate(t, dev(x)).cpu().numpy()
+        assert np.array_equal(fa, t.weights())
+        assert np.array_equal(a, b)
+        K.kitc_set_degrees(t, None)   # back to the uniform path
+        K.kitc_modified_weights(t, dev(f))
+        assert np.array_equal(a, K.kitc_evaluate(t, dev(x)).cpu().numpy())
+        t.free()
+
+
+def test_degree_errors(K):
+    import torch
+    x, f = wl.uniform_cube(5000, 73)
+    p = K.Params(theta=0.7, degree=4, leaf_size=100, eps=0.01, mac=K.MAC_BATCH)
+    t = K.kitc_build_tree(dev(x), p)
+    m = t.stats()["n_clusters"]
+    with pytest.raises(RuntimeError):
+        K.kitc_set_degrees(t, np.full(m, 17, np.int32))
+    with pytest.raises(RuntimeError):
+        K.kitc_set_degrees(t, np.full(m, -1, np.int32))
+    # every cluster at degree 0: any accepted cluster is an error, not a wrong sum
+    K.kitc_set_degrees(t, np.zeros(m, np.int32))
+    K.kitc_modified_weights(t, dev(f))
+    with pytest.raises(K.KitcError) as e:
+        K.kitc_evaluate(t, dev(x))
+    assert e.value.status == 1
+    # a device-resident map and kitc_apply (graph replay) with it
+    d = torch.from_numpy(random_degrees(m, 74, 3, 9)).cuda()
+    K.kitc_set_degrees(t, d)
+    K.kitc_modified_weights(t, dev(f))
+    out = K.kitc_evaluate(t, dev(x))
+    ref = out.clone()
+    f2 = dev(f)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):              # eager run + capture + replay, then replay
+            out.zero_()
+            K.kitc_apply(t, f2, out)
+            assert torch.equal(out, ref)
+    t.free()
