@@ -96,6 +96,13 @@ typedef struct {
     int weights;       /* kitc_weights_mode                                               */
 } kitc_params;
 
+/* Per-cluster degree selector (kitc_cluster_features, kitc_mlp_*). */
+#define KITC_NFEAT 12        /* features per cluster                          */
+#define KITC_MLP_HIDDEN 64   /* units of each of the two hidden layers        */
+#define KITC_MLP_CLASSES 6   /* outputs: degree classes                       */
+/* parameters: mu[12] sd[12] W1[64][12] b1[64] W2[64][64] b2[64] W3[6][64] b3[6] */
+#define KITC_MLP_NPARAM (2 * 12 + 64 * 12 + 64 + 64 * 64 + 64 + 6 * 64 + 6)
+
 typedef struct kitc_tree_s *kitc_tree; /* opaque; owned by the library */
 
 typedef struct {
@@ -176,6 +183,70 @@ kitc_status kitc_apply(kitc_tree t, const double *w, double *out, void *stream);
  * (n_c+1)^3 x w_in values for every cluster with n_c > 0.  Synchronizes
  * `stream`.  KITC_ERR_INVALID_ARG for a degree outside 0..16. */
 kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream);
+
+/* Builds the target tree and the interaction lists of Algorithm 2 for the
+ * targets tgt_xyz (device, n_tgt x 3) without evaluating anything: the MAC of
+ * Eq. MAC does not involve the degree, so the lists exist before the degrees
+ * are chosen.  Feeds kitc_cluster_features / kitc_cluster_far_errors.
+ * KITC_ERR_STATE on a forest.  Synchronizes `stream`. */
+kitc_status kitc_plan_targets(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, void *stream);
+
+/* Features of every source cluster c for the degree selector, written as
+ * FP32 row c of features (device, n_clusters x KITC_NFEAT):
+ *   0 log(1 + N_c)            1 log r_c (cluster radius, Sec. 6)
+ *   2..4 min, mean, max of r_c / |x - y_c| over the targets x that accept c
+ *        in the lists of the last kitc_plan_targets / kitc_evaluate (0 if none)
+ *   5 min(eps / r_c, 10)      6 log |sum_j f_j|   7 log sum_j |f_j|
+ *   8 log max_j |f_j|         (sums over c's sources, w: device n_src x w_in)
+ *   9, 10 middle / longest and shortest / longest side of c's box
+ *   11 level of c in the tree.
+ * The paper has no degree selector; the features describe the quantities its
+ * error analysis involves (Sec. 3 and the MAC of Algorithm 2).
+ * KITC_ERR_STATE without lists. */
+kitc_status kitc_cluster_features(kitc_tree t, const double *w, float *features, void *stream);
+
+/* Measured far-field error of every cluster at its current modified weights
+ * (uniform degree or the map of kitc_set_degrees): of the targets that accept
+ * cluster c in the current lists, a sample of about max_samples (each taken
+ * with probability min(1, max_samples / accepting targets) by a counter-based
+ * hash of (seed, c, target slot)) is evaluated both with the cluster's far field
+ * (Eq. pc_approximation_3D, FP64) and with the direct sum over c's sources
+ * (Eq. pc_interaction_3D, FP64, w: device n_src x w_in).  err2[c] (device,
+ * double) = sum over the samples of |difference|^2 (velocity units, 1/(8 pi)
+ * included), n_samples[c] (device, int32) = their number.  KITC_ERR_STATE
+ * without lists or weights.  Synchronizes `stream`. */
+kitc_status kitc_cluster_far_errors(kitc_tree t, const double *w, int max_samples, uint64_t seed,
+                                    double *err2, int32_t *n_samples, void *stream);
+
+/* The degree selector network (FP32, parameters in the KITC_MLP_NPARAM
+ * layout above; all pointers device memory unless stated).  The paper has no
+ * counterpart: it fixes one degree n for every cluster.
+ *
+ * kitc_mlp_forward: logits (m x KITC_MLP_CLASSES, may be NULL) of the rows of
+ * features (m x KITC_NFEAT) and, when degrees is not NULL, degrees[i] =
+ * class_degree[argmax_o logits[i][o]] (class_degree: HOST array of
+ * KITC_MLP_CLASSES degrees in 0..16; the first maximum wins ties); with
+ * zero_unused, a row whose features 2, 3 and 4 are all 0 (a cluster no
+ * target accepts, see kitc_cluster_features) gets degree 0 instead.
+ *
+ * kitc_mlp_loss_grad: loss[0] = mean softmax cross-entropy of the rows
+ * against labels (int32 in 0..KITC_MLP_CLASSES-1), loss[1] = number of rows
+ * whose label is out of range (left out of the sums), grad = gradient of
+ * loss[0] (KITC_MLP_NPARAM floats; zero for mu and sd).  work: device scratch
+ * of kitc_mlp_workspace_bytes(m) bytes, 16-byte aligned.  Fixed summation
+ * order: the same inputs give the same bits.
+ *
+ * kitc_mlp_adam_step: one bias-corrected Adam update (step counts from 1) of
+ * params with first and second moments m1, m2 (KITC_MLP_NPARAM floats each,
+ * zero before step 1); mu and sd are not updated. */
+size_t kitc_mlp_workspace_bytes(int64_t m);
+kitc_status kitc_mlp_forward(const float *params, const float *features, int64_t m, float *logits,
+                             const int32_t *class_degree, int zero_unused, int32_t *degrees,
+                             void *stream);
+kitc_status kitc_mlp_loss_grad(const float *params, const float *features, const int32_t *labels,
+                               int64_t m, float *loss, float *grad, void *work, void *stream);
+kitc_status kitc_mlp_adam_step(float *params, const float *grad, float *m1, float *m2, int step,
+                               float lr, float beta1, float beta2, float eps, void *stream);
 
 /* Eq. N-body by direct summation over all sources (self term included;
  * with eps = 0 a pair at r = 0 is skipped).  All pointers device.  Uses

@@ -39,6 +39,8 @@ struct kitc_tree_s {
     std::vector<int32_t> hdeg;
     DevBuf cdeg, roff, chebt;  // int32 [nclus], int64 [nclus] record offsets, double [17][17]
     int64_t proxy_bytes = 0;
+    bool lists_ready = false;  // target tree + lists of the last plan or evaluation
+    DevBuf learn;              // scratch of the feature and error kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -185,7 +187,7 @@ void free_handle(kitc_tree t)
     t->wts.release(s);
     t->lists.release(s);
     t->flags.release(s);
-    for (DevBuf *b : {&t->cdeg, &t->roff, &t->chebt}) b->release(s);
+    for (DevBuf *b : {&t->cdeg, &t->roff, &t->chebt, &t->learn}) b->release(s);
     if (t->ev_ok)
         for (auto &e : t->ev) cudaEventDestroy(e);
     delete t;
@@ -349,6 +351,20 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream)
     return KITC_OK;
 }
 
+// Target tree (leaf size = target batch) and the interaction lists.
+static kitc_status plan_impl(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
+                             const int64_t *counts, int nsys, cudaStream_t s)
+{
+    const kitc_params &p = t->p;
+    int B = p.target_batch;
+    t->lists_ready = false;
+    KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt, counts, nsys));
+    KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, t->var ? t->cdeg.as<int32_t>() : nullptr,
+                         p.mac, s, t->lists));
+    t->lists_ready = true;
+    return KITC_OK;
+}
+
 static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
                                  const int64_t *counts, int nsys, double *out, void *stream)
 {
@@ -361,9 +377,7 @@ static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_t
     int B = p.target_batch;
     t->evaluated = false;
     record(t, 4, s);
-    KITC_TRY(tree_build(tgt_xyz, n_tgt, B, s, t->tgt, counts, nsys));
-    KITC_TRY(lists_build(t->src, t->tgt, B, p.theta, p.degree, t->var ? t->cdeg.as<int32_t>() : nullptr,
-                          p.mac, s, t->lists));
+    KITC_TRY(plan_impl(t, tgt_xyz, n_tgt, counts, nsys, s));
     record(t, 5, s);
     EvalArgs a{};
     a.tx = t->tgt.xs.as<double>();
@@ -753,6 +767,91 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream)
     t->hdeg.swap(h);
     t->var = true;
     return KITC_OK;
+}
+
+
+kitc_status kitc_plan_targets(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, void *stream)
+{
+    if (!t || !valid_count(n_tgt) || !device_accessible(tgt_xyz)) return KITC_ERR_INVALID_ARG;
+    if (t->src.nsys > 1) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t->stream = s;
+    t->evaluated = false;
+    return plan_impl(t, tgt_xyz, n_tgt, nullptr, 1, s);
+}
+
+static kitc_status ensure_cheb_table(kitc_tree t, cudaStream_t s)
+{
+    if (t->chebt.ptr) return KITC_OK;
+    std::vector<double> tab((KITC_MAX_DEGREE + 1) * (KITC_MAX_DEGREE + 1), 0.0);
+    for (int d = 1; d <= KITC_MAX_DEGREE; ++d) cheb_cos_table(d, &tab[(size_t)d * (KITC_MAX_DEGREE + 1)]);
+    KITC_TRY(t->chebt.reserve(sizeof(double) * tab.size(), s));
+    KITC_CUDA(cudaMemcpyAsync(t->chebt.ptr, tab.data(), sizeof(double) * tab.size(),
+                              cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return KITC_OK;
+}
+
+static LearnArgs learn_args(kitc_tree t)
+{
+    LearnArgs a;
+    a.nclus = t->src.nclus;
+    a.win = t->win;
+    a.degree = t->p.degree;
+    a.eps = t->p.eps;
+    a.cbegin = t->src.begin.as<int32_t>();
+    a.cend = t->src.end.as<int32_t>();
+    a.perm = t->src.perm.as<int32_t>();
+    a.level = t->src.level.as<int32_t>();
+    a.cdeg = t->var ? t->cdeg.as<int32_t>() : nullptr;
+    a.ctr = t->src.ctr.as<dvec4>();
+    a.clo = t->src.lo.as<dvec4>();
+    a.chi = t->src.hi.as<dvec4>();
+    a.sxs = t->src.xs.as<double>();
+    a.ns = t->src.n;
+    a.txs = t->tgt.xs.as<double>();
+    a.nt = t->lists.nt;
+    a.nb = t->lists.nb;
+    a.batch = t->lists.batch;
+    a.bdesc = t->lists.forest ? t->lists.bdesc.as<int32_t>() : nullptr;
+    a.far_off = t->lists.far_off.as<int64_t>();
+    a.far_id = t->lists.far_id.as<int32_t>();
+    a.far_mask = t->lists.far_mask.as<uint64_t>();
+    a.fhat = t->wts.fhat.as<double>();
+    a.foff = t->var ? weights_foff(t->src, t->wts) : nullptr;
+    a.chebt = t->chebt.as<double>();
+    a.err = t->flags.as<int>() + 1;
+    return a;
+}
+
+kitc_status kitc_cluster_features(kitc_tree t, const double *w, float *features, void *stream)
+{
+    if (!t || !device_accessible(w) || !device_accessible(features)) return KITC_ERR_INVALID_ARG;
+    if (!t->lists_ready) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    KITC_TRY(ensure_cheb_table(t, s));
+    return learn_features(learn_args(t), w, features, t->learn, s);
+}
+
+kitc_status kitc_cluster_far_errors(kitc_tree t, const double *w, int max_samples, uint64_t seed,
+                                    double *err2, int32_t *n_samples, void *stream)
+{
+    if (!t || !device_accessible(w) || !device_accessible(err2) || !device_accessible(n_samples) ||
+        max_samples < 1 || t->p.kernel == KITC_TEST_POLY)
+        return KITC_ERR_INVALID_ARG;
+    if (!t->lists_ready || !t->has_weights) return KITC_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    KITC_TRY(ensure_cheb_table(t, s));
+    LearnArgs a = learn_args(t);
+    if (t->var && !a.foff) return KITC_ERR_STATE;
+    KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
+    KITC_TRY(learn_far_errors(t->p.kernel, a, w, max_samples, (unsigned long long)seed, err2,
+                              n_samples, t->learn, s));
+    int *h = nullptr;
+    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h)));
+    KITC_CUDA(cudaMemcpyAsync(h, t->flags.as<int>() + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    return h[0] ? KITC_ERR_INVALID_ARG : KITC_OK;
 }
 
 }  // extern "C"

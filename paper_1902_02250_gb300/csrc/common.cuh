@@ -227,6 +227,37 @@ struct EvalArgs {
 
 kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Per-cluster degree selection: features and measured far-field errors.
+// ---------------------------------------------------------------------------
+struct LearnArgs {
+    int nclus = 0, win = 3, degree = 1;
+    double eps = 0.0;
+    const int32_t *cbegin = nullptr, *cend = nullptr, *perm = nullptr, *level = nullptr;
+    const int32_t *cdeg = nullptr;           // degree map (NULL: degree everywhere)
+    const dvec4 *ctr = nullptr, *clo = nullptr, *chi = nullptr;
+    const double *sxs = nullptr;             // sources, SoA [3][ns] in tree order
+    int64_t ns = 0;
+    const double *txs = nullptr;             // targets, SoA [3][nt] in target-tree order
+    int64_t nt = 0, nb = 0;
+    int batch = 0;
+    const int32_t *bdesc = nullptr;          // forests: first slot, size, root per batch
+    const int64_t *far_off = nullptr;
+    const int32_t *far_id = nullptr;
+    const uint64_t *far_mask = nullptr;
+    const double *fhat = nullptr;            // FP64 modified weights
+    const int64_t *foff = nullptr;           // with a degree map: offset of each cluster's weights
+    const double *chebt = nullptr;           // [17][17] cos(k pi / n)
+    int *err = nullptr;
+};
+
+kitc_status learn_features(const LearnArgs &a, const double *w, float *feat, DevBuf &scratch,
+                           cudaStream_t s);
+kitc_status learn_far_errors(int kernel, const LearnArgs &a, const double *w, int S,
+                             unsigned long long seed, double *err2, int *nsamp, DevBuf &scratch,
+                             cudaStream_t s);
+const int64_t *weights_foff(const TreeDev &t, const WeightsDev &wd);
+
 // Counts one kernel launch of this library (see kitc_launch_count).
 void kitc_count_launch();
 

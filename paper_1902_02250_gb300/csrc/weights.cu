@@ -840,3 +840,10 @@ kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
+
+const int64_t *weights_foff(const TreeDev &t, const WeightsDev &wd)
+{
+    if (!wd.planned || !wd.var) return nullptr;
+    const Item *d_items = reinterpret_cast<const Item *>(wd.items.ptr);
+    return reinterpret_cast<const int64_t *>(d_items + wd.nitems) + t.nclus;
+}

@@ -77,7 +77,9 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_solve_host", "kitc_get_stats", "kitc_tree_download", "kitc_weights_download",
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
-           "kitc_launch_count", "kitc_set_degrees"]
+           "kitc_launch_count", "kitc_set_degrees", "kitc_plan_targets",
+           "kitc_cluster_features", "kitc_cluster_far_errors", "kitc_mlp_workspace_bytes",
+           "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step"]
 
 
 def library_path():
@@ -118,12 +120,23 @@ def lib():
         L.kitc_launch_count.argtypes = []
         L.kitc_launch_count.restype = I64
         L.kitc_set_degrees.argtypes = [P, P, P]
+        L.kitc_plan_targets.argtypes = [P, P, I64, P]
+        L.kitc_cluster_features.argtypes = [P, P, P, P]
+        L.kitc_cluster_far_errors.argtypes = [P, P, I, ctypes.c_uint64, P, P, P]
+        L.kitc_mlp_workspace_bytes.argtypes = [I64]
+        L.kitc_mlp_workspace_bytes.restype = ctypes.c_size_t
+        L.kitc_mlp_forward.argtypes = [P, P, I64, P, P, I, P, P]
+        L.kitc_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, P]
+        F = ctypes.c_float
+        L.kitc_mlp_adam_step.argtypes = [P, P, P, P, I, F, F, F, F, P]
         for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest", "kitc_apply",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_direct_noalloc",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest",
-                     "kitc_set_degrees"):
+                     "kitc_set_degrees", "kitc_plan_targets", "kitc_cluster_features",
+                     "kitc_cluster_far_errors", "kitc_mlp_forward", "kitc_mlp_loss_grad",
+                     "kitc_mlp_adam_step"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -388,3 +401,114 @@ def treecode(src_xyz, w, params, tgt_xyz=None, stream=None):
         return out, t.stats()
     finally:
         t.free()
+
+
+# ------------------------------------------------------- degree selection
+NFEAT, MLP_HIDDEN, MLP_CLASSES = 12, 64, 6
+MLP_NPARAM = 2 * 12 + 64 * 12 + 64 + 64 * 64 + 64 + 6 * 64 + 6
+
+
+def _dev(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s" % (name, shape))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kitc_plan_targets(tree, tgt_xyz, stream=None):
+    """Target tree and interaction lists for tgt_xyz, without evaluating."""
+    _check(lib().kitc_plan_targets(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
+                                   _stream(stream)), "kitc_plan_targets")
+
+
+def kitc_cluster_features(tree, w, out=None, stream=None):
+    """FP32 features (n_clusters x 12) of every source cluster."""
+    import torch
+    m = tree.stats()["n_clusters"]
+    if out is None:
+        out = torch.empty((m, NFEAT), dtype=torch.float32, device=w.device)
+    _check(lib().kitc_cluster_features(tree.handle, _dptr(w, kernel_win(tree.params.kernel), "w"),
+                                       _dev(out, torch.float32, (m, NFEAT), "out"),
+                                       _stream(stream)), "kitc_cluster_features")
+    return out
+
+
+def kitc_cluster_far_errors(tree, w, max_samples=32, seed=1, stream=None):
+    """(err2, n_samples) per cluster: summed squared far-field error of sampled
+    accepting targets against the direct sum over the cluster's sources."""
+    import torch
+    m = tree.stats()["n_clusters"]
+    err2 = torch.empty(m, dtype=torch.float64, device=w.device)
+    ns = torch.empty(m, dtype=torch.int32, device=w.device)
+    _check(lib().kitc_cluster_far_errors(tree.handle, _dptr(w, kernel_win(tree.params.kernel), "w"),
+                                         int(max_samples), int(seed) & (2 ** 64 - 1),
+                                         ctypes.c_void_p(err2.data_ptr()),
+                                         ctypes.c_void_p(ns.data_ptr()), _stream(stream)),
+           "kitc_cluster_far_errors")
+    return err2, ns
+
+
+def kitc_mlp_forward(params, features, class_degree=None, logits=True, zero_unused=False,
+                     stream=None):
+    """(logits or None, degrees or None) of the selector for the feature rows;
+    zero_unused gives degree 0 to clusters that no target accepts."""
+    import torch
+    m = features.shape[0]
+    lg = torch.empty((m, MLP_CLASSES), dtype=torch.float32, device=features.device) if logits else None
+    deg = None
+    cls = None
+    if class_degree is not None:
+        cls = np.ascontiguousarray(class_degree, np.int32)
+        if cls.shape != (MLP_CLASSES,):
+            raise ValueError("class_degree must hold %d degrees" % MLP_CLASSES)
+        deg = torch.empty(m, dtype=torch.int32, device=features.device)
+    _check(lib().kitc_mlp_forward(_dev(params, torch.float32, (MLP_NPARAM,), "params"),
+                                  _dev(features, torch.float32, (m, NFEAT), "features"), m,
+                                  None if lg is None else ctypes.c_void_p(lg.data_ptr()),
+                                  None if cls is None else _np(cls), int(bool(zero_unused)),
+                                  None if deg is None else ctypes.c_void_p(deg.data_ptr()),
+                                  _stream(stream)), "kitc_mlp_forward")
+    return lg, deg
+
+
+class MLPTrainer:
+    """Device buffers of one training run (gradient, Adam moments, workspace)."""
+
+    def __init__(self, params, m):
+        import torch
+        self.params = params
+        self.m = int(m)
+        dev_ = params.device
+        self.grad = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=dev_)
+        self.m1 = torch.zeros_like(self.grad)
+        self.m2 = torch.zeros_like(self.grad)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=dev_)
+        nb = lib().kitc_mlp_workspace_bytes(self.m)
+        self.work = torch.empty((nb + 15) // 16 * 4, dtype=torch.float32, device=dev_)
+        self.step_count = 0
+
+    def loss_grad(self, features, labels, stream=None):
+        import torch
+        _check(lib().kitc_mlp_loss_grad(_dev(self.params, torch.float32, (MLP_NPARAM,), "params"),
+                                        _dev(features, torch.float32, (self.m, NFEAT), "features"),
+                                        _dev(labels, torch.int32, (self.m,), "labels"), self.m,
+                                        ctypes.c_void_p(self.loss.data_ptr()),
+                                        ctypes.c_void_p(self.grad.data_ptr()),
+                                        ctypes.c_void_p(self.work.data_ptr()), _stream(stream)),
+               "kitc_mlp_loss_grad")
+        return self.loss, self.grad
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.step_count += 1
+        _check(lib().kitc_mlp_adam_step(ctypes.c_void_p(self.params.data_ptr()),
+                                        ctypes.c_void_p(self.grad.data_ptr()),
+                                        ctypes.c_void_p(self.m1.data_ptr()),
+                                        ctypes.c_void_p(self.m2.data_ptr()), self.step_count,
+                                        lr, beta1, beta2, eps, _stream(stream)),
+               "kitc_mlp_adam_step")
+
+    def step(self, features, labels, lr, stream=None):
+        self.loss_grad(features, labels, stream)
+        self.adam(lr, stream=stream)
