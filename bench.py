@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
-    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched"],
-                    help="batched: 256 independent systems (a parity/measurement case, not "
-                         "the headline line)")
+    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned"],
+                    help="batched: 256 independent systems; learned: per-cluster degrees "
+                         "chosen by the trained selector on an 8M Plummer system (measurement "
+                         "cases beside the headline line)")
     ap.add_argument("--literal", action="store_true",
                     help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
     args = ap.parse_args()
@@ -453,11 +454,162 @@ def run_batched(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# Learned-degree workload: 8M Plummer system (7.2M Plummer, a = 0.1, truncated at
+# r = 2, plus 0.8M uniform in [-2,2]^3), Stokeslet, eps = 1e-3, theta = 0.7,
+# batch MAC, mixed, N0 = 2000.  The selector is trained on another system of
+# the same recipe (seed 15); labels aim at a far-field error of LEARNED_BUDGET so
+# that the whole error stays under 1e-6.
+LEARNED_N = 8_000_000
+LEARNED_SEED, LEARNED_TRAIN_SEED = 5, 15
+LEARNED_LEAF = 2000
+LEARNED_BUDGET = 0.5e-6
+LEARNED_TARGET_E = 1e-6
+
+
+def run_learned(args, ws, rank, local):
+    """Learned per-cluster degree vs the fixed-degree treecode at matched error."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K, learned as LD, workloads as wl
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def P(**kw):
+        b = dict(theta=0.7, degree=8, leaf_size=LEARNED_LEAF, eps=EPS, kernel=K.STOKESLET,
+                 precision=K.MIXED, mac=K.MAC_BATCH, target_batch=BATCH)
+        b.update(kw)
+        return K.Params(**b)
+
+    # training: the treecode measures per-cluster far-field errors on another system
+    t0 = time.perf_counter()
+    xt, ft = wl.plummer_with_background(LEARNED_N, LEARNED_TRAIN_SEED + rank)
+    xtd, ftd = torch.from_numpy(xt).to(dev), torch.from_numpy(ft).to(dev)
+    meas = LD.measure(xtd, ftd, P())
+    lab, valid, tau = LD.labels(meas, LEARNED_BUDGET)
+    rows = torch.from_numpy(np.nonzero(valid)[0]).to(dev)
+    params, rep = LD.train(meas["features"][rows].contiguous(), lab[valid])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del xtd, ftd, meas
+
+    n = LEARNED_N
+    x, f = wl.plummer_with_background(n, LEARNED_SEED + rank)
+    xd, fd = torch.from_numpy(x).to(dev), torch.from_numpy(f).to(dev)
+    out = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    idx = wl.sample_indices(n, N_SAMPLE, SAMPLE_SEED)
+    ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd, fd,
+                        K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
+
+    def fixed_step(p, o):
+        t = K.kitc_build_tree(xd, p)
+        try:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate(t, xd, o)
+            return t.stats()
+        finally:
+            t.free()
+
+    def learned_step(p, o):
+        return LD.learned_step(xd, fd, p, params, o)
+
+    def timed(fn, p, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            fn(p, out)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms, st = [], None
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = fn(p, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return reduce_max(sum(ms), ws) / steps, st
+
+    # the fixed degree: the smallest n with E <= 1e-6 (work grows with n)
+    fixed = []
+    best = None
+    for nd in range(7, 14):
+        ms, st = timed(fixed_step, P(degree=nd), 1, 1)
+        E = rel_l2(ref, out.cpu().numpy()[idx])
+        fixed.append({"degree": nd, "ms": ms, "E": E, "far_points": st["far_points"]})
+        if E <= LEARNED_TARGET_E:
+            best = nd
+            break
+    # timed comparison: learned, then the fixed degree, same protocol
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = K.kitc_launch_count()
+    ms_l, st_l = timed(learned_step, P(), args.steps, args.warmup)
+    launches = K.kitc_launch_count() - l0
+    clk = clocks.stop()
+    E_l = rel_l2(ref, out.cpu().numpy()[idx])
+    ms_f, st_f = timed(fixed_step, P(degree=best), args.steps, 1) if best else (None, None)
+    E_f = rel_l2(ref, out.cpu().numpy()[idx]) if best else None
+    fallback = E_l > LEARNED_TARGET_E
+    value_l = ws * n / (ms_l / 1e3)
+    value_f = ws * n / (ms_f / 1e3) if best else None
+    value = value_f if (fallback and best) else value_l
+    flops = FLOPS_PER_INTERACTION * (st_l["near_pairs"] + st_l["far_points"])
+    achieved = flops / (st_l["ms_evaluate"] / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {"metric": "Stokeslet targets/sec at 1e-6 rel. L2 error, N=8M Plummer, learned "
+                      "per-cluster degree vs fixed degree",
+            "value": value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_f if (fallback and best) else ms_l,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
+            "config": {"workload": "Plummer a = 0.1 truncated at r = 2 (7.2M) + U[-2,2]^3 (0.8M), "
+                                   "seed %d + rank; f ~ U[-1,1]^3" % LEARNED_SEED,
+                       "eps": EPS, "theta": 0.7, "leaf_size": LEARNED_LEAF, "target_batch": BATCH,
+                       "mac": "batch", "precision": "mixed",
+                       "degree_classes": list(LD.CLASSES),
+                       "training": "selector trained on seed %d (same recipe), labels at "
+                                   "far-field budget %.1e" % (LEARNED_TRAIN_SEED, LEARNED_BUDGET),
+                       "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "learned": {"value": value_l, "ms": ms_l, "E": E_l, "far_points": st_l["far_points"],
+                        "near_pairs": st_l["near_pairs"],
+                        "stage_ms": {k: st_l[k] for k in ("ms_tree", "ms_weights", "ms_lists",
+                                                          "ms_evaluate")}},
+            "fixed": {"degree": best, "value": value_f, "ms": ms_f, "E": E_f,
+                      "far_points": st_f["far_points"] if st_f else None, "search": fixed},
+            "fallback_to_fixed": bool(fallback),
+            "speedup_vs_fixed": (value_l / value_f) if (best and not fallback) else None,
+            "training": {"seconds": train_s, "clusters": int(valid.sum()), "tau": tau,
+                         "accuracy": rep["accuracy"],
+                         "label_hist": np.bincount(lab[valid], minlength=len(LD.CLASSES)).tolist()},
+            "roofline": {"kernel": "k_eval<Stokeslet, mixed> (learned degrees)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "flops_per_interaction": FLOPS_PER_INTERACTION,
+                         "launch_ms": st_l["ms_evaluate"], "traffic": None},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_fp64 and best:
+        pf = P(degree=best, precision=K.FP64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fixed_step(pf, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        line["plain_fp64"] = {"value": n / (ms64 / 1e3), "unit": "targets/s", "ms_per_step": ms64,
+                              "degree": best, "E": rel_l2(ref, out.cpu().numpy()[idx])}
+        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
     if args.workload == "batched" and args.impl != "reference":
         run_batched(args, ws, rank, local)
+    elif args.workload == "learned" and args.impl != "reference":
+        run_learned(args, ws, rank, local)
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:

@@ -108,7 +108,7 @@ typedef struct kitc_tree_s *kitc_tree; /* opaque; owned by the library */
 typedef struct {
     int64_t n_sources, n_clusters, n_leaves;
     int32_t depth, degree;
-    int64_t n_targets, n_batches;          /* of the last kitc_evaluate                */
+    int64_t n_targets, n_batches;          /* of the last kitc_evaluate or plan        */
     int64_t far_entries, near_entries;     /* interaction-list entries (batch, cluster) */
     int64_t near_pairs, far_points;        /* (target, source) and (target, grid point)
                                               kernel evaluations that count toward u   */
@@ -190,6 +190,15 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream);
  * are chosen.  Feeds kitc_cluster_features / kitc_cluster_far_errors.
  * KITC_ERR_STATE on a forest.  Synchronizes `stream`. */
 kitc_status kitc_plan_targets(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, void *stream);
+
+/* Algorithm 2 at the targets of the last kitc_plan_targets (or evaluation),
+ * reusing its target tree and lists (the target coordinates were copied at
+ * planning): the evaluation of kitc_evaluate without the list build.  Under a
+ * degree map set after planning, the far-field counts are recomputed and
+ * KITC_ERR_INVALID_ARG is returned if an accepted cluster has degree 0.
+ * out: device, n_tgt x w_out in the planned targets' order.  KITC_ERR_STATE
+ * without lists or weights. */
+kitc_status kitc_evaluate_planned(kitc_tree t, double *out, void *stream);
 
 /* Features of every source cluster c for the degree selector, written as
  * FP32 row c of features (device, n_clusters x KITC_NFEAT):

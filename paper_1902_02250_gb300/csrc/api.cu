@@ -365,19 +365,25 @@ static kitc_status plan_impl(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
     return KITC_OK;
 }
 
+// tgt_xyz == NULL: the targets and lists of the last plan (kitc_evaluate_planned).
 static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
                                  const int64_t *counts, int nsys, double *out, void *stream)
 {
-    if (!t || !valid_count(n_tgt) || !device_accessible(tgt_xyz) || !device_accessible(out))
-        return KITC_ERR_INVALID_ARG;
-    if (!t->has_weights) return KITC_ERR_STATE;
+    if (!t || !device_accessible(out)) return KITC_ERR_INVALID_ARG;
+    if (tgt_xyz && (!valid_count(n_tgt) || !device_accessible(tgt_xyz))) return KITC_ERR_INVALID_ARG;
+    if (!t->has_weights || (!tgt_xyz && !t->lists_ready)) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     t->stream = s;
     const kitc_params &p = t->p;
     int B = p.target_batch;
     t->evaluated = false;
     record(t, 4, s);
-    KITC_TRY(plan_impl(t, tgt_xyz, n_tgt, counts, nsys, s));
+    if (tgt_xyz) {
+        KITC_TRY(plan_impl(t, tgt_xyz, n_tgt, counts, nsys, s));
+    } else {
+        n_tgt = t->lists.nt;
+        if (t->var) KITC_TRY(lists_recount(t->cdeg.as<int32_t>(), s, t->lists));
+    }
     record(t, 5, s);
     EvalArgs a{};
     a.tx = t->tgt.xs.as<double>();
@@ -428,6 +434,11 @@ kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, dou
 {
     if (t && t->src.nsys > 1) return KITC_ERR_STATE;
     return evaluate_impl(t, tgt_xyz, n_tgt, nullptr, 1, out, stream);
+}
+
+kitc_status kitc_evaluate_planned(kitc_tree t, double *out, void *stream)
+{
+    return evaluate_impl(t, nullptr, 0, nullptr, 1, out, stream);
 }
 
 kitc_status kitc_evaluate_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
@@ -537,7 +548,7 @@ kitc_status kitc_get_stats(kitc_tree t, kitc_stats *s)
     s->n_leaves = t->src.nleaves;
     s->depth = t->src.depth;
     s->degree = t->p.degree;
-    if (t->evaluated) {
+    if (t->evaluated || t->lists_ready) {
         s->n_targets = t->lists.nt;
         s->n_batches = t->lists.nb;
         s->far_entries = t->lists.nfar;
@@ -613,9 +624,28 @@ kitc_status kitc_weights_download(kitc_tree t, double *fhat, void *stream)
     if (!t || !fhat) return KITC_ERR_INVALID_ARG;
     if (!t->has_weights) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (t->var) {  // gather each cluster's weights, in cluster order
+        const int m = t->src.nclus;
+        std::vector<double> all((size_t)std::max<int64_t>(t->wts.fhat_len, 1));
+        std::vector<int64_t> fo(m);
+        const int64_t *d_f = weights_foff(t->src, t->wts);
+        if (!d_f) return KITC_ERR_STATE;
+        KITC_CUDA(cudaMemcpyAsync(all.data(), t->wts.fhat.ptr, sizeof(double) * t->wts.fhat_len,
+                                  cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaMemcpyAsync(fo.data(), d_f, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        size_t o = 0;
+        for (int c = 0; c < m; ++c) {
+            int d = t->hdeg[c];
+            if (d <= 0) continue;
+            size_t k = (size_t)(d + 1) * (d + 1) * (d + 1) * t->win;
+            memcpy(fhat + o, all.data() + fo[c], sizeof(double) * k);
+            o += k;
+        }
+        return KITC_OK;
+    }
     int np = t->p.degree + 1;
-    size_t bytes = t->var ? sizeof(double) * (size_t)t->wts.fhat_len
-                          : sizeof(double) * (size_t)t->src.nclus * np * np * np * t->win;
+    size_t bytes = sizeof(double) * (size_t)t->src.nclus * np * np * np * t->win;
     KITC_CUDA(cudaMemcpyAsync(fhat, t->wts.fhat.ptr, bytes, cudaMemcpyDeviceToHost, s));
     KITC_CUDA(cudaStreamSynchronize(s));
     return KITC_OK;
@@ -803,6 +833,8 @@ static LearnArgs learn_args(kitc_tree t)
     a.cend = t->src.end.as<int32_t>();
     a.perm = t->src.perm.as<int32_t>();
     a.level = t->src.level.as<int32_t>();
+    a.first_child = t->src.first_child.as<int32_t>();
+    a.n_child = t->src.n_child.as<int32_t>();
     a.cdeg = t->var ? t->cdeg.as<int32_t>() : nullptr;
     a.ctr = t->src.ctr.as<dvec4>();
     a.clo = t->src.lo.as<dvec4>();
@@ -830,7 +862,7 @@ kitc_status kitc_cluster_features(kitc_tree t, const double *w, float *features,
     if (!t->lists_ready) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     KITC_TRY(ensure_cheb_table(t, s));
-    return learn_features(learn_args(t), w, features, t->learn, s);
+    return learn_features(learn_args(t), t->src.level_start, w, features, t->learn, s);
 }
 
 kitc_status kitc_cluster_far_errors(kitc_tree t, const double *w, int max_samples, uint64_t seed,

@@ -115,7 +115,9 @@ struct WeightsDev {
     };
     std::vector<Group> groups;
     bool var = false;
-    int64_t fhat_len = 0;  // doubles of fhat in use
+    bool var_upward = false;  // degree map: upward form (else Algorithm 1 on every cluster)
+    int var_pmax = 0;         // degree map: largest grid size of the upward form
+    int64_t fhat_len = 0;     // doubles of fhat in use
     DevBuf fhat;      // double [nclus][P][win]
     DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
     DevBuf src;       // evaluator records of the sources in tree order
@@ -186,6 +188,9 @@ struct ListsDev {
 
 kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
                         int degree, const int32_t *cdeg, int mac, cudaStream_t s, ListsDev &L);
+// Far-field point counts of existing lists under the degree map cdeg;
+// KITC_ERR_INVALID_ARG if an accepted cluster has degree 0.
+kitc_status lists_recount(const int32_t *cdeg, cudaStream_t s, ListsDev &L);
 
 // ---------------------------------------------------------------------------
 // Fused near/far evaluator.
@@ -235,6 +240,7 @@ struct LearnArgs {
     double eps = 0.0;
     const int32_t *cbegin = nullptr, *cend = nullptr, *perm = nullptr, *level = nullptr;
     const int32_t *cdeg = nullptr;           // degree map (NULL: degree everywhere)
+    const int32_t *first_child = nullptr, *n_child = nullptr;
     const dvec4 *ctr = nullptr, *clo = nullptr, *chi = nullptr;
     const double *sxs = nullptr;             // sources, SoA [3][ns] in tree order
     int64_t ns = 0;
@@ -251,8 +257,8 @@ struct LearnArgs {
     int *err = nullptr;
 };
 
-kitc_status learn_features(const LearnArgs &a, const double *w, float *feat, DevBuf &scratch,
-                           cudaStream_t s);
+kitc_status learn_features(const LearnArgs &a, const std::vector<int32_t> &level_start,
+                           const double *w, float *feat, DevBuf &scratch, cudaStream_t s);
 kitc_status learn_far_errors(int kernel, const LearnArgs &a, const double *w, int S,
                              unsigned long long seed, double *err2, int *nsamp, DevBuf &scratch,
                              cudaStream_t s);

@@ -42,46 +42,60 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-// Block per cluster: |sum_j f_j|, sum_j |f_j| and max_j |f_j| over its sources.
-__global__ void k_feat_sources(const LearnArgs a, const double *__restrict__ w, double *__restrict__ acc)
+// Weight statistics of a cluster, 8 doubles: sum_j f_j (w_in <= 6 components),
+// sum_j |f_j|, max_j |f_j|.
+constexpr int WS = 8;
+
+// Block per leaf: the statistics over the leaf's sources.
+__global__ void k_feat_leaf(const LearnArgs a, const double *__restrict__ w, double *__restrict__ acc)
 {
     const int c = blockIdx.x;
+    if (a.n_child[c] != 0) return;
     const int p0 = a.cbegin[c], p1 = a.cend[c];
-    double s[6] = {0, 0, 0, 0, 0, 0}, sabs = 0.0, smax = 0.0;
+    double v[WS] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const double *f = w + (int64_t)a.perm[p] * a.win;
         double q = 0.0;
         for (int l = 0; l < a.win; ++l) {
-            s[l] += f[l];
+            v[l] += f[l];
             q += f[l] * f[l];
         }
         q = sqrt(q);
-        sabs += q;
-        smax = fmax(smax, q);
+        v[6] += q;
+        v[7] = fmax(v[7], q);
     }
-    __shared__ double red[8][8];
+    __shared__ double red[4][WS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double v[8] = {s[0], s[1], s[2], s[3], s[4], s[5], sabs, smax};
 #pragma unroll
     for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[7] = fmax(v[7], __shfl_xor_sync(0xffffffffu, v[7], o));
     if (lane == 0)
-        for (int k = 0; k < 8; ++k) red[wid][k] = v[k];
+        for (int k = 0; k < WS; ++k) red[wid][k] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = 0; q < nw; ++q) {
-            for (int k = 0; k < 7; ++k) t[k] += red[q][k];
-            t[7] = fmax(t[7], red[q][7]);
-        }
-        double n2 = 0.0;
-        for (int l = 0; l < a.win; ++l) n2 += t[l] * t[l];
-        acc[3 * c + 0] = sqrt(n2);
-        acc[3 * c + 1] = t[6];
-        acc[3 * c + 2] = t[7];
+    if (threadIdx.x < WS) {
+        const int k = threadIdx.x;
+        double t = red[0][k];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = k == 7 ? fmax(t, red[q][k]) : t + red[q][k];
+        acc[(size_t)c * WS + k] = t;
     }
+}
+
+// Thread per cluster of one level: the statistics of an internal cluster from
+// its children's (in child order).
+__global__ void k_feat_merge(const LearnArgs a, int lb, int le, double *__restrict__ acc)
+{
+    const int c = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= le) return;
+    const int nch = a.n_child[c];
+    if (nch == 0) return;
+    double v[WS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < nch; ++i) {
+        const double *u = acc + (size_t)(a.first_child[c] + i) * WS;
+        for (int k = 0; k < 7; ++k) v[k] += u[k];
+        v[7] = fmax(v[7], u[7]);
+    }
+    for (int k = 0; k < WS; ++k) acc[(size_t)c * WS + k] = v[k];
 }
 
 // Warp per target batch: for every far entry (batch, cluster) the accepting
@@ -104,23 +118,26 @@ __global__ void k_feat_targets(const LearnArgs a, unsigned long long *__restrict
         const int c = a.far_id[e];
         const uint64_t mk = a.far_mask[e];
         const dvec4 g = a.ctr[c];
-        double qs = 0.0;
+        // FP32 ratios (the features are FP32): offsets formed in FP64 first
+        const float r = (float)g.w;
+        float qs = 0.f;
         float mn = FLT_MAX, mx = 0.f;
         for (int t = 0; t < 2; ++t) {
             if (!((mk >> (lane + 32 * t)) & 1ull)) continue;
-            double dx = x[t][0] - g.x, dy = x[t][1] - g.y, dz = x[t][2] - g.z;
-            double R = sqrt(dx * dx + dy * dy + dz * dz);
-            double q = R > 0.0 ? g.w / R : 0.0;
+            float dx = (float)(x[t][0] - g.x), dy = (float)(x[t][1] - g.y), dz = (float)(x[t][2] - g.z);
+            float R2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float q = R2 > 0.f ? r * rsqrtf(R2) : 0.f;
             qs += q;
-            mn = fminf(mn, (float)q);
-            mx = fmaxf(mx, (float)q);
+            mn = fminf(mn, q);
+            mx = fmaxf(mx, q);
         }
-        qs = warp_sum(qs);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
         mn = warp_min(mn);
         mx = warp_max(mx);
         if (lane == 0 && mk) {
             atomicAdd(cnt + c, (unsigned long long)__popcll(mk));
-            atomicAdd(qsum + c, qs);
+            atomicAdd(qsum + c, (double)qs);
             atomicMin(qmin + c, __float_as_uint(mn));  // q >= 0: bit order is value order
             atomicMax(qmax + c, __float_as_uint(mx));
         }
@@ -165,9 +182,12 @@ __global__ void k_feat_final(const LearnArgs a, int m, const double *__restrict_
     o[3] = k ? (float)(qsum[c] / (double)k) : 0.f;
     o[4] = k ? __uint_as_float(qmax[c]) : 0.f;
     o[5] = (float)fmin(a.eps / fmax(r, 1e-300), 10.0);
-    o[6] = (float)log(1e-30 + acc[3 * c + 0]);
-    o[7] = (float)log(1e-30 + acc[3 * c + 1]);
-    o[8] = (float)log(1e-30 + acc[3 * c + 2]);
+    const double *u = acc + (size_t)c * WS;
+    double n2 = 0.0;
+    for (int l = 0; l < a.win; ++l) n2 += u[l] * u[l];
+    o[6] = (float)log(1e-30 + sqrt(n2));
+    o[7] = (float)log(1e-30 + u[6]);
+    o[8] = (float)log(1e-30 + u[7]);
     o[9] = side[0] > 0.0 ? (float)(side[1] / side[0]) : 1.f;
     o[10] = side[0] > 0.0 ? (float)(side[2] / side[0]) : 1.f;
     o[11] = (float)a.level[c];
@@ -273,15 +293,15 @@ __global__ void k_far_errors(const LearnArgs a, const double *__restrict__ w, in
 
 }  // namespace
 
-kitc_status learn_features(const LearnArgs &a, const double *w, float *feat, DevBuf &scratch,
-                           cudaStream_t s)
+kitc_status learn_features(const LearnArgs &a, const std::vector<int32_t> &level_start,
+                           const double *w, float *feat, DevBuf &scratch, cudaStream_t s)
 {
     const int m = a.nclus;
-    size_t bytes = (size_t)m * (3 * sizeof(double) + sizeof(unsigned long long) + sizeof(double) +
+    size_t bytes = (size_t)m * (WS * sizeof(double) + sizeof(unsigned long long) + sizeof(double) +
                                 2 * sizeof(unsigned));
     KITC_TRY(scratch.reserve(bytes + 64, s));
     double *acc = scratch.as<double>();
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(acc + 3 * (size_t)m);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(acc + WS * (size_t)m);
     double *qsum = reinterpret_cast<double *>(cnt + m);
     unsigned *qmin = reinterpret_cast<unsigned *>(qsum + m);
     unsigned *qmax = qmin + m;
@@ -289,7 +309,13 @@ kitc_status learn_features(const LearnArgs &a, const double *w, float *feat, Dev
     kitc_count_launch();
     k_feat_init<<<g, 256, 0, s>>>(m, cnt, qsum, qmin, qmax);
     kitc_count_launch();
-    k_feat_sources<<<m, 128, 0, s>>>(a, w, acc);
+    k_feat_leaf<<<m, 128, 0, s>>>(a, w, acc);
+    for (int L = (int)level_start.size() - 2; L >= 0; --L) {  // deepest level first
+        const int lb = level_start[L], le = level_start[L + 1];
+        if (le <= lb) continue;
+        kitc_count_launch();
+        k_feat_merge<<<(le - lb + 127) / 128, 128, 0, s>>>(a, lb, le, acc);
+    }
     if (a.nb > 0) {
         kitc_count_launch();
         k_feat_targets<<<(unsigned)((a.nb + 7) / 8), 256, 0, s>>>(a, cnt, qsum, qmin, qmax);

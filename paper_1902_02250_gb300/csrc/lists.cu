@@ -230,7 +230,65 @@ __global__ void k_scan64(const int64_t *__restrict__ in, int64_t m, int64_t *__r
     }
 }
 
+// Far-field grid points of existing lists under a degree map: warp per batch;
+// totals[0] += points the batches' targets use, totals[1] += points evaluated,
+// *err = 2 when an accepted cluster has degree 0.
+__global__ void k_far_recount(int64_t nt, int batch, int64_t nb, const int32_t *__restrict__ bdesc,
+                              const int64_t *__restrict__ far_off, const int32_t *__restrict__ far_id,
+                              const uint64_t *__restrict__ far_mask, const int32_t *__restrict__ cdeg,
+                              unsigned long long *__restrict__ totals, int *__restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nb) return;
+    const int64_t s0 = bdesc ? (int64_t)bdesc[b] : b * batch;
+    const int64_t s1 = bdesc ? s0 + bdesc[nb + b] : min(nt, s0 + batch);
+    const unsigned long long nvalid = (unsigned long long)(s1 - s0);
+    unsigned long long pts = 0, xpts = 0;
+    for (int64_t e = far_off[b] + lane; e < far_off[b + 1]; e += 32) {
+        const int g = cdeg[far_id[e]] + 1;
+        if (g < 2) atomicExch(err, 2);
+        const unsigned long long g3 = (unsigned long long)g * g * g;
+        pts += (unsigned long long)__popcll(far_mask[e]) * g3;
+        xpts += nvalid * g3;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pts += __shfl_xor_sync(0xffffffffu, pts, o);
+        xpts += __shfl_xor_sync(0xffffffffu, xpts, o);
+    }
+    if (lane == 0 && pts) {
+        atomicAdd(totals, pts);
+        atomicAdd(totals + 1, xpts);
+    }
+}
+
 }  // namespace
+
+kitc_status lists_recount(const int32_t *cdeg, cudaStream_t s, ListsDev &L)
+{
+    int64_t *tot = L.totals.as<int64_t>();
+    KITC_CUDA(cudaMemsetAsync(tot + 6, 0, sizeof(int64_t) * 2, s));
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(tot + 6);
+    int *err = reinterpret_cast<int *>(L.counts.as<int64_t>());  // the pass-0 counts are spent
+    KITC_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (L.nb > 0) {
+        kitc_count_launch();
+        k_far_recount<<<(unsigned)((L.nb + LW - 1) / LW), LW * 32, 0, s>>>(
+            L.nt, L.batch, L.nb, L.forest ? L.bdesc.as<int32_t>() : nullptr, L.far_off.as<int64_t>(),
+            L.far_id.as<int32_t>(), L.far_mask.as<uint64_t>(), cdeg, acc, err);
+        KITC_CUDA(cudaGetLastError());
+    }
+    int64_t *h = nullptr;
+    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h)));
+    KITC_CUDA(cudaMemcpyAsync(h, tot + 6, sizeof(int64_t) * 2, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(h + 2, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaStreamSynchronize(s));
+    if (reinterpret_cast<int *>(h + 2)[0] != 0) return KITC_ERR_INVALID_ARG;
+    L.far_points = h[0];
+    L.far_exec = h[1];
+    return KITC_OK;
+}
 
 void ListsDev::release(cudaStream_t s)
 {

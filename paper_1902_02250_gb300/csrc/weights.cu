@@ -646,28 +646,122 @@ kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, i
 // ---------------------------------------------------------------------------
 // Degree per cluster (kitc_set_degrees).  Cluster c has degree deg[c] (0: no
 // modified weights); its FP64 weights start at fhat + foff[c] and its grid
-// records at proxy + roff[c] bytes.  Every cluster runs Algorithm 1 (one
-// launch per distinct degree); the upward pass is not used because a child of
-// lower degree does not reproduce its parent's Lagrange polynomials.
+// records at proxy + roff[c] bytes.
+//
+// Upward form (used when its shared memory fits): let A_c be the largest degree
+// on the path from the root to c.  Leaves get Algorithm 1 at degree A_c, every
+// parent gets the weights at A_p from its children through the parent's
+// barycentric basis at the children's points (exact: A_child >= A_p, so a
+// child's degree-A_child interpolation reproduces the parent's degree-A_p
+// Lagrange polynomials, Sec. 2), and a cluster with deg[c] < A_c is then taken
+// down to deg[c] the same way with its own points as the source (exact for
+// the same reason).  Otherwise every cluster runs Algorithm 1 at deg[c].
+// Either way fhat equals Eq. modified_weights at each cluster's degree up to
+// rounding.
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void k_weights_reduce_var(const int32_t *__restrict__ deg, int win,
+// Sums the work-item partials of cluster c (icount[c] > 0) into fhat + roff[c]
+// at degree rdeg[c].
+__global__ void k_weights_reduce_var(const int32_t *__restrict__ rdeg, int win,
                                      const int64_t *__restrict__ pstart,
                                      const int32_t *__restrict__ icount,
-                                     const int64_t *__restrict__ foff,
+                                     const int64_t *__restrict__ roff,
                                      const double *__restrict__ partial, double *__restrict__ fhat)
 {
     int c = blockIdx.x;
-    int d = deg[c];
-    if (d <= 0) return;
-    int np = d + 1, pw = np * np * np * win;
+    int ni = icount[c];
+    if (ni <= 0) return;
+    int np = rdeg[c] + 1, pw = np * np * np * win;
     const double *src = partial + pstart[c];
     for (int o = threadIdx.x; o < pw; o += blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < icount[c]; ++i) s += src[(size_t)i * pw + o];
-        fhat[foff[c] + o] = s;
+        for (int i = 0; i < ni; ++i) s += src[(size_t)i * pw + o];
+        fhat[roff[c] + o] = s;
     }
+}
+
+// Block per destination cluster p of [lb, lb + gridDim.x).  UP: p's weights at
+// degree adeg[p] from its children's (degree adeg[child], at goff); otherwise
+// p's own weights at adeg[p] taken down to deg[p] (written at foff[p]).
+// Three 1D contractions per source (the grids are tensor products).
+template <bool UP>
+__global__ void __launch_bounds__(WT) k_transfer(
+    int lb, const Cheb *__restrict__ chebs, const dvec4 *__restrict__ lo,
+    const dvec4 *__restrict__ hi, const int32_t *__restrict__ first_child,
+    const int32_t *__restrict__ n_child, const int32_t *__restrict__ adeg,
+    const int32_t *__restrict__ deg, const int64_t *__restrict__ goff,
+    const int64_t *__restrict__ foff, int win, int pmax, double *__restrict__ fhat)
+{
+    extern __shared__ double sm[];
+    const int p = lb + blockIdx.x;
+    int dd, nsrc, src0;
+    double *dst;
+    if (UP) {
+        dd = adeg[p];
+        nsrc = n_child[p];
+        if (dd <= 0 || nsrc == 0) return;
+        src0 = first_child[p];
+        dst = fhat + goff[p];
+    } else {
+        dd = deg[p];
+        if (dd <= 0 || dd == adeg[p]) return;
+        nsrc = 1;
+        src0 = p;
+        dst = fhat + foff[p];
+    }
+    const Cheb &cd = chebs[dd];
+    const int pd = dd + 1, pdw = pd * pd * pd * win;
+    const size_t big = (size_t)pmax * pmax * pmax * win;
+    double *T1 = sm, *T2 = T1 + big, *A = T2 + big, *M = A + big;  // M[l][k'][k] = L^dst_k(s^src_k')
+    for (int i = threadIdx.x; i < pdw; i += WT) A[i] = 0.0;
+    const dvec4 plo = lo[p], phi = hi[p];
+    for (int ci = 0; ci < nsrc; ++ci) {
+        const int c = src0 + ci;
+        const int ds = adeg[c], ps = ds + 1;
+        const Cheb &cs = chebs[ds];
+        const dvec4 clo = lo[c], chi = hi[c];
+        __syncthreads();
+        for (int q = threadIdx.x; q < 3 * ps; q += WT) {
+            int l = q / ps, kp = q % ps;
+            double ca = l == 0 ? clo.x : (l == 1 ? clo.y : clo.z);
+            double cb_ = l == 0 ? chi.x : (l == 1 ? chi.y : chi.z);
+            double pa = l == 0 ? plo.x : (l == 1 ? plo.y : plo.z);
+            double pb = l == 0 ? phi.x : (l == 1 ? phi.y : phi.z);
+            double y = __dmul_rn(0.5, __dadd_rn(__dadd_rn(ca, cb_), __dmul_rn(cs.t[kp], __dsub_rn(cb_, ca))));
+            double L[KITC_MAX_DEGREE + 1];
+            bary_basis(cd, pa, pb, y, L);
+            for (int k = 0; k < pd; ++k) M[(l * ps + kp) * pd + k] = L[k];
+        }
+        __syncthreads();
+        const double *F = fhat + goff[c];  // [ks1][ks2][ks3][q]
+        const int n1 = ps * ps * pd * win;
+        for (int o = threadIdx.x; o < n1; o += WT) {  // T1[ks1][ks2][kd3][q]
+            int q = o % win, k3 = (o / win) % pd, r = o / (win * pd);
+            double v = 0.0;
+            for (int kp = 0; kp < ps; ++kp) v = fma(M[(2 * ps + kp) * pd + k3], F[(r * ps + kp) * win + q], v);
+            T1[o] = v;
+        }
+        __syncthreads();
+        const int n2 = ps * pd * pd * win;
+        for (int o = threadIdx.x; o < n2; o += WT) {  // T2[ks1][kd2][kd3][q]
+            int q = o % win, k3 = (o / win) % pd, k2 = (o / (win * pd)) % pd, k1 = o / (win * pd * pd);
+            double v = 0.0;
+            for (int kp = 0; kp < ps; ++kp)
+                v = fma(M[(ps + kp) * pd + k2], T1[((k1 * ps + kp) * pd + k3) * win + q], v);
+            T2[o] = v;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < pdw; o += WT) {  // A[kd1][kd2][kd3][q] += ...
+            int q = o % win, k3 = (o / win) % pd, k2 = (o / (win * pd)) % pd, k1 = o / (win * pd * pd);
+            double v = 0.0;
+            for (int kp = 0; kp < ps; ++kp)
+                v = fma(M[kp * pd + k1], T2[((kp * pd + k2) * pd + k3) * win + q], v);
+            A[o] += v;
+        }
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < pdw; o += WT) dst[o] = A[o];
 }
 
 // Block per cluster: grid records of the cluster, paired (FP32x2 Stokeslet)
@@ -713,62 +807,113 @@ __global__ void k_pack_proxies_var(const int32_t *__restrict__ deg, int win,
     }
 }
 
+
+size_t transfer_smem(int pmax, int win)
+{
+    size_t big = (size_t)pmax * pmax * pmax * win;
+    return sizeof(double) * (3 * big + 3 * (size_t)pmax * pmax);
+}
+
 }  // namespace
 
 kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
                              cudaStream_t s, WeightsDev &wd)
 {
     wd.planned = false;
-    std::vector<int32_t> hb(t.nclus), he(t.nclus);
-    KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * t.nclus, cudaMemcpyDeviceToHost, s));
-    KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * t.nclus, cudaMemcpyDeviceToHost, s));
+    const int m = t.nclus;
+    std::vector<int32_t> hb(m), he(m), hpar(m), hnc(m);
+    KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(hpar.data(), t.parent.ptr, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+    KITC_CUDA(cudaMemcpyAsync(hnc.data(), t.n_child.ptr, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
     KITC_CUDA(cudaStreamSynchronize(s));
-    // items grouped by degree; per cluster: offset of its partials and item count
+    // A_c: largest degree on the path root..c (parents precede children)
+    std::vector<int32_t> adeg(m);
+    int amax = 0;
+    for (int c = 0; c < m; ++c) {
+        int up = hpar[c] >= 0 && hpar[c] < c ? adeg[hpar[c]] : 0;
+        adeg[c] = std::max(hdeg[c], up);
+        amax = std::max(amax, adeg[c]);
+    }
+    const bool upward = amax > 0 && transfer_smem(amax + 1, win) <= UP_SMEM_MAX;
+    // degree of the Algorithm 1 work of each cluster, and which clusters get it
+    std::vector<int32_t> rdeg(m, 0);
+    for (int c = 0; c < m; ++c)
+        rdeg[c] = upward ? (hnc[c] == 0 ? adeg[c] : 0) : hdeg[c];
+    std::vector<int64_t> goff(m, 0), foff(m, 0), pstart(m, 0);
+    int64_t ofs = 0;
+    auto P = [&](int d) { return (int64_t)(d + 1) * (d + 1) * (d + 1) * win; };
+    if (upward) {
+        for (int c = 0; c < m; ++c)
+            if (adeg[c] > 0) goff[c] = ofs, ofs += P(adeg[c]);
+        for (int c = 0; c < m; ++c) {
+            if (hdeg[c] <= 0) continue;
+            if (hdeg[c] == adeg[c]) foff[c] = goff[c];
+            else foff[c] = ofs, ofs += P(hdeg[c]);
+        }
+    } else {
+        for (int c = 0; c < m; ++c)
+            if (hdeg[c] > 0) foff[c] = goff[c] = ofs, ofs += P(hdeg[c]);
+    }
+    // Algorithm 1 work items grouped by degree
     std::vector<Item> items;
-    std::vector<int64_t> pstart(t.nclus, 0), foff(t.nclus, 0);
-    std::vector<int32_t> icount(t.nclus, 0);
+    std::vector<int32_t> icount(m, 0);
     wd.groups.clear();
-    int64_t pofs = 0, fofs = 0;
+    int64_t pofs = 0;
     for (int d = 1; d <= KITC_MAX_DEGREE; ++d) {
         WeightsDev::Group g;
         g.degree = d;
         g.item0 = items.size();
         g.pofs = pofs;
-        int np = d + 1, pw = np * np * np * win;
-        for (int c = 0; c < t.nclus; ++c) {
-            if (hdeg[c] != d) continue;
+        for (int c = 0; c < m; ++c) {
+            if (rdeg[c] != d) continue;
             pstart[c] = pofs;
             for (int32_t p = hb[c]; p < he[c]; p += CHUNK) {
                 items.push_back(Item{c, p, std::min(he[c], p + CHUNK), 0});
-                pofs += pw;
+                pofs += P(d);
                 icount[c]++;
             }
         }
         g.nitems = items.size() - g.item0;
         if (g.nitems) wd.groups.push_back(g);
     }
-    for (int c = 0; c < t.nclus; ++c) {
-        foff[c] = fofs;
-        if (hdeg[c] > 0) fofs += (int64_t)(hdeg[c] + 1) * (hdeg[c] + 1) * (hdeg[c] + 1) * win;
-    }
     size_t ni = items.size();
-    size_t bytes = sizeof(Item) * ni + sizeof(int64_t) * 2 * t.nclus + sizeof(int32_t) * t.nclus + 64;
+    size_t bytes = sizeof(Item) * ni + sizeof(int64_t) * 3 * m + sizeof(int32_t) * 4 * m +
+                   sizeof(Cheb) * (KITC_MAX_DEGREE + 1) + 256;
     KITC_TRY(wd.items.reserve(bytes, s));
     Item *d_items = wd.items.as<Item>();
     int64_t *d_p = reinterpret_cast<int64_t *>(d_items + ni);
-    int64_t *d_f = d_p + t.nclus;
-    int32_t *d_c = reinterpret_cast<int32_t *>(d_f + t.nclus);
+    int64_t *d_f = d_p + m, *d_g = d_f + m;
+    int32_t *d_c = reinterpret_cast<int32_t *>(d_g + m);
+    int32_t *d_r = d_c + m, *d_a = d_r + m, *d_d = d_a + m;
+    Cheb *d_cheb = reinterpret_cast<Cheb *>(
+        (reinterpret_cast<uintptr_t>(d_d + m) + 15) & ~static_cast<uintptr_t>(15));
+    std::vector<Cheb> chebs(KITC_MAX_DEGREE + 1);
+    for (int d = 1; d <= KITC_MAX_DEGREE; ++d) chebs[d] = make_cheb(d);
+    chebs[0] = make_cheb(1);
     KITC_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * ni, cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d_p, pstart.data(), sizeof(int64_t) * t.nclus, cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d_f, foff.data(), sizeof(int64_t) * t.nclus, cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d_c, icount.data(), sizeof(int32_t) * t.nclus, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_p, pstart.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_f, foff.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_g, goff.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_c, icount.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_r, rdeg.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_a, adeg.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_d, hdeg.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(d_cheb, chebs.data(), sizeof(Cheb) * chebs.size(), cudaMemcpyHostToDevice, s));
     KITC_TRY(wd.partial.reserve(sizeof(double) * std::max<int64_t>(pofs, 1), s));
-    KITC_TRY(wd.fhat.reserve(sizeof(double) * std::max<int64_t>(fofs, 1), s));
+    KITC_TRY(wd.fhat.reserve(sizeof(double) * std::max<int64_t>(ofs, 1), s));
     KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+    if (upward) {
+        size_t sm = transfer_smem(amax + 1, win);
+        KITC_CUDA(cudaFuncSetAttribute(k_transfer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        KITC_CUDA(cudaFuncSetAttribute(k_transfer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
     wd.nitems = ni;
-    wd.fhat_len = fofs;
+    wd.fhat_len = ofs;
     wd.win = win;
     wd.degree = -1;
+    wd.var_upward = upward;
+    wd.var_pmax = amax + 1;
     wd.var = true;
     wd.planned = true;
     return KITC_OK;
@@ -777,12 +922,16 @@ kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_
 kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int32_t *d_deg,
                                WeightsDev &wd, cudaStream_t s)
 {
+    (void)d_deg;
     if (!wd.planned || !wd.var) return KITC_ERR_STATE;
-    const int win = wd.win;
+    const int win = wd.win, m = t.nclus;
     Item *d_items = wd.items.as<Item>();
     int64_t *d_p = reinterpret_cast<int64_t *>(d_items + wd.nitems);
-    int64_t *d_f = d_p + t.nclus;
-    int32_t *d_c = reinterpret_cast<int32_t *>(d_f + t.nclus);
+    int64_t *d_f = d_p + m, *d_g = d_f + m;
+    int32_t *d_c = reinterpret_cast<int32_t *>(d_g + m);
+    int32_t *d_r = d_c + m, *d_a = d_r + m, *d_d = d_a + m;
+    const Cheb *d_cheb = reinterpret_cast<const Cheb *>(
+        (reinterpret_cast<uintptr_t>(d_d + m) + 15) & ~static_cast<uintptr_t>(15));
     static constexpr ChunkLauncher table[ACC_MAX] = {
         &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
         &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
@@ -800,9 +949,26 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int
                                 wd.partial.as<double>() + g.pofs));
     }
     kitc_count_launch();
-    k_weights_reduce_var<<<t.nclus, 256, 0, s>>>(d_deg, win, d_p, d_c, d_f, wd.partial.as<double>(),
-                                                 wd.fhat.as<double>());
+    k_weights_reduce_var<<<m, 256, 0, s>>>(d_r, win, d_p, d_c, wd.var_upward ? d_g : d_f,
+                                           wd.partial.as<double>(), wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
+    if (wd.var_upward) {
+        const size_t sm = transfer_smem(wd.var_pmax, win);
+        for (int L = (int)t.level_start.size() - 2; L >= 0; --L) {
+            int lb = t.level_start[L], le = t.level_start[L + 1];
+            if (le <= lb) continue;
+            kitc_count_launch();
+            k_transfer<true><<<le - lb, WT, sm, s>>>(lb, d_cheb, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                                     t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                                                     d_a, d_d, d_g, d_f, win, wd.var_pmax,
+                                                     wd.fhat.as<double>());
+        }
+        kitc_count_launch();
+        k_transfer<false><<<m, WT, sm, s>>>(0, d_cheb, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                            t.first_child.as<int32_t>(), t.n_child.as<int32_t>(), d_a,
+                                            d_d, d_g, d_f, win, wd.var_pmax, wd.fhat.as<double>());
+        KITC_CUDA(cudaGetLastError());
+    }
     return KITC_OK;
 }
 

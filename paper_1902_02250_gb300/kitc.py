@@ -78,7 +78,8 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
            "kitc_launch_count", "kitc_set_degrees", "kitc_plan_targets",
-           "kitc_cluster_features", "kitc_cluster_far_errors", "kitc_mlp_workspace_bytes",
+           "kitc_evaluate_planned", "kitc_cluster_features", "kitc_cluster_far_errors",
+           "kitc_mlp_workspace_bytes",
            "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step"]
 
 
@@ -121,6 +122,7 @@ def lib():
         L.kitc_launch_count.restype = I64
         L.kitc_set_degrees.argtypes = [P, P, P]
         L.kitc_plan_targets.argtypes = [P, P, I64, P]
+        L.kitc_evaluate_planned.argtypes = [P, P, P]
         L.kitc_cluster_features.argtypes = [P, P, P, P]
         L.kitc_cluster_far_errors.argtypes = [P, P, I, ctypes.c_uint64, P, P, P]
         L.kitc_mlp_workspace_bytes.argtypes = [I64]
@@ -134,7 +136,8 @@ def lib():
                      "kitc_direct_noalloc",
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest",
-                     "kitc_set_degrees", "kitc_plan_targets", "kitc_cluster_features",
+                     "kitc_set_degrees", "kitc_plan_targets", "kitc_evaluate_planned",
+                     "kitc_cluster_features",
                      "kitc_cluster_far_errors", "kitc_mlp_forward", "kitc_mlp_loss_grad",
                      "kitc_mlp_adam_step"):
             getattr(L, name).restype = I
@@ -421,6 +424,18 @@ def kitc_plan_targets(tree, tgt_xyz, stream=None):
     """Target tree and interaction lists for tgt_xyz, without evaluating."""
     _check(lib().kitc_plan_targets(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
                                    _stream(stream)), "kitc_plan_targets")
+
+
+def kitc_evaluate_planned(tree, out=None, stream=None):
+    """Algorithm 2 at the targets of the last kitc_plan_targets (no list build)."""
+    import torch
+    wout = kernel_wout(tree.params.kernel)
+    nt = tree.stats()["n_targets"]
+    if out is None:
+        out = torch.empty((nt, wout), dtype=torch.float64, device="cuda")
+    _check(lib().kitc_evaluate_planned(tree.handle, _dptr(out, wout, "out"), _stream(stream)),
+           "kitc_evaluate_planned")
+    return out
 
 
 def kitc_cluster_features(tree, w, out=None, stream=None):

@@ -38,12 +38,16 @@ def random_degrees(m, seed, lo=1, hi=12):
     return np.random.default_rng(seed).integers(lo, hi + 1, m).astype(np.int32)
 
 
-def test_weights_per_cluster_degree(K, orc):
+@pytest.mark.parametrize("hi", [16, 12, 9])
+def test_weights_per_cluster_degree(K, orc, hi):
+    """hi = 16: Algorithm 1 on every cluster (the upward form's shared memory
+    does not fit); hi <= 12: leaves at the largest degree on their root path,
+    parents from children, then each cluster down to its own degree."""
     x, f = wl.plummer_with_background(12000, 61)
     p = K.Params(theta=0.7, degree=6, leaf_size=150, eps=0.01)
     t = K.kitc_build_tree(dev(x), p)
     m = t.stats()["n_clusters"]
-    deg = random_degrees(m, 62, 0, 16)
+    deg = random_degrees(m, 62 + hi, 0, hi)
     deg[0] = 0
     K.kitc_set_degrees(t, deg)
     K.kitc_modified_weights(t, dev(f))
@@ -56,6 +60,25 @@ def test_weights_per_cluster_degree(K, orc):
         if deg[c] == 0:
             continue
         k = (int(deg[c]) + 1) ** 3 * 3
+        a, b = got[foff[c]:foff[c] + k], ref[foff[c]:foff[c] + k]
+        assert np.linalg.norm(a - b) <= FP64_TOL * max(np.linalg.norm(b), 1e-300), c
+    t.free()
+
+
+def test_weights_per_cluster_degree_six_components(K, orc):
+    """Stokeslet + rotlet weights (w_in = 6) in the upward form (degrees <= 9)."""
+    x, f = wl.uniform_cube(9000, 60, win=6)
+    p = K.Params(theta=0.7, degree=5, leaf_size=150, eps=0.01, kernel=SR)
+    t = K.kitc_build_tree(dev(x), p)
+    m = t.stats()["n_clusters"]
+    deg = random_degrees(m, 59, 0, 9)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = t.weights()
+    ref, foff = orc.Tree(x, 150).modified_weights_var(f, deg)
+    assert len(got) == len(ref)
+    for c in np.nonzero(deg)[0]:
+        k = (int(deg[c]) + 1) ** 3 * 6
         a, b = got[foff[c]:foff[c] + k], ref[foff[c]:foff[c] + k]
         assert np.linalg.norm(a - b) <= FP64_TOL * max(np.linalg.norm(b), 1e-300), c
     t.free()
@@ -135,12 +158,13 @@ def test_mixed_per_cluster_degree(K, orc, kernel, mac):
 
 
 def test_uniform_map_equals_fixed_degree(K):
-    """A map with n_c = n everywhere reproduces the fixed-degree path that uses
-    Algorithm 1 (same sums in the same order)."""
+    """A map with n_c = n everywhere reproduces the fixed-degree path with the
+    upward pass (leaves by Algorithm 1, parents from children: the same sums in
+    the same order)."""
     x, f = wl.uniform_cube(30000, 72)
     for prec in (K.FP64, K.MIXED):
         p = K.Params(theta=0.7, degree=7, leaf_size=400, eps=0.001, precision=prec,
-                     weights=K.WEIGHTS_ALGORITHM1, mac=K.MAC_BATCH)
+                     weights=K.WEIGHTS_UPWARD, mac=K.MAC_BATCH)
         t = K.kitc_build_tree(dev(x), p)
         K.kitc_modified_weights(t, dev(f))
         a = K.kitc_evaluate(t, dev(x)).cpu().numpy()
@@ -185,4 +209,49 @@ def test_degree_errors(K):
             out.zero_()
             K.kitc_apply(t, f2, out)
             assert torch.equal(out, ref)
+    t.free()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_evaluate_planned_equals_evaluate(K, prec):
+    """Lists built before the degree map (kitc_plan_targets) serve the
+    evaluation after it: same bits and counts as a full kitc_evaluate."""
+    x, f = wl.plummer_with_background(25000, 75)
+    p = K.Params(theta=0.7, degree=6, leaf_size=300, eps=0.001, precision=prec, mac=K.MAC_BATCH)
+    t = K.kitc_build_tree(dev(x), p)
+    K.kitc_plan_targets(t, dev(x))
+    st0 = t.stats()
+    assert st0["n_targets"] == len(x) and st0["far_entries"] > 0
+    deg = random_degrees(st0["n_clusters"], 76, 2, 12)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    a = K.kitc_evaluate_planned(t).cpu().numpy()
+    sa = t.stats()
+    b = K.kitc_evaluate(t, dev(x)).cpu().numpy()
+    sb = t.stats()
+    assert np.array_equal(a, b)
+    for k in ("far_points", "near_pairs", "far_exec", "near_exec", "far_entries"):
+        assert sa[k] == sb[k], k
+    # a map with degree 0 on an accepted cluster is refused at evaluation
+    deg0 = deg.copy()
+    lists = t.lists()
+    deg0[lists["far"][0]] = 0
+    K.kitc_set_degrees(t, deg0)
+    K.kitc_modified_weights(t, dev(f))
+    with pytest.raises(K.KitcError) as e:
+        K.kitc_evaluate_planned(t)
+    assert e.value.status == 1
+    t.free()
+
+
+def test_evaluate_planned_needs_a_plan(K):
+    x, f = wl.uniform_cube(3000, 77)
+    p = K.Params(theta=0.7, degree=4, leaf_size=100, eps=0.01)
+    t = K.kitc_build_tree(dev(x), p)
+    K.kitc_modified_weights(t, dev(f))
+    import torch
+    out = torch.empty((len(x), 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(K.KitcError) as e:
+        K.kitc_evaluate_planned(t, out)
+    assert e.value.status == 5
     t.free()
