@@ -198,17 +198,22 @@ __device__ __forceinline__ void load_source(const unsigned char *rec, R *yh, R *
     }
 }
 
-// CTAs per SM the register budget targets: two for the FP32 Stokeslet (no
-// spills at 96 registers), one for the wider FP64 and rotlet variants.
+// CTAs per SM the register budget targets: two for the FP32 Stokeslet, one
+// for the wider FP64 and rotlet variants.  KITC_PAIR_MAXNREG > 0 gives the
+// FP32 Stokeslet kernel that register cap instead of the launch bound (two CTAs
+// of 288 threads fit up to 112 registers per thread).
 #ifndef KITC_PAIR_MINB
 #define KITC_PAIR_MINB 2
+#endif
+#ifndef KITC_PAIR_MAXNREG
+#define KITC_PAIR_MAXNREG 0
 #endif
 template <int K, bool MIXED> struct MinBlocks {
     static constexpr int value = (MIXED && K == KITC_STOKESLET) ? KITC_PAIR_MINB : 1;
 };
 
 template <int K, bool MIXED, bool EPS0>
-__global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
+__device__ __forceinline__ void eval_body(const EvalArgs &a)
 {
     constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
     constexpr int SREC = Rec<MIXED, WIN>::SRC, PREC = Rec<MIXED, WIN>::PROXY;
@@ -720,6 +725,20 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     }
 }
 
+template <int K, bool MIXED, bool EPS0>
+__global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
+{
+    eval_body<K, MIXED, EPS0>(a);
+}
+
+#if KITC_PAIR_MAXNREG > 0
+template <bool EPS0>
+__global__ void __maxnreg__(KITC_PAIR_MAXNREG) k_eval_pair(const EvalArgs a)
+{
+    eval_body<KITC_STOKESLET, true, EPS0>(a);
+}
+#endif
+
 // One thread waits on a barrier that is never completed; the bounded wait
 // gives up after limit_ns and records the time-out.
 __global__ void k_watchdog(unsigned long long limit_ns, int *err)
@@ -748,22 +767,25 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
     if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
         return KITC_ERR_INVALID_ARG;
     size_t smem = Smem<K>::TOTAL;
+    void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0>;
+#if KITC_PAIR_MAXNREG > 0
+    if constexpr (PAIR) kern = k_eval_pair<EPS0>;
+#endif
     static int configured[64] = {0};
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && !configured[dev]) {
-        KITC_CUDA(cudaFuncSetAttribute(k_eval<K, MIXED, EPS0>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KITC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured[dev] = 1;
     }
     int sms = 0, occ = 0;
     KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    KITC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<K, MIXED, EPS0>, NTH, smem));
+    KITC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTH, smem));
     if (occ < 1) return KITC_ERR_CUDA;
     int64_t grid = std::min<int64_t>(a.nb, (int64_t)sms * occ);
     if (grid < 1) return KITC_OK;
     kitc_count_launch();
-    k_eval<K, MIXED, EPS0><<<(unsigned)grid, NTH, smem, s>>>(a);
+    kern<<<(unsigned)grid, NTH, smem, s>>>(a);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }

@@ -116,6 +116,40 @@ def train(features, lab, steps=3000, lr=3e-3, seed=11, log=None):
     return params, dict(loss=hist, accuracy=acc)
 
 
+def calibrate(xd, fd, p, meas, budgets=(0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6), target=0.8e-6,
+              n_sample=4000, seed=21, steps=3000, log=None):
+    """Trains one selector per label budget (ascending) and keeps the last whose
+    learned run on the training system itself stays within `target` relative
+    L2 error against the FP64 direct sum on sampled targets.  Returns
+    (params, budget, record) or None when even the first budget misses."""
+    import torch
+    n = xd.shape[0]
+    idx = np.random.Generator(np.random.PCG64(seed)).choice(n, min(n, n_sample), replace=False)
+    idx_d = torch.from_numpy(idx).to(xd.device)
+    q = K.Params(eps=p.eps, kernel=p.kernel, precision=K.FP64)
+    ref = K.kitc_direct(xd[idx_d].contiguous(), xd, fd, q)
+    out = torch.empty((n, K.kernel_wout(p.kernel)), dtype=torch.float64, device=xd.device)
+    rows = None
+    best = None
+    for b in budgets:
+        lab, valid, tau = labels(meas, b)
+        if rows is None:
+            rows = torch.from_numpy(np.nonzero(valid)[0]).to(xd.device)
+        params, rep = train(meas["features"][rows].contiguous(), lab[valid], steps=steps)
+        st = learned_step(xd, fd, p, params, out)
+        d = out[idx_d] - ref
+        E = float(torch.sqrt((d ** 2).sum() / (ref ** 2).sum()))
+        rec = dict(budget=b, tau=tau, E_train=E, accuracy=rep["accuracy"],
+                   far_points=st["far_points"],
+                   label_hist=np.bincount(lab[valid], minlength=len(CLASSES)).tolist())
+        if log:
+            log(rec)
+        if E > target:
+            break
+        best = (params, b, rec)
+    return best
+
+
 def select_degrees(tree, fd, params):
     """Degree per cluster (CUDA int32) from the network; the tree's lists must
     exist (kitc_plan_targets or kitc_evaluate)."""
