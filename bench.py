@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
-    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned"],
+    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned", "sphere"],
                     help="batched: 256 independent systems; learned: per-cluster degrees "
-                         "chosen by the trained selector on an 8M Plummer system (measurement "
-                         "cases beside the headline line)")
+                         "chosen by the trained selector on an 8M Plummer system; sphere: rotlet "
+                         "theta x n sweep on the unit sphere (measurement cases beside the "
+                         "headline line)")
     ap.add_argument("--literal", action="store_true",
                     help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
     args = ap.parse_args()
@@ -613,6 +614,81 @@ def run_learned(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# Rotlet sweep workload: N = 1M points on the unit sphere surface (x = g/|g|,
+# g ~ N(0, I3)), torque weights N(0,1), regularized rotlet (output u and w),
+# eps = 0.005, N0 = 2000, per-target MAC; theta x n grid, FP64 and mixed.
+SPHERE_N, SPHERE_SEED, SPHERE_EPS, SPHERE_LEAF = 1_000_000, 3, 0.005, 2000
+SPHERE_THETAS, SPHERE_DEGREES = (0.5, 0.7, 0.9), (2, 4, 6, 8, 10)
+
+
+def run_sphere(args, ws, rank, local):
+    """E and time of the rotlet treecode over the theta x n grid, both precisions."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K, workloads as wl
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    x, f = wl.sphere_surface(SPHERE_N, SPHERE_SEED + rank)
+    xd, fd = torch.from_numpy(x).to(dev), torch.from_numpy(f).to(dev)
+    idx = wl.sample_indices(SPHERE_N, N_SAMPLE, SAMPLE_SEED)
+    ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd, fd,
+                        K.Params(eps=SPHERE_EPS, kernel=K.ROTLET, precision=K.FP64)).cpu().numpy()
+    out = torch.empty((SPHERE_N, 6), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(p):
+        t = K.kitc_build_tree(xd, p)
+        try:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate(t, xd, out)
+            return t.stats()
+        finally:
+            t.free()
+
+    precisions = [("mixed", K.MIXED)] + ([] if args.no_fp64 else [("fp64", K.FP64)])
+    rows = []
+    l0 = K.kitc_launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    for pname, prec in precisions:
+        for th in SPHERE_THETAS:
+            for n in SPHERE_DEGREES:
+                p = K.Params(theta=th, degree=n, leaf_size=SPHERE_LEAF, eps=SPHERE_EPS,
+                             kernel=K.ROTLET, precision=prec, mac=K.MAC_PARTICLE, target_batch=BATCH)
+                if not rows:
+                    step(p)  # warm-up
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = step(p)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = reduce_max(e0.elapsed_time(e1), ws)
+                rows.append({"precision": pname, "theta": th, "degree": n, "ms": ms,
+                             "targets_per_s": ws * SPHERE_N / (ms / 1e3),
+                             "E": rel_l2(ref, out.cpu().numpy()[idx]),
+                             "far_points": st["far_points"], "near_pairs": st["near_pairs"]})
+    clk = clocks.stop()
+    launches = K.kitc_launch_count() - l0
+    ok = [r for r in rows if r["precision"] == "mixed" and r["E"] <= 1e-6]
+    best = max(ok, key=lambda r: r["targets_per_s"]) if ok else None
+    line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
+            "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
+            "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
+            "config": {"workload": "unit sphere surface, N = 1,000,000 (seed 3 + rank), torque "
+                                   "weights N(0,1), regularized rotlet (u and w)",
+                       "eps": SPHERE_EPS, "leaf_size": SPHERE_LEAF, "mac": "particle",
+                       "target_batch": BATCH, "value": "fastest mixed point with E <= 1e-6",
+                       "error": "rel. L2 of (u, w) vs FP64 direct sum on %d sampled targets"
+                                % N_SAMPLE,
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "best": best, "sweep": rows, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -620,6 +696,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload == "learned" and args.impl != "reference":
         run_learned(args, ws, rank, local)
+    elif args.workload == "sphere" and args.impl != "reference":
+        run_sphere(args, ws, rank, local)
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
