@@ -151,13 +151,21 @@ template <bool MIXED, int WIN> struct Rec {
     static constexpr int PROXY = MIXED ? (WIN == 3 ? 16 : 32) : (WIN == 3 ? 32 : 48);
 };
 
+// Keep the per-target FP64 sums and the third FP32 sum level of the mixed
+// path in shared memory instead of registers (they change every 8 / 64 runs).
+#ifndef KITC_SMEM_ACC
+#define KITC_SMEM_ACC 0
+#endif
+
 template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
     static constexpr size_t META = STAGES * sizeof(TileMeta);
     static constexpr size_t BARS = (2 * STAGES + 2) * sizeof(uint64_t);
     static constexpr size_t GRID = (size_t)NCW * 3 * (KITC_MAX_DEGREE + 1) * sizeof(double);
-    static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID;
+    // KITC_SMEM_ACC: the FP64 sums and the third FP32 level of the mixed path
+    static constexpr size_t ACCS = KITC_SMEM_ACC ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
+    static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID + ACCS;
 };
 
 // Weight components of a record as R values.
@@ -230,6 +238,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     double *gridc = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bars) +
                                                Smem<K>::BARS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr bool SACC = MIXED && KITC_SMEM_ACC;
+    double *accs = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) + Smem<K>::GRID) +
+                   (size_t)warp * KITC_MAX_BATCH * WOUT;  // [64 targets][WOUT]
+    float *a3s = reinterpret_cast<float *>(reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) +
+                                                                      Smem<K>::GRID) +
+                                           (size_t)NCW * KITC_MAX_BATCH * WOUT) +
+                 (size_t)warp * KITC_MAX_BATCH * WOUT;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
     const uint32_t rbw = smem_u32(bars + 2 * STAGES), rbr = smem_u32(bars + 2 * STAGES + 1);
     if (threadIdx.x == 0) {
@@ -384,7 +399,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
         for (int t = 0; t < 2; ++t)
 #pragma unroll
             for (int c = 0; c < WOUT; ++c) {
-                acc[t][c] += (double)(a3[t][c] + a2[t][c]);
+                if constexpr (SACC) {
+                    const int i = (lane + 32 * t) * WOUT + c;
+                    accs[i] += (double)(a3s[i] + (float)a2[t][c]);
+                    a3s[i] = 0.f;
+                } else {
+                    acc[t][c] += (double)(a3[t][c] + a2[t][c]);
+                }
                 a2[t][c] = a3[t][c] = R(0);
             }
         c2 = c3 = 0;
@@ -402,7 +423,11 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
 #pragma unroll
                 for (int t = 0; t < 2; ++t)
 #pragma unroll
-                    for (int c = 0; c < WOUT; ++c) a3[t][c] += a2[t][c], a2[t][c] = R(0);
+                    for (int c = 0; c < WOUT; ++c) {
+                        if constexpr (SACC) a3s[(lane + 32 * t) * WOUT + c] += (float)a2[t][c];
+                        else a3[t][c] += a2[t][c];
+                        a2[t][c] = R(0);
+                    }
                 if (++c3 == 8) to_fp64();
             }
         } else {
@@ -458,7 +483,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     }
                 }
 #pragma unroll
-                for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0;
+                for (int c = 0; c < WOUT; ++c) {
+                    acc[t][c] = 0.0;
+                    if constexpr (SACC) {
+                        accs[(lane + 32 * t) * WOUT + c] = 0.0;
+                        a3s[(lane + 32 * t) * WOUT + c] = 0.f;
+                    }
+                }
                 if constexpr (PAIR) {
 #pragma unroll
                     for (int l = 0; l < 3; ++l) {
@@ -703,7 +734,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int c = 0; c < WOUT; ++c)
-                    red[((size_t)warp * KITC_MAX_BATCH + lane + 32 * t) * WOUT + c] = acc[t][c];
+                    red[((size_t)warp * KITC_MAX_BATCH + lane + 32 * t) * WOUT + c] =
+                        SACC ? accs[(lane + 32 * t) * WOUT + c] : acc[t][c];
             __syncwarp();
             if (lane == 0) mbar_arrive(rbw);
             if (!mbar_wait(rbw, nbd & 1u, wait_ns)) { atomicExch(a.err, 1); break; }
