@@ -37,6 +37,7 @@ THETA, DEGREE, LEAF, MAC = 0.7, 9, 4000, "batch"
 LITERAL = (0.7, 8, 2000, "particle")
 BATCH = 64
 N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacement)
+CPU_SAMPLE = 60_000      # targets of the CPU oracle's timed sample (about 10-15 s on 16 cores)
 SAMPLE_SEED = 102
 L2_FLUSH_BYTES = 256 << 20
 FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
@@ -338,7 +339,7 @@ def run_kitc(args, ws, rank, local):
                    "h2d_bytes_per_step": int(x.nbytes + f.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args, x, f, 2000, 1234)
+        line["cpu_baseline"] = oracle_sample(args, x, f, CPU_SAMPLE, 1234)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
