@@ -42,7 +42,7 @@ LITERAL = (0.7, 8, 2000, "particle")
 FP64_POINT = (0.65, 8, 4000, "batch")
 BATCH = 64
 N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacement)
-CPU_SAMPLE = 60_000      # targets of the CPU oracle's timed sample (about 10-15 s on 16 cores)
+CPU_SAMPLE = 100_000     # targets of the CPU oracle's timed sample (about 12 s on 16 cores)
 SAMPLE_SEED = 102
 L2_FLUSH_BYTES = 256 << 20
 FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
@@ -61,11 +61,11 @@ def parse():
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
-    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned", "sphere"],
+    ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned", "sphere", "paper"],
                     help="batched: 256 independent systems; learned: per-cluster degrees "
                          "chosen by the trained selector on an 8M Plummer system; sphere: rotlet "
-                         "theta x n sweep on the unit sphere (measurement cases beside the "
-                         "headline line)")
+                         "theta x n sweep on the unit sphere; paper: the paper's Examples 1 and 2 "
+                         "(measurement cases beside the headline line)")
     ap.add_argument("--literal", action="store_true",
                     help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
     args = ap.parse_args()
@@ -698,6 +698,100 @@ def run_sphere(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# The paper's own workloads (theta = 0.7, n = 7).  Example 1 (Sec. 8.1):
+# organisms in a cube of side 10, eps = l = 0.02 (Table CaseI_new) and eps = l in
+# 0.005..0.08 at N = 640K (Table CaseI_DiffEps), N0 = 2000, Stokeslet.  Example 2
+# (Sec. 8.2): 80^2 helical rods of 151 points (N = 966,400), eps = 0.3, N0 = 1000,
+# Stokeslet + rotlet (Table case_2_parallel).  The paper's E values are printed
+# beside ours; its random draws are unpublished, so they agree in magnitude only.
+PAPER_EX1_E = {10_000: 2.25e-6, 80_000: 1.44e-5, 640_000: 3.17e-5, 5_120_000: 1.62e-5,
+               40_960_000: 7.06e-6}
+PAPER_EX1_DIFFEPS_E = {0.005: 7.68e-6, 0.01: 2.08e-5, 0.02: 3.17e-5, 0.04: 2.78e-5, 0.08: 1.93e-5}
+PAPER_EX2 = {"n_side": 80, "E": 2.24e-5, "cpu_s_24_cores": 43.63, "cpu_s_1_core": 720.87}
+PAPER_FP64_MAX_N = 5_120_000
+
+
+def run_paper(args, ws, rank, local):
+    """Examples 1 and 2 of the paper on the GPU, mixed and FP64."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K, workloads as wl
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def case(x, f, kernel, eps, leaf, seed):
+        n = len(x)
+        xd, fd = torch.from_numpy(x).to(dev), torch.from_numpy(f).to(dev)
+        idx = wl.sample_indices(n, N_SAMPLE, seed)
+        ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd, fd,
+                            K.Params(eps=eps, kernel=kernel, precision=K.FP64)).cpu().numpy()
+        out = torch.empty((n, K.kernel_wout(kernel)), dtype=torch.float64, device=dev)
+        res = {"N": n}
+        for pname, prec in (("mixed", K.MIXED), ("fp64", K.FP64)):
+            if prec == K.FP64 and (args.no_fp64 or n > PAPER_FP64_MAX_N):
+                continue
+            p = K.Params(theta=0.7, degree=7, leaf_size=leaf, eps=eps, kernel=kernel,
+                         precision=prec, mac=K.MAC_PARTICLE, target_batch=BATCH)
+            ms = []
+            for i in range(2 if prec == K.MIXED else 1):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t = K.kitc_build_tree(xd, p)
+                K.kitc_modified_weights(t, fd)
+                K.kitc_evaluate(t, xd, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                st = t.stats()
+                t.free()
+                ms.append(e0.elapsed_time(e1))
+            m = ms[-1]
+            res[pname] = {"ms": m, "targets_per_s": n / (m / 1e3),
+                          "E": rel_l2(ref, out.cpu().numpy()[idx]),
+                          "far_points": st["far_points"], "near_pairs": st["near_pairs"]}
+        del xd, fd, out
+        torch.cuda.empty_cache()
+        return res
+
+    l0 = K.kitc_launch_count()
+    clocks = Clocks(local)
+    clocks.start()
+    ex1 = []
+    for n, e_paper in PAPER_EX1_E.items():
+        x, f = wl.organisms(n // 2, 31 + rank)
+        r = case(x, f, K.STOKESLET, 0.02, 2000, 131)
+        r["E_paper"] = e_paper
+        ex1.append(r)
+    ex1_eps = []
+    for eps, e_paper in PAPER_EX1_DIFFEPS_E.items():
+        x, f = wl.organisms(320_000, 32 + rank, ell=eps)
+        r = case(x, f, K.STOKESLET, eps, 2000, 132)
+        r.update(eps=eps, E_paper=e_paper)
+        ex1_eps.append(r)
+    ns = PAPER_EX2["n_side"]
+    x, f = wl.helical_rods(ns, 33 + rank, spacing=16.0 / (ns - 1))
+    ex2 = case(x, f, K.STOKESLET_ROTLET, 0.3, 1000, 133)
+    ex2.update(E_paper=PAPER_EX2["E"], paper_cpu_s_24_cores=PAPER_EX2["cpu_s_24_cores"],
+               paper_cpu_s_1_core=PAPER_EX2["cpu_s_1_core"])
+    clk = clocks.stop()
+    launches = K.kitc_launch_count() - l0
+    line = {"metric": "Example 2 (helical rods, Stokeslet + rotlet, N = 966,400) targets/sec, "
+                      "theta = 0.7, n = 7, mixed",
+            "value": ex2["mixed"]["targets_per_s"], "unit": "targets/s", "n_gpus": ws, "steps": 1,
+            "warmup": 1, "ms_per_step": ex2["mixed"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 kernel values, f64 sums",
+            "data": "synthetic",
+            "config": {"workload": "the paper's Examples 1 and 2 (synthetic draws of their recipes)",
+                       "theta": 0.7, "degree": 7, "mac": "particle", "target_batch": BATCH,
+                       "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "example1": ex1, "example1_eps": ex1_eps, "example2": ex2,
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -707,6 +801,8 @@ def main():
         run_learned(args, ws, rank, local)
     elif args.workload == "sphere" and args.impl != "reference":
         run_sphere(args, ws, rank, local)
+    elif args.workload == "paper" and args.impl != "reference":
+        run_paper(args, ws, rank, local)
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
