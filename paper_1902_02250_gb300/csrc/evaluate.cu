@@ -157,6 +157,13 @@ template <bool MIXED, int WIN> struct Rec {
 #define KITC_SMEM_ACC 0
 #endif
 
+// FP32x2 Stokeslet: keep a run's packed sums (even / odd points or sources)
+// as float2 through the second summation level instead of adding the halves
+// at every run.
+#ifndef KITC_PACKED_RUNS
+#define KITC_PACKED_RUNS 0
+#endif
+
 template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
@@ -379,6 +386,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     R X[2][3], XL[2][3], XO[2][3];
     double acc[2][WOUT];
     R a1[2][WOUT], a2[2][WOUT], a3[2][WOUT];
+    constexpr bool PRUN = PAIR && KITC_PACKED_RUNS;
+    float2 a2p[2][3];  // PRUN: second level of packed run sums
     int c2 = 0, c3 = 0;
     dvec4 cB = make_dvec4(0, 0, 0, 0);
     double xd[2][3];
@@ -393,18 +402,27 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0, a1[t][c] = a2[t][c] = a3[t][c] = R(0);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a2p[t][c] = make_float2(0.f, 0.f);
 
     auto to_fp64 = [&]() {
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
             for (int c = 0; c < WOUT; ++c) {
+                R p = R(0);
+                if constexpr (PRUN) {
+                    p = (R)(a2p[t][c].x + a2p[t][c].y);
+                    a2p[t][c] = make_float2(0.f, 0.f);
+                }
                 if constexpr (SACC) {
                     const int i = (lane + 32 * t) * WOUT + c;
-                    accs[i] += (double)(a3s[i] + (float)a2[t][c]);
+                    accs[i] += (double)(a3s[i] + (float)(a2[t][c] + p));
                     a3s[i] = 0.f;
                 } else {
-                    acc[t][c] += (double)(a3[t][c] + a2[t][c]);
+                    acc[t][c] += (double)(a3[t][c] + (a2[t][c] + p));
                 }
                 a2[t][c] = a3[t][c] = R(0);
             }
@@ -437,6 +455,28 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 acc[1][c] += u1 ? a1[1][c] : 0.0;
                 a1[0][c] = a1[1][c] = 0.0;
             }
+        }
+    };
+
+    // PRUN: one run given as packed sums v0 (target lane) and v1 (target lane + 32)
+    auto step2 = [&](bool u0, bool u1, const float2 *v0, const float2 *v1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a2p[0][c] = u0 ? add2(a2p[0][c], v0[c]) : a2p[0][c];
+            a2p[1][c] = u1 ? add2(a2p[1][c], v1[c]) : a2p[1][c];
+        }
+        if (++c2 == 8) {
+            c2 = 0;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float h = a2p[t][c].x + a2p[t][c].y;
+                    if constexpr (SACC) a3s[(lane + 32 * t) * WOUT + c] += h;
+                    else a3[t][c] += (R)h;
+                    a2p[t][c] = make_float2(0.f, 0.f);
+                }
+            if (++c3 == 8) to_fp64();
         }
     };
 
@@ -565,11 +605,18 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         for (int t = 0; t < 2; ++t) {  // the x and y parts of d s, summed over the row
                             ux[t] = fma2(dx2[t], S[t], ux[t]);
                             uy[t] = fma2(dy2[t], S[t], uy[t]);
-                            a1[t][0] += ux[t].x + ux[t].y;
-                            a1[t][1] += uy[t].x + uy[t].y;
-                            a1[t][2] += uz[t].x + uz[t].y;
+                            if constexpr (!PRUN) {
+                                a1[t][0] += ux[t].x + ux[t].y;
+                                a1[t][1] += uy[t].x + uy[t].y;
+                                a1[t][2] += uz[t].x + uz[t].y;
+                            }
                         }
-                        step(u0, u1);
+                        if constexpr (PRUN) {
+                            const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
+                            step2(u0, u1, v0, v1);
+                        } else {
+                            step(u0, u1);
+                        }
                         k2 += NCW;
                         while (k2 >= np) {
                             k2 -= np;
@@ -629,13 +676,18 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     } else {
                         for (int idx = blk * 4; idx < cnt; ++idx) body(idx);
                     }
+                    if constexpr (PRUN) {
+                        const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
+                        step2(u0, u1, v0, v1);
+                    } else {
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        a1[t][0] += ux[t].x + ux[t].y;
-                        a1[t][1] += uy[t].x + uy[t].y;
-                        a1[t][2] += uz[t].x + uz[t].y;
+                        for (int t = 0; t < 2; ++t) {
+                            a1[t][0] += ux[t].x + ux[t].y;
+                            a1[t][1] += uy[t].x + uy[t].y;
+                            a1[t][2] += uz[t].x + uz[t].y;
+                        }
+                        step(u0, u1);
                     }
-                    step(u0, u1);
                 }
             }
         } else if (kind == K_FAR) {
