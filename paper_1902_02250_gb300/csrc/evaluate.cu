@@ -35,10 +35,10 @@ namespace {
 constexpr int NCW = KITC_NCW;          // consumer warps
 constexpr int NTH = (NCW + 1) * 32;    // plus one producer warp
 #ifndef KITC_STAGES
-#define KITC_STAGES 4
+#define KITC_STAGES 3
 #endif
 #ifndef KITC_TILE
-#define KITC_TILE 16384
+#define KITC_TILE 24576
 #endif
 constexpr int STAGES = KITC_STAGES;    // ring of shared-memory stages
 constexpr int TILE = KITC_TILE;        // bytes per stage
@@ -161,7 +161,7 @@ template <bool MIXED, int WIN> struct Rec {
 // as float2 through the second summation level instead of adding the halves
 // at every run.
 #ifndef KITC_PACKED_RUNS
-#define KITC_PACKED_RUNS 0
+#define KITC_PACKED_RUNS 1
 #endif
 
 template <int K> struct Smem {
