@@ -11,6 +11,12 @@
 #include <atomic>
 
 int g_wait_limit_ms = 2000;
+// Split-precision weight products for the mixed form (KITC_WEIGHTS_SPLIT=0 at
+// build time turns them off).
+#ifndef KITC_WEIGHTS_SPLIT
+#define KITC_WEIGHTS_SPLIT 1
+#endif
+static const bool g_weights_split = KITC_WEIGHTS_SPLIT != 0;
 
 static std::atomic<int64_t> g_launches{0};
 
@@ -320,6 +326,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 
 static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
 {
+    t->wts.split = t->p.precision == KITC_MIXED && g_weights_split;
     if (t->var) {
         if (!t->wts.planned || !t->wts.var) {
             KITC_TRY(weights_plan_var(t->src, t->win, t->hdeg, s, t->wts));

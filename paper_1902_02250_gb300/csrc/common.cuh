@@ -114,6 +114,7 @@ struct WeightsDev {
         int64_t pofs = 0;
     };
     std::vector<Group> groups;
+    bool split = false;       // split-precision products (mixed form)
     bool var = false;
     bool var_upward = false;  // degree map: upward form (else Algorithm 1 on every cluster)
     int var_pmax = 0;         // degree map: largest grid size of the upward form

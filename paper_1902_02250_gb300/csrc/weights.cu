@@ -15,6 +15,13 @@
 // L_k3 f_j[q] in shared memory and every thread accumulates its outputs with
 // one FP64 FMA per particle.  Chunks of one cluster write partial sums that a
 // second kernel adds in a fixed order, so the result is deterministic.
+//
+// Split-precision products (SPLIT, used by the mixed-precision form): h and g
+// are held as FP32 pairs hi + lo (h - hi rounded), each product h g is formed
+// from the exact FP32 product hi_h hi_g (TwoProduct by FMA) plus the two cross
+// terms, the run over a chunk of <= 64 particles is summed in FP32 pairs with
+// TwoSum, and the run's value is added to the FP64 accumulator; products carry
+// about 2^-48 relative error, the accumulation stays FP64.
 #include <float.h>
 
 #include <algorithm>
@@ -79,7 +86,7 @@ __device__ void bary_basis(const Cheb &cb, double a, double b, double y, double 
     }
 }
 
-template <int ACC>
+template <int ACC, bool SPLIT>
 __global__ void __launch_bounds__(WT) k_weights_chunk(
     Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
     const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
@@ -119,17 +126,53 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
         __syncthreads();
         for (int q = threadIdx.x; q < cnt * np2; q += WT) {
             int j = q / np2, r = q % np2;
-            hs[j * np2 + r] = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
+            double v = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
+            if (SPLIT) {
+                float hi = (float)v;
+                reinterpret_cast<float2 *>(hs)[j * np2 + r] = make_float2(hi, (float)(v - (double)hi));
+            } else {
+                hs[j * np2 + r] = v;
+            }
         }
         for (int q = threadIdx.x; q < cnt * nw; q += WT) {
             int j = q / nw, r = q % nw;
-            gs[j * nw + r] = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
+            double v = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
+            if (SPLIT) {
+                float hi = (float)v;
+                reinterpret_cast<float2 *>(gs)[j * nw + r] = make_float2(hi, (float)(v - (double)hi));
+            } else {
+                gs[j * nw + r] = v;
+            }
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            const double *h = hs + j * np2, *g = gs + j * nw;
+        if constexpr (SPLIT) {
+            float sh[ACC], sl[ACC];
 #pragma unroll
-            for (int i = 0; i < ACC; ++i) acc[i] = fma(h[rowoff[i]], g[coloff[i]], acc[i]);
+            for (int i = 0; i < ACC; ++i) sh[i] = sl[i] = 0.f;
+            const float2 *h2 = reinterpret_cast<const float2 *>(hs);
+            const float2 *g2 = reinterpret_cast<const float2 *>(gs);
+            for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+                for (int i = 0; i < ACC; ++i) {
+                    const float2 a = h2[j * np2 + rowoff[i]], b = g2[j * nw + coloff[i]];
+                    const float p = a.x * b.x;
+                    const float e = __fmaf_rn(a.x, b.x, -p);                       // a.x b.x = p + e
+                    const float c = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));  // + cross terms
+                    const float t = sh[i] + p;                                     // TwoSum(sh, p)
+                    const float bb = t - sh[i];
+                    const float err = (sh[i] - (t - bb)) + (p - bb);
+                    sh[i] = t;
+                    sl[i] += err + c;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < ACC; ++i) acc[i] += (double)sh[i] + (double)sl[i];
+        } else {
+            for (int j = 0; j < cnt; ++j) {
+                const double *h = hs + j * np2, *g = gs + j * nw;
+#pragma unroll
+                for (int i = 0; i < ACC; ++i) acc[i] = fma(h[rowoff[i]], g[coloff[i]], acc[i]);
+            }
         }
         __syncthreads();
     }
@@ -367,7 +410,7 @@ size_t WeightsDev::bytes() const
     return fhat.bytes + proxy.bytes + src.bytes + pbegin.bytes + partial.bytes + items.bytes;
 }
 
-template <int ACC>
+template <int ACC, bool SPLIT>
 kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
                           const TreeDev &t, const double *w, int win, int sb, double *partial)
 {
@@ -375,12 +418,12 @@ kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || smem > configured[dev]) {
-        KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC>,
+        KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (dev >= 0 && dev < 64) configured[dev] = smem;
     }
     kitc_count_launch();
-    k_weights_chunk<ACC><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
+    k_weights_chunk<ACC, SPLIT><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
                                                 t.perm.as<int32_t>(), w, win, t.lo.as<dvec4>(),
                                                 t.hi.as<dvec4>(), sb, partial);
     KITC_CUDA(cudaGetLastError());
@@ -389,6 +432,26 @@ kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb
 
 using ChunkLauncher = kitc_status (*)(dim3, size_t, cudaStream_t, const Cheb &, const Item *,
                                       const TreeDev &, const double *, int, int, double *);
+
+// Launchers of k_weights_chunk<1..16, split>.
+const ChunkLauncher *chunk_table(bool split)
+{
+    static constexpr ChunkLauncher t64[ACC_MAX] = {
+        &launch_chunks<1, false>, &launch_chunks<2, false>, &launch_chunks<3, false>,
+        &launch_chunks<4, false>, &launch_chunks<5, false>, &launch_chunks<6, false>,
+        &launch_chunks<7, false>, &launch_chunks<8, false>, &launch_chunks<9, false>,
+        &launch_chunks<10, false>, &launch_chunks<11, false>, &launch_chunks<12, false>,
+        &launch_chunks<13, false>, &launch_chunks<14, false>, &launch_chunks<15, false>,
+        &launch_chunks<16, false>};
+    static constexpr ChunkLauncher t32[ACC_MAX] = {
+        &launch_chunks<1, true>, &launch_chunks<2, true>, &launch_chunks<3, true>,
+        &launch_chunks<4, true>, &launch_chunks<5, true>, &launch_chunks<6, true>,
+        &launch_chunks<7, true>, &launch_chunks<8, true>, &launch_chunks<9, true>,
+        &launch_chunks<10, true>, &launch_chunks<11, true>, &launch_chunks<12, true>,
+        &launch_chunks<13, true>, &launch_chunks<14, true>, &launch_chunks<15, true>,
+        &launch_chunks<16, true>};
+    return split ? t32 : t64;
+}
 
 size_t upward_smem(int np, int win)
 {
@@ -469,11 +532,7 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
     Item *d_items = wd.items.as<Item>();
     int32_t *d_first = reinterpret_cast<int32_t *>(d_items + wd.nitems);
     const Cheb cb = make_cheb(wd.degree);
-    static constexpr ChunkLauncher table[ACC_MAX] = {
-        &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
-        &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
-        &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
-        &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
+    const ChunkLauncher *table = chunk_table(wd.split);
     if (wd.nitems > 0)
         KITC_TRY(table[wd.acc - 1](dim3((unsigned)wd.nitems, (unsigned)wd.npass), wd.smem, s, cb,
                                    d_items, t, w_user, win, wd.sb, wd.partial.as<double>()));
@@ -932,11 +991,7 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int
     int32_t *d_r = d_c + m, *d_a = d_r + m, *d_d = d_a + m;
     const Cheb *d_cheb = reinterpret_cast<const Cheb *>(
         (reinterpret_cast<uintptr_t>(d_d + m) + 15) & ~static_cast<uintptr_t>(15));
-    static constexpr ChunkLauncher table[ACC_MAX] = {
-        &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
-        &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
-        &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
-        &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
+    const ChunkLauncher *table = chunk_table(wd.split);
     for (const auto &g : wd.groups) {
         int np = g.degree + 1, pwin = np * np * np * win;
         size_t per = sizeof(double) * (3 * np + np * np + np * win);
