@@ -302,7 +302,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
     const bool mixed = t->p.precision == KITC_MIXED;
     const bool pairs = mixed && t->p.kernel == KITC_STOKESLET;
     if (t->var) {
-        KITC_TRY(weights_launch_var(t->src, w, t->cdeg.as<int32_t>(), t->wts, s));
+        KITC_TRY(weights_launch_var(t->src, w, t->wts, s));
         KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
                                   mixed, pairs, s));
         if (pairs)

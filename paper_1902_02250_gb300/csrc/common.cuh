@@ -150,8 +150,8 @@ kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
 kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
                              cudaStream_t s, WeightsDev &wd);
-kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int32_t *d_deg,
-                               WeightsDev &wd, cudaStream_t s);
+kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDev &wd,
+                               cudaStream_t s);
 int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed, bool pairs,
                           std::vector<int64_t> &roff);
 kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,

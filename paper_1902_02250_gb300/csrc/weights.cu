@@ -978,10 +978,9 @@ kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_
     return KITC_OK;
 }
 
-kitc_status weights_launch_var(const TreeDev &t, const double *w_user, const int32_t *d_deg,
-                               WeightsDev &wd, cudaStream_t s)
+kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDev &wd,
+                               cudaStream_t s)
 {
-    (void)d_deg;
     if (!wd.planned || !wd.var) return KITC_ERR_STATE;
     const int win = wd.win, m = t.nclus;
     Item *d_items = wd.items.as<Item>();

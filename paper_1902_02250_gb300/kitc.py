@@ -330,7 +330,8 @@ def kitc_set_degrees(tree, degrees, stream=None):
         h = np.ascontiguousarray(degrees, np.int32)
         ptr = _np(h)
     else:
-        if degrees.dtype.__str__() != "torch.int32" or not degrees.is_contiguous():
+        import torch
+        if degrees.dtype != torch.int32 or not degrees.is_contiguous():
             raise ValueError("degrees must be a contiguous int32 tensor")
         h = degrees.cpu().numpy()
         ptr = degrees.data_ptr()
