@@ -421,19 +421,50 @@ def run_batched(args, ws, rank, local):
     t.free()
     # error per system on <= 1000 sampled targets against the FP64 direct sum
     off = np.concatenate([[0], np.cumsum(counts)])
-    res = out.cpu().numpy()
-    num = den = 0.0
-    worst = 0.0
+    refs, idxs = [], []
     for k in range(len(counts)):
         idx = wl.sample_indices(int(counts[k]), 1000, 4000 + k) + off[k]
         xs = xd[off[k]:off[k + 1]]
-        ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xs, fd[off[k]:off[k + 1]],
-                            K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
-        d2 = float(((ref - res[idx]) ** 2).sum())
-        r2 = float((ref ** 2).sum())
-        num += d2
-        den += r2
-        worst = max(worst, math.sqrt(d2 / r2))
+        refs.append(K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xs,
+                                  fd[off[k]:off[k + 1]], K.Params(eps=EPS, precision=K.FP64)).cpu().numpy())
+        idxs.append(idx)
+
+    def errors(res):
+        num = den = worst = 0.0
+        for ref, idx in zip(refs, idxs):
+            d2 = float(((ref - res[idx]) ** 2).sum())
+            r2 = float((ref ** 2).sum())
+            num += d2
+            den += r2
+            worst = max(worst, math.sqrt(d2 / r2))
+        return math.sqrt(num / den), worst
+
+    E_all, worst = errors(out.cpu().numpy())
+    # the same forest at its fastest (n, MAC) point with E <= 1e-6 over all systems
+    at1e6 = None
+    for mac_name, mac_v in (("batch", K.MAC_BATCH), ("particle", K.MAC_PARTICLE)):
+        for nd in (8, 9, 10, 11):
+            p6 = K.Params(theta=0.7, degree=nd, leaf_size=tuned.leaf_size, eps=EPS, precision=K.MIXED,
+                          mac=mac_v, target_batch=tuned.target_batch)
+            step(p6, out)
+            torch.cuda.synchronize()
+            e6, w6 = errors(out.cpu().numpy())
+            if e6 <= 1e-6:
+                ms6 = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    step(p6, out)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms6.append(e0.elapsed_time(e1))
+                m6 = reduce_max(sum(ms6), ws) / args.steps
+                cand = {"degree": nd, "mac": mac_name, "theta": 0.7, "E_all": e6, "E_worst_system": w6,
+                        "ms": m6, "value": ws * ntot / (m6 / 1e3)}
+                if at1e6 is None or cand["ms"] < at1e6["ms"]:
+                    at1e6 = cand
+                break
     line = {"metric": "batched Stokeslet targets/sec, 256 systems", "value": value,
             "unit": "targets/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -444,7 +475,8 @@ def run_batched(args, ws, rank, local):
                        "leaf_size": tuned.leaf_size, "target_batch": tuned.target_batch,
                        "tuning": "N0 in {250,500,1000,2000} x batch in {32,64}, fastest step",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "E_all": math.sqrt(num / den), "E_worst_system": worst,
+            "E_all": E_all, "E_worst_system": worst,
+            "at_1e-6": at1e6,
             "apply_graph": {"value": ntot / (apply_ms / 1e3), "unit": "targets/s",
                             "ms": apply_ms,
                             "what": "kitc_apply: new weights, same geometry, CUDA-graph replay"},
