@@ -59,11 +59,13 @@ kitc_status kitc_from_cuda(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? KITC_ERR_OOM : KITC_ERR_CUDA;
 }
 
+// 64 bytes of pinned host memory per calling thread for the small read-backs
+// (error flags, totals).  Every call that uses it synchronizes its stream
+// before reading, so calls of one thread never overlap on it, and threads
+// never share it.
 kitc_status host_readback_buffer(void **p)
 {
-    static std::mutex mu;
-    static void *buf = nullptr;
-    std::lock_guard<std::mutex> g(mu);
+    static thread_local void *buf = nullptr;
     if (!buf) KITC_CUDA(cudaHostAlloc(&buf, 64, cudaHostAllocPortable));
     *p = buf;
     return KITC_OK;
@@ -71,10 +73,10 @@ kitc_status host_readback_buffer(void **p)
 
 kitc_status dev_alloc(void **p, size_t bytes, cudaStream_t s)
 {
-    static bool pool_set[64] = {false};
+    static std::atomic<bool> pool_set[64] = {};
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !pool_set[dev]) {
+    if (dev >= 0 && dev < 64 && !pool_set[dev].load()) {
         // keep freed blocks in this process's pool between calls
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {

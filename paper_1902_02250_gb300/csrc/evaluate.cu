@@ -23,6 +23,7 @@
 //    error flag, the CTA drains its own copies in flight and returns.
 #include <type_traits>
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "kmath.cuh"
@@ -855,12 +856,12 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
 #if KITC_PAIR_MAXNREG > 0
     if constexpr (PAIR) kern = k_eval_pair<EPS0>;
 #endif
-    static int configured[64] = {0};
+    static std::atomic<int> configured[64] = {};  // the attribute's value never changes
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !configured[dev]) {
+    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
         KITC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured[dev] = 1;
+        if (dev >= 0 && dev < 64) configured[dev].store(1);
     }
     int sms = 0, occ = 0;
     KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

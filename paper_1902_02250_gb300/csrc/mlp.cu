@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -285,13 +286,13 @@ kitc_status kitc_mlp_loss_grad(const float *params, const float *features, const
     const int nblk = (int)((m + ROWS - 1) / ROWS);
     float *part = reinterpret_cast<float *>(work);
     float *lpart = part + (size_t)nblk * NP;
-    static int configured[64] = {0};
+    static std::atomic<int> configured[64] = {};  // the attribute's value never changes
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !configured[dev]) {
+    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
         KITC_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)grad_smem()));
-        if (dev >= 0 && dev < 64) configured[dev] = 1;
+        if (dev >= 0 && dev < 64) configured[dev].store(1);
     }
     kitc_count_launch();
     k_mlp_grad<<<nblk, GT, grad_smem(), s>>>(params, features, labels, m, part, lpart);

@@ -25,6 +25,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -35,6 +36,8 @@ constexpr int WT = 256;       // threads of the weights kernels
 constexpr int ACC_MAX = 16;   // outputs per thread per pass, at most
 constexpr int CHUNK = 2048;   // particles per work item
 constexpr size_t UP_SMEM_MAX = 200 * 1024;
+constexpr size_t CHUNK_SMEM_MAX = 96 * 1024;  // dynamic shared memory of k_weights_chunk
+kitc_status allow_up_smem();  // shared-memory attribute of the upward kernels
 
 struct Cheb {
     double t[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
@@ -414,13 +417,16 @@ template <int ACC, bool SPLIT>
 kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
                           const TreeDev &t, const double *w, int win, int sb, double *partial)
 {
-    static size_t configured[64] = {0};  // largest dynamic shared memory set, per device
+    // every plan keeps a chunk's shared memory within CHUNK_SMEM_MAX, so one
+    // attribute value per device serves all launches (no race between threads)
+    static std::atomic<int> configured[64] = {};
+    if (smem > CHUNK_SMEM_MAX) return KITC_ERR_INVALID_ARG;
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || smem > configured[dev]) {
+    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
         KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC, SPLIT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 64) configured[dev] = smem;
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SMEM_MAX));
+        if (dev >= 0 && dev < 64) configured[dev].store(1);
     }
     kitc_count_launch();
     k_weights_chunk<ACC, SPLIT><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
@@ -505,7 +511,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     KITC_CUDA(cudaStreamSynchronize(s));
     size_t per = sizeof(double) * (3 * np + np * np + np * win);
     int sb = 64;
-    while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
+    while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
     wd.sb = sb;
     wd.smem = per * sb;
     // the fewest accumulators per thread that cover the outputs in one pass
@@ -513,9 +519,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     wd.npass = (pwin + wd.acc * WT - 1) / (wd.acc * WT);
     wd.nitems = nitems;
     wd.upward = upward;
-    if (upward)
-        KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)upward_smem(np, win)));
+    if (upward) KITC_TRY(allow_up_smem());
     wd.degree = degree;
     wd.win = win;
     wd.mode = mode;
@@ -873,6 +877,24 @@ size_t transfer_smem(int pmax, int win)
     return sizeof(double) * (3 * big + 3 * (size_t)pmax * pmax);
 }
 
+// The upward kernels run with at most UP_SMEM_MAX bytes of dynamic shared
+// memory (their plans check it); the attribute is set to that bound once per
+// device, so concurrent plans never lower it under each other's launches.
+kitc_status allow_up_smem()
+{
+    static std::atomic<int> done[64] = {};
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev].load()) return KITC_OK;
+    KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UP_SMEM_MAX));
+    KITC_CUDA(cudaFuncSetAttribute(k_transfer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)UP_SMEM_MAX));
+    KITC_CUDA(cudaFuncSetAttribute(k_transfer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)UP_SMEM_MAX));
+    if (dev >= 0 && dev < 64) done[dev].store(1);
+    return KITC_OK;
+}
+
 }  // namespace
 
 kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
@@ -962,11 +984,7 @@ kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_
     KITC_TRY(wd.partial.reserve(sizeof(double) * std::max<int64_t>(pofs, 1), s));
     KITC_TRY(wd.fhat.reserve(sizeof(double) * std::max<int64_t>(ofs, 1), s));
     KITC_CUDA(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
-    if (upward) {
-        size_t sm = transfer_smem(amax + 1, win);
-        KITC_CUDA(cudaFuncSetAttribute(k_transfer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        KITC_CUDA(cudaFuncSetAttribute(k_transfer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    }
+    if (upward) KITC_TRY(allow_up_smem());
     wd.nitems = ni;
     wd.fhat_len = ofs;
     wd.win = win;
@@ -995,7 +1013,7 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDe
         int np = g.degree + 1, pwin = np * np * np * win;
         size_t per = sizeof(double) * (3 * np + np * np + np * win);
         int sb = 64;
-        while (sb > 8 && per * sb > 96 * 1024) sb /= 2;
+        while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
         int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
         int npass = (pwin + acc * WT - 1) / (acc * WT);
         KITC_TRY(table[acc - 1](dim3((unsigned)g.nitems, (unsigned)npass), per * sb, s,
