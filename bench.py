@@ -199,6 +199,45 @@ def oracle_sample(args, x, f, n_eval, seed):
             "seconds": {"tree": t1 - t0, "weights": t2 - t1, "eval_sample": t3 - t2}}
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for ln in info:
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    parts = {ln.split(":", 1)[0].strip(): ln.split(":", 1)[1].strip() for ln in info if ":" in ln}
+    if "CPU implementer" in parts:
+        return "implementer %s part %s" % (parts.get("CPU implementer"), parts.get("CPU part"))
+    return "unknown"
+
+
+def oracle_extra(args, x, f):
+    """The oracle on one core (a smaller sample, scaled to N) and the oracle's
+    FP64 direct sum on sampled targets, both on this host."""
+    import oracle
+    from paper_1902_02250_gb300 import workloads as wl
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        one = oracle_sample(args, x, f, 3000, 4321)
+    finally:
+        oracle.set_num_threads(cores)
+    idx = wl.sample_indices(len(x), 1000, 4322)
+    t0 = time.perf_counter()
+    oracle.direct(oracle.STOKESLET, EPS, x[idx], x, f)
+    dt = time.perf_counter() - t0
+    return {"one_core": {"value": one["value"], "unit": "targets/s", "cores": 1,
+                         "sample": one["sample"]},
+            "direct_sampled": {"value": len(idx) / dt, "unit": "targets/s", "cores": cores,
+                               "sample": "FP64 direct sum over all %d sources at %d sampled "
+                                         "targets (%.1f s)" % (len(x), len(idx), dt)},
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -374,6 +413,7 @@ def run_kitc(args, ws, rank, local):
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args, x, f, CPU_SAMPLE, 1234)
+        line["cpu_baseline"].update(oracle_extra(args, x, f))
     if rank == 0:
         print(json.dumps(line), flush=True)
 
