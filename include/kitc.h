@@ -69,8 +69,11 @@ typedef enum { KITC_FP64 = 0, KITC_MIXED = 1 } kitc_precision;
  * with R = |x - y_C| (Eq. MAC), and the target then skips C's subtree.
  * KITC_MAC_BATCH takes one decision per target batch: C is accepted iff
  * r_C <= theta * dist(box_B, y_C), box_B the smallest box enclosing the
- * batch; every accepted C then also passes Eq. MAC for each target. */
-typedef enum { KITC_MAC_PARTICLE = 0, KITC_MAC_BATCH = 1 } kitc_mac;
+ * batch; every accepted C then also passes Eq. MAC for each target.
+ * KITC_MAC_ALL also takes one decision per batch: C is accepted iff every
+ * target of the batch accepts it by Eq. MAC (weaker than the box rule, so
+ * fewer interactions; each accepted interaction is one Algorithm 2 takes). */
+typedef enum { KITC_MAC_PARTICLE = 0, KITC_MAC_BATCH = 1, KITC_MAC_ALL = 2 } kitc_mac;
 
 /* How the modified weights of Eq. modified_weights are formed.  Both give the
  * same values up to rounding.  KITC_WEIGHTS_ALGORITHM1 runs Algorithm 1 on

@@ -622,24 +622,39 @@ static void blist_push(int64_t **a, int64_t *m, int64_t *cap, int64_t v)
     (*a)[(*m)++] = v;
 }
 
-static void batch_lists(const tc_ctx *q, const double *blo, const double *bhi, int64_t c,
-                        blist *L)
+/* bt == NULL: the box rule, C accepted iff r <= theta * dist(box_B, y_c).
+ * bt != NULL (bn targets, 3 coordinates each): the all-targets rule, C accepted
+ * iff every target of the batch accepts it by Eq. MAC (the test of
+ * compute_velocity); otherwise every target descends. */
+static void batch_lists(const tc_ctx *q, const double *blo, const double *bhi, const double *bt,
+                        int64_t bn, int64_t c, blist *L)
 {
     double yc[3], r, e[3];
     cluster_geometry(q->t, c, yc, &r);
-    for (int l = 0; l < 3; ++l) {
-        if (yc[l] < blo[l]) e[l] = blo[l] - yc[l];
-        else if (yc[l] > bhi[l]) e[l] = yc[l] - bhi[l];
-        else e[l] = 0.0;
+    int accept;
+    if (bt) {
+        accept = 1;
+        for (int64_t i = 0; i < bn && accept; ++i) {
+            double d0 = bt[3 * i] - yc[0], d1 = bt[3 * i + 1] - yc[1], d2 = bt[3 * i + 2] - yc[2];
+            double R = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            accept = r <= q->theta * R;
+        }
+    } else {
+        for (int l = 0; l < 3; ++l) {
+            if (yc[l] < blo[l]) e[l] = blo[l] - yc[l];
+            else if (yc[l] > bhi[l]) e[l] = yc[l] - bhi[l];
+            else e[l] = 0.0;
+        }
+        double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        accept = r <= q->theta * dist;
     }
-    double dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-    if (r <= q->theta * dist) {
+    if (accept) {
         blist_push(&L->far, &L->nfar, &L->capfar, c);
     } else if (q->t->n_child[c] == 0) {
         blist_push(&L->near, &L->nnear, &L->capnear, c);
     } else {
         for (int k = 0; k < q->t->n_child[c]; ++k)
-            batch_lists(q, blo, bhi, q->t->first_child[c] + k, L);
+            batch_lists(q, blo, bhi, bt, bn, q->t->first_child[c] + k, L);
     }
 }
 
@@ -665,7 +680,7 @@ static void treecode_batch_impl(const or_tree *t, const double *x, const double 
                                 int lists_only, const unsigned char *sel, double *out,
                                 int64_t *counts, int64_t *tperm, int64_t *nfar, int64_t *nnear,
                                 int64_t *far_list, int64_t far_cap, int64_t *near_list,
-                                int64_t near_cap)
+                                int64_t near_cap, int all_targets)
 {
     tc_ctx q = {t, x, w, fhat, NULL, n, kernel, or_kernel_win(kernel),
                 or_kernel_wout(kernel), eps, theta, deg, foff, 0};
@@ -692,7 +707,14 @@ static void treecode_batch_impl(const or_tree *t, const double *x, const double 
                     if (v > bhi[l]) bhi[l] = v;
                 }
             blist *L = &lists[b];
-            if (t->nclus > 0) batch_lists(&q, blo, bhi, 0, L);
+            double *bt = NULL;
+            if (all_targets) {
+                bt = malloc(sizeof(double) * 3 * (size_t)(s1 - s0));
+                for (int64_t p = s0; p < s1; ++p)
+                    for (int l = 0; l < 3; ++l) bt[3 * (p - s0) + l] = tgt[3 * tt->perm[p] + l];
+            }
+            if (t->nclus > 0) batch_lists(&q, blo, bhi, bt, s1 - s0, 0, L);
+            free(bt);
             int64_t npair = 0;
             for (int64_t m = 0; m < L->nnear; ++m)
                 npair += t->end[L->near[m]] - t->begin[L->near[m]];
@@ -762,7 +784,23 @@ void or_treecode_batch(const or_tree *t, const double *x, const double *w,
 {
     treecode_batch_impl(t, x, w, fhat, n, NULL, NULL, kernel, eps, theta, tgt, nt, batch,
                         tgt_leaf, lists_only, sel, out, counts, tperm, nfar, nnear, far_list,
-                        far_cap, near_list, near_cap);
+                        far_cap, near_list, near_cap, 0);
+}
+
+/* The same with the all-targets rule: a cluster is accepted for a batch iff
+ * every target of the batch accepts it by Eq. MAC (so each accepted
+ * interaction is one Algorithm 2 also takes), otherwise all targets descend. */
+void or_treecode_batch_all(const or_tree *t, const double *x, const double *w,
+                           const double *fhat, int n, int kernel, double eps, double theta,
+                           const double *tgt, int64_t nt, int batch, int tgt_leaf,
+                           int lists_only, const unsigned char *sel, double *out,
+                           int64_t *counts, int64_t *tperm,
+                           int64_t *nfar, int64_t *nnear, int64_t *far_list, int64_t far_cap,
+                           int64_t *near_list, int64_t near_cap)
+{
+    treecode_batch_impl(t, x, w, fhat, n, NULL, NULL, kernel, eps, theta, tgt, nt, batch,
+                        tgt_leaf, lists_only, sel, out, counts, tperm, nfar, nnear, far_list,
+                        far_cap, near_list, near_cap, 1);
 }
 
 /* Batch-MAC variant with a degree per cluster (see or_treecode_var). */
@@ -772,7 +810,7 @@ void or_treecode_batch_var(const or_tree *t, const double *x, const double *w,
                            int tgt_leaf, const unsigned char *sel, double *out, int64_t *counts)
 {
     treecode_batch_impl(t, x, w, fhat, 0, deg, foff, kernel, eps, theta, tgt, nt, batch, tgt_leaf,
-                        0, sel, out, counts, NULL, NULL, NULL, NULL, 0, NULL, 0);
+                        0, sel, out, counts, NULL, NULL, NULL, NULL, 0, NULL, 0, 0);
 }
 
 /* Eq. modified_weights with a degree n_c per cluster: cluster c (deg[c] > 0)

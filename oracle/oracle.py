@@ -70,6 +70,7 @@ def lib():
         L.or_num_batches.restype = I64
         L.or_treecode_batch.argtypes = [P, P, P, P, I, I, D, D, P, I64, I, I, I, P, P, P, P,
                                         P, P, P, I64, P, I64]
+        L.or_treecode_batch_all.argtypes = L.or_treecode_batch.argtypes
         _lib = L
     return _lib
 
@@ -268,11 +269,13 @@ class Tree:
         return out, cnt
 
     def treecode_batch(self, w, fhat, n, kernel, eps, theta, tgt, batch, tgt_leaf,
-                       lists=False, evaluate=True, select=None):
+                       lists=False, evaluate=True, select=None, all_targets=False):
         """Batch-MAC variant (targets grouped by the tree on the targets).
         Returns a dict with out, counts, tperm, nfar, nnear and, when lists,
         far_list / near_list (concatenated per batch, traversal order).
-        select: optional target indices; only those rows of out are summed."""
+        select: optional target indices; only those rows of out are summed.
+        all_targets: a cluster is accepted for a batch iff every target of the
+        batch accepts it by Eq. MAC (instead of the box-distance rule)."""
         w = _f64(w, (self.n, kernel_win(kernel)))
         fhat = _f64(fhat)
         tgt = _f64(tgt, (-1, 3))
@@ -288,7 +291,8 @@ class Tree:
         if select is not None:
             sel = np.zeros(nt, np.uint8)
             sel[np.asarray(select)] = 1
-        L.or_treecode_batch(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
+        fn = L.or_treecode_batch_all if all_targets else L.or_treecode_batch
+        fn(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
                             float(theta), _p(tgt), nt, batch, tgt_leaf, 0 if evaluate else 1,
                             _p(sel), _p(out), _p(cnt), _p(tperm), _p(nfar), _p(nnear), None, 0,
                             None, 0)
@@ -296,7 +300,7 @@ class Tree:
         if lists:
             fl = np.empty(max(1, int(nfar.sum())), np.int64)
             nl = np.empty(max(1, int(nnear.sum())), np.int64)
-            L.or_treecode_batch(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
+            fn(self._h, _p(self.x), _p(w), _p(fhat), n, kernel, float(eps),
                                 float(theta), _p(tgt), nt, batch, tgt_leaf, 1, None, None, None,
                                 None, None, None, _p(fl), len(fl), _p(nl), len(nl))
             res["far_list"] = fl[:int(nfar.sum())]

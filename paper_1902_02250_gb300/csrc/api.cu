@@ -138,7 +138,8 @@ bool valid_params(const kitc_params *p)
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
     if (kitc_kernel_win(p->kernel) < 0) return false;
     if (p->precision != KITC_FP64 && p->precision != KITC_MIXED) return false;
-    if (p->mac != KITC_MAC_PARTICLE && p->mac != KITC_MAC_BATCH) return false;
+    if (p->mac != KITC_MAC_PARTICLE && p->mac != KITC_MAC_BATCH && p->mac != KITC_MAC_ALL)
+        return false;
     if (p->target_batch < 0 || p->target_batch > KITC_MAX_BATCH) return false;
     if (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED) return false;
     if (p->weights != KITC_WEIGHTS_UPWARD && p->weights != KITC_WEIGHTS_ALGORITHM1) return false;

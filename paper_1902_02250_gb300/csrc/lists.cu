@@ -7,6 +7,7 @@
 //   KITC_MAC_PARTICLE: A = {targets of M with r_C <= theta |x - y_C|} (Eq. MAC,
 //     decided per target, so every target sees exactly Algorithm 2);
 //   KITC_MAC_BATCH:    A = M if r_C <= theta dist(box_B, y_C), else empty.
+//   KITC_MAC_ALL:      A = M if every target of M passes Eq. MAC, else empty.
 // A non-empty A is a far entry (C, A); the rest R = M \ A becomes a near
 // entry (C, R) if C is a leaf, else R descends into C's children.
 // The MAC expressions round exactly as written (no contraction), so they
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
             return 2;
         };
         uint64_t A;
-        if (mac == KITC_MAC_PARTICLE) {
+        if (mac != KITC_MAC_BATCH) {
             float da0 = xoa[0] - cc[0], da1 = xoa[1] - cc[1], da2 = xoa[2] - cc[2];
             float db0 = xob[0] - cc[0], db1 = xob[1] - cc[1], db2 = xob[2] - cc[2];
             int pa = pretest(sqrtf(fmaf(da0, da0, fmaf(da1, da1, da2 * da2))), 2e-7f * (sxa + scc));
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
             }
             A = ((uint64_t)__ballot_sync(0xffffffffu, pa == 1) |
                  ((uint64_t)__ballot_sync(0xffffffffu, pb == 1) << 32)) & M;
+            if (mac == KITC_MAC_ALL && A != M) A = 0;  // one decision for the batch
         } else {
             float gap[3];
             for (int l = 0; l < 3; ++l)

@@ -15,7 +15,7 @@ from . import build as _build
 
 STOKESLET, ROTLET, STOKESLET_ROTLET, TEST_POLY = 0, 1, 2, 99
 FP64, MIXED = 0, 1
-MAC_PARTICLE, MAC_BATCH = 0, 1
+MAC_PARTICLE, MAC_BATCH, MAC_ALL = 0, 1, 2
 WEIGHTS_UPWARD, WEIGHTS_ALGORITHM1 = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",

@@ -22,7 +22,7 @@ from . import workloads as wl
 THETAS = (0.8, 0.75, 0.7, 0.65, 0.6, 0.55, 0.5)
 DEGREES = (6, 7, 8, 9, 10)
 LEAVES = (1000, 2000, 4000)
-MACS = (K.MAC_PARTICLE, K.MAC_BATCH)
+MACS = (K.MAC_PARTICLE, K.MAC_BATCH, K.MAC_ALL)
 
 
 def _rel(a, b):

@@ -164,3 +164,48 @@ def test_variable_degree_batch_matches_per_target_form(orc):
     u1, c1, _ = t.treecode_var(f, fv, deg, foff, ST, 0.01, 0.7, x)
     u2, c2 = t.treecode_batch_var(f, fv, deg, foff, ST, 0.01, 0.7, x, 1, 1)
     assert np.array_equal(c1, c2) and orc.rel_l2(u1, u2) < 1e-14
+
+
+def test_all_targets_rule_batch_of_one_is_per_target(orc):
+    # with one target per batch the all-targets rule is Eq. MAC itself
+    x, f = wl.uniform_cube(1500, 34)
+    t = orc.Tree(x, 80)
+    fh = t.modified_weights(f, 4)
+    u1, c1 = t.treecode(f, fh, 4, ST, 0.01, 0.7, x)
+    r = t.treecode_batch(f, fh, 4, ST, 0.01, 0.7, x, 1, 1, all_targets=True)
+    assert np.array_equal(c1, r["counts"])
+    assert orc.rel_l2(u1, r["out"]) < 1e-14
+
+
+@pytest.mark.parametrize("batch", [16, 64])
+def test_all_targets_rule_lists(orc, batch):
+    """Every accepted cluster passes Eq. MAC for each target of its batch; a
+    cluster that fails it for some target is never accepted for the batch; the
+    lists cover every source once per target; the work lies between the
+    per-target MAC's and the box rule's."""
+    x, f = wl.uniform_cube(3000, 35)
+    t = orc.Tree(x, 100)
+    fh = t.modified_weights(f, 3)
+    r = t.treecode_batch(f, fh, 3, ST, 0.01, 0.7, x, batch, batch, lists=True, all_targets=True)
+    rb = t.treecode_batch(f, fh, 3, ST, 0.01, 0.7, x, batch, batch, all_targets=False)
+    _, cp = t.treecode(f, fh, 3, ST, 0.01, 0.7, x)
+    assert r["counts"][0] + r["counts"][4] == len(x) ** 2
+    work = lambda c: c[0] + c[1]  # noqa: E731
+    assert work(cp) <= work(r["counts"]) <= work(rb["counts"])
+    ctr = 0.5 * (t.lo + t.hi)
+    rad = 0.5 * np.linalg.norm(t.hi - t.lo, axis=1)
+    of = on = 0
+    for b in range(len(r["nfar"])):
+        tg = x[r["tperm"][b * batch:(b + 1) * batch]]
+        far = r["far_list"][of:of + r["nfar"][b]]
+        near = r["near_list"][on:on + r["nnear"][b]]
+        of += r["nfar"][b]
+        on += r["nnear"][b]
+        for c in far:
+            assert np.all(rad[c] <= 0.7 * np.linalg.norm(tg - ctr[c], axis=1))
+        for c in near:  # a leaf kept near fails Eq. MAC for some target
+            assert np.any(rad[c] > 0.7 * np.linalg.norm(tg - ctr[c], axis=1))
+        cover = np.zeros(len(x), int)
+        for c in np.concatenate([far, near]):
+            cover[t.begin[c]:t.end[c]] += 1
+        assert np.all(cover == 1)
