@@ -28,6 +28,9 @@
  *     breadth-first order, the children of a cluster being contiguous;
  *   - cluster centre = box midpoint, cluster radius r = half the diagonal;
  *   - MAC (Eq. MAC): the interaction is well separated iff r <= theta * R;
+ *   - target batches (not in the paper) take one decision per batch, either
+ *     by the box rule r <= theta * dist(box_B, y_c) or by the all-targets
+ *     rule (every target of the batch passes Eq. MAC); both are additions;
  *   - the coincident-point tolerance is DBL_MIN, as Sec. 3 states;
  *   - the modified weights are the definition of Eq. modified_weights with
  *     each L_k in barycentric form (Eq. Barycentric-1D), i.e. Algorithm 1
