@@ -16,12 +16,14 @@
 // one FP64 FMA per particle.  Chunks of one cluster write partial sums that a
 // second kernel adds in a fixed order, so the result is deterministic.
 //
-// Split-precision products (SPLIT, used by the mixed-precision form): h and g
-// are held as FP32 pairs hi + lo (h - hi rounded), each product h g is formed
-// from the exact FP32 product hi_h hi_g (TwoProduct by FMA) plus the two cross
-// terms, the run over a chunk of <= 64 particles is summed in FP32 pairs with
-// TwoSum, and the run's value is added to the FP64 accumulator; products carry
-// about 2^-48 relative error, the accumulation stays FP64.
+// Split-precision products (SPLIT, used by the mixed-precision form): the FP64
+// basis values L and the weights f are held as FP32 pairs hi + lo (lo the
+// rounded remainder); h = L1 L2 and g = L3 f and then each product h g are
+// formed from pairs (the exact product of the high parts by FMA, TwoProduct,
+// plus the cross terms); the run over a chunk of <= 64 particles is summed in
+// FP32 pairs with TwoSum, and the run's value is added to the FP64
+// accumulator.  Products carry about 2^-47 relative error; the barycentric
+// denominators and the accumulation stay FP64.
 #include <float.h>
 
 #include <algorithm>
@@ -89,6 +91,24 @@ __device__ void bary_basis(const Cheb &cb, double a, double b, double y, double 
     }
 }
 
+// An FP64 value as an FP32 pair hi + lo (lo = the rounded remainder).
+__device__ __forceinline__ float2 split_f2(double v)
+{
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// (a.x + a.y)(b.x + b.y) as an FP32 pair: the exact product of the high parts
+// (TwoProduct by FMA) plus the cross terms, renormalised (Fast2Sum).
+__device__ __forceinline__ float2 mul_f2(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    const float e = __fmaf_rn(a.x, b.x, -p);
+    const float c = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+    const float hi = p + c;
+    return make_float2(hi, c - (hi - p));
+}
+
 template <int ACC, bool SPLIT>
 __global__ void __launch_bounds__(WT) k_weights_chunk(
     Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
@@ -103,6 +123,7 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
     double *Ls = sm;                        // [sb][3][np]
     double *hs = Ls + (size_t)sb * 3 * np;  // [sb][np2]
     double *gs = hs + (size_t)sb * np2;     // [sb][nw]
+    float2 *wsf = reinterpret_cast<float2 *>(gs + (size_t)sb * nw);  // SPLIT: [sb][win]
     Item it = items[blockIdx.x];
     int obase = blockIdx.y * ACC * WT;
     dvec4 blo = lo[it.c], bhi = hi[it.c];
@@ -124,30 +145,43 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
             double b = l == 0 ? bhi.x : (l == 1 ? bhi.y : bhi.z);
             double L[KITC_MAX_DEGREE + 1];
             bary_basis(cb, a, b, xs[l * n + j0 + j], L);
-            for (int k = 0; k < np; ++k) Ls[(j * 3 + l) * np + k] = L[k];
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < cnt * np2; q += WT) {
-            int j = q / np2, r = q % np2;
-            double v = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
-            if (SPLIT) {
-                float hi = (float)v;
-                reinterpret_cast<float2 *>(hs)[j * np2 + r] = make_float2(hi, (float)(v - (double)hi));
+            if (SPLIT) {  // the FP64 basis as FP32 hi/lo pairs
+                float2 *Lf = reinterpret_cast<float2 *>(Ls);
+                for (int k = 0; k < np; ++k) Lf[(j * 3 + l) * np + k] = split_f2(L[k]);
             } else {
-                hs[j * np2 + r] = v;
+                for (int k = 0; k < np; ++k) Ls[(j * 3 + l) * np + k] = L[k];
             }
         }
-        for (int q = threadIdx.x; q < cnt * nw; q += WT) {
-            int j = q / nw, r = q % nw;
-            double v = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
-            if (SPLIT) {
-                float hi = (float)v;
-                reinterpret_cast<float2 *>(gs)[j * nw + r] = make_float2(hi, (float)(v - (double)hi));
-            } else {
-                gs[j * nw + r] = v;
+        if (SPLIT) {
+            for (int q = threadIdx.x; q < cnt * win; q += WT)
+                wsf[q] = split_f2(w[(int64_t)perm[j0 + q / win] * win + q % win]);
+            __syncthreads();
+            // h = L1 L2 and g = L3 f as FP32 pairs: products of pairs (TwoProduct)
+            const float2 *Lf = reinterpret_cast<const float2 *>(Ls);
+            for (int q = threadIdx.x; q < cnt * np2; q += WT) {
+                int j = q / np2, r = q % np2;
+                reinterpret_cast<float2 *>(hs)[j * np2 + r] =
+                    mul_f2(Lf[(j * 3 + 0) * np + r / np], Lf[(j * 3 + 1) * np + r % np]);
             }
+            for (int q = threadIdx.x; q < cnt * nw; q += WT) {
+                int j = q / nw, r = q % nw;
+                reinterpret_cast<float2 *>(gs)[j * nw + r] =
+                    mul_f2(Lf[(j * 3 + 2) * np + r / win], wsf[j * win + r % win]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (!SPLIT) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < cnt * np2; q += WT) {
+                int j = q / np2, r = q % np2;
+                hs[j * np2 + r] = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
+            }
+            for (int q = threadIdx.x; q < cnt * nw; q += WT) {
+                int j = q / nw, r = q % nw;
+                gs[j * nw + r] = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
+            }
+            __syncthreads();
+        }
         if constexpr (SPLIT) {
             float sh[ACC], sl[ACC];
 #pragma unroll
@@ -509,7 +543,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
     // the host vectors must outlive the copies above
     KITC_CUDA(cudaStreamSynchronize(s));
-    size_t per = sizeof(double) * (3 * np + np * np + np * win);
+    size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
     int sb = 64;
     while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
     wd.sb = sb;
@@ -1011,7 +1045,7 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDe
     const ChunkLauncher *table = chunk_table(wd.split);
     for (const auto &g : wd.groups) {
         int np = g.degree + 1, pwin = np * np * np * win;
-        size_t per = sizeof(double) * (3 * np + np * np + np * win);
+        size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
         int sb = 64;
         while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
         int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
