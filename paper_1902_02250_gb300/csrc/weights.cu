@@ -20,9 +20,8 @@
 // basis values L and the weights f are held as FP32 pairs hi + lo (lo the
 // rounded remainder); h = L1 L2 and g = L3 f and then each product h g are
 // formed from pairs (the exact product of the high parts by FMA, TwoProduct,
-// plus the cross terms); the run over a chunk of <= 64 particles is summed in
-// FP32 pairs with TwoSum, and the run's value is added to the FP64
-// accumulator.  Products carry about 2^-47 relative error; the barycentric
+// plus the cross terms); runs of up to 256 particles are summed in FP32 pairs
+// with TwoSum, and each run's value is added to the FP64 accumulator.  Products carry about 2^-47 relative error; the barycentric
 // denominators and the accumulation stay FP64.
 #include <float.h>
 
@@ -79,14 +78,16 @@ __device__ void bary_basis(const Cheb &cb, double a, double b, double y, double 
             flag = k;
             L[k] = 0.0;
         } else {
-            L[k] = cb.w[k] / diff;
+            // w_k is +-1 or +-1/2, so w_k times the correctly rounded 1/diff is
+            // exactly the correctly rounded w_k / diff (scaling by a power of 2)
+            L[k] = cb.w[k] * __drcp_rn(diff);
             sum += L[k];
         }
     }
     if (flag >= 0) {
         for (int k = 0; k <= n; ++k) L[k] = (k == flag) ? 1.0 : 0.0;
     } else {
-        double inv = 1.0 / sum;
+        double inv = __drcp_rn(sum);  // = 1.0 / sum, correctly rounded
         for (int k = 0; k <= n; ++k) L[k] *= inv;
     }
 }
@@ -137,6 +138,12 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
         rowoff[i] = o < pwin ? o / nw : 0;
         coloff[i] = o < pwin ? o % nw : 0;
     }
+    // SPLIT: FP32-pair run sums of up to FLUSH chunks (<= FLUSH * 64 particles)
+    constexpr int FLUSH = 4;
+    float sh[ACC], sl[ACC];
+#pragma unroll
+    for (int i = 0; i < ACC; ++i) sh[i] = sl[i] = 0.f;
+    int nrun = 0;
     for (int j0 = it.p0; j0 < it.p1; j0 += sb) {
         int cnt = min(sb, it.p1 - j0);
         for (int q = threadIdx.x; q < cnt * 3; q += WT) {
@@ -183,9 +190,6 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
             __syncthreads();
         }
         if constexpr (SPLIT) {
-            float sh[ACC], sl[ACC];
-#pragma unroll
-            for (int i = 0; i < ACC; ++i) sh[i] = sl[i] = 0.f;
             const float2 *h2 = reinterpret_cast<const float2 *>(hs);
             const float2 *g2 = reinterpret_cast<const float2 *>(gs);
             for (int j = 0; j < cnt; ++j) {
@@ -202,8 +206,15 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
                     sl[i] += err + c;
                 }
             }
+            // into the FP64 sums every FLUSH chunks and at the item's end
+            if (++nrun == FLUSH || j0 + sb >= it.p1) {
 #pragma unroll
-            for (int i = 0; i < ACC; ++i) acc[i] += (double)sh[i] + (double)sl[i];
+                for (int i = 0; i < ACC; ++i) {
+                    acc[i] += (double)sh[i] + (double)sl[i];
+                    sh[i] = sl[i] = 0.f;
+                }
+                nrun = 0;
+            }
         } else {
             for (int j = 0; j < cnt; ++j) {
                 const double *h = hs + j * np2, *g = gs + j * nw;

@@ -1,6 +1,6 @@
 """Modified weights of the mixed-precision form, whose products are formed in
-split precision (FP32 hi/lo pairs with exact FMA products, TwoSum over a chunk
-of particles, FP64 accumulation across chunks), against the oracle's FP64
+split precision (FP32 hi/lo pairs with exact FMA products, TwoSum over runs
+of up to 256 particles, FP64 accumulation across runs), against the oracle's FP64
 Eq. modified_weights.
 
 Tolerance: each product carries about 2^-48 ~ 3.6e-15 relative error and each
