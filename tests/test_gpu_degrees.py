@@ -255,3 +255,30 @@ def test_evaluate_planned_needs_a_plan(K):
         K.kitc_evaluate_planned(t, out)
     assert e.value.status == 5
     t.free()
+
+
+def test_plan_on_side_stream_beside_weights(K):
+    """The target tree and lists built on a second stream while the modified
+    weights run on the first (they need only the source tree) give the same
+    bits as the serial kitc_evaluate."""
+    import torch
+    x, f = wl.uniform_cube(200000, 78)
+    p = K.Params(theta=0.7, degree=9, leaf_size=2000, eps=0.001, precision=K.MIXED, mac=K.MAC_BATCH)
+    xd, fd = dev(x), dev(f)
+    t = K.kitc_build_tree(xd, p)
+    K.kitc_modified_weights(t, fd)
+    ref = K.kitc_evaluate(t, xd).cpu().numpy()
+    t.free()
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        t = K.kitc_build_tree(xd, p)
+        built = torch.cuda.Event()
+        built.record(main)
+        K.kitc_modified_weights(t, fd)
+        side.wait_event(built)
+        K.kitc_plan_targets(t, xd, stream=side)
+        main.wait_stream(side)
+        out = K.kitc_evaluate_planned(t)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        t.free()
