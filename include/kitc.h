@@ -287,9 +287,11 @@ kitc_status kitc_direct_noalloc(const double *tgt_xyz, int64_t n_tgt, const doub
                                 void *stream);
 
 /* End to end from host memory: copies the sources, weights and targets to
- * the device, builds the tree, computes the modified weights, evaluates,
- * and copies u back.  All pointers host; tgt_xyz = NULL means the targets
- * are the sources (n_tgt ignored).  Synchronizes `stream` before returning. */
+ * the device, builds the tree, computes the modified weights while building
+ * the target tree and lists on a second stream (they need only the source
+ * tree), evaluates, and copies u back.  All pointers host; tgt_xyz = NULL
+ * means the targets are the sources (n_tgt ignored).  Synchronizes `stream`
+ * before returning. */
 kitc_status kitc_solve_host(const double *src_xyz, const double *w, int64_t n_src,
                             const double *tgt_xyz, int64_t n_tgt, const kitc_params *p,
                             double *out, void *stream);

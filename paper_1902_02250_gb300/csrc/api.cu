@@ -536,10 +536,28 @@ kitc_status kitc_solve_host(const double *src_xyz, const double *w, int64_t n_sr
         st = kitc_from_cuda(cudaMemcpyAsync(dt.ptr, tgt_xyz, sizeof(double) * 3 * n_tgt,
                                             cudaMemcpyHostToDevice, s));
     if (st == KITC_OK) st = kitc_build_tree(dx.as<double>(), n_src, p, stream, &t);
+    // The target tree and lists need only the source tree: they are built on a
+    // second stream while the modified weights run on `stream`, and the
+    // evaluation waits for both.
+    cudaStream_t side = nullptr;
+    cudaEvent_t built = nullptr, planned = nullptr;
+    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaEventCreateWithFlags(&built, cudaEventDisableTiming));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaEventCreateWithFlags(&planned, cudaEventDisableTiming));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaEventRecord(built, s));
     if (st == KITC_OK) st = kitc_modified_weights(t, dw.as<double>(), stream);
+    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamWaitEvent(side, built, 0));
     if (st == KITC_OK)
-        st = kitc_evaluate(t, tgt_xyz ? dt.as<double>() : dx.as<double>(), n_tgt,
-                           dout.as<double>(), stream);
+        st = kitc_plan_targets(t, tgt_xyz ? dt.as<double>() : dx.as<double>(), n_tgt, side);
+    if (st == KITC_OK) st = kitc_from_cuda(cudaEventRecord(planned, side));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamWaitEvent(s, planned, 0));
+    if (st == KITC_OK) st = kitc_evaluate_planned(t, dout.as<double>(), stream);
+    if (side) {
+        cudaStreamSynchronize(side);  // nothing of this call may still run on it
+        cudaStreamDestroy(side);
+    }
+    if (built) cudaEventDestroy(built);
+    if (planned) cudaEventDestroy(planned);
     if (st == KITC_OK)
         st = kitc_from_cuda(cudaMemcpyAsync(out, dout.ptr, sizeof(double) * wout * n_tgt,
                                             cudaMemcpyDeviceToHost, s));
