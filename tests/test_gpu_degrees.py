@@ -282,3 +282,47 @@ def test_plan_on_side_stream_beside_weights(K):
         out = K.kitc_evaluate_planned(t)
         assert np.array_equal(out.cpu().numpy(), ref)
         t.free()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forest_with_degree_map(K, orc, prec):
+    """Per-cluster degrees on a forest of independent systems: a uniform map
+    reproduces the fixed-degree forest bit for bit, and a random map matches
+    the oracle system by system."""
+    systems = wl.batched_systems(5, 79, nmin=400, nmax=5000)
+    counts = [len(s[0]) for s in systems]
+    x = np.vstack([s[0] for s in systems])
+    f = np.vstack([s[1] for s in systems])
+    p = K.Params(theta=0.7, degree=5, leaf_size=250, eps=0.01, precision=prec, mac=K.MAC_BATCH)
+    t = K.kitc_build_forest(dev(x), counts, p)
+    K.kitc_modified_weights(t, dev(f))
+    a = K.kitc_evaluate_forest(t, dev(x), counts).cpu().numpy()
+    m = t.stats()["n_clusters"]
+    K.kitc_set_degrees(t, np.full(m, 5, np.int32))
+    K.kitc_modified_weights(t, dev(f))
+    assert np.array_equal(a, K.kitc_evaluate_forest(t, dev(x), counts).cpu().numpy())
+    if prec == 1:
+        t.free()
+        return
+    # a random map: compare each system with the oracle on that system alone
+    tr = t.download()
+    deg = np.random.default_rng(80).integers(2, 10, m).astype(np.int32)
+    K.kitc_set_degrees(t, deg)
+    K.kitc_modified_weights(t, dev(f))
+    got = K.kitc_evaluate_forest(t, dev(x), counts).cpu().numpy()
+    t.free()
+    off = np.concatenate([[0], np.cumsum(counts)])
+    # clusters of system k: its root and descendants; roots are the clusters without parent
+    roots = np.nonzero(tr["parent"] < 0)[0]
+    assert len(roots) == len(counts)
+    sys_of = np.empty(m, np.int64)
+    for c in range(m):
+        sys_of[c] = np.searchsorted(roots, c, side="right") - 1 if tr["parent"][c] < 0 else sys_of[tr["parent"][c]]
+    for k in range(len(counts)):
+        xs, fs = x[off[k]:off[k + 1]], f[off[k]:off[k + 1]]
+        o = orc.Tree(xs, 250)
+        dk = deg[sys_of == k]
+        assert len(dk) == o.nclusters
+        fh, foff = o.modified_weights_var(fs, dk)
+        ref = o.treecode_batch_var(fs, fh, dk, foff, 0, 0.01, 0.7, xs, 64, 64)[0]
+        assert orc.rel_l2(ref, got[off[k]:off[k + 1]]) <= FP64_TOL, k
