@@ -61,7 +61,9 @@ typedef enum {
  * from hi/lo FP32 pairs, far-field points taken relative to the target
  * batch's centre), FP32 partial sums over short runs, FP64 accumulation
  * of the per-leaf and per-cluster sums.  The tree, the MAC decisions, the
- * barycentric denominators and the modified-weight sums are FP64 in both. */
+ * barycentric denominators and the modified-weight sums are FP64 in both;
+ * the mixed form forms the modified-weight products in split precision
+ * (FP32 hi/lo pairs, about 2^-47 relative error per product). */
 typedef enum { KITC_FP64 = 0, KITC_MIXED = 1 } kitc_precision;
 
 /* Traversal.  KITC_MAC_PARTICLE takes Algorithm 2's decision for every
