@@ -165,6 +165,16 @@ template <bool MIXED, int WIN> struct Rec {
 #define KITC_PACKED_RUNS 1
 #endif
 
+// FP32x2 Stokeslet: grid rows per run of the far field (a warp's rows r,
+// r + NCW, ...) and source pairs per run of the near field.
+#ifndef KITC_RPR
+#define KITC_RPR 1
+#endif
+#ifndef KITC_NPB
+#define KITC_NPB 4
+#endif
+constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
+
 template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
@@ -569,9 +579,17 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     for (int q = 0; q < NPAIR; ++q) ngz[q] = *reinterpret_cast<const float2 *>(gsf + 36 + 2 * q);
                     int r = (warp + rot) % NCW;
                     int k1 = ta + r / np, k2 = r % np;  // advanced incrementally below
-                    for (; r < rows; r += NCW) {
-                        const unsigned char *row = tile + (size_t)r * row_bytes;
-                        float2 dx2[2], dy2[2], rxy2[2], z2[2], ux[2], uy[2], uz[2], S[2];
+                    // a run is RPR rows of this warp (r, r + NCW, ...): one fold
+                    // into the hierarchical sums per run
+                    for (; r < rows; r += RPR * NCW) {
+                        float2 ux[2], uy[2], uz[2];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int j = 0; j < RPR; ++j) {
+                        if (j > 0 && r + j * NCW >= rows) break;  // uniform over the warp
+                        const unsigned char *row = tile + (size_t)(r + j * NCW) * row_bytes;
+                        float2 dx2[2], dy2[2], rxy2[2], z2[2], S[2];
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
                             float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
@@ -579,7 +597,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             dy2[t] = bc2(dy);
                             rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
                             z2[t] = bc2(XO[t][2]);
-                            ux[t] = uy[t] = uz[t] = S[t] = make_float2(0.f, 0.f);
+                            S[t] = make_float2(0.f, 0.f);
                         }
 #pragma unroll
                         for (int q = 0; q < NPAIR; ++q) {
@@ -606,22 +624,24 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         for (int t = 0; t < 2; ++t) {  // the x and y parts of d s, summed over the row
                             ux[t] = fma2(dx2[t], S[t], ux[t]);
                             uy[t] = fma2(dy2[t], S[t], uy[t]);
-                            if constexpr (!PRUN) {
-                                a1[t][0] += ux[t].x + ux[t].y;
-                                a1[t][1] += uy[t].x + uy[t].y;
-                                a1[t][2] += uz[t].x + uz[t].y;
-                            }
-                        }
-                        if constexpr (PRUN) {
-                            const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
-                            step2(u0, u1, v0, v1);
-                        } else {
-                            step(u0, u1);
                         }
                         k2 += NCW;
                         while (k2 >= np) {
                             k2 -= np;
                             ++k1;
+                        }
+                        }
+                        if constexpr (PRUN) {
+                            const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
+                            step2(u0, u1, v0, v1);
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                a1[t][0] += ux[t].x + ux[t].y;
+                                a1[t][1] += uy[t].x + uy[t].y;
+                                a1[t][2] += uz[t].x + uz[t].y;
+                            }
+                            step(u0, u1);
                         }
                     }
                 };
@@ -638,7 +658,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 }
             } else {
                 const int cnt = tb - ta;  // source pairs
-                const int nb4 = (cnt + 3) >> 2, nfull = cnt >> 2;
+                const int nb4 = (cnt + NPB - 1) / NPB, nfull = cnt / NPB;
                 float2 ux[2], uy[2], uz[2];
                 auto body = [&](int idx) {
                     const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
@@ -673,9 +693,9 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
                     if (blk < nfull) {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) body(blk * 4 + j);
+                        for (int j = 0; j < NPB; ++j) body(blk * NPB + j);
                     } else {
-                        for (int idx = blk * 4; idx < cnt; ++idx) body(idx);
+                        for (int idx = blk * NPB; idx < cnt; ++idx) body(idx);
                     }
                     if constexpr (PRUN) {
                         const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
