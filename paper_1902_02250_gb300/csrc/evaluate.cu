@@ -168,19 +168,24 @@ template <bool MIXED, int WIN> struct Rec {
 // FP32x2 Stokeslet: grid rows per run of the far field (a warp's rows r,
 // r + NCW, ...) and source pairs per run of the near field.
 #ifndef KITC_RPR
-#define KITC_RPR 1
+#define KITC_RPR 2
 #endif
 #ifndef KITC_NPB
-#define KITC_NPB 4
+#define KITC_NPB 8
 #endif
 constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
+// FP32x2 Stokeslet: per-row set-up of the far field in packed form from
+// target offsets held as pairs and negated grid offsets stored as pairs.
+#ifndef KITC_PSETUP
+#define KITC_PSETUP 0
+#endif
 
 template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
     static constexpr size_t META = STAGES * sizeof(TileMeta);
     static constexpr size_t BARS = (2 * STAGES + 2) * sizeof(uint64_t);
-    static constexpr size_t GRID = (size_t)NCW * 3 * (KITC_MAX_DEGREE + 1) * sizeof(double);
+    static constexpr size_t GRID = (size_t)NCW * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1) * sizeof(double);
     // KITC_SMEM_ACC: the FP64 sums and the third FP32 level of the mixed path
     static constexpr size_t ACCS = KITC_SMEM_ACC ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
     static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID + ACCS;
@@ -402,9 +407,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     int c2 = 0, c3 = 0;
     dvec4 cB = make_dvec4(0, 0, 0, 0);
     double xd[2][3];
-    R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
-    float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
+    R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1));
+    float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1));
     float2 Xh2[2][3], Xl2[2][3];
+    float2 XO2[2][3];  // KITC_PSETUP: batch-centre offsets of the targets as pairs
     const float2 e22 = bc2((float)(a.eps * a.eps));
     uint32_t it = 0, nbd = 0;
     int64_t bslot = 0;
@@ -546,6 +552,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     for (int l = 0; l < 3; ++l) {
                         Xh2[t][l] = bc2(X[t][l]);
                         Xl2[t][l] = bc2(XL[t][l]);
+                        if (KITC_PSETUP) XO2[t][l] = bc2(XO[t][l]);
                     }
                 }
             }
@@ -564,6 +571,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
                         float v = (float)(sk - cb_l);
                         gsf[18 * l + k] = l == 2 ? -v : v;
+                        if (KITC_PSETUP && l < 2)  // -x, -y as pairs after the scalar tables
+                            reinterpret_cast<float2 *>(gsf + 54)[18 * l + k] = bc2(-v);
                     }
                     if (lane == 0 && (np & 1)) gsf[36 + np] = -1e18f;
                     __syncwarp();
@@ -592,11 +601,19 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         float2 dx2[2], dy2[2], rxy2[2], z2[2], S[2];
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
-                            float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
-                            dx2[t] = bc2(dx);
-                            dy2[t] = bc2(dy);
-                            rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
-                            z2[t] = bc2(XO[t][2]);
+                            if constexpr (KITC_PSETUP) {
+                                const float2 *ng2 = reinterpret_cast<const float2 *>(gsf + 54);
+                                dx2[t] = add2(XO2[t][0], ng2[k1]);
+                                dy2[t] = add2(XO2[t][1], ng2[18 + k2]);
+                                rxy2[t] = fma2(dx2[t], dx2[t], fma2(dy2[t], dy2[t], e22));
+                                z2[t] = XO2[t][2];
+                            } else {
+                                float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
+                                dx2[t] = bc2(dx);
+                                dy2[t] = bc2(dy);
+                                rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
+                                z2[t] = bc2(XO[t][2]);
+                            }
                             S[t] = make_float2(0.f, 0.f);
                         }
 #pragma unroll
