@@ -306,7 +306,8 @@ def run_kitc(args, ws, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    side = torch.cuda.Stream()
+    # the lists are the longer branch beside the weights: give them priority
+    side = torch.cuda.Stream(priority=-1)
     plan_events = []
 
     def step(params, o):

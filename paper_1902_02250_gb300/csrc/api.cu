@@ -541,7 +541,10 @@ kitc_status kitc_solve_host(const double *src_xyz, const double *w, int64_t n_sr
     // evaluation waits for both.
     cudaStream_t side = nullptr;
     cudaEvent_t built = nullptr, planned = nullptr;
-    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    int prio_lo = 0, prio_hi = 0;  // the lists are the longer branch: highest priority
+    if (st == KITC_OK) st = kitc_from_cuda(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    if (st == KITC_OK)
+        st = kitc_from_cuda(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi));
     if (st == KITC_OK) st = kitc_from_cuda(cudaEventCreateWithFlags(&built, cudaEventDisableTiming));
     if (st == KITC_OK) st = kitc_from_cuda(cudaEventCreateWithFlags(&planned, cudaEventDisableTiming));
     if (st == KITC_OK) st = kitc_from_cuda(cudaEventRecord(built, s));
