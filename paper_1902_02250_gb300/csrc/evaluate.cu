@@ -127,34 +127,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 }
 
 // Packed FP32x2 arithmetic of sm_100+ (one instruction, two FP32 lanes).
-// rsqrt of both halves of a pair, unpacked and repacked inside one PTX block
-// (KITC_RSQ2; with eps = 0 a zero gives 0, as rsq<true>).
-#ifndef KITC_RSQ2
-#define KITC_RSQ2 0
-#endif
-template <bool EPS0> __device__ __forceinline__ float2 rsq2(float2 v)
-{
-#if KITC_RSQ2
-    unsigned long long in = *reinterpret_cast<const unsigned long long *>(&v), out;
-    if constexpr (EPS0) {
-        asm("{\n\t.reg .f32 a, b, ra, rb;\n\t.reg .pred pa, pb;\n\tmov.b64 {a, b}, %1;\n\t"
-            "rsqrt.approx.ftz.f32 ra, a;\n\trsqrt.approx.ftz.f32 rb, b;\n\t"
-            "setp.gt.f32 pa, a, 0f00000000;\n\tsetp.gt.f32 pb, b, 0f00000000;\n\t"
-            "selp.f32 ra, ra, 0f00000000, pa;\n\tselp.f32 rb, rb, 0f00000000, pb;\n\t"
-            "mov.b64 %0, {ra, rb};\n\t}"
-            : "=l"(out) : "l"(in));
-    } else {
-        asm("{\n\t.reg .f32 a, b;\n\tmov.b64 {a, b}, %1;\n\t"
-            "rsqrt.approx.ftz.f32 a, a;\n\trsqrt.approx.ftz.f32 b, b;\n\t"
-            "mov.b64 %0, {a, b};\n\t}"
-            : "=l"(out) : "l"(in));
-    }
-    return *reinterpret_cast<const float2 *>(&out);
-#else
-    return make_float2(rsq<EPS0>(v.x), rsq<EPS0>(v.y));
-#endif
-}
-
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -654,7 +626,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             for (int t = 0; t < 2; ++t) {
                                 float2 dz = add2(z2[t], ngz[q]);
                                 float2 r2 = fma2(dz, dz, rxy2[t]);
-                                float2 ri = rsq2<EPS0>(r2);
+                                float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
                                 float2 ri3 = mul2(mul2(ri, ri), ri);
                                 float2 H1 = fma2(e22, ri3, ri);
                                 float2 fd = fma2(fx, dx2[t], fma2(fy, dy2[t], mul2(fz, dz)));
@@ -723,7 +695,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
                         float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
                         float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e22)));
-                        float2 ri = rsq2<EPS0>(r2);
+                        float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
                         float2 ri3 = mul2(mul2(ri, ri), ri);
                         float2 H1 = fma2(e22, ri3, ri);
                         float2 fd = fma2(fx, dx, fma2(fy, dy, mul2(fz, dz)));
