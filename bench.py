@@ -466,11 +466,24 @@ def run_batched(args, ws, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
+    lists_stream = torch.cuda.Stream(priority=-1)
+
     def step(p, o):
+        """Forest; the modified weights on this stream while the target trees and
+        lists of every system are built on a second one; one evaluator launch."""
         t = K.kitc_build_forest(xd, counts, p)
         try:
+            if args.serial:
+                K.kitc_modified_weights(t, fd)
+                K.kitc_evaluate_forest(t, xd, counts, o)
+                return t.stats()
+            built = torch.cuda.Event()
+            built.record(stream)
             K.kitc_modified_weights(t, fd)
-            K.kitc_evaluate_forest(t, xd, counts, o)
+            lists_stream.wait_event(built)
+            K.kitc_plan_targets_forest(t, xd, counts, stream=lists_stream)
+            stream.wait_stream(lists_stream)
+            K.kitc_evaluate_planned(t, o)
             return t.stats()
         finally:
             t.free()

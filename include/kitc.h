@@ -196,6 +196,12 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream);
  * KITC_ERR_STATE on a forest.  Synchronizes `stream`. */
 kitc_status kitc_plan_targets(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, void *stream);
 
+/* kitc_plan_targets for a forest: tgt_counts[k] (host) rows of tgt_xyz are
+ * the targets of system k, ordered and batched per system as in
+ * kitc_evaluate_forest.  kitc_evaluate_planned then evaluates them. */
+kitc_status kitc_plan_targets_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
+                                     void *stream);
+
 /* Algorithm 2 at the targets of the last kitc_plan_targets (or evaluation),
  * reusing its target tree and lists (the target coordinates were copied at
  * planning): the evaluation of kitc_evaluate without the list build.  Under a

@@ -841,6 +841,23 @@ kitc_status kitc_plan_targets(kitc_tree t, const double *tgt_xyz, int64_t n_tgt,
     return plan_impl(t, tgt_xyz, n_tgt, nullptr, 1, s);
 }
 
+kitc_status kitc_plan_targets_forest(kitc_tree t, const double *tgt_xyz, const int64_t *tgt_counts,
+                                     void *stream)
+{
+    if (!t || !tgt_counts || !device_accessible(tgt_xyz)) return KITC_ERR_INVALID_ARG;
+    const int nsys = t->src.nsys;
+    int64_t tot = 0;
+    for (int k = 0; k < nsys; ++k) {
+        if (tgt_counts[k] < 1) return KITC_ERR_INVALID_ARG;
+        tot += tgt_counts[k];
+    }
+    if (!valid_count(tot)) return KITC_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    t->stream = s;
+    t->evaluated = false;
+    return plan_impl(t, tgt_xyz, tot, tgt_counts, nsys, s);
+}
+
 static kitc_status ensure_cheb_table(kitc_tree t, cudaStream_t s)
 {
     if (t->chebt.ptr) return KITC_OK;

@@ -78,7 +78,8 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_lists_download", "kitc_free_tree", "kitc_status_string", "kitc_kernel_win",
            "kitc_kernel_wout", "kitc_set_wait_limit_ms", "kitc_watchdog_selftest",
            "kitc_launch_count", "kitc_set_degrees", "kitc_plan_targets",
-           "kitc_evaluate_planned", "kitc_cluster_features", "kitc_cluster_far_errors",
+           "kitc_evaluate_planned", "kitc_plan_targets_forest", "kitc_cluster_features",
+           "kitc_cluster_far_errors",
            "kitc_mlp_workspace_bytes",
            "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step"]
 
@@ -123,6 +124,7 @@ def lib():
         L.kitc_set_degrees.argtypes = [P, P, P]
         L.kitc_plan_targets.argtypes = [P, P, I64, P]
         L.kitc_evaluate_planned.argtypes = [P, P, P]
+        L.kitc_plan_targets_forest.argtypes = [P, P, P, P]
         L.kitc_cluster_features.argtypes = [P, P, P, P]
         L.kitc_cluster_far_errors.argtypes = [P, P, I, ctypes.c_uint64, P, P, P]
         L.kitc_mlp_workspace_bytes.argtypes = [I64]
@@ -137,6 +139,7 @@ def lib():
                      "kitc_solve_host", "kitc_get_stats", "kitc_tree_download",
                      "kitc_weights_download", "kitc_lists_download", "kitc_watchdog_selftest",
                      "kitc_set_degrees", "kitc_plan_targets", "kitc_evaluate_planned",
+                     "kitc_plan_targets_forest",
                      "kitc_cluster_features",
                      "kitc_cluster_far_errors", "kitc_mlp_forward", "kitc_mlp_loss_grad",
                      "kitc_mlp_adam_step"):
@@ -425,6 +428,14 @@ def kitc_plan_targets(tree, tgt_xyz, stream=None):
     """Target tree and interaction lists for tgt_xyz, without evaluating."""
     _check(lib().kitc_plan_targets(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"), tgt_xyz.shape[0],
                                    _stream(stream)), "kitc_plan_targets")
+
+
+def kitc_plan_targets_forest(tree, tgt_xyz, tgt_counts, stream=None):
+    """Target trees and lists of every system of a forest, without evaluating."""
+    tgt_counts = np.ascontiguousarray(tgt_counts, np.int64)
+    _check(lib().kitc_plan_targets_forest(tree.handle, _dptr(tgt_xyz, 3, "tgt_xyz"),
+                                          _np(tgt_counts), _stream(stream)),
+           "kitc_plan_targets_forest")
 
 
 def kitc_evaluate_planned(tree, out=None, stream=None):

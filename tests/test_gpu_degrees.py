@@ -326,3 +326,34 @@ def test_forest_with_degree_map(K, orc, prec):
         fh, foff = o.modified_weights_var(fs, dk)
         ref = o.treecode_batch_var(fs, fh, dk, foff, 0, 0.01, 0.7, xs, 64, 64)[0]
         assert orc.rel_l2(ref, got[off[k]:off[k + 1]]) <= FP64_TOL, k
+
+
+def test_forest_plan_on_side_stream(K):
+    """Forest: target trees and lists planned on a second stream beside the
+    weights, then kitc_evaluate_planned, equal kitc_evaluate_forest bit for bit."""
+    import torch
+    systems = wl.batched_systems(6, 81, nmin=500, nmax=8000)
+    counts = [len(s[0]) for s in systems]
+    x = np.vstack([s[0] for s in systems])
+    f = np.vstack([s[1] for s in systems])
+    xd, fd = dev(x), dev(f)
+    p = K.Params(theta=0.7, degree=6, leaf_size=400, eps=0.001, precision=K.MIXED)
+    t = K.kitc_build_forest(xd, counts, p)
+    K.kitc_modified_weights(t, fd)
+    ref = K.kitc_evaluate_forest(t, xd, counts).cpu().numpy()
+    st_ref = t.stats()
+    t.free()
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    t = K.kitc_build_forest(xd, counts, p)
+    built = torch.cuda.Event()
+    built.record(main)
+    K.kitc_modified_weights(t, fd)
+    side.wait_event(built)
+    K.kitc_plan_targets_forest(t, xd, counts, stream=side)
+    main.wait_stream(side)
+    out = K.kitc_evaluate_planned(t)
+    st = t.stats()
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert st["far_points"] == st_ref["far_points"] and st["near_pairs"] == st_ref["near_pairs"]
+    t.free()
