@@ -173,9 +173,6 @@ template <bool MIXED, int WIN> struct Rec {
 #ifndef KITC_NPB
 #define KITC_NPB 8
 #endif
-#ifndef KITC_RPR_UNROLL
-#define KITC_RPR_UNROLL 1
-#endif
 constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
 // FP32x2 Stokeslet: per-row set-up of the far field in packed form from
 // target offsets held as pairs and negated grid offsets stored as pairs.
@@ -597,11 +594,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         float2 ux[2], uy[2], uz[2];
 #pragma unroll
                         for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
-#if KITC_RPR_UNROLL
 #pragma unroll
-#else
-#pragma unroll 1
-#endif
                         for (int j = 0; j < RPR; ++j) {
                         if (j > 0 && r + j * NCW >= rows) break;  // uniform over the warp
                         const unsigned char *row = tile + (size_t)(r + j * NCW) * row_bytes;
