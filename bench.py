@@ -47,6 +47,7 @@ CPU_SAMPLE = 100_000     # targets of the CPU oracle's timed sample (about 12 s 
 SAMPLE_SEED = 102
 L2_FLUSH_BYTES = 256 << 20
 FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
+ROTLET_FLOPS_PER_INTERACTION = 57   # one rotlet (u, w) pair, counted the same way
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -816,11 +817,27 @@ def run_sphere(args, ws, rank, local):
                 rows.append({"precision": pname, "theta": th, "degree": n, "ms": ms,
                              "targets_per_s": ws * SPHERE_N / (ms / 1e3),
                              "E": rel_l2(ref, out.cpu().numpy()[idx]),
-                             "far_points": st["far_points"], "near_pairs": st["near_pairs"]})
+                             "far_points": st["far_points"], "near_pairs": st["near_pairs"],
+                             "far_exec": st["far_exec"], "near_exec": st["near_exec"],
+                             "ms_evaluate": st["ms_evaluate"]})
     clk = clocks.stop()
     launches = K.kitc_launch_count() - l0
     ok = [r for r in rows if r["precision"] == "mixed" and r["E"] <= 1e-6]
     best = max(ok, key=lambda r: r["targets_per_s"]) if ok else None
+    roof = None
+    if best:
+        # the per-target MAC is Algorithm 2, so every counted interaction is useful;
+        # the evaluations of masked lanes are the executed overhead
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        sec = best["ms_evaluate"] / 1e3
+        achieved = ROTLET_FLOPS_PER_INTERACTION * (best["near_pairs"] + best["far_points"]) / sec / 1e12
+        executed = ROTLET_FLOPS_PER_INTERACTION * (best["near_exec"] + best["far_exec"]) / sec / 1e12
+        roof = {"kernel": "k_eval<rotlet, mixed> (FP32x2 evaluator)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "flops_per_interaction": ROTLET_FLOPS_PER_INTERACTION,
+                "useful_work": "Algorithm 2 (per-target MAC) interactions",
+                "executed_tflops": executed, "executed_frac": executed / peak,
+                "launch_ms": best["ms_evaluate"], "traffic": None}
     line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
             "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
@@ -833,7 +850,8 @@ def run_sphere(args, ws, rank, local):
                        "error": "rel. L2 of (u, w) vs FP64 direct sum on %d sampled targets"
                                 % N_SAMPLE,
                        "l2": "flushed before every timed step (256 MiB write)"},
-            "best": best, "sweep": rows, "gpu_launches": int(launches), "clocks": clk}
+            "best": best, "roofline": roof, "sweep": rows, "gpu_launches": int(launches),
+            "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

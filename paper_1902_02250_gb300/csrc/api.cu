@@ -303,7 +303,7 @@ kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int 
 static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 {
     const bool mixed = t->p.precision == KITC_MIXED;
-    const bool pairs = mixed && t->p.kernel == KITC_STOKESLET;
+    const bool pairs = uses_pair_records(t->p.kernel, mixed);
     if (t->var) {
         KITC_TRY(weights_launch_var(t->src, w, t->wts, s));
         KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
@@ -338,7 +338,7 @@ static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
     } else {
         KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
     }
-    if (t->p.precision == KITC_MIXED && t->p.kernel == KITC_STOKESLET && !t->pairs_planned) {
+    if (uses_pair_records(t->p.kernel, t->p.precision == KITC_MIXED) && !t->pairs_planned) {
         KITC_TRY(pack_pairs_plan(&t->src, t->src.n, s, t->wts.src, t->wts.pbegin,
                                  &t->wts.pair_ranges));
         t->pairs_planned = true;
@@ -481,7 +481,7 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
     int win = kitc_kernel_win(p->kernel);
     int B = batch_of(*p);
     DevBuf rec, flags, pb;
-    kitc_status st = (mixed && p->kernel == KITC_STOKESLET)
+    kitc_status st = uses_pair_records(p->kernel, mixed)
                          ? pack_pairs(nullptr, src_xyz, w, n_src, s, rec, pb)
                          : pack_sources(nullptr, src_xyz, w, n_src, win, mixed, s, rec);
     if (st == KITC_OK) st = flags.reserve(4 * sizeof(int), s);
@@ -812,7 +812,7 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream)
     t->var = false;
     if (!degrees) return KITC_OK;
     const bool mixed = t->p.precision == KITC_MIXED;
-    const bool pairs = mixed && t->p.kernel == KITC_STOKESLET;
+    const bool pairs = uses_pair_records(t->p.kernel, mixed);
     std::vector<int64_t> ro;
     t->proxy_bytes = proxy_offsets_var(h, t->win, mixed, pairs, ro);
     std::vector<double> tab((KITC_MAX_DEGREE + 1) * (KITC_MAX_DEGREE + 1), 0.0);

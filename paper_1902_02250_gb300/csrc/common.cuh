@@ -143,7 +143,13 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
 kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double *w_user,
                          int64_t n, int win, bool mixed, cudaStream_t s, DevBuf &out);
 kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStream_t s);
-// Paired FP32 records of the FP32x2 Stokeslet evaluator; pbegin receives the
+// The FP32x2 evaluator (mixed precision, three weight components: the
+// Stokeslet and the rotlet) reads paired source and grid records.
+constexpr bool uses_pair_records(int kernel, bool mixed)
+{
+    return mixed && (kernel == KITC_STOKESLET || kernel == KITC_ROTLET);
+}
+// Paired FP32 records of the FP32x2 evaluator; pbegin receives the
 // first pair of every leaf (-1 for other clusters), followed by scratch.
 kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
                        cudaStream_t s, DevBuf &out, DevBuf &pbegin);

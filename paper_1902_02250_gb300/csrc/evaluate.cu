@@ -180,6 +180,12 @@ constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
 #define KITC_PSETUP 0
 #endif
 
+// FP32x2 rotlet: FP64 sums and third FP32 level in shared memory (they change
+// every 8 / 64 runs), which leaves the registers to the six-component run sums.
+#ifndef KITC_ROT_SACC
+#define KITC_ROT_SACC 1
+#endif
+
 template <int K> struct Smem {
     static constexpr int WOUT = KT<K>::WOUT;
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
@@ -187,7 +193,8 @@ template <int K> struct Smem {
     static constexpr size_t BARS = (2 * STAGES + 2) * sizeof(uint64_t);
     static constexpr size_t GRID = (size_t)NCW * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1) * sizeof(double);
     // KITC_SMEM_ACC: the FP64 sums and the third FP32 level of the mixed path
-    static constexpr size_t ACCS = KITC_SMEM_ACC ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
+    static constexpr bool SA = KITC_SMEM_ACC || (KITC_ROT_SACC && K == KITC_ROTLET);
+    static constexpr size_t ACCS = SA ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
     static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID + ACCS;
 };
 
@@ -248,8 +255,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
 {
     constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
     constexpr int SREC = Rec<MIXED, WIN>::SRC, PREC = Rec<MIXED, WIN>::PROXY;
-    // FP32x2 path: paired source records and paired grid points (see pack_pairs)
-    constexpr bool PAIR = MIXED && K == KITC_STOKESLET;
+    // FP32x2 path (Stokeslet, rotlet): paired source records and paired grid
+    // points (see pack_pairs)
+    constexpr bool PAIR = MIXED && (K == KITC_STOKESLET || K == KITC_ROTLET);
+    constexpr bool ROT = K == KITC_ROTLET;
     constexpr int PAIR_REC = 80;
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -261,7 +270,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     double *gridc = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bars) +
                                                Smem<K>::BARS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr bool SACC = MIXED && KITC_SMEM_ACC;
+    constexpr bool SACC = MIXED && Smem<K>::SA;
     double *accs = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) + Smem<K>::GRID) +
                    (size_t)warp * KITC_MAX_BATCH * WOUT;  // [64 targets][WOUT]
     float *a3s = reinterpret_cast<float *>(reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) +
@@ -402,8 +411,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     R X[2][3], XL[2][3], XO[2][3];
     double acc[2][WOUT];
     R a1[2][WOUT], a2[2][WOUT], a3[2][WOUT];
-    constexpr bool PRUN = PAIR && KITC_PACKED_RUNS;
-    float2 a2p[2][3];  // PRUN: second level of packed run sums
+    constexpr bool PRUN = PAIR && (KITC_PACKED_RUNS || ROT);  // the rotlet path always packs
+    float2 a2p[2][WOUT];  // PRUN: second level of packed run sums
     int c2 = 0, c3 = 0;
     dvec4 cB = make_dvec4(0, 0, 0, 0);
     double xd[2][3];
@@ -412,6 +421,12 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     float2 Xh2[2][3], Xl2[2][3];
     float2 XO2[2][3];  // KITC_PSETUP: batch-centre offsets of the targets as pairs
     const float2 e22 = bc2((float)(a.eps * a.eps));
+    // rotlet (times 8 pi): Q/2 = ri3 + 1.5 eps^2 ri5, D2/4 = ri5 (1.5 + 3.75 eps^2 ri2),
+    // D1/4 = ri3 (-0.5 + ri2 (-0.75 eps^2 + 3.75 eps^4 ri2))
+    const float2 cq = bc2((float)(1.5 * a.eps * a.eps)), cd2a = bc2((float)(3.75 * a.eps * a.eps));
+    const float2 cd1a = bc2((float)(3.75 * a.eps * a.eps * a.eps * a.eps));
+    const float2 cd1b = bc2((float)(-0.75 * a.eps * a.eps));
+    const float2 c15 = bc2(1.5f), cm05 = bc2(-0.5f), m1 = bc2(-1.f);
     uint32_t it = 0, nbd = 0;
     int64_t bslot = 0;
     int bsize = 0;
@@ -422,7 +437,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a2p[t][c] = make_float2(0.f, 0.f);
+        for (int c = 0; c < WOUT; ++c) a2p[t][c] = make_float2(0.f, 0.f);
 
     auto to_fp64 = [&]() {
 #pragma unroll
@@ -478,7 +493,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     // PRUN: one run given as packed sums v0 (target lane) and v1 (target lane + 32)
     auto step2 = [&](bool u0, bool u1, const float2 *v0, const float2 *v1) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < WOUT; ++c) {
             a2p[0][c] = u0 ? add2(a2p[0][c], v0[c]) : a2p[0][c];
             a2p[1][c] = u1 ? add2(a2p[1][c], v1[c]) : a2p[1][c];
         }
@@ -487,7 +502,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
 #pragma unroll
             for (int t = 0; t < 2; ++t)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
+                for (int c = 0; c < WOUT; ++c) {
                     const float h = a2p[t][c].x + a2p[t][c].y;
                     if constexpr (SACC) a3s[(lane + 32 * t) * WOUT + c] += h;
                     else a3[t][c] += (R)h;
@@ -495,6 +510,15 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 }
             if (++c3 == 8) to_fp64();
         }
+    };
+
+    // rotlet factors of a pair of points from rho^2: hQ = Q/2, qD1 = D1/4, qD2 = D2/4
+    auto rot_factors = [&](float2 r2, float2 &hQ, float2 &qD1, float2 &qD2) {
+        const float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
+        const float2 ri2 = mul2(ri, ri), ri3 = mul2(ri2, ri), ri5 = mul2(ri3, ri2);
+        hQ = fma2(cq, ri5, ri3);
+        qD2 = mul2(ri5, fma2(cd2a, ri2, c15));
+        qD1 = mul2(ri3, fma2(fma2(cd1a, ri2, cd1b), ri2, cm05));
     };
 
     for (;;) {
@@ -662,16 +686,94 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         }
                     }
                 };
+                // rotlet: one row per run.  With d = (dx, dy, dz_k) on a row, the
+                // row needs per point only the sums S = sum hQ n, B = sum hQ dz n
+                // (x, y), W = sum qD1 n, T = sum t, Z = sum t dz (t = (n.d) qD2):
+                //   u = (B_y - dy S_z, dx S_z - B_x, dy S_x - dx S_y),
+                //   w = (W_x + dx T, W_y + dy T, W_z + Z).
+                auto far_rows_rot = [&](auto npc) {
+                    constexpr int NPAIR = decltype(npc)::value;
+                    float2 ngz[NPAIR];
+#pragma unroll
+                    for (int q = 0; q < NPAIR; ++q) ngz[q] = *reinterpret_cast<const float2 *>(gsf + 36 + 2 * q);
+                    int r = (warp + rot) % NCW;
+                    int k1 = ta + r / np, k2 = r % np;
+                    for (; r < rows; r += NCW) {
+                        const unsigned char *row = tile + (size_t)r * row_bytes;
+                        float2 v[2][WOUT];
+                        float dxs[2], dys[2];
+                        float2 dx2[2], dy2[2], rxy2[2], z2[2];
+                        float2 S0[2], S1[2], S2[2], B0[2], B1[2], W0[2], W1[2], W2[2], T[2], Z[2];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            dxs[t] = XO[t][0] - gsf[k1];
+                            dys[t] = XO[t][1] - gsf[18 + k2];
+                            dx2[t] = bc2(dxs[t]);
+                            dy2[t] = bc2(dys[t]);
+                            rxy2[t] = bc2(fmaf(dxs[t], dxs[t], fmaf(dys[t], dys[t], (float)e2)));
+                            z2[t] = bc2(XO[t][2]);
+                            S0[t] = S1[t] = S2[t] = B0[t] = B1[t] = make_float2(0.f, 0.f);
+                            W0[t] = W1[t] = W2[t] = T[t] = Z[t] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NPAIR; ++q) {
+                            const float4 A = *reinterpret_cast<const float4 *>(row + q * 32);
+                            const float4 B = *reinterpret_cast<const float4 *>(row + q * 32 + 16);
+                            const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w);
+                            const float2 nz = make_float2(B.x, B.y);
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                const float2 dz = add2(z2[t], ngz[q]);
+                                float2 hQ, qD1, qD2;
+                                rot_factors(fma2(dz, dz, rxy2[t]), hQ, qD1, qD2);
+                                const float2 nd = fma2(nx, dx2[t], fma2(ny, dy2[t], mul2(nz, dz)));
+                                const float2 tt = mul2(nd, qD2);
+                                S0[t] = fma2(hQ, nx, S0[t]);
+                                S1[t] = fma2(hQ, ny, S1[t]);
+                                S2[t] = fma2(hQ, nz, S2[t]);
+                                const float2 hz = mul2(hQ, dz);
+                                B0[t] = fma2(hz, nx, B0[t]);
+                                B1[t] = fma2(hz, ny, B1[t]);
+                                W0[t] = fma2(nx, qD1, W0[t]);
+                                W1[t] = fma2(ny, qD1, W1[t]);
+                                W2[t] = fma2(nz, qD1, W2[t]);
+                                T[t] = add2(T[t], tt);
+                                Z[t] = fma2(dz, tt, Z[t]);
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) {
+                            v[t][0] = fma2(bc2(-dys[t]), S2[t], B1[t]);
+                            v[t][1] = fma2(dx2[t], S2[t], mul2(m1, B0[t]));
+                            v[t][2] = fma2(dy2[t], S0[t], mul2(bc2(-dxs[t]), S1[t]));
+                            if constexpr (WOUT == 6) {
+                                v[t][3] = fma2(dx2[t], T[t], W0[t]);
+                                v[t][4] = fma2(dy2[t], T[t], W1[t]);
+                                v[t][5] = add2(W2[t], Z[t]);
+                            }
+                        }
+                        step2(u0, u1, v[0], v[1]);
+                        k2 += NCW;
+                        while (k2 >= np) {
+                            k2 -= np;
+                            ++k1;
+                        }
+                    }
+                };
+                auto far_any = [&](auto npc) {
+                    if constexpr (ROT) far_rows_rot(npc);
+                    else far_rows(npc);
+                };
                 switch (npair) {
-                case 1: far_rows(std::integral_constant<int, 1>{}); break;
-                case 2: far_rows(std::integral_constant<int, 2>{}); break;
-                case 3: far_rows(std::integral_constant<int, 3>{}); break;
-                case 4: far_rows(std::integral_constant<int, 4>{}); break;
-                case 5: far_rows(std::integral_constant<int, 5>{}); break;
-                case 6: far_rows(std::integral_constant<int, 6>{}); break;
-                case 7: far_rows(std::integral_constant<int, 7>{}); break;
-                case 8: far_rows(std::integral_constant<int, 8>{}); break;
-                default: far_rows(std::integral_constant<int, 9>{}); break;
+                case 1: far_any(std::integral_constant<int, 1>{}); break;
+                case 2: far_any(std::integral_constant<int, 2>{}); break;
+                case 3: far_any(std::integral_constant<int, 3>{}); break;
+                case 4: far_any(std::integral_constant<int, 4>{}); break;
+                case 5: far_any(std::integral_constant<int, 5>{}); break;
+                case 6: far_any(std::integral_constant<int, 6>{}); break;
+                case 7: far_any(std::integral_constant<int, 7>{}); break;
+                case 8: far_any(std::integral_constant<int, 8>{}); break;
+                default: far_any(std::integral_constant<int, 9>{}); break;
                 }
             } else {
                 const int cnt = tb - ta;  // source pairs
@@ -705,6 +807,65 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         uz[t] = fma2(fz, H1, fma2(dz, sv, uz[t]));
                     }
                 };
+                // rotlet: u = hQ n x d as the positive (P) and negative (M)
+                // products of the cross product, summed separately over a run
+                float2 P[2][3], M[2][3], Wr[2][3];
+                auto body_rot = [&](int idx) {
+                    const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
+                    const float4 A = *reinterpret_cast<const float4 *>(rec);
+                    const float4 B = *reinterpret_cast<const float4 *>(rec + 16);
+                    const float4 C = *reinterpret_cast<const float4 *>(rec + 32);
+                    const float4 D = *reinterpret_cast<const float4 *>(rec + 48);
+                    const float4 E = *reinterpret_cast<const float4 *>(rec + 64);
+                    const float2 hx = make_float2(A.x, A.y), hy = make_float2(A.z, A.w);
+                    const float2 hz = make_float2(B.x, B.y), lx = make_float2(B.z, B.w);
+                    const float2 ly = make_float2(C.x, C.y), lz = make_float2(C.z, C.w);
+                    const float2 nx = make_float2(D.x, D.y), ny = make_float2(D.z, D.w);
+                    const float2 nz = make_float2(E.x, E.y);
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
+                        const float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
+                        const float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
+                        float2 hQ, qD1, qD2;
+                        rot_factors(fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e22))), hQ, qD1, qD2);
+                        const float2 nd = fma2(nx, dx, fma2(ny, dy, mul2(nz, dz)));
+                        const float2 tt = mul2(nd, qD2);
+                        const float2 h0 = mul2(hQ, nx), h1 = mul2(hQ, ny), h2 = mul2(hQ, nz);
+                        P[t][0] = fma2(h1, dz, P[t][0]);
+                        M[t][0] = fma2(h2, dy, M[t][0]);
+                        P[t][1] = fma2(h2, dx, P[t][1]);
+                        M[t][1] = fma2(h0, dz, M[t][1]);
+                        P[t][2] = fma2(h0, dy, P[t][2]);
+                        M[t][2] = fma2(h1, dx, M[t][2]);
+                        Wr[t][0] = fma2(nx, qD1, fma2(dx, tt, Wr[t][0]));
+                        Wr[t][1] = fma2(ny, qD1, fma2(dy, tt, Wr[t][1]));
+                        Wr[t][2] = fma2(nz, qD1, fma2(dz, tt, Wr[t][2]));
+                    }
+                };
+                if constexpr (ROT) {
+                    for (int blk = (warp + rot) % NCW; blk < nb4; blk += NCW) {
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) P[t][c] = M[t][c] = Wr[t][c] = make_float2(0.f, 0.f);
+                        if (blk < nfull) {
+#pragma unroll
+                            for (int j = 0; j < NPB; ++j) body_rot(blk * NPB + j);
+                        } else {
+                            for (int idx = blk * NPB; idx < cnt; ++idx) body_rot(idx);
+                        }
+                        float2 v[2][WOUT];
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                v[t][c] = fma2(m1, M[t][c], P[t][c]);
+                                if constexpr (WOUT == 6) v[t][3 + c] = Wr[t][c];
+                            }
+                        step2(u0, u1, v[0], v[1]);
+                    }
+                } else
                 for (int blk = (warp + rot) % NCW; blk < nb4; blk += NCW) {
 #pragma unroll
                     for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
@@ -878,7 +1039,7 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
 {
     constexpr int WIN = KT<K>::WIN;
     int np = a.cdeg ? KITC_MAX_DEGREE + 1 : a.degree + 1;  // the largest grid of the launch
-    constexpr bool PAIR = MIXED && K == KITC_STOKESLET;
+    constexpr bool PAIR = MIXED && (K == KITC_STOKESLET || K == KITC_ROTLET);
     if (a.cdeg && (!a.roff || !a.chebt)) return KITC_ERR_INVALID_ARG;
     size_t plane = PAIR ? (size_t)np * ((np + 1) / 2) * 32 : (size_t)np * np * Rec<MIXED, WIN>::PROXY;
     if (plane > (size_t)TILE) return KITC_ERR_INVALID_ARG;

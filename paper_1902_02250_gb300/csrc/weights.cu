@@ -373,9 +373,10 @@ __global__ void k_pack_sources(int64_t n, int win, const double *__restrict__ xs
     }
 }
 
-// Paired records for the FP32x2 Stokeslet evaluator: two consecutive sources
-// of one leaf share a 80-byte record (negated hi/lo coordinates, so that the
-// packed add forms x - y, then the weights):
+// Paired records for the FP32x2 evaluator (Stokeslet forces or rotlet torques
+// as the weights): two consecutive sources of one leaf share a 80-byte record
+// (negated hi/lo coordinates, so that the packed add forms x - y, then the
+// weights):
 //   [-yh_x0 -yh_x1 -yh_y0 -yh_y1][-yh_z0 -yh_z1 -yl_x0 -yl_x1]
 //   [-yl_y0 -yl_y1 -yl_z0 -yl_z1][f_x0 f_x1 f_y0 f_y1][f_z0 f_z1 0 0]
 // A leaf of odd size is padded with a zero-weight point at 1e18, whose term is
@@ -872,7 +873,7 @@ __global__ void __launch_bounds__(WT) k_transfer(
     for (int o = threadIdx.x; o < pdw; o += WT) dst[o] = A[o];
 }
 
-// Block per cluster: grid records of the cluster, paired (FP32x2 Stokeslet)
+// Block per cluster: grid records of the cluster, paired (FP32x2 evaluator)
 // or one record per point (other forms), at proxy + roff[c].
 template <int FORM>  // 0: pairs, 1: FP32 float4 per point, 2: FP64 per point
 __global__ void k_pack_proxies_var(const int32_t *__restrict__ deg, int win,
