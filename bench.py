@@ -265,16 +265,19 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def traffic_per_launch():
-    """DRAM bytes of one evaluator launch from the committed ncu capture, if it
-    was taken on the current evaluator source; else None."""
+def traffic_per_launch(kernel=None):
+    """DRAM bytes of one evaluator launch (the Stokeslet bench point, or the
+    record named kernel) from the committed ncu capture, if it was taken on the
+    current evaluator source; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "eval_traffic.json")
     src = os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu")
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec["dram_bytes_per_launch"] if rec.get("evaluate_cu_sha256") == sha else None
+        if rec.get("evaluate_cu_sha256") != sha:
+            return None
+        return (rec[kernel] if kernel else rec)["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         return None
 
@@ -837,7 +840,9 @@ def run_sphere(args, ws, rank, local):
                 "flops_per_interaction": ROTLET_FLOPS_PER_INTERACTION,
                 "useful_work": "Algorithm 2 (per-target MAC) interactions",
                 "executed_tflops": executed, "executed_frac": executed / peak,
-                "launch_ms": best["ms_evaluate"], "traffic": None}
+                "launch_ms": best["ms_evaluate"],
+                "traffic": traffic_per_launch("rotlet") if (best["theta"], best["degree"]) == (0.5, 4)
+                else None}
     line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
             "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
