@@ -512,6 +512,20 @@ def run_batched(args, ws, rank, local):
     clk = clocks.stop()
     total = reduce_max(sum(ms), ws)
     value = ws * args.steps * ntot / (total / 1e3)
+    # roofline of the one evaluator launch of the last step; the per-target MAC is
+    # Algorithm 2, so every counted interaction is useful
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ev_s = st["ms_evaluate"] / 1e3
+    roof = {"kernel": "k_eval<Stokeslet, mixed> (one launch over all systems)", "bound": "alu",
+            "achieved": FLOPS_PER_INTERACTION * (st["near_pairs"] + st["far_points"]) / ev_s / 1e12,
+            "peak": peak, "unit": "TFLOP/s",
+            "flops_per_interaction": FLOPS_PER_INTERACTION,
+            "useful_work": "Algorithm 2 (per-target MAC) interactions",
+            "executed_tflops": FLOPS_PER_INTERACTION * (st["near_exec"] + st["far_exec"]) / ev_s / 1e12,
+            "launch_ms": st["ms_evaluate"], "traffic": None}
+    roof["frac"] = roof["achieved"] / peak
+    roof["executed_frac"] = roof["executed_tflops"] / peak
+    stage_ms = {k: st[k] for k in ("ms_tree", "ms_weights", "ms_lists", "ms_evaluate")}
     # repeated products with the same geometry: CUDA-graph replay of weights + evaluator
     t = K.kitc_build_forest(xd, counts, tuned)
     K.kitc_modified_weights(t, fd)
@@ -585,7 +599,7 @@ def run_batched(args, ws, rank, local):
                        "leaf_size": tuned.leaf_size, "target_batch": tuned.target_batch,
                        "tuning": "N0 in {250,500,1000,2000} x batch in {32,64}, fastest step",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "E_all": E_all, "E_worst_system": worst,
+            "E_all": E_all, "E_worst_system": worst, "stage_ms": stage_ms, "roofline": roof,
             "at_1e-6": at1e6,
             "apply_graph": {"value": ntot / (apply_ms / 1e3), "unit": "targets/s",
                             "ms": apply_ms,
