@@ -629,7 +629,7 @@ def run_batched(args, ws, rank, local):
 LEARNED_N = 8_000_000
 LEARNED_SEED, LEARNED_TRAIN_SEED = 5, 15
 LEARNED_LEAF = 2000
-LEARNED_BUDGETS = (0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6)
+LEARNED_BUDGETS = (0.25e-6, 0.35e-6, 0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6)
 LEARNED_TRAIN_E = 0.8e-6     # the training system's learned run must stay within this
 LEARNED_TARGET_E = 1e-6
 
@@ -654,7 +654,8 @@ def run_learned(args, ws, rank, local):
     xtd, ftd = torch.from_numpy(xt).to(dev), torch.from_numpy(ft).to(dev)
     meas = LD.measure(xtd, ftd, P())
     calib = []
-    cal = LD.calibrate(xtd, ftd, P(), meas, target=LEARNED_TRAIN_E, log=calib.append)
+    cal = LD.calibrate(xtd, ftd, P(), meas, budgets=LEARNED_BUDGETS, target=LEARNED_TRAIN_E,
+                       log=calib.append)
     if cal is None:  # even the tightest budget misses on the training system
         lab, valid, tau = LD.labels(meas, LEARNED_BUDGETS[0])
         rows = torch.from_numpy(np.nonzero(valid)[0]).to(dev)

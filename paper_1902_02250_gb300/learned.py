@@ -2,8 +2,10 @@
 
 The paper interpolates every cluster at one degree n (Sec. 3), so the degree
 that a few hard clusters need is paid by all of them.  Here the degree of
-cluster c is picked from classes (2, 4, 6, 8, 10, 12) by a 12-64-64-6
+cluster c is picked from classes (6, 7, 8, 9, 10, 11) by a 12-64-64-6
 perceptron (FP32) that reads the cluster features of kitc_cluster_features.
+Consecutive degrees around the ones the Plummer workloads need most let a
+cluster stop one degree short of the next even one.
 
 Training data come from the treecode itself: on a training system, the
 library measures each cluster's far-field error at sampled accepting targets
@@ -30,7 +32,7 @@ import numpy as np
 
 from . import kitc as K
 
-CLASSES = (2, 4, 6, 8, 10, 12)
+CLASSES = (6, 7, 8, 9, 10, 11)
 
 
 def init_params(seed, mu, sd):
@@ -116,7 +118,8 @@ def train(features, lab, steps=3000, lr=3e-3, seed=11, log=None):
     return params, dict(loss=hist, accuracy=acc)
 
 
-def calibrate(xd, fd, p, meas, budgets=(0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6), target=0.8e-6,
+def calibrate(xd, fd, p, meas, budgets=(0.25e-6, 0.35e-6, 0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6),
+              target=0.8e-6,
               n_sample=4000, seed=21, steps=3000, log=None):
     """Trains one selector per label budget (ascending) and keeps the last whose
     learned run on the training system itself stays within `target` relative
