@@ -19,6 +19,9 @@
 //    rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
 //    terms, those runs summed over at most 8, and so on one more level; the
 //    per-leaf / per-cluster sums are accumulated in FP64.
+//  * The mixed Stokeslet and rotlet run on packed FP32x2 arithmetic over pairs
+//    of sources or grid points (paired records); the other forms take one
+//    point at a time.
 //  * Every barrier wait is bounded (globaltimer); a wait that runs out sets an
 //    error flag, the CTA drains its own copies in flight and returns.
 #include <type_traits>
@@ -158,15 +161,16 @@ template <bool MIXED, int WIN> struct Rec {
 #define KITC_SMEM_ACC 0
 #endif
 
-// FP32x2 Stokeslet: keep a run's packed sums (even / odd points or sources)
+// FP32x2 path: keep a run's packed sums (even / odd points or sources)
 // as float2 through the second summation level instead of adding the halves
 // at every run.
 #ifndef KITC_PACKED_RUNS
 #define KITC_PACKED_RUNS 1
 #endif
 
-// FP32x2 Stokeslet: grid rows per run of the far field (a warp's rows r,
-// r + NCW, ...) and source pairs per run of the near field.
+// FP32x2 path: grid rows per run of the Stokeslet far field (a warp's rows r,
+// r + NCW, ...; the rotlet takes one) and source pairs per run of the near
+// field.
 #ifndef KITC_RPR
 #define KITC_RPR 2
 #endif
@@ -174,11 +178,6 @@ template <bool MIXED, int WIN> struct Rec {
 #define KITC_NPB 8
 #endif
 constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
-// FP32x2 Stokeslet: per-row set-up of the far field in packed form from
-// target offsets held as pairs and negated grid offsets stored as pairs.
-#ifndef KITC_PSETUP
-#define KITC_PSETUP 0
-#endif
 
 // FP32x2 rotlet: FP64 sums and third FP32 level in shared memory (they change
 // every 8 / 64 runs), which leaves the registers to the six-component run sums.
@@ -191,7 +190,7 @@ template <int K> struct Smem {
     static constexpr size_t RED = (size_t)NCW * KITC_MAX_BATCH * WOUT * sizeof(double);
     static constexpr size_t META = STAGES * sizeof(TileMeta);
     static constexpr size_t BARS = (2 * STAGES + 2) * sizeof(uint64_t);
-    static constexpr size_t GRID = (size_t)NCW * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1) * sizeof(double);
+    static constexpr size_t GRID = (size_t)NCW * 3 * (KITC_MAX_DEGREE + 1) * sizeof(double);
     // KITC_SMEM_ACC: the FP64 sums and the third FP32 level of the mixed path
     static constexpr bool SA = KITC_SMEM_ACC || (KITC_ROT_SACC && K == KITC_ROTLET);
     static constexpr size_t ACCS = SA ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
@@ -236,15 +235,11 @@ __device__ __forceinline__ void load_source(const unsigned char *rec, R *yh, R *
     }
 }
 
-// CTAs per SM the register budget targets: two for the FP32 Stokeslet, one
-// for the wider FP64 and rotlet variants.  KITC_PAIR_MAXNREG > 0 gives the
-// FP32 Stokeslet kernel that register cap instead of the launch bound (two CTAs
-// of 288 threads fit up to 112 registers per thread).
+// CTAs per SM the register budget targets: two for the FP32 Stokeslet (96
+// registers a thread: a 9-warp CTA puts up to five warps of two CTAs on one
+// scheduler), one for the wider FP64 and rotlet variants (168).
 #ifndef KITC_PAIR_MINB
 #define KITC_PAIR_MINB 2
-#endif
-#ifndef KITC_PAIR_MAXNREG
-#define KITC_PAIR_MAXNREG 0
 #endif
 template <int K, bool MIXED> struct MinBlocks {
     static constexpr int value = (MIXED && K == KITC_STOKESLET) ? KITC_PAIR_MINB : 1;
@@ -416,10 +411,9 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     int c2 = 0, c3 = 0;
     dvec4 cB = make_dvec4(0, 0, 0, 0);
     double xd[2][3];
-    R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1));
-    float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * (KITC_PSETUP ? 5 : 3) * (KITC_MAX_DEGREE + 1));
+    R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
+    float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
     float2 Xh2[2][3], Xl2[2][3];
-    float2 XO2[2][3];  // KITC_PSETUP: batch-centre offsets of the targets as pairs
     const float2 e22 = bc2((float)(a.eps * a.eps));
     // rotlet (times 8 pi): Q/2 = ri3 + 1.5 eps^2 ri5, D2/4 = ri5 (1.5 + 3.75 eps^2 ri2),
     // D1/4 = ri3 (-0.5 + ri2 (-0.75 eps^2 + 3.75 eps^4 ri2))
@@ -576,7 +570,6 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     for (int l = 0; l < 3; ++l) {
                         Xh2[t][l] = bc2(X[t][l]);
                         Xl2[t][l] = bc2(XL[t][l]);
-                        if (KITC_PSETUP) XO2[t][l] = bc2(XO[t][l]);
                     }
                 }
             }
@@ -595,8 +588,6 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         double cb_l = l == 0 ? cB.x : (l == 1 ? cB.y : cB.z);
                         float v = (float)(sk - cb_l);
                         gsf[18 * l + k] = l == 2 ? -v : v;
-                        if (KITC_PSETUP && l < 2)  // -x, -y as pairs after the scalar tables
-                            reinterpret_cast<float2 *>(gsf + 54)[18 * l + k] = bc2(-v);
                     }
                     if (lane == 0 && (np & 1)) gsf[36 + np] = -1e18f;
                     __syncwarp();
@@ -625,19 +616,11 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         float2 dx2[2], dy2[2], rxy2[2], z2[2], S[2];
 #pragma unroll
                         for (int t = 0; t < 2; ++t) {
-                            if constexpr (KITC_PSETUP) {
-                                const float2 *ng2 = reinterpret_cast<const float2 *>(gsf + 54);
-                                dx2[t] = add2(XO2[t][0], ng2[k1]);
-                                dy2[t] = add2(XO2[t][1], ng2[18 + k2]);
-                                rxy2[t] = fma2(dx2[t], dx2[t], fma2(dy2[t], dy2[t], e22));
-                                z2[t] = XO2[t][2];
-                            } else {
-                                float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
-                                dx2[t] = bc2(dx);
-                                dy2[t] = bc2(dy);
-                                rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
-                                z2[t] = bc2(XO[t][2]);
-                            }
+                            const float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
+                            dx2[t] = bc2(dx);
+                            dy2[t] = bc2(dy);
+                            rxy2[t] = bc2(fmaf(dx, dx, fmaf(dy, dy, (float)e2)));
+                            z2[t] = bc2(XO[t][2]);
                             S[t] = make_float2(0.f, 0.f);
                         }
 #pragma unroll
@@ -1014,13 +997,6 @@ __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(cons
     eval_body<K, MIXED, EPS0>(a);
 }
 
-#if KITC_PAIR_MAXNREG > 0
-template <bool EPS0>
-__global__ void __maxnreg__(KITC_PAIR_MAXNREG) k_eval_pair(const EvalArgs a)
-{
-    eval_body<KITC_STOKESLET, true, EPS0>(a);
-}
-#endif
 
 // One thread waits on a barrier that is never completed; the bounded wait
 // gives up after limit_ns and records the time-out.
@@ -1051,9 +1027,6 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
         return KITC_ERR_INVALID_ARG;
     size_t smem = Smem<K>::TOTAL;
     void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0>;
-#if KITC_PAIR_MAXNREG > 0
-    if constexpr (PAIR) kern = k_eval_pair<EPS0>;
-#endif
     static std::atomic<int> configured[64] = {};  // the attribute's value never changes
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));

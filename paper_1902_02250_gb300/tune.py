@@ -99,18 +99,20 @@ def time_forest(xd, fd, counts, p, out, reps=2):
     return best
 
 
-def tune_forest(xd, fd, counts, base, leaves=(250, 500, 1000, 2000), batches=(32, 64), log=None):
-    """Fastest leaf size N0 and target-batch size for a forest at fixed theta, n."""
+def tune_forest(xd, fd, counts, base, leaves=(250, 500, 1000, 2000), batches=(32, 64), macs=None,
+                log=None):
+    """Fastest leaf size N0, target-batch size and MAC mode (of macs, default
+    base's) for a forest at fixed theta, n."""
     import torch
     out = torch.empty((xd.shape[0], K.kernel_wout(base.kernel)), dtype=torch.float64, device=xd.device)
     best = None
-    for leaf, b in itertools.product(leaves, batches):
+    for leaf, b, mac in itertools.product(leaves, batches, macs or (base.mac,)):
         p = K.Params(theta=base.theta, degree=base.degree, leaf_size=leaf, eps=base.eps,
-                     kernel=base.kernel, precision=base.precision, mac=base.mac, target_batch=b,
+                     kernel=base.kernel, precision=base.precision, mac=mac, target_batch=b,
                      weights=base.weights)
         ms = time_forest(xd, fd, counts, p, out)
         if log:
-            log(dict(leaf_size=leaf, target_batch=b, ms=ms))
+            log(dict(leaf_size=leaf, target_batch=b, mac=mac, ms=ms))
         if best is None or ms < best[1]:
             best = (p, ms)
     return best
