@@ -825,11 +825,15 @@ def run_sphere(args, ws, rank, local):
     l0 = K.kitc_launch_count()
     clocks = Clocks(local)
     clocks.start()
-    for pname, prec in precisions:
+    # the mixed form also runs with the all-targets MAC (one decision per batch,
+    # taken only when every target of the batch passes Eq. MAC)
+    sweep = [(pn, pr, mac) for pn, pr in precisions
+             for mac in ((K.MAC_PARTICLE, K.MAC_ALL) if pr == K.MIXED else (K.MAC_PARTICLE,))]
+    for pname, prec, mac in sweep:
         for th in SPHERE_THETAS:
             for n in SPHERE_DEGREES:
                 p = K.Params(theta=th, degree=n, leaf_size=SPHERE_LEAF, eps=SPHERE_EPS,
-                             kernel=K.ROTLET, precision=prec, mac=K.MAC_PARTICLE, target_batch=BATCH)
+                             kernel=K.ROTLET, precision=prec, mac=mac, target_batch=BATCH)
                 if not rows:
                     step(p)  # warm-up
                 flush.zero_()
@@ -839,7 +843,7 @@ def run_sphere(args, ws, rank, local):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = reduce_max(e0.elapsed_time(e1), ws)
-                rows.append({"precision": pname, "theta": th, "degree": n, "ms": ms,
+                rows.append({"precision": pname, "mac": MAC_NAMES[mac], "theta": th, "degree": n, "ms": ms,
                              "targets_per_s": ws * SPHERE_N / (ms / 1e3),
                              "E": rel_l2(ref, out.cpu().numpy()[idx]),
                              "far_points": st["far_points"], "near_pairs": st["near_pairs"],
@@ -851,11 +855,14 @@ def run_sphere(args, ws, rank, local):
     best = max(ok, key=lambda r: r["targets_per_s"]) if ok else None
     roof = None
     if best:
-        # the per-target MAC is Algorithm 2, so every counted interaction is useful;
-        # the evaluations of masked lanes are the executed overhead
+        # useful work: Algorithm 2's (per-target MAC) interactions at the same theta,
+        # n, N0; the evaluations of masked lanes are the executed overhead
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         sec = best["ms_evaluate"] / 1e3
-        achieved = ROTLET_FLOPS_PER_INTERACTION * (best["near_pairs"] + best["far_points"]) / sec / 1e12
+        a2 = best if best["mac"] == "particle" else algorithm2_counts(
+            K, xd, K.Params(theta=best["theta"], degree=best["degree"], leaf_size=SPHERE_LEAF,
+                            eps=SPHERE_EPS, kernel=K.ROTLET, precision=K.MIXED, target_batch=BATCH))
+        achieved = ROTLET_FLOPS_PER_INTERACTION * (a2["near_pairs"] + a2["far_points"]) / sec / 1e12
         executed = ROTLET_FLOPS_PER_INTERACTION * (best["near_exec"] + best["far_exec"]) / sec / 1e12
         roof = {"kernel": "k_eval<rotlet, mixed> (FP32x2 evaluator)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -863,8 +870,8 @@ def run_sphere(args, ws, rank, local):
                 "useful_work": "Algorithm 2 (per-target MAC) interactions",
                 "executed_tflops": executed, "executed_frac": executed / peak,
                 "launch_ms": best["ms_evaluate"],
-                "traffic": traffic_per_launch("rotlet") if (best["theta"], best["degree"]) == (0.5, 4)
-                else None}
+                "traffic": traffic_per_launch("rotlet")
+                if (best["theta"], best["degree"], best["mac"]) == (0.5, 4, "particle") else None}
     line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
             "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
@@ -872,8 +879,10 @@ def run_sphere(args, ws, rank, local):
             "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
             "config": {"workload": "unit sphere surface, N = 1,000,000 (seed 3 + rank), torque "
                                    "weights N(0,1), regularized rotlet (u and w)",
-                       "eps": SPHERE_EPS, "leaf_size": SPHERE_LEAF, "mac": "particle",
-                       "target_batch": BATCH, "value": "fastest mixed point with E <= 1e-6",
+                       "eps": SPHERE_EPS, "leaf_size": SPHERE_LEAF,
+                       "mac": best["mac"] if best else None,
+                       "target_batch": BATCH,
+                       "value": "fastest mixed point (theta, n, MAC in {particle, all}) with E <= 1e-6",
                        "error": "rel. L2 of (u, w) vs FP64 direct sum on %d sampled targets"
                                 % N_SAMPLE,
                        "l2": "flushed before every timed step (256 MiB write)"},
