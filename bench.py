@@ -572,7 +572,7 @@ def run_batched(args, ws, rank, local):
     E_all, worst = errors(out.cpu().numpy())
     # the same forest at its fastest (n, MAC) point with E <= 1e-6 over all systems
     at1e6 = None
-    for mac_name, mac_v in (("batch", K.MAC_BATCH), ("particle", K.MAC_PARTICLE)):
+    for mac_name, mac_v in (("batch", K.MAC_BATCH), ("particle", K.MAC_PARTICLE), ("all", K.MAC_ALL)):
         for nd in (8, 9, 10, 11):
             p6 = K.Params(theta=0.7, degree=nd, leaf_size=tuned.leaf_size, eps=EPS, precision=K.MIXED,
                           mac=mac_v, target_batch=tuned.target_batch)
