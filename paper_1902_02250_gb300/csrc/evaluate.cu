@@ -46,6 +46,11 @@ constexpr int NTH = (NCW + 1) * 32;    // plus one producer warp
 #endif
 constexpr int STAGES = KITC_STAGES;    // ring of shared-memory stages
 constexpr int TILE = KITC_TILE;        // bytes per stage
+// Batches of <= 32 targets run the mixed Stokeslet with one target per lane
+// instead of two (KITC_TPL1=0: two, the second idle).
+#ifndef KITC_TPL1
+#define KITC_TPL1 1
+#endif
 constexpr double INV8PI = 0.039788735772973836;
 
 enum { K_FAR = 0, K_NEAR = 1, K_EXIT = 2 };
@@ -245,9 +250,11 @@ template <int K, bool MIXED> struct MinBlocks {
     static constexpr int value = (MIXED && K == KITC_STOKESLET) ? KITC_PAIR_MINB : 1;
 };
 
-template <int K, bool MIXED, bool EPS0>
+template <int K, bool MIXED, bool EPS0, int TPL>
 __device__ __forceinline__ void eval_body(const EvalArgs &a)
 {
+    static_assert(TPL == 1 || TPL == 2, "one or two targets per lane");
+    using SM = Smem<K>;
     constexpr int WIN = KT<K>::WIN, WOUT = KT<K>::WOUT;
     constexpr int SREC = Rec<MIXED, WIN>::SRC, PREC = Rec<MIXED, WIN>::PROXY;
     // FP32x2 path (Stokeslet, rotlet): paired source records and paired grid
@@ -259,17 +266,17 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tiles = smem;
     double *red = reinterpret_cast<double *>(smem + (size_t)STAGES * TILE);
-    TileMeta *meta = reinterpret_cast<TileMeta *>(smem + (size_t)STAGES * TILE + Smem<K>::RED);
+    TileMeta *meta = reinterpret_cast<TileMeta *>(smem + (size_t)STAGES * TILE + SM::RED);
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(meta) +
-                                                  Smem<K>::META);
+                                                  SM::META);
     double *gridc = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bars) +
-                                               Smem<K>::BARS);
+                                               SM::BARS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr bool SACC = MIXED && Smem<K>::SA;
-    double *accs = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) + Smem<K>::GRID) +
+    constexpr bool SACC = MIXED && SM::SA;
+    double *accs = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) + SM::GRID) +
                    (size_t)warp * KITC_MAX_BATCH * WOUT;  // [64 targets][WOUT]
     float *a3s = reinterpret_cast<float *>(reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(gridc) +
-                                                                      Smem<K>::GRID) +
+                                                                      SM::GRID) +
                                            (size_t)NCW * KITC_MAX_BATCH * WOUT) +
                  (size_t)warp * KITC_MAX_BATCH * WOUT;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
@@ -403,17 +410,17 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     // sources) and is added to a2 only if the target uses the entry; a2 holds
     // <= 8 runs, a3 <= 8 a2's, and every 64 runs a3 goes into the FP64 sum.
     const R e2 = (R)(a.eps * a.eps), e4 = (R)(a.eps * a.eps * a.eps * a.eps);
-    R X[2][3], XL[2][3], XO[2][3];
-    double acc[2][WOUT];
-    R a1[2][WOUT], a2[2][WOUT], a3[2][WOUT];
+    R X[TPL][3], XL[TPL][3], XO[TPL][3];
+    double acc[TPL][WOUT];
+    R a1[TPL][WOUT], a2[TPL][WOUT], a3[TPL][WOUT];
     constexpr bool PRUN = PAIR && (KITC_PACKED_RUNS || ROT);  // the rotlet path always packs
-    float2 a2p[2][WOUT];  // PRUN: second level of packed run sums
+    float2 a2p[TPL][WOUT];  // PRUN: second level of packed run sums
     int c2 = 0, c3 = 0;
     dvec4 cB = make_dvec4(0, 0, 0, 0);
-    double xd[2][3];
+    double xd[TPL][3];
     R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
     float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
-    float2 Xh2[2][3], Xl2[2][3];
+    float2 Xh2[TPL][3], Xl2[TPL][3];
     const float2 e22 = bc2((float)(a.eps * a.eps));
     // rotlet (times 8 pi): Q/2 = ri3 + 1.5 eps^2 ri5, D2/4 = ri5 (1.5 + 3.75 eps^2 ri2),
     // D1/4 = ri3 (-0.5 + ri2 (-0.75 eps^2 + 3.75 eps^4 ri2))
@@ -425,17 +432,17 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     int64_t bslot = 0;
     int bsize = 0;
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < TPL; ++t)
 #pragma unroll
         for (int c = 0; c < WOUT; ++c) acc[t][c] = 0.0, a1[t][c] = a2[t][c] = a3[t][c] = R(0);
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
+    for (int t = 0; t < TPL; ++t)
 #pragma unroll
         for (int c = 0; c < WOUT; ++c) a2p[t][c] = make_float2(0.f, 0.f);
 
     auto to_fp64 = [&]() {
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int t = 0; t < TPL; ++t)
 #pragma unroll
             for (int c = 0; c < WOUT; ++c) {
                 R p = R(0);
@@ -457,15 +464,16 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     auto step = [&](bool u0, bool u1) {
         if constexpr (MIXED) {
 #pragma unroll
-            for (int c = 0; c < WOUT; ++c) {
-                a2[0][c] += u0 ? a1[0][c] : R(0);
-                a2[1][c] += u1 ? a1[1][c] : R(0);
-                a1[0][c] = a1[1][c] = R(0);
-            }
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c) {
+                    a2[t][c] += (t == 0 ? u0 : u1) ? a1[t][c] : R(0);
+                    a1[t][c] = R(0);
+                }
             if (++c2 == 8) {
                 c2 = 0;
 #pragma unroll
-                for (int t = 0; t < 2; ++t)
+                for (int t = 0; t < TPL; ++t)
 #pragma unroll
                     for (int c = 0; c < WOUT; ++c) {
                         if constexpr (SACC) a3s[(lane + 32 * t) * WOUT + c] += (float)a2[t][c];
@@ -476,25 +484,27 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < WOUT; ++c) {
-                acc[0][c] += u0 ? a1[0][c] : 0.0;
-                acc[1][c] += u1 ? a1[1][c] : 0.0;
-                a1[0][c] = a1[1][c] = 0.0;
-            }
+            for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                for (int c = 0; c < WOUT; ++c) {
+                    acc[t][c] += (t == 0 ? u0 : u1) ? a1[t][c] : 0.0;
+                    a1[t][c] = 0.0;
+                }
         }
     };
 
-    // PRUN: one run given as packed sums v0 (target lane) and v1 (target lane + 32)
+    // PRUN: one run given as packed sums v0 (target lane) and v1 (target lane + 32;
+    // not read with one target per lane)
     auto step2 = [&](bool u0, bool u1, const float2 *v0, const float2 *v1) {
 #pragma unroll
-        for (int c = 0; c < WOUT; ++c) {
-            a2p[0][c] = u0 ? add2(a2p[0][c], v0[c]) : a2p[0][c];
-            a2p[1][c] = u1 ? add2(a2p[1][c], v1[c]) : a2p[1][c];
-        }
+        for (int t = 0; t < TPL; ++t)
+#pragma unroll
+            for (int c = 0; c < WOUT; ++c)
+                a2p[t][c] = (t == 0 ? u0 : u1) ? add2(a2p[t][c], (t == 0 ? v0 : v1)[c]) : a2p[t][c];
         if (++c2 == 8) {
             c2 = 0;
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < TPL; ++t)
 #pragma unroll
                 for (int c = 0; c < WOUT; ++c) {
                     const float h = a2p[t][c].x + a2p[t][c].y;
@@ -530,13 +540,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
         const int np = mr.np, npair = (np + 1) / 2;
         const int row_bytes = PAIR ? npair * 32 : np * PREC;
         const unsigned char *tile = tiles + (size_t)s * TILE;
-        const bool u0 = (mask >> lane) & 1ull, u1 = (mask >> (lane + 32)) & 1ull;
+        const bool u0 = (mask >> lane) & 1ull, u1 = TPL > 1 && ((mask >> (lane + 32)) & 1ull);
         if (flags & F_FIRST_BATCH) {
             bslot = a.bstart ? (int64_t)a.bstart[batch] : (int64_t)batch * a.batch;
             bsize = a.bcount ? a.bcount[batch] : (int)min((int64_t)a.batch, a.nt - bslot);
             if (MIXED && a.bctr) cB = a.bctr[batch];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < TPL; ++t) {
                 int i = lane + 32 * t;
                 int64_t slot = bslot + i;
                 int64_t sl = i < bsize ? slot : bslot;
@@ -606,16 +616,16 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     // a run is RPR rows of this warp (r, r + NCW, ...): one fold
                     // into the hierarchical sums per run
                     for (; r < rows; r += RPR * NCW) {
-                        float2 ux[2], uy[2], uz[2];
+                        float2 ux[TPL], uy[TPL], uz[TPL];
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
+                        for (int t = 0; t < TPL; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int j = 0; j < RPR; ++j) {
                         if (j > 0 && r + j * NCW >= rows) break;  // uniform over the warp
                         const unsigned char *row = tile + (size_t)(r + j * NCW) * row_bytes;
-                        float2 dx2[2], dy2[2], rxy2[2], z2[2], S[2];
+                        float2 dx2[TPL], dy2[TPL], rxy2[TPL], z2[TPL], S[TPL];
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
+                        for (int t = 0; t < TPL; ++t) {
                             const float dx = XO[t][0] - gsf[k1], dy = XO[t][1] - gsf[18 + k2];
                             dx2[t] = bc2(dx);
                             dy2[t] = bc2(dy);
@@ -630,7 +640,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             const float2 fx = make_float2(A.x, A.y), fy = make_float2(A.z, A.w);
                             const float2 fz = make_float2(B.x, B.y);
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
+                            for (int t = 0; t < TPL; ++t) {
                                 float2 dz = add2(z2[t], ngz[q]);
                                 float2 r2 = fma2(dz, dz, rxy2[t]);
                                 float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
@@ -645,7 +655,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             }
                         }
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {  // the x and y parts of d s, summed over the row
+                        for (int t = 0; t < TPL; ++t) {  // the x and y parts of d s, summed over the row
                             ux[t] = fma2(dx2[t], S[t], ux[t]);
                             uy[t] = fma2(dy2[t], S[t], uy[t]);
                         }
@@ -656,11 +666,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         }
                         }
                         if constexpr (PRUN) {
-                            const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
-                            step2(u0, u1, v0, v1);
+                            float2 v[TPL][3];
+#pragma unroll
+                            for (int t = 0; t < TPL; ++t) v[t][0] = ux[t], v[t][1] = uy[t], v[t][2] = uz[t];
+                            step2(u0, u1, v[0], v[TPL - 1]);
                         } else {
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
+                            for (int t = 0; t < TPL; ++t) {
                                 a1[t][0] += ux[t].x + ux[t].y;
                                 a1[t][1] += uy[t].x + uy[t].y;
                                 a1[t][2] += uz[t].x + uz[t].y;
@@ -683,12 +695,12 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     int k1 = ta + r / np, k2 = r % np;
                     for (; r < rows; r += NCW) {
                         const unsigned char *row = tile + (size_t)r * row_bytes;
-                        float2 v[2][WOUT];
-                        float dxs[2], dys[2];
-                        float2 dx2[2], dy2[2], rxy2[2], z2[2];
-                        float2 S0[2], S1[2], S2[2], B0[2], B1[2], W0[2], W1[2], W2[2], T[2], Z[2];
+                        float2 v[TPL][WOUT];
+                        float dxs[TPL], dys[TPL];
+                        float2 dx2[TPL], dy2[TPL], rxy2[TPL], z2[TPL];
+                        float2 S0[TPL], S1[TPL], S2[TPL], B0[TPL], B1[TPL], W0[TPL], W1[TPL], W2[TPL], T[TPL], Z[TPL];
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
+                        for (int t = 0; t < TPL; ++t) {
                             dxs[t] = XO[t][0] - gsf[k1];
                             dys[t] = XO[t][1] - gsf[18 + k2];
                             dx2[t] = bc2(dxs[t]);
@@ -705,7 +717,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w);
                             const float2 nz = make_float2(B.x, B.y);
 #pragma unroll
-                            for (int t = 0; t < 2; ++t) {
+                            for (int t = 0; t < TPL; ++t) {
                                 const float2 dz = add2(z2[t], ngz[q]);
                                 float2 hQ, qD1, qD2;
                                 rot_factors(fma2(dz, dz, rxy2[t]), hQ, qD1, qD2);
@@ -725,7 +737,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             }
                         }
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
+                        for (int t = 0; t < TPL; ++t) {
                             v[t][0] = fma2(bc2(-dys[t]), S2[t], B1[t]);
                             v[t][1] = fma2(dx2[t], S2[t], mul2(m1, B0[t]));
                             v[t][2] = fma2(dy2[t], S0[t], mul2(bc2(-dxs[t]), S1[t]));
@@ -735,7 +747,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                                 v[t][5] = add2(W2[t], Z[t]);
                             }
                         }
-                        step2(u0, u1, v[0], v[1]);
+                        step2(u0, u1, v[0], v[TPL - 1]);
                         k2 += NCW;
                         while (k2 >= np) {
                             k2 -= np;
@@ -761,7 +773,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             } else {
                 const int cnt = tb - ta;  // source pairs
                 const int nb4 = (cnt + NPB - 1) / NPB, nfull = cnt / NPB;
-                float2 ux[2], uy[2], uz[2];
+                float2 ux[TPL], uy[TPL], uz[TPL];
                 auto body = [&](int idx) {
                     const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
                     const float4 A = *reinterpret_cast<const float4 *>(rec);
@@ -775,7 +787,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     const float2 fx = make_float2(D.x, D.y), fy = make_float2(D.z, D.w);
                     const float2 fz = make_float2(E.x, E.y);
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
+                    for (int t = 0; t < TPL; ++t) {
                         float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
                         float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
                         float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
@@ -792,7 +804,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 };
                 // rotlet: u = hQ n x d as the positive (P) and negative (M)
                 // products of the cross product, summed separately over a run
-                float2 P[2][3], M[2][3], Wr[2][3];
+                float2 P[TPL][3], M[TPL][3], Wr[TPL][3];
                 auto body_rot = [&](int idx) {
                     const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
                     const float4 A = *reinterpret_cast<const float4 *>(rec);
@@ -806,7 +818,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     const float2 nx = make_float2(D.x, D.y), ny = make_float2(D.z, D.w);
                     const float2 nz = make_float2(E.x, E.y);
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
+                    for (int t = 0; t < TPL; ++t) {
                         const float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
                         const float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
                         const float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
@@ -829,7 +841,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 if constexpr (ROT) {
                     for (int blk = (warp + rot) % NCW; blk < nb4; blk += NCW) {
 #pragma unroll
-                        for (int t = 0; t < 2; ++t)
+                        for (int t = 0; t < TPL; ++t)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) P[t][c] = M[t][c] = Wr[t][c] = make_float2(0.f, 0.f);
                         if (blk < nfull) {
@@ -838,20 +850,20 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         } else {
                             for (int idx = blk * NPB; idx < cnt; ++idx) body_rot(idx);
                         }
-                        float2 v[2][WOUT];
+                        float2 v[TPL][WOUT];
 #pragma unroll
-                        for (int t = 0; t < 2; ++t)
+                        for (int t = 0; t < TPL; ++t)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) {
                                 v[t][c] = fma2(m1, M[t][c], P[t][c]);
                                 if constexpr (WOUT == 6) v[t][3 + c] = Wr[t][c];
                             }
-                        step2(u0, u1, v[0], v[1]);
+                        step2(u0, u1, v[0], v[TPL - 1]);
                     }
                 } else
                 for (int blk = (warp + rot) % NCW; blk < nb4; blk += NCW) {
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
+                    for (int t = 0; t < TPL; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
                     if (blk < nfull) {
 #pragma unroll
                         for (int j = 0; j < NPB; ++j) body(blk * NPB + j);
@@ -859,11 +871,13 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         for (int idx = blk * NPB; idx < cnt; ++idx) body(idx);
                     }
                     if constexpr (PRUN) {
-                        const float2 v0[3] = {ux[0], uy[0], uz[0]}, v1[3] = {ux[1], uy[1], uz[1]};
-                        step2(u0, u1, v0, v1);
+                        float2 v[TPL][3];
+#pragma unroll
+                        for (int t = 0; t < TPL; ++t) v[t][0] = ux[t], v[t][1] = uy[t], v[t][2] = uz[t];
+                        step2(u0, u1, v[0], v[TPL - 1]);
                     } else {
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) {
+                        for (int t = 0; t < TPL; ++t) {
                             a1[t][0] += ux[t].x + ux[t].y;
                             a1[t][1] += uy[t].x + uy[t].y;
                             a1[t][2] += uz[t].x + uz[t].y;
@@ -892,9 +906,9 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             for (int r = (warp + rot) % NCW; r < rows; r += NCW) {
                 const int k1 = ta + r / np, k2 = r % np;
                 const unsigned char *row = tile + (size_t)r * np * PREC;
-                R dx[2], dy[2], rxy[2];
+                R dx[TPL], dy[TPL], rxy[TPL];
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
+                for (int t = 0; t < TPL; ++t) {
                     dx[t] = XO[t][0] - gx[k1];
                     dy[t] = XO[t][1] - gy[k2];
                     rxy[t] = fma(dx[t], dx[t], fma(dy[t], dy[t], e2));
@@ -905,7 +919,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     load_proxy<MIXED, WIN, R>(row + (size_t)k3 * PREC, f);
                     const R gzk = gz[k3];
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
+                    for (int t = 0; t < TPL; ++t) {
                         if constexpr (K == KITC_TEST_POLY) {
                             pair_poly(xd[t], (double)gx[k1], (double)gy[k2], (double)gzk,
                                       reinterpret_cast<const double *>(f),
@@ -926,7 +940,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 R f[WIN], yh[3], yl[3];
                 load_source<MIXED, WIN, R>(tile + (size_t)idx * SREC, yh, yl, f);
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
+                for (int t = 0; t < TPL; ++t) {
                     if constexpr (K == KITC_TEST_POLY) {
                         pair_poly(xd[t], (double)yh[0], (double)yh[1], (double)yh[2],
                                   reinterpret_cast<const double *>(f),
@@ -965,7 +979,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             // cross-warp sum: write partials, wait for all warps, add, write out
             if (!mbar_wait(rbr, (nbd & 1u) ^ 1u, wait_ns)) { atomicExch(a.err, 1); break; }
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < TPL; ++t)
 #pragma unroll
                 for (int c = 0; c < WOUT; ++c)
                     red[((size_t)warp * KITC_MAX_BATCH + lane + 32 * t) * WOUT + c] =
@@ -991,10 +1005,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     }
 }
 
-template <int K, bool MIXED, bool EPS0>
+template <int K, bool MIXED, bool EPS0, int TPL>
 __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
 {
-    eval_body<K, MIXED, EPS0>(a);
+    eval_body<K, MIXED, EPS0, TPL>(a);
 }
 
 
@@ -1018,6 +1032,9 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
     constexpr bool PAIR = MIXED && (K == KITC_STOKESLET || K == KITC_ROTLET);
     if (a.cdeg && (!a.roff || !a.chebt)) return KITC_ERR_INVALID_ARG;
     size_t plane = PAIR ? (size_t)np * ((np + 1) / 2) * 32 : (size_t)np * np * Rec<MIXED, WIN>::PROXY;
+    // one target per lane for batches of <= 32 (mixed Stokeslet)
+    constexpr bool ONE = KITC_TPL1 && MIXED && K == KITC_STOKESLET;
+    const bool one = ONE && a.batch <= 32;
     if (plane > (size_t)TILE) return KITC_ERR_INVALID_ARG;
     if (PAIR && a.near_off && !a.pbegin) return KITC_ERR_INVALID_ARG;
     // bulk copies need 16-byte aligned sources; records are multiples of 16 bytes
@@ -1025,14 +1042,17 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
         return KITC_ERR_INVALID_ARG;
     if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
         return KITC_ERR_INVALID_ARG;
-    size_t smem = Smem<K>::TOTAL;
-    void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0>;
-    static std::atomic<int> configured[64] = {};  // the attribute's value never changes
+    const size_t smem = Smem<K>::TOTAL;
+    void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0, 2>;
+    if constexpr (ONE) {
+        if (one) kern = k_eval<K, MIXED, EPS0, 1>;
+    }
+    static std::atomic<int> configured[2][64] = {};  // the attribute's value never changes
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
+    if (dev < 0 || dev >= 64 || !configured[one][dev].load()) {
         KITC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 64) configured[dev].store(1);
+        if (dev >= 0 && dev < 64) configured[one][dev].store(1);
     }
     int sms = 0, occ = 0;
     KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -174,6 +174,29 @@ def test_mixed_treecode_matches_oracle(K, orc, kernel, mac):
     assert e <= MIXED_TOL
 
 
+@pytest.mark.parametrize("B", [32, 17])
+@pytest.mark.parametrize("mac", [0, 1, 2])
+def test_mixed_one_target_per_lane(K, orc, B, mac):
+    """Batches of <= 32 targets run the mixed Stokeslet with one target per lane."""
+    x, f = wl.uniform_cube(20011, 46)
+    kw = dict(eps=0.005, theta=0.6, degree=6, leaf_size=400, mac=mac, target_batch=B,
+              precision=K.MIXED)
+    got, st = gpu_treecode(K, x, f, **kw)
+    o = orc.Tree(x, 400)
+    fh = o.modified_weights(f, 6)
+    if mac == 0:
+        ref = o.treecode(f, fh, 6, ST, 0.005, 0.6, x)[0]
+    else:
+        ref = o.treecode_batch(f, fh, 6, ST, 0.005, 0.6, x, B, B, all_targets=(mac == 2))["out"]
+    e = orc.rel_l2(ref, got)
+    print("mixed one target per lane B=%d mac=%d rel_l2=%.3e" % (B, mac, e))
+    assert st["far_points"] > 0 and e <= MIXED_TOL
+    y, _ = wl.uniform_cube(1001, 47)
+    d = K.kitc_direct(dev(y), dev(x), dev(f), K.Params(eps=0.005, precision=K.MIXED,
+                                                       target_batch=B)).cpu().numpy()
+    assert orc.rel_l2(orc.direct(ST, 0.005, y, x, f), d) <= MIXED_TOL
+
+
 def test_separate_targets_ragged(K, orc):
     x, f = wl.uniform_cube(9000, 41)
     y, _ = wl.uniform_cube(1234, 42, -1.6, 1.4)
