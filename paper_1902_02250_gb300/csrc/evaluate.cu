@@ -464,12 +464,14 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     auto step = [&](bool u0, bool u1) {
         if constexpr (MIXED) {
 #pragma unroll
-            for (int t = 0; t < TPL; ++t)
-#pragma unroll
-                for (int c = 0; c < WOUT; ++c) {
-                    a2[t][c] += (t == 0 ? u0 : u1) ? a1[t][c] : R(0);
-                    a1[t][c] = R(0);
+            for (int c = 0; c < WOUT; ++c) {
+                a2[0][c] += u0 ? a1[0][c] : R(0);
+                a1[0][c] = R(0);
+                if constexpr (TPL > 1) {
+                    a2[TPL - 1][c] += u1 ? a1[TPL - 1][c] : R(0);
+                    a1[TPL - 1][c] = R(0);
                 }
+            }
             if (++c2 == 8) {
                 c2 = 0;
 #pragma unroll
@@ -484,12 +486,14 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
             }
         } else {
 #pragma unroll
-            for (int t = 0; t < TPL; ++t)
-#pragma unroll
-                for (int c = 0; c < WOUT; ++c) {
-                    acc[t][c] += (t == 0 ? u0 : u1) ? a1[t][c] : 0.0;
-                    a1[t][c] = 0.0;
+            for (int c = 0; c < WOUT; ++c) {
+                acc[0][c] += u0 ? a1[0][c] : 0.0;
+                a1[0][c] = 0.0;
+                if constexpr (TPL > 1) {
+                    acc[TPL - 1][c] += u1 ? a1[TPL - 1][c] : 0.0;
+                    a1[TPL - 1][c] = 0.0;
                 }
+            }
         }
     };
 
@@ -497,10 +501,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     // not read with one target per lane)
     auto step2 = [&](bool u0, bool u1, const float2 *v0, const float2 *v1) {
 #pragma unroll
-        for (int t = 0; t < TPL; ++t)
-#pragma unroll
-            for (int c = 0; c < WOUT; ++c)
-                a2p[t][c] = (t == 0 ? u0 : u1) ? add2(a2p[t][c], (t == 0 ? v0 : v1)[c]) : a2p[t][c];
+        for (int c = 0; c < WOUT; ++c) {
+            a2p[0][c] = u0 ? add2(a2p[0][c], v0[c]) : a2p[0][c];
+            if constexpr (TPL > 1) a2p[TPL - 1][c] = u1 ? add2(a2p[TPL - 1][c], v1[c]) : a2p[TPL - 1][c];
+        }
         if (++c2 == 8) {
             c2 = 0;
 #pragma unroll
