@@ -58,6 +58,23 @@ def test_sphere_rows_of_every_pair_count(K, orc, n, mac):
     assert np.all(np.isfinite(got)) and e <= MIXED_TOL
 
 
+@pytest.mark.parametrize("mac", [0, 1, 2])
+@pytest.mark.parametrize("B", [32, 17])
+def test_small_batches(K, orc, B, mac):
+    """Batches of <= 32 targets (the second target slot of a lane stays idle)."""
+    x, f = wl.sphere_surface(9001, 67)
+    got, _ = _run(K, x, f, eps=0.005, theta=0.6, degree=5, leaf_size=301, mac=mac, target_batch=B)
+    o = orc.Tree(x, 301)
+    fh = o.modified_weights(f, 5)
+    if mac == 0:
+        ref = o.treecode(f, fh, 5, RO, 0.005, 0.6, x)[0]
+    else:
+        ref = o.treecode_batch(f, fh, 5, RO, 0.005, 0.6, x, B, B, all_targets=(mac == 2))["out"]
+    e = orc.rel_l2(ref, got)
+    print("rotlet small batches B=%d mac=%d rel_l2=%.3e" % (B, mac, e))
+    assert np.all(np.isfinite(got)) and e <= MIXED_TOL
+
+
 def test_eps_zero_leaves_out_coincident_pairs(K, orc):
     x, f = wl.uniform_cube(3000, 62)
     x = np.vstack([x, x[:7]])                     # seven sources twice: coincident pairs
