@@ -7,6 +7,11 @@
   theta = 0.7, n = 9, N0 = 4000) in the launch configuration the bench times:
   sampled targets against the oracle's batch-MAC treecode computed one by one,
   and the relative L2 error against the FP64 direct sum within 1e-6.
+* N = 1,000,000 on the unit sphere (seed 3), torques N(0,1), rotlet, eps = 0.005:
+  the sphere sweep's fastest point with E <= 1e-6 (all-targets MAC, theta = 0.7,
+  n = 6, N0 = 2000) and the per-target MAC at theta = 0.5, n = 4, each on the
+  FP32x2 rotlet path: sampled targets against the oracle one by one, exact
+  interaction counts, and E against the FP64 direct sum within 1e-6.
 """
 import numpy as np
 import pytest
@@ -67,4 +72,31 @@ def test_config_bench_point_1m(K, orc):
     d = K.kitc_direct(xd[idx].contiguous(), xd, fd, K.Params(eps=1e-3, precision=K.FP64)).cpu().numpy()
     e = orc.rel_l2(d, got[idx.cpu().numpy()])
     print("bench point E vs direct on 2000 samples: %.3e" % e)
+    assert e <= 1e-6
+
+
+@pytest.mark.parametrize("theta,n,mac", [(0.7, 6, 2), (0.5, 4, 0)])
+def test_config_sphere_rotlet_1m(K, orc, theta, n, mac):
+    import torch
+    x, f = wl.sphere_surface(1_000_000, 3)
+    xd, fd = dev(x), dev(f)
+    p = K.Params(theta=theta, degree=n, leaf_size=2000, eps=0.005, kernel=K.ROTLET,
+                 precision=K.MIXED, mac=mac, target_batch=64)
+    out, st = K.treecode(xd, fd, p)
+    got = out.cpu().numpy()
+    sel = wl.sample_indices(len(x), 300, 2025)
+    o = orc.Tree(x, 2000)
+    fh = o.modified_weights(f, n)
+    if mac == 0:
+        ref, cnt = o.treecode(f, fh, n, orc.ROTLET, 0.005, theta, x[sel])
+        assert orc.rel_l2(ref, got[sel]) <= 1e-6
+    else:
+        r = o.treecode_batch(f, fh, n, orc.ROTLET, 0.005, theta, x, 64, 64, select=sel, all_targets=True)
+        assert orc.rel_l2(r["out"][sel], got[sel]) <= 1e-6
+        assert st["far_points"] == r["counts"][1] and st["near_pairs"] == r["counts"][0]
+    idx = torch.from_numpy(wl.sample_indices(len(x), 2000, 102)).cuda()
+    d = K.kitc_direct(xd[idx].contiguous(), xd, fd,
+                      K.Params(eps=0.005, kernel=K.ROTLET, precision=K.FP64)).cpu().numpy()
+    e = orc.rel_l2(d, got[idx.cpu().numpy()])
+    print("sphere rotlet theta=%.1f n=%d mac=%d E vs direct on 2000 samples: %.3e" % (theta, n, mac, e))
     assert e <= 1e-6
