@@ -97,7 +97,9 @@ typedef struct {
     int mac;           /* kitc_mac                                                        */
     int target_batch;  /* targets per batch, 1..64 (0 = 64).  Targets are ordered by the
                           Sec. 6 tree built on them with leaf size target_batch; batch b
-                          is the slots [b*B, (b+1)*B) of that order                      */
+                          is the slots [b*B, (b+1)*B) of that order.  The evaluator holds
+                          two targets per lane; the mixed Stokeslet with B <= 32 holds
+                          one, other forms leave the second slot idle              */
     int weights;       /* kitc_weights_mode                                               */
 } kitc_params;
 
