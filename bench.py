@@ -470,7 +470,8 @@ def run_batched(args, ws, rank, local):
     xd = torch.from_numpy(x).to(dev)
     fd = torch.from_numpy(f).to(dev)
     base = K.Params(theta=0.7, degree=6, eps=EPS, precision=K.MIXED, mac=K.MAC_PARTICLE)
-    tuned = tune.tune_forest(xd, fd, counts, base, macs=(K.MAC_PARTICLE, K.MAC_BATCH, K.MAC_ALL))[0]
+    tuned = tune.tune_forest(xd, fd, counts, base, leaves=(500, 1000, 2000, 4000, 8000),
+                             macs=(K.MAC_PARTICLE, K.MAC_BATCH, K.MAC_ALL))[0]
     out = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -603,7 +604,7 @@ def run_batched(args, ws, rank, local):
                                    "boxes of side U[0.5, 2], total %d targets" % ntot,
                        "eps": EPS, "theta": 0.7, "degree": 6, "mac": MAC_NAMES[tuned.mac],
                        "leaf_size": tuned.leaf_size, "target_batch": tuned.target_batch,
-                       "tuning": "N0 in {250,500,1000,2000} x batch in {32,64} x MAC in "
+                       "tuning": "N0 in {500,1000,2000,4000,8000} x batch in {32,64} x MAC in "
                                  "{particle, batch, all}, fastest step",
                        "l2": "flushed between timed steps (256 MiB write)"},
             "E_all": E_all, "E_worst_system": worst, "stage_ms": stage_ms, "roofline": roof,
