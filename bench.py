@@ -640,6 +640,7 @@ LEARNED_LEAF = 2000
 LEARNED_BUDGETS = (0.25e-6, 0.35e-6, 0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6)
 LEARNED_TRAIN_E = 0.8e-6     # the training system's learned run must stay within this
 LEARNED_TARGET_E = 1e-6
+LEARNED_MAC = 1              # the box rule (KITC_MAC_BATCH), for both forms
 
 
 def run_learned(args, ws, rank, local):
@@ -652,7 +653,7 @@ def run_learned(args, ws, rank, local):
 
     def P(**kw):
         b = dict(theta=0.7, degree=8, leaf_size=LEARNED_LEAF, eps=EPS, kernel=K.STOKESLET,
-                 precision=K.MIXED, mac=K.MAC_BATCH, target_batch=BATCH)
+                 precision=K.MIXED, mac=LEARNED_MAC, target_batch=BATCH)
         b.update(kw)
         return K.Params(**b)
 
@@ -750,7 +751,7 @@ def run_learned(args, ws, rank, local):
             "config": {"workload": "Plummer a = 0.1 truncated at r = 2 (7.2M) + U[-2,2]^3 (0.8M), "
                                    "seed %d + rank; f ~ U[-1,1]^3" % LEARNED_SEED,
                        "eps": EPS, "theta": 0.7, "leaf_size": LEARNED_LEAF, "target_batch": BATCH,
-                       "mac": "batch", "precision": "mixed",
+                       "mac": MAC_NAMES[LEARNED_MAC], "precision": "mixed",
                        "degree_classes": list(LD.CLASSES),
                        "training": "selector trained on seed %d (same recipe), label budget "
                                    "%.1e calibrated to E <= %.1e on the training system"
