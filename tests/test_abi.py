@@ -61,3 +61,12 @@ def test_product_code_does_not_touch_the_oracle():
 def test_build_is_for_sm_103a_only():
     from paper_1902_02250_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_raises_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: without the built library every call fails loudly."""
+    from paper_1902_02250_gb300 import build, kitc
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing" / "libkitc.so"))
+    monkeypatch.setattr(kitc, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        kitc.lib()
