@@ -873,7 +873,7 @@ def run_sphere(args, ws, rank, local):
                 "executed_tflops": executed, "executed_frac": executed / peak,
                 "launch_ms": best["ms_evaluate"],
                 "traffic": traffic_per_launch("rotlet")
-                if (best["theta"], best["degree"], best["mac"]) == (0.5, 4, "particle") else None}
+                if (best["theta"], best["degree"], best["mac"]) == (0.7, 6, "all") else None}
     line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
             "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
