@@ -180,7 +180,10 @@ template <bool MIXED, int WIN> struct Rec {
 #define KITC_RPR 2
 #endif
 #ifndef KITC_NPB
-#define KITC_NPB 8
+#define KITC_NPB 8   // rotlet
+#endif
+#ifndef KITC_NPB_S
+#define KITC_NPB_S 16  // Stokeslet
 #endif
 constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
 
@@ -776,7 +779,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 }
             } else {
                 const int cnt = tb - ta;  // source pairs
-                const int nb4 = (cnt + NPB - 1) / NPB, nfull = cnt / NPB;
+                constexpr int NPBK = ROT ? NPB : KITC_NPB_S;  // source pairs per run
+                const int nb4 = (cnt + NPBK - 1) / NPBK, nfull = cnt / NPBK;
                 float2 ux[TPL], uy[TPL], uz[TPL];
                 auto body = [&](int idx) {
                     const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
@@ -870,9 +874,9 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     for (int t = 0; t < TPL; ++t) ux[t] = uy[t] = uz[t] = make_float2(0.f, 0.f);
                     if (blk < nfull) {
 #pragma unroll
-                        for (int j = 0; j < NPB; ++j) body(blk * NPB + j);
+                        for (int j = 0; j < NPBK; ++j) body(blk * NPBK + j);
                     } else {
-                        for (int idx = blk * NPB; idx < cnt; ++idx) body(idx);
+                        for (int idx = blk * NPBK; idx < cnt; ++idx) body(idx);
                     }
                     if constexpr (PRUN) {
                         float2 v[TPL][3];
