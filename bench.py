@@ -799,7 +799,8 @@ SPHERE_THETAS, SPHERE_DEGREES = (0.5, 0.7, 0.9), (2, 4, 6, 8, 10)
 
 
 def run_sphere(args, ws, rank, local):
-    """E and time of the rotlet treecode over the theta x n grid, both precisions."""
+    """E and time of the rotlet treecode over the theta x n grid: both precisions
+    under the per-target MAC, and the mixed form under the all-targets MAC."""
     import torch
     from paper_1902_02250_gb300 import kitc as K, workloads as wl
     torch.cuda.set_device(local)
