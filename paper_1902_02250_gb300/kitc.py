@@ -81,7 +81,8 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_evaluate_planned", "kitc_plan_targets_forest", "kitc_cluster_features",
            "kitc_cluster_far_errors",
            "kitc_mlp_workspace_bytes",
-           "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step"]
+           "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step",
+           "kitc_peak_launch", "kitc_peak_ops_per_launch"]
 
 
 def library_path():
@@ -133,6 +134,9 @@ def lib():
         L.kitc_mlp_loss_grad.argtypes = [P, P, P, I64, P, P, P, P]
         F = ctypes.c_float
         L.kitc_mlp_adam_step.argtypes = [P, P, P, P, I, F, F, F, F, P]
+        L.kitc_peak_launch.argtypes = [I, I, I, I, P, P]
+        L.kitc_peak_ops_per_launch.argtypes = [I, I, I, I]
+        L.kitc_peak_ops_per_launch.restype = ctypes.c_double
         for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest", "kitc_apply",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_direct_noalloc",
@@ -142,7 +146,7 @@ def lib():
                      "kitc_plan_targets_forest",
                      "kitc_cluster_features",
                      "kitc_cluster_far_errors", "kitc_mlp_forward", "kitc_mlp_loss_grad",
-                     "kitc_mlp_adam_step"):
+                     "kitc_mlp_adam_step", "kitc_peak_launch"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -192,6 +196,59 @@ def kitc_launch_count():
 def kitc_watchdog_selftest(limit_ms=50, stream=None):
     """Status of a bounded device wait on a barrier nothing completes (4 = timed out)."""
     return lib().kitc_watchdog_selftest(int(limit_ms), _stream(stream))
+
+
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA, PEAK_RSQRT = 0, 1, 2, 3
+
+
+def kitc_peak_launch(kind, blocks, threads, iters, sink, stream=None):
+    """One arithmetic-issue micro-benchmark launch (include/kitc_peak.h);
+    sink: CUDA float32 tensor of >= blocks * threads elements."""
+    import torch
+    if not (isinstance(sink, torch.Tensor) and sink.is_cuda and sink.dtype == torch.float32
+            and sink.numel() >= blocks * threads):
+        raise ValueError("sink must be a CUDA float32 tensor of >= blocks * threads elements")
+    _check(lib().kitc_peak_launch(int(kind), int(blocks), int(threads), int(iters),
+                                  ctypes.c_void_p(sink.data_ptr()), _stream(stream)),
+           "kitc_peak_launch")
+
+
+def kitc_peak_ops_per_launch(kind, blocks, threads, iters):
+    """Flops (FMA kinds) or reciprocal square roots of one kitc_peak_launch."""
+    return lib().kitc_peak_ops_per_launch(int(kind), int(blocks), int(threads), int(iters))
+
+
+def measure_peak(kind, target_ms=40.0, repeats=3, device=None):
+    """Measured issue rate of one pipe (ops/s): the micro-benchmark sized to run
+    about target_ms, on every SM (8 CTAs of 256 threads each), best of
+    `repeats` timed launches with CUDA events on the launching stream."""
+    import torch
+    dev = torch.device("cuda") if device is None else device
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = sms * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def run(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kitc_peak_launch(kind, blocks, threads, iters, sink, stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    iters = 64
+    run(iters)
+    ms = run(iters)
+    while ms < target_ms / 4 and iters < (1 << 24):
+        iters *= 4
+        ms = run(iters)
+    iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+    run(iters)
+    best = min(run(iters) for _ in range(repeats))
+    ops = kitc_peak_ops_per_launch(kind, blocks, threads, iters)
+    return {"ops_per_s": ops / (best / 1e3), "ms": best, "iters": iters, "blocks": blocks,
+            "threads": threads}
 
 
 class Tree:
