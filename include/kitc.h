@@ -284,14 +284,17 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
  * whose own allocator owns all of the device's memory, or error handling that
  * runs when memory is already exhausted.  Arguments and results are those of
  * kitc_direct; the caller still passes (device) inputs and outputs.
- * Scratch is one file-scope device array of 8 MiB (held by every GPU that
- * loads the library until the process exits); n_src is limited to 100000
- * sources (KITC_ERR_TOO_LARGE beyond).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls share the array: each
- * call clears the flags it needs and rewrites the records, and calls that
- * overlap on the GPU (other streams, other threads) race on it.  Synchronizes
- * `stream`. */
+ * Scratch is one file-scope device array of 8 MiB; n_src is limited to 100000
+ * sources (KITC_ERR_TOO_LARGE beyond).
+ * Set-up: the first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress) and loads every kernel this
+ * call can launch.  With lazy module loading (the CUDA default) that loading
+ * allocates device memory, and from then on the device holds the array until
+ * the process exits; so make one call per device at initialisation, before any
+ * stream capture.  Every later call on that device allocates nothing.
+ * All calls share the array: each call clears the flags it needs and rewrites
+ * the records, and calls that overlap on the GPU (other streams, other
+ * threads) race on it.  Synchronizes `stream` (the error flag is read back). */
 kitc_status kitc_direct_noalloc(const double *tgt_xyz, int64_t n_tgt, const double *src_xyz,
                                 const double *w, int64_t n_src, const kitc_params *p, double *out,
                                 void *stream);

@@ -127,6 +127,28 @@ void cheb_cos_table(int n, double *t)
     for (int k = 0; k <= KITC_MAX_DEGREE; ++k) t[k] = k <= n ? cos((double)k * pi / (double)n) : 0.0;
 }
 
+bool valid_count(int64_t n) { return n >= 1 && n <= (int64_t)INT32_MAX - 1024; }
+
+bool device_accessible(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+           at.type == cudaMemoryTypeHost;
+}
+
+bool valid_direct_params(const kitc_params *p)
+{
+    return p && kitc_kernel_win(p->kernel) >= 0 && p->eps >= 0.0 && isfinite(p->eps) &&
+           (p->precision == KITC_FP64 || p->precision == KITC_MIXED) && p->target_batch >= 0 &&
+           p->target_batch <= KITC_MAX_BATCH &&
+           !(p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED);
+}
+
 namespace {
 
 bool valid_params(const kitc_params *p)
@@ -144,21 +166,6 @@ bool valid_params(const kitc_params *p)
     if (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED) return false;
     if (p->weights != KITC_WEIGHTS_UPWARD && p->weights != KITC_WEIGHTS_ALGORITHM1) return false;
     return true;
-}
-
-bool valid_count(int64_t n) { return n >= 1 && n <= (int64_t)INT32_MAX - 1024; }
-
-// A pointer the kernels may read or write: device, managed or registered host memory.
-bool device_accessible(const void *ptr)
-{
-    if (!ptr) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-           at.type == cudaMemoryTypeHost;
 }
 
 int batch_of(const kitc_params &p) { return p.target_batch == 0 ? KITC_MAX_BATCH : p.target_batch; }
@@ -468,11 +475,7 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
                         const double *w, int64_t n_src, const kitc_params *p, double *out,
                         void *stream)
 {
-    if (!p || kitc_kernel_win(p->kernel) < 0 || !(p->eps >= 0.0) || !isfinite(p->eps) ||
-        (p->precision != KITC_FP64 && p->precision != KITC_MIXED) || p->target_batch < 0 ||
-        p->target_batch > KITC_MAX_BATCH ||
-        (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED))
-        return KITC_ERR_INVALID_ARG;
+    if (!valid_direct_params(p)) return KITC_ERR_INVALID_ARG;
     if (!valid_count(n_tgt) || !valid_count(n_src) || !device_accessible(tgt_xyz) ||
         !device_accessible(src_xyz) || !device_accessible(w) || !device_accessible(out))
         return KITC_ERR_INVALID_ARG;
@@ -480,10 +483,11 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
     bool mixed = p->precision == KITC_MIXED;
     int win = kitc_kernel_win(p->kernel);
     int B = batch_of(*p);
-    DevBuf rec, flags, pb;
-    kitc_status st = uses_pair_records(p->kernel, mixed)
-                         ? pack_pairs(nullptr, src_xyz, w, n_src, s, rec, pb)
-                         : pack_sources(nullptr, src_xyz, w, n_src, win, mixed, s, rec);
+    DevBuf rec, flags;
+    kitc_status st = rec.reserve(direct_record_bytes(n_src, win, mixed, uses_pair_records(p->kernel, mixed)), s);
+    if (st == KITC_OK)
+        st = pack_direct_records(src_xyz, w, n_src, win, mixed, uses_pair_records(p->kernel, mixed),
+                                 rec.ptr, s);
     if (st == KITC_OK) st = flags.reserve(4 * sizeof(int), s);
     if (st == KITC_OK) {
         EvalArgs a{};
@@ -507,7 +511,6 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
     }
     rec.release(s);
     flags.release(s);
-    pb.release(s);
     return st;
 }
 

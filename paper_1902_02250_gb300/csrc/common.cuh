@@ -149,10 +149,7 @@ constexpr bool uses_pair_records(int kernel, bool mixed)
 {
     return mixed && (kernel == KITC_STOKESLET || kernel == KITC_ROTLET);
 }
-// Paired FP32 records of the FP32x2 evaluator; pbegin receives the
-// first pair of every leaf (-1 for other clusters), followed by scratch.
-kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
-                       cudaStream_t s, DevBuf &out, DevBuf &pbegin);
+// Paired FP32x2 grid records of the modified weights.
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
 kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
                              cudaStream_t s, WeightsDev &wd);
@@ -162,16 +159,33 @@ int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed,
                           std::vector<int64_t> &roff);
 kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,
                              const int64_t *d_roff, bool mixed, bool pairs, cudaStream_t s);
+// Paired FP32 records of the FP32x2 evaluator (pack_pairs_plan once per tree,
+// then pack_pairs_launch); pbegin receives the first pair of every leaf (-1
+// for other clusters), followed by the ranges of the packing launch.
 kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
                             DevBuf &pbegin, int *nranges);
 kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
                               int64_t n, int nranges, cudaStream_t s, DevBuf &out, DevBuf &pbegin);
-// Direct-sum source records written to caller-provided device memory (no
-// allocation); pairs selects the paired FP32x2 format, range3 is 3 int32 of
-// device scratch used by that format.
+// Direct-sum source records in the caller's order, written to caller-provided
+// device memory of direct_record_bytes() bytes (no allocation, no host copy);
+// pairs selects the paired FP32x2 format.
 size_t direct_record_bytes(int64_t n, int win, bool mixed, bool pairs);
 kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, int win, bool mixed,
-                                bool pairs, int32_t *range3, void *out, cudaStream_t s);
+                                bool pairs, void *out, cudaStream_t s);
+// Loads every kernel pack_direct_records may launch on the current device
+// (lazy module loading defers that to the first launch otherwise) and raises
+// *lmem to the largest per-thread local memory among them.
+kitc_status pack_direct_preload(size_t *lmem);
+// The same for every evaluator instantiation evaluate_launch may run, which
+// also get their shared-memory attribute set.
+kitc_status evaluate_preload(size_t *lmem);
+
+// Argument checks shared by the entry points.
+bool valid_count(int64_t n);              // 1 <= n <= INT32_MAX - 1024
+// A pointer the kernels may read or write: device, managed or registered host memory.
+bool device_accessible(const void *ptr);
+// kitc_params fields used by the direct sums (kernel, eps, precision, batch).
+bool valid_direct_params(const kitc_params *p);
 
 // ---------------------------------------------------------------------------
 // Interaction lists of target batches (Algorithm 2 traversal).

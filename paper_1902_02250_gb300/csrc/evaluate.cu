@@ -1074,6 +1074,28 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
     return KITC_OK;
 }
 
+template <int K, bool MIXED, bool EPS0>
+kitc_status preload_k(size_t *lmem)
+{
+    cudaFuncAttributes at;
+    KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 2>));
+    *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
+    if constexpr (KITC_TPL1 && MIXED && K == KITC_STOKESLET) {
+        KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 1>));
+        *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
+    }
+    return KITC_OK;
+}
+
+template <int K>
+kitc_status preload_kernel(size_t *lmem)
+{
+    KITC_TRY((preload_k<K, true, true>(lmem)));
+    KITC_TRY((preload_k<K, true, false>(lmem)));
+    KITC_TRY((preload_k<K, false, true>(lmem)));
+    return preload_k<K, false, false>(lmem);
+}
+
 template <int K, bool MIXED>
 kitc_status launch_eps(const EvalArgs &a, cudaStream_t s)
 {
@@ -1088,6 +1110,14 @@ kitc_status watchdog_launch(unsigned long long limit_ns, int *err, cudaStream_t 
     k_watchdog<<<1, 32, 0, s>>>(limit_ns, err);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
+}
+
+kitc_status evaluate_preload(size_t *lmem)
+{
+    KITC_TRY(preload_kernel<KITC_STOKESLET>(lmem));
+    KITC_TRY(preload_kernel<KITC_ROTLET>(lmem));
+    KITC_TRY(preload_kernel<KITC_STOKESLET_ROTLET>(lmem));
+    return preload_k<KITC_TEST_POLY, false, false>(lmem);
 }
 
 kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s)

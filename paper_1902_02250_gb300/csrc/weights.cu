@@ -380,7 +380,21 @@ __global__ void k_pack_sources(int64_t n, int win, const double *__restrict__ xs
 //   [-yh_x0 -yh_x1 -yh_y0 -yh_y1][-yh_z0 -yh_z1 -yl_x0 -yl_x1]
 //   [-yl_y0 -yl_y1 -yl_z0 -yl_z1][f_x0 f_x1 f_y0 f_y1][f_z0 f_z1 0 0]
 // A leaf of odd size is padded with a zero-weight point at 1e18, whose term is
-// exactly zero.  Block r packs the slot range [rb[r], re[r]) from pair pb[r].
+// exactly zero.  put_pair_half writes half h (0 or 1) of record rec.
+__device__ __forceinline__ void put_pair_half(float *__restrict__ rec, int h, const double *x,
+                                              const double *f)
+{
+    for (int l = 0; l < 3; ++l) {
+        float hi = __double2float_rn(x[l]);
+        float lo = __double2float_rn(x[l] - (double)hi);
+        rec[2 * l + h] = -hi;
+        rec[6 + 2 * l + h] = -lo;
+        rec[12 + 2 * l + h] = (float)f[l];
+    }
+    rec[18 + h] = 0.f;
+}
+
+// Block r packs the slot range [rb[r], re[r]) from pair pb[r].
 __global__ void k_pack_pairs(const int32_t *__restrict__ rb, const int32_t *__restrict__ re,
                              const int32_t *__restrict__ pb, int64_t n,
                              const double *__restrict__ xs, const int32_t *__restrict__ perm,
@@ -405,17 +419,23 @@ __global__ void k_pack_pairs(const int32_t *__restrict__ rb, const int32_t *__re
                 f[l] = 0.0;
             }
         }
-        float *rec = out + ((int64_t)pb[r] + i / 2) * 20;
-        int h = (int)(i & 1);
-        for (int l = 0; l < 3; ++l) {
-            float hi = __double2float_rn(x[l]);
-            float lo = __double2float_rn(x[l] - (double)hi);
-            rec[2 * l + h] = -hi;
-            rec[6 + 2 * l + h] = -lo;
-            rec[12 + 2 * l + h] = (float)f[l];
-        }
-        rec[18 + h] = 0.f;
+        put_pair_half(out + ((int64_t)pb[r] + i / 2) * 20, (int)(i & 1), x, f);
     }
+}
+
+// Paired records of n sources in the caller's order (a direct sum): one
+// thread per slot of the padded range [0, 2 ceil(n/2)).
+__global__ void k_pack_pairs_flat(int64_t n, const double *__restrict__ xyz,
+                                  const double *__restrict__ w, float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ((n + 1) / 2) * 2) return;
+    double x[3], f[3];
+    for (int l = 0; l < 3; ++l) {
+        x[l] = i < n ? xyz[3 * i + l] : 1e18;
+        f[l] = i < n ? w[3 * i + l] : 0.0;
+    }
+    put_pair_half(out + (i / 2) * 20, (int)(i & 1), x, f);
 }
 
 // Paired modified-weight records: each grid row (k1, k2) holds ceil((n+1)/2)
@@ -705,14 +725,6 @@ kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const do
     return KITC_OK;
 }
 
-kitc_status pack_pairs(const TreeDev *t, const double *xyz_user, const double *w_user, int64_t n,
-                       cudaStream_t s, DevBuf &out, DevBuf &pbegin)
-{
-    int nr = 0;
-    KITC_TRY(pack_pairs_plan(t, n, s, out, pbegin, &nr));
-    return pack_pairs_launch(t, xyz_user, w_user, n, nr, s, out, pbegin);
-}
-
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)
 {
     int np = wd.degree + 1, npair = (np + 1) / 2;
@@ -731,15 +743,12 @@ size_t direct_record_bytes(int64_t n, int win, bool mixed, bool pairs)
 }
 
 kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, int win, bool mixed,
-                                bool pairs, int32_t *range3, void *out, cudaStream_t s)
+                                bool pairs, void *out, cudaStream_t s)
 {
     if (pairs) {
-        // one range [0, n) starting at pair 0, read by the pair-packing kernel
-        const int32_t h[3] = {0, (int32_t)n, 0};
-        KITC_CUDA(cudaMemcpyAsync(range3, h, sizeof(h), cudaMemcpyHostToDevice, s));
+        unsigned g = (unsigned)((((n + 1) / 2) * 2 + 255) / 256);
         kitc_count_launch();
-        k_pack_pairs<<<1, 256, 0, s>>>(range3, range3 + 1, range3 + 2, n, nullptr, nullptr, xyz, w,
-                                      reinterpret_cast<float *>(out));
+        k_pack_pairs_flat<<<g, 256, 0, s>>>(n, xyz, w, reinterpret_cast<float *>(out));
     } else {
         unsigned g = (unsigned)((n + 255) / 256);
         kitc_count_launch();
@@ -749,6 +758,19 @@ kitc_status pack_direct_records(const double *xyz, const double *w, int64_t n, i
             k_pack_sources<false><<<g, 256, 0, s>>>(n, win, nullptr, nullptr, xyz, w, out);
     }
     KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status pack_direct_preload(size_t *lmem)
+{
+    const void *kerns[] = {reinterpret_cast<const void *>(k_pack_pairs_flat),
+                           reinterpret_cast<const void *>(k_pack_sources<true>),
+                           reinterpret_cast<const void *>(k_pack_sources<false>)};
+    for (const void *k : kerns) {
+        cudaFuncAttributes at;
+        KITC_CUDA(cudaFuncGetAttributes(&at, k));
+        *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
+    }
     return KITC_OK;
 }
 

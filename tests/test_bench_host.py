@@ -3,7 +3,6 @@ traffic of an evaluator launch reported only while the evaluator source is
 the one the ncu capture was taken on."""
 import json
 import os
-import shutil
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -18,18 +17,30 @@ def test_defaults(monkeypatch):
 
 
 def test_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
+    import hashlib
     import bench
-    rec = json.load(open(os.path.join(ROOT, "profiles", "eval_traffic.json")))
-    assert bench.traffic_per_launch() == rec["dram_bytes_per_launch"]
-    assert bench.traffic_per_launch("rotlet") == rec["rotlet"]["dram_bytes_per_launch"]
-    # a copy of the tree whose evaluator differs by one byte reports no traffic
+    src = open(os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu"), "rb").read()
+    rec = {"evaluate_cu_sha256": hashlib.sha256(src).hexdigest(), "dram_bytes_per_launch": 123.0,
+           "rotlet": {"dram_bytes_per_launch": 456.0}}
     (tmp_path / "profiles").mkdir()
-    shutil.copy(os.path.join(ROOT, "profiles", "eval_traffic.json"), tmp_path / "profiles")
+    json.dump(rec, open(tmp_path / "profiles" / "eval_traffic.json", "w"))
     csrc = tmp_path / "paper_1902_02250_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    src = open(os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu"), "rb").read()
-    (csrc / "evaluate.cu").write_bytes(src + b"\n")
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_per_launch() is None and bench.traffic_per_launch("rotlet") is None
     (csrc / "evaluate.cu").write_bytes(src)
-    assert bench.traffic_per_launch() == rec["dram_bytes_per_launch"]
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_per_launch() == 123.0
+    assert bench.traffic_per_launch("rotlet") == 456.0
+    # an evaluator that differs by one byte from the captured one reports no traffic
+    (csrc / "evaluate.cu").write_bytes(src + b"\n")
+    assert bench.traffic_per_launch() is None and bench.traffic_per_launch("rotlet") is None
+
+
+def test_committed_traffic_matches_its_source_or_is_withheld():
+    import hashlib
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "eval_traffic.json")))
+    src = open(os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu"), "rb").read()
+    if rec["evaluate_cu_sha256"] == hashlib.sha256(src).hexdigest():
+        assert bench.traffic_per_launch() == rec["dram_bytes_per_launch"]
+    else:
+        assert bench.traffic_per_launch() is None
