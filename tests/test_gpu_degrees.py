@@ -11,6 +11,8 @@ import pytest
 
 from paper_1902_02250_gb300 import workloads as wl
 
+from mixed_parity import check_mixed
+
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
@@ -151,9 +153,7 @@ def test_mixed_per_cluster_degree(K, orc, kernel, mac):
     else:
         ref = o.treecode_batch_var(f, fh, deg, foff, kernel, 0.005, 0.6, x, 64, 64,
                                    select=sel)[0][sel]
-    e = orc.rel_l2(ref, got[sel])
-    print("mixed per-cluster degree kernel=%d mac=%d rel_l2=%.3e" % (kernel, mac, e))
-    assert e <= MIXED_TOL
+    check_mixed(ref, got[sel], "per-cluster degree kernel=%d mac=%d" % (kernel, mac))
     t.free()
 
 

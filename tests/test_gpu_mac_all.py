@@ -6,6 +6,8 @@ import pytest
 
 from paper_1902_02250_gb300 import workloads as wl
 
+from mixed_parity import check_mixed
+
 pytestmark = pytest.mark.gpu
 
 ST, RO, SR = 0, 1, 2
@@ -60,5 +62,8 @@ def test_treecode_matches_oracle(K, orc, kernel, prec):
     r = o.treecode_batch(f, o.modified_weights(f, 6), 6, kernel, 0.01, 0.7, x, 64, 64,
                          select=sel, all_targets=True)
     assert st["far_points"] == r["counts"][1] and st["near_pairs"] == r["counts"][0]
-    e = orc.rel_l2(r["out"][sel], got[sel])
-    assert e <= (1e-12 if prec == 0 else 1e-6), e
+    if prec == 0:
+        e = orc.rel_l2(r["out"][sel], got[sel])
+        assert e <= 1e-12, e
+    else:
+        check_mixed(r["out"][sel], got[sel], "all-targets MAC kernel=%d" % kernel)

@@ -14,6 +14,8 @@ import pytest
 
 from paper_1902_02250_gb300 import workloads as wl
 
+from mixed_parity import check_mixed
+
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
@@ -169,9 +171,7 @@ def test_mixed_treecode_matches_oracle(K, orc, kernel, mac):
               precision=K.MIXED)
     got, _ = gpu_treecode(K, x, f, **kw)
     ref = _oracle(orc, x, f, kernel, 0.005, 0.6, 6, 400, mac, 64)
-    e = orc.rel_l2(ref, got)
-    print("mixed kernel=%d mac=%d rel_l2=%.3e" % (kernel, mac, e))
-    assert e <= MIXED_TOL
+    check_mixed(ref, got, "kernel=%d mac=%d" % (kernel, mac))
 
 
 @pytest.mark.parametrize("B", [32, 17])
@@ -188,13 +188,12 @@ def test_mixed_one_target_per_lane(K, orc, B, mac):
         ref = o.treecode(f, fh, 6, ST, 0.005, 0.6, x)[0]
     else:
         ref = o.treecode_batch(f, fh, 6, ST, 0.005, 0.6, x, B, B, all_targets=(mac == 2))["out"]
-    e = orc.rel_l2(ref, got)
-    print("mixed one target per lane B=%d mac=%d rel_l2=%.3e" % (B, mac, e))
-    assert st["far_points"] > 0 and e <= MIXED_TOL
+    assert st["far_points"] > 0
+    check_mixed(ref, got, "one target per lane B=%d mac=%d" % (B, mac))
     y, _ = wl.uniform_cube(1001, 47)
     d = K.kitc_direct(dev(y), dev(x), dev(f), K.Params(eps=0.005, precision=K.MIXED,
                                                        target_batch=B)).cpu().numpy()
-    assert orc.rel_l2(orc.direct(ST, 0.005, y, x, f), d) <= MIXED_TOL
+    check_mixed(orc.direct(ST, 0.005, y, x, f), d, "direct B=%d" % B)
 
 
 def test_separate_targets_ragged(K, orc):
@@ -227,6 +226,8 @@ def test_direct_matches_oracle(K, orc, precision, tol, kernel):
     e = orc.rel_l2(ref, got)
     print("direct kernel=%d precision=%d rel_l2=%.3e" % (kernel, precision, e))
     assert e <= tol
+    if precision == 1:
+        check_mixed(ref, got, "direct kernel=%d" % kernel)
 
 
 # --------------------------------------------------------------- edge cases
@@ -336,6 +337,8 @@ def test_forest_matches_oracle_per_system(K, orc, mac, precision, tol):
         near += cnt[0]
         far += cnt[1]
         assert orc.rel_l2(ref, got[off[k]:off[k + 1]]) <= tol, k
+        if precision == 1:
+            check_mixed(ref, got[off[k]:off[k + 1]], "forest system %d" % k)
     assert st["near_pairs"] == near and st["far_points"] == far
 
 

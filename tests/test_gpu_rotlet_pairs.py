@@ -9,6 +9,8 @@ import pytest
 
 from paper_1902_02250_gb300 import workloads as wl
 
+from mixed_parity import check_mixed
+
 pytestmark = pytest.mark.gpu
 
 MIXED_TOL = 1e-6
@@ -52,10 +54,8 @@ def test_sphere_rows_of_every_pair_count(K, orc, n, mac):
     x, f = wl.sphere_surface(12001, 61)           # ragged: 12001 = 187 * 64 + 33
     got, st = _run(K, x, f, eps=0.005, theta=0.6, degree=n, leaf_size=301, mac=mac)
     ref = _oracle(orc, x, f, 0.005, 0.6, n, 301, mac, 64)
-    e = orc.rel_l2(ref, got)
-    print("rotlet mixed n=%d mac=%d rel_l2=%.3e" % (n, mac, e))
     assert st["far_points"] > 0 and st["near_pairs"] > 0
-    assert np.all(np.isfinite(got)) and e <= MIXED_TOL
+    check_mixed(ref, got, "rotlet n=%d mac=%d" % (n, mac))
 
 
 @pytest.mark.parametrize("mac", [0, 1, 2])
@@ -70,9 +70,7 @@ def test_small_batches(K, orc, B, mac):
         ref = o.treecode(f, fh, 5, RO, 0.005, 0.6, x)[0]
     else:
         ref = o.treecode_batch(f, fh, 5, RO, 0.005, 0.6, x, B, B, all_targets=(mac == 2))["out"]
-    e = orc.rel_l2(ref, got)
-    print("rotlet small batches B=%d mac=%d rel_l2=%.3e" % (B, mac, e))
-    assert np.all(np.isfinite(got)) and e <= MIXED_TOL
+    check_mixed(ref, got, "rotlet small batches B=%d mac=%d" % (B, mac))
 
 
 def test_eps_zero_leaves_out_coincident_pairs(K, orc):
@@ -81,8 +79,7 @@ def test_eps_zero_leaves_out_coincident_pairs(K, orc):
     f = np.vstack([f, f[:7]])
     got, _ = _run(K, x, f, eps=0.0, theta=0.6, degree=5, leaf_size=100)
     ref = _oracle(orc, x, f, 0.0, 0.6, 5, 100, 0, 64)
-    assert np.all(np.isfinite(got))
-    assert orc.rel_l2(ref, got) <= MIXED_TOL
+    check_mixed(ref, got, "rotlet eps=0")
 
 
 def test_separate_targets_ragged_batches(K, orc):
@@ -90,7 +87,7 @@ def test_separate_targets_ragged_batches(K, orc):
     y, _ = wl.uniform_cube(1234, 64, -1.3, 1.3)
     got, _ = _run(K, x, f, tgt=y, eps=0.01, theta=0.7, degree=6, leaf_size=250, target_batch=40)
     ref = _oracle(orc, x, f, 0.01, 0.7, 6, 250, 0, 40, tgt=y)
-    assert orc.rel_l2(ref, got) <= MIXED_TOL
+    check_mixed(ref, got, "rotlet separate targets")
 
 
 def test_direct_sum_of_paired_records(K, orc):
@@ -98,4 +95,4 @@ def test_direct_sum_of_paired_records(K, orc):
     y, _ = wl.uniform_cube(777, 66)
     got = K.kitc_direct(dev(y), dev(x), dev(f), K.Params(kernel=RO, precision=K.MIXED, eps=0.003))
     ref = orc.direct(RO, 0.003, y, x, f)
-    assert orc.rel_l2(ref, got.cpu().numpy()) <= MIXED_TOL
+    check_mixed(ref, got.cpu().numpy(), "rotlet direct")
