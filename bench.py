@@ -7,6 +7,16 @@ order.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kitc|reference]
 
+The default line also carries, measured in the same run:
+  * the arithmetic peaks of this GPU (micro-benchmarks; the roofline's
+    denominators), the roofline of the evaluator, and sub-rooflines of the
+    plain FP64 evaluator, the modified weights and the tree build;
+  * the plain FP64 treecode over the same K steps (the metric's comparison);
+  * "forms": the batched, learned-degree and sphere-rotlet forms at their
+    own E <= 1e-6 points, each with its plain FP64 counterpart;
+  * the CPU oracle on the host cores (cpu_baseline) and the end-to-end rate
+    through the host API (e2e).
+
 With N > 1 (torchrun) every rank solves its own independent system (weak
 scaling; no data-path collective); timings are reduced with MAX over ranks.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
@@ -43,13 +53,14 @@ LITERAL = (0.7, 8, 2000, "particle")
 FP64_POINT = (0.65, 8, 4000, "batch")
 BATCH = 64
 MAC_NAMES = {0: "particle", 1: "batch", 2: "all"}
+MAC_IDS = {v: k for k, v in MAC_NAMES.items()}
 N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacement)
-CPU_SAMPLE = 100_000     # targets of the CPU oracle's timed sample (about 12 s on 16 cores)
+CPU_SAMPLE = 30_000      # targets of one timed CPU-oracle sample (both CPU legs)
 SAMPLE_SEED = 102
 L2_FLUSH_BYTES = 256 << 20
 FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
 ROTLET_FLOPS_PER_INTERACTION = 57   # one rotlet (u, w) pair, counted the same way
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+TARGET_E = 1e-6
 
 
 def parse():
@@ -58,14 +69,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kitc", choices=["kitc", "reference"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison steps")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    ap.add_argument("--mac", default=None, choices=["particle", "batch"])
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched, learned and sphere forms of the default line")
+    ap.add_argument("--mac", default=None, choices=["particle", "batch", "all"])
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--workload", default="uniform1m", choices=["uniform1m", "batched", "learned", "sphere", "paper"],
-                    help="batched: 256 independent systems; learned: per-cluster degrees "
+                    help="batched: 256 independent systems (tuned); learned: per-cluster degrees "
                          "chosen by the trained selector on an 8M Plummer system; sphere: rotlet "
                          "theta x n sweep on the unit sphere; paper: the paper's Examples 1 and 2 "
                          "(measurement cases beside the headline line)")
@@ -164,6 +177,14 @@ def rel_l2(a, b):
     return float(math.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (GB/s), or the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 METRIC = "Stokeslet targets/sec at 1e-6 rel. L2 error, N=1M, vs plain FP64 GPU treecode"
 
 
@@ -176,10 +197,12 @@ def config(args, precision):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+# ---------------------------------------------------------------- CPU oracle
 def oracle_sample(args, x, f, n_eval, seed):
-    """The CPU oracle as it stands on this host: tree + modified weights over
-    all N sources, the traversal (Algorithm 2, or its batch-MAC variant) on
-    n_eval sampled targets, time scaled to N."""
+    """The CPU oracle as it stands on this host: tree and modified weights over
+    all N sources and, for the batch MAC, the interaction lists of every target
+    batch (all timed as they are), then the evaluation at n_eval sampled
+    targets, whose time alone is scaled by N / n_eval."""
     import oracle
     from paper_1902_02250_gb300 import workloads as wl
     t0 = time.perf_counter()
@@ -188,20 +211,34 @@ def oracle_sample(args, x, f, n_eval, seed):
     fh = t.modified_weights(f, args.degree)
     t2 = time.perf_counter()
     idx = wl.sample_indices(len(x), n_eval, seed)
-    if args.mac == "batch":
-        t.treecode_batch(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x, BATCH, BATCH,
-                         select=idx)
-    else:
+    if args.mac == "particle":
+        t3 = t2
         t.treecode(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x[idx])
-    t3 = time.perf_counter()
-    total = (t1 - t0) + (t2 - t1) + (t3 - t2) * len(x) / n_eval
+        t4 = time.perf_counter()
+        lists, ev = 0.0, t4 - t3
+    else:
+        allt = args.mac == "all"
+        # the lists of every batch (the traversal), unscaled ...
+        t.treecode_batch(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x, BATCH, BATCH,
+                         evaluate=False, all_targets=allt)
+        t3 = time.perf_counter()
+        # ... then lists again plus the evaluation of the sampled targets
+        t.treecode_batch(f, fh, args.degree, oracle.STOKESLET, EPS, args.theta, x, BATCH, BATCH,
+                         select=idx, all_targets=allt)
+        t4 = time.perf_counter()
+        lists = t3 - t2
+        ev = max(t4 - t3 - lists, 0.0)
+    total = (t1 - t0) + (t2 - t1) + lists + ev * len(x) / n_eval
     return {"value": len(x) / total, "unit": "targets/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "tree + modified weights over all %d sources, the %s traversal on %d "
-                      "sampled targets, evaluation time scaled by N/%d; %.1f s of CPU work"
-                      % (len(x), "batch-MAC" if args.mac == "batch" else "Algorithm 2 (per-target MAC)",
-                         n_eval, n_eval, t3 - t0),
-            "seconds": {"tree": t1 - t0, "weights": t2 - t1, "eval_sample": t3 - t2}}
+            "kind": "oracle", "extrapolated": True,
+            "sample": "tree, modified weights%s over all %d sources and targets, timed as they are; "
+                      "the %s evaluation at %d sampled targets, its time scaled by N/%d; "
+                      "%.1f s of CPU work"
+                      % ("" if args.mac == "particle" else " and the lists of every target batch",
+                         len(x), "Algorithm 2 (per-target MAC)" if args.mac == "particle"
+                         else "%s-MAC" % args.mac, n_eval, n_eval, t4 - t0),
+            "seconds": {"tree": t1 - t0, "weights": t2 - t1, "lists": lists, "eval_sample": ev,
+                        "wall": t4 - t0}}
 
 
 def cpu_model():
@@ -220,11 +257,15 @@ def cpu_model():
     return "unknown"
 
 
-def oracle_extra(args, x, f):
-    """The oracle on one core (a smaller sample, scaled to N) and the oracle's
-    FP64 direct sum on sampled targets, both on this host."""
+def cpu_baseline(args, x, f):
+    """The oracle on all host cores (two samples of CPU_SAMPLE targets), on
+    one core, and its FP64 direct sum at sampled targets."""
     import oracle
     from paper_1902_02250_gb300 import workloads as wl
+    runs = [oracle_sample(args, x, f, CPU_SAMPLE, 1234 + i) for i in range(2)]
+    res = dict(runs[-1])
+    res["value"] = float(np.mean([r["value"] for r in runs]))
+    res["samples"] = len(runs)
     cores = oracle.num_threads()
     oracle.set_num_threads(1)
     try:
@@ -235,15 +276,19 @@ def oracle_extra(args, x, f):
     t0 = time.perf_counter()
     oracle.direct(oracle.STOKESLET, EPS, x[idx], x, f)
     dt = time.perf_counter() - t0
-    return {"one_core": {"value": one["value"], "unit": "targets/s", "cores": 1,
-                         "sample": one["sample"]},
-            "direct_sampled": {"value": len(idx) / dt, "unit": "targets/s", "cores": cores,
-                               "sample": "FP64 direct sum over all %d sources at %d sampled "
-                                         "targets (%.1f s)" % (len(x), len(idx), dt)},
-            "cpu": cpu_model(), "nproc": os.cpu_count()}
+    res.update({"one_core": {"value": one["value"], "unit": "targets/s", "cores": 1,
+                             "sample": one["sample"]},
+                "direct_sampled": {"value": len(idx) / dt, "unit": "targets/s", "cores": cores,
+                                   "sample": "FP64 direct sum over all %d sources at %d sampled "
+                                             "targets (%.1f s)" % (len(x), len(idx), dt)},
+                "cpu": cpu_model(), "nproc": os.cpu_count()})
+    return res
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle on the host cores, each step one
+    bounded sample (CPU_SAMPLE targets) of the bench workload, extrapolated
+    to N targets as oracle_sample describes."""
     if rank != 0:
         return
     from paper_1902_02250_gb300 import workloads as wl
@@ -251,14 +296,17 @@ def run_reference(args, ws, rank):
     oracle.build()
     x, f = wl.uniform_cube(N, SEED)
     for i in range(args.warmup):
-        oracle_sample(args, x, f, 200, 900 + i)
-    vals = [oracle_sample(args, x, f, 1000, 1000 + i) for i in range(args.steps)]
+        oracle_sample(args, x, f, 1000, 900 + i)
+    vals = [oracle_sample(args, x, f, CPU_SAMPLE, 1000 + i) for i in range(args.steps)]
     v = float(np.mean([r["value"] for r in vals]))
-    ms = 1e3 * N / v
+    wall_ms = 1e3 * float(np.mean([r["seconds"]["wall"] for r in vals]))
     cb = dict(vals[-1])
     cb["value"] = v
     line = {"metric": METRIC, "value": v, "unit": "targets/s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms,
+            "ms_per_step_is": "wall time of one sampled step (%d of %d targets evaluated)"
+                              % (CPU_SAMPLE, N),
+            "ms_per_full_step_extrapolated": 1e3 * N / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, "fp64 (CPU oracle)"),
             "cpu_baseline": cb,
@@ -266,6 +314,7 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- GPU helpers
 def traffic_per_launch(kernel=None):
     """DRAM bytes of one evaluator launch (the Stokeslet bench point, or the
     record named kernel) from the committed ncu capture, if it was taken on the
@@ -300,12 +349,137 @@ def algorithm2_counts(K, xd, p, counts=None):
         t.free()
 
 
+def measure_peaks(K, dev):
+    """Issue rates of this GPU from the library's micro-benchmarks (kitc_peak.h):
+    FP32 FMA (scalar and packed FP32x2), FP64 FMA, MUFU rsqrt; each about
+    30 ms on every SM, best of 3 CUDA-event timings."""
+    r = {name: K.measure_peak(kind, target_ms=30.0, repeats=3, device=dev)
+         for name, kind in (("ffma", K.PEAK_FFMA), ("ffma2", K.PEAK_FFMA2),
+                            ("dfma", K.PEAK_DFMA), ("rsqrt", K.PEAK_RSQRT))}
+    return {"fp32_tflops": max(r["ffma"]["ops_per_s"], r["ffma2"]["ops_per_s"]) / 1e12,
+            "ffma_tflops": r["ffma"]["ops_per_s"] / 1e12,
+            "ffma2_tflops": r["ffma2"]["ops_per_s"] / 1e12,
+            "fp64_tflops": r["dfma"]["ops_per_s"] / 1e12,
+            "rsqrt_per_s": r["rsqrt"]["ops_per_s"],
+            "how": "kitc_peak_launch: 8 independent FMA (or rsqrt) chains per thread, "
+                   "8 CTAs x 256 threads per SM, ~30 ms, best of 3 (CUDA events)"}
+
+
+def eval_roofline(kernel, flops_per, useful, executed, ms, peak, peak_source, traffic=None):
+    """Roofline entry of one evaluator launch: useful and executed interactions
+    x flops each / launch time, against a measured issue peak (TFLOP/s)."""
+    achieved = flops_per * useful / (ms / 1e3) / 1e12
+    ex = flops_per * executed / (ms / 1e3) / 1e12
+    return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": peak_source, "flops_per_interaction": flops_per,
+            "executed_tflops": ex, "executed_frac": ex / peak, "launch_ms": ms, "traffic": traffic}
+
+
+def weights_roofline(st, n, win, ms, peaks, split):
+    """Modified weights (Algorithm 1 on the leaves, upward pass to the parents):
+    FP64-equivalent flops per source: (n+1)^3 w_in FMAs, (n+1)^2 + (n+1)^3
+    basis products; per child cluster 3 (n+1)^4 w_in FMAs of the upward pass."""
+    p1 = n + 1
+    per_src = 2 * p1 ** 3 * win + p1 ** 2 + p1 ** 3
+    upward = 2 * 3 * p1 ** 4 * win * max(st["n_clusters"] - 1, 0)
+    flops = st["n_sources"] * per_src + upward
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = peaks["fp32_tflops"] if split else peaks["fp64_tflops"]
+    return {"kernel": "k_weights_chunk + k_weights_reduce + k_upward (+ record packing)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_source": ("measured FP32 FMA rate: the products run in split FP32 arithmetic "
+                            "(FP64-equivalent flops counted)" if split else "measured FP64 FMA rate"),
+            "vs_fp64_pipe": achieved / peaks["fp64_tflops"],
+            "flops": flops, "stage_ms": ms, "traffic": None}
+
+
+def tree_roofline(n, depth, ms):
+    """Tree build (gather to SoA, root box, per splitting level: octant codes,
+    counts, stable scatter): algorithmic bytes 24 + 24 + 4 (gather) + 24 (root
+    box) per particle, plus per splitting level 24 + 4 read, 24 + 4 written,
+    24 + 4 re-read for the codes.  depth counts the levels of clusters; the
+    last one splits nothing."""
+    peak, src = hbm_peak_gbs()
+    splits = max(depth - 1, 0)
+    bytes_ = n * (52 + 24 + splits * 84)
+    achieved = bytes_ / (ms / 1e3) / 1e9
+    return {"kernel": "tree build (k_init, k_root*, k_split/k_count/k_children/k_scatter per "
+                      "level, k_geometry)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": src + " copy bandwidth",
+            "bytes": bytes_, "splitting_levels": splits, "stage_ms": ms, "traffic": None,
+            "note": "one host read-back per level: at this size the stage is bound by launch "
+                    "and synchronization latency, not by HBM"}
+
+
+def event_pair():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed(stream, flush, fn, steps, warmup):
+    """warmup untimed calls, then steps calls timed one by one with CUDA events
+    (L2 flushed before each); returns (ms list, last result)."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    ms, res = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = event_pair()
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, res
+
+
+def pipeline_step(K, xd, fd, p, out, stream, side, serial=False, plan_events=None):
+    """Tree; then the modified weights on `stream` and, concurrently on `side`,
+    the target tree and lists (they need only the source tree); then the
+    evaluation on the planned lists.  Returns the handle's stats."""
+    import torch
+    t = K.kitc_build_tree(xd, p)
+    try:
+        if serial:
+            K.kitc_modified_weights(t, fd)
+            K.kitc_evaluate(t, xd, out)
+            return t.stats()
+        built = torch.cuda.Event()
+        built.record(stream)
+        K.kitc_modified_weights(t, fd)
+        side.wait_event(built)
+        p0, p1 = event_pair()
+        p0.record(side)
+        K.kitc_plan_targets(t, xd, stream=side)
+        p1.record(side)
+        if plan_events is not None:
+            plan_events.append((p0, p1))
+        stream.wait_stream(side)
+        K.kitc_evaluate_planned(t, out)
+        return t.stats()
+    finally:
+        t.free()
+
+
+def sampled_error(K, xd, fd, out, idx, params):
+    """Relative L2 error of out at the targets idx against the FP64 direct sum."""
+    import torch
+    ref = K.kitc_direct(xd[torch.from_numpy(idx).to(xd.device)].contiguous(), xd, fd,
+                        params).cpu().numpy()
+    return rel_l2(ref, out.cpu().numpy()[idx]), ref
+
+
+# ---------------------------------------------------------------- headline
 def run_kitc(args, ws, rank, local):
     import torch
     from paper_1902_02250_gb300 import kitc as K, workloads as wl
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    mac = K.MAC_PARTICLE if args.mac == "particle" else K.MAC_BATCH
+    mac = MAC_IDS[args.mac]
     x, f = wl.uniform_cube(N, SEED + rank)
     xd = torch.from_numpy(x).to(dev)
     fd = torch.from_numpy(f).to(dev)
@@ -314,36 +488,13 @@ def run_kitc(args, ws, rank, local):
     out = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-
-    # the lists are the longer branch beside the weights: give them priority
-    side = torch.cuda.Stream(priority=-1)
+    side = torch.cuda.Stream(priority=-1)  # the lists are the longer branch beside the weights
     plan_events = []
 
     def step(params, o):
-        """Tree; then the modified weights on this stream and, concurrently on a
-        side stream, the target tree and lists (they need only the source
-        tree); then the evaluation on the planned lists."""
-        t = K.kitc_build_tree(xd, params)
-        try:
-            if args.serial:
-                K.kitc_modified_weights(t, fd)
-                K.kitc_evaluate(t, xd, o)
-                return t.stats()
-            built = torch.cuda.Event()
-            built.record(stream)
-            K.kitc_modified_weights(t, fd)
-            side.wait_event(built)
-            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            p0.record(side)
-            K.kitc_plan_targets(t, xd, stream=side)
-            p1.record(side)
-            plan_events.append((p0, p1))
-            stream.wait_stream(side)
-            K.kitc_evaluate_planned(t, o)
-            return t.stats()
-        finally:
-            t.free()
+        return pipeline_step(K, xd, fd, params, o, stream, side, args.serial, plan_events)
 
+    peaks = measure_peaks(K, dev)
     for _ in range(args.warmup):
         flush.zero_()
         step(p, out)
@@ -355,7 +506,7 @@ def run_kitc(args, ws, rank, local):
     step_ms, stats = [], []
     for _ in range(args.steps):
         flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = event_pair()
         e0.record(stream)
         st = step(p, out)
         e1.record(stream)
@@ -370,9 +521,8 @@ def run_kitc(args, ws, rank, local):
 
     # error of the timed result on sampled targets, against the FP64 direct sum on the GPU
     idx = wl.sample_indices(N, N_SAMPLE, SAMPLE_SEED)
+    E, ref = sampled_error(K, xd, fd, out, idx, K.Params(eps=EPS, precision=K.FP64))
     yd = xd[torch.from_numpy(idx).to(dev)].contiguous()
-    ref = K.kitc_direct(yd, xd, fd, K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
-    E = rel_l2(ref, out.cpu().numpy()[idx])
 
     st = stats[-1]
     ev_ms = float(np.mean([s["ms_evaluate"] for s in stats]))
@@ -384,10 +534,13 @@ def run_kitc(args, ws, rank, local):
     # useful work: Algorithm 2's interactions (per-target MAC) at the same theta, n, N0;
     # the batch MAC's extra pairs and grid points count as overhead
     a2 = algorithm2_counts(K, xd, p)
-    flops = FLOPS_PER_INTERACTION * (a2["near_pairs"] + a2["far_points"])
-    achieved = flops / (ev_ms / 1e3) / 1e12
-    executed = FLOPS_PER_INTERACTION * (st["near_exec"] + st["far_exec"]) / (ev_ms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    src32 = "measured: FP32 FMA micro-benchmark (max of scalar and packed FP32x2), %.1f TFLOP/s" \
+            % peaks["fp32_tflops"]
+    roof = eval_roofline("k_eval<Stokeslet, mixed> (fused near/far evaluator)", FLOPS_PER_INTERACTION,
+                         a2["near_pairs"] + a2["far_points"], st["near_exec"] + st["far_exec"],
+                         ev_ms, peaks["fp32_tflops"], src32, traffic_per_launch())
+    roof["useful_work"] = ("Algorithm 2 (per-target MAC) interactions at the same theta, n, N0; "
+                           "batch-MAC extra work is overhead")
     # precision floor of the mixed form: mixed direct sum vs FP64 direct sum, same samples
     mixed_direct = K.kitc_direct(yd, xd, fd, K.Params(eps=EPS, precision=K.MIXED)).cpu().numpy()
     floor_E = rel_l2(ref, mixed_direct)
@@ -401,37 +554,36 @@ def run_kitc(args, ws, rank, local):
                                         "algorithm2_near": a2["near_pairs"] / N,
                                         "algorithm2_far": a2["far_points"] / N},
             "mixed_floor_E": floor_E,
-            "roofline": {"kernel": "k_eval<Stokeslet, mixed> (fused near/far evaluator)",
-                         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz "
-                                        "(unit counts and maximum SM clock; no measured FP32 peak)",
-                         "flops_per_interaction": FLOPS_PER_INTERACTION,
-                         "useful_work": "Algorithm 2 (per-target MAC) interactions at the same "
-                                        "theta, n, N0; batch-MAC extra work is overhead",
-                         "executed_tflops": executed, "executed_frac": executed / peak,
-                         "launch_ms": ev_ms, "traffic": traffic_per_launch()},
+            "roofline": roof,
+            "rooflines": {"weights": weights_roofline(st, args.degree, 3, stage_ms["ms_weights"],
+                                                      peaks, split=True),
+                          "tree": tree_roofline(N, st["depth"], stage_ms["ms_tree"])},
+            "peaks": peaks,
             "gpu_launches": int(launches), "clocks": clk}
 
     if rank == 0 and ws == 1 and not args.no_fp64:
         th64, n64, leaf64, mac64 = FP64_POINT
         pf = K.Params(theta=th64, degree=n64, leaf_size=leaf64, eps=EPS, precision=K.FP64,
-                      mac=K.MAC_BATCH if mac64 == "batch" else K.MAC_PARTICLE, target_batch=BATCH)
+                      mac=MAC_IDS[mac64], target_batch=BATCH)
         out64 = torch.empty_like(out)
-        step(pf, out64)
-        torch.cuda.synchronize()
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(pf, out64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        line["plain_fp64"] = {"value": N / (ms64 / 1e3), "unit": "targets/s", "ms_per_step": ms64,
+        ms64, st64 = timed(stream, flush, lambda: step(pf, out64), args.steps, 1)
+        a264 = algorithm2_counts(K, xd, pf)
+        line["plain_fp64"] = {"value": N / (np.mean(ms64) / 1e3), "unit": "targets/s",
+                              "ms_per_step": float(np.mean(ms64)), "steps": args.steps, "warmup": 1,
                               "E": rel_l2(ref, out64.cpu().numpy()[idx]),
                               "point": {"theta": th64, "degree": n64, "leaf_size": leaf64,
                                         "mac": mac64, "why": "fastest FP64 point with E <= 1e-6"}}
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+        line["rooflines"]["k_eval_fp64"] = eval_roofline(
+            "k_eval<Stokeslet, FP64> (plain FP64 evaluator)", FLOPS_PER_INTERACTION,
+            a264["near_pairs"] + a264["far_points"], st64["near_exec"] + st64["far_exec"],
+            st64["ms_evaluate"], peaks["fp64_tflops"],
+            "measured: FP64 FMA micro-benchmark, %.2f TFLOP/s" % peaks["fp64_tflops"])
+        line["rooflines"]["k_eval_fp64"]["note"] = (
+            "the FP64 reciprocal square root (a refined MUFU seed, several FP64 FMAs) counts "
+            "as 1 flop of the 32")
+        line["rooflines"]["weights_fp64"] = weights_roofline(st64, n64, 3, st64["ms_weights"],
+                                                             peaks, split=False)
 
     # end to end through the host API: pinned host inputs in, result out, every step
     xh = torch.from_numpy(x).pin_memory().numpy()
@@ -446,47 +598,77 @@ def run_kitc(args, ws, rank, local):
     e2e_s = reduce_max(time.perf_counter() - t0, ws)
     line["e2e"] = {"value": ws * ke * N / e2e_s, "unit": "targets/s",
                    "h2d_bytes_per_step": int(x.nbytes + f.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
+    del xd, fd, out, yd
+    torch.cuda.empty_cache()
+
+    if rank == 0 and ws == 1 and not args.no_forms:
+        forms = {}
+        fsteps, fwarm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 2))
+        for name, fn in (("batched", lambda: form_batched(args, 0, dev, fsteps, fwarm, tune_it=False)),
+                         ("learned", lambda: form_learned(args, 0, dev, LEARNED_FORM_N, fsteps, fwarm)),
+                         ("sphere", lambda: form_sphere(args, 0, dev, fsteps, fwarm))):
+            t0 = time.perf_counter()
+            try:
+                forms[name] = fn()
+            except Exception as e:  # a failing form must not cost the headline line
+                forms[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+            forms[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        line["forms"] = forms
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args, x, f, CPU_SAMPLE, 1234)
-        line["cpu_baseline"].update(oracle_extra(args, x, f))
+        line["cpu_baseline"] = cpu_baseline(args, x, f)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_batched(args, ws, rank, local):
-    """256 independent Stokeslet systems, N_s log-uniform in [1e3, 2e5], each
-    uniform in its own box: one forest, one persistent evaluator launch per
-    step; theta = 0.7, n = 6, mixed; N0 and the batch size from tune_forest."""
+# ------------------------------------------------------------ batched form
+# 256 independent Stokeslet systems.  N0, batch size and MAC of the configured
+# point (theta = 0.7, n = 6) as tune_forest picked them on a GB300 (N0 in
+# {500, ..., 8000} x batch in {32, 64} x MAC in {particle, batch, all});
+# the E <= 1e-6 point is searched over n and the MAC at theta = 0.7.
+BATCHED_SYSTEMS, BATCHED_SEED = 256, 4
+BATCHED_POINT = dict(theta=0.7, degree=6, leaf_size=4000, target_batch=64, mac="all")
+BATCHED_1E6_SEARCH = (("all", (8, 9, 10, 11)), ("batch", (8, 9, 10, 11)))
+
+
+def form_batched(args, rank, dev, steps, warmup, tune_it=False, fp64=True):
+    """The batched form: forest build, weights, lists and one persistent
+    evaluator launch per step over all systems; E per system on <= 1000
+    sampled targets against the FP64 direct sum."""
     import torch
     from paper_1902_02250_gb300 import kitc as K, tune, workloads as wl
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    systems = wl.batched_systems(256, 4 + rank)
+    systems = wl.batched_systems(BATCHED_SYSTEMS, BATCHED_SEED + rank)
     counts = np.array([len(s[0]) for s in systems], np.int64)
     x = np.vstack([s[0] for s in systems])
     f = np.vstack([s[1] for s in systems])
     ntot = len(x)
     xd = torch.from_numpy(x).to(dev)
     fd = torch.from_numpy(f).to(dev)
-    base = K.Params(theta=0.7, degree=6, eps=EPS, precision=K.MIXED, mac=K.MAC_PARTICLE)
-    tuned = tune.tune_forest(xd, fd, counts, base, leaves=(500, 1000, 2000, 4000, 8000),
-                             macs=(K.MAC_PARTICLE, K.MAC_BATCH, K.MAC_ALL))[0]
-    out = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    del systems
     stream = torch.cuda.current_stream()
-
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     lists_stream = torch.cuda.Stream(priority=-1)
+    out = torch.empty((ntot, 3), dtype=torch.float64, device=dev)
+
+    def P(prec=K.MIXED, **kw):
+        b = dict(BATCHED_POINT)
+        b.update(kw)
+        return K.Params(theta=b["theta"], degree=b["degree"], leaf_size=b["leaf_size"], eps=EPS,
+                        precision=prec, mac=MAC_IDS[b["mac"]], target_batch=b["target_batch"])
+
+    if tune_it:
+        base = P(mac="particle")
+        tuned = tune.tune_forest(xd, fd, counts, base, leaves=(500, 1000, 2000, 4000, 8000),
+                                 macs=(K.MAC_PARTICLE, K.MAC_BATCH, K.MAC_ALL))[0]
+        point = dict(BATCHED_POINT, leaf_size=tuned.leaf_size, target_batch=tuned.target_batch,
+                     mac=MAC_NAMES[tuned.mac])
+    else:
+        point = dict(BATCHED_POINT)
 
     def step(p, o):
-        """Forest; the modified weights on this stream while the target trees and
-        lists of every system are built on a second one; one evaluator launch."""
         t = K.kitc_build_forest(xd, counts, p)
         try:
-            if args.serial:
-                K.kitc_modified_weights(t, fd)
-                K.kitc_evaluate_forest(t, xd, counts, o)
-                return t.stats()
             built = torch.cuda.Event()
             built.record(stream)
             K.kitc_modified_weights(t, fd)
@@ -498,157 +680,145 @@ def run_batched(args, ws, rank, local):
         finally:
             t.free()
 
-    for _ in range(args.warmup):
-        step(tuned, out)
-    torch.cuda.synchronize()
-    barrier(ws)
-    clocks = Clocks(local)
-    clocks.start()
-    l0 = K.kitc_launch_count()
-    ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = step(tuned, out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    launches = K.kitc_launch_count() - l0
-    clk = clocks.stop()
-    total = reduce_max(sum(ms), ws)
-    value = ws * args.steps * ntot / (total / 1e3)
-    # roofline of the one evaluator launch of the last step: useful work is
-    # Algorithm 2's (per-target MAC) interactions at the same theta, n, N0
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    ev_s = st["ms_evaluate"] / 1e3
-    a2 = st if tuned.mac == K.MAC_PARTICLE else algorithm2_counts(K, xd, tuned, counts)
-    roof = {"kernel": "k_eval<Stokeslet, mixed> (one launch over all systems)", "bound": "alu",
-            "achieved": FLOPS_PER_INTERACTION * (a2["near_pairs"] + a2["far_points"]) / ev_s / 1e12,
-            "peak": peak, "unit": "TFLOP/s",
-            "flops_per_interaction": FLOPS_PER_INTERACTION,
-            "useful_work": "Algorithm 2 (per-target MAC) interactions at the same theta, n, N0",
-            "executed_tflops": FLOPS_PER_INTERACTION * (st["near_exec"] + st["far_exec"]) / ev_s / 1e12,
-            "launch_ms": st["ms_evaluate"], "traffic": None}
-    roof["frac"] = roof["achieved"] / peak
-    roof["executed_frac"] = roof["executed_tflops"] / peak
-    stage_ms = {k: st[k] for k in ("ms_tree", "ms_weights", "ms_lists", "ms_evaluate")}
-    # repeated products with the same geometry: CUDA-graph replay of weights + evaluator
-    t = K.kitc_build_forest(xd, counts, tuned)
-    K.kitc_modified_weights(t, fd)
-    K.kitc_evaluate_forest(t, xd, counts, out)
-    side = torch.cuda.Stream()
-    out2 = torch.empty_like(out)
-    with torch.cuda.stream(side):
-        K.kitc_apply(t, fd, out2)
-        side.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(side)
-        for _ in range(args.steps):
-            K.kitc_apply(t, fd, out2)
-        a1.record(side)
-        side.synchronize()
-    apply_ms = a0.elapsed_time(a1) / args.steps
-    t.free()
-    # error per system on <= 1000 sampled targets against the FP64 direct sum
+    # FP64 direct sums at <= 1000 sampled targets of every system
     off = np.concatenate([[0], np.cumsum(counts)])
     refs, idxs = [], []
     for k in range(len(counts)):
         idx = wl.sample_indices(int(counts[k]), 1000, 4000 + k) + off[k]
-        xs = xd[off[k]:off[k + 1]]
-        refs.append(K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xs,
+        refs.append(K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd[off[k]:off[k + 1]],
                                   fd[off[k]:off[k + 1]], K.Params(eps=EPS, precision=K.FP64)).cpu().numpy())
         idxs.append(idx)
 
     def errors(res):
         num = den = worst = 0.0
-        for ref, idx in zip(refs, idxs):
-            d2 = float(((ref - res[idx]) ** 2).sum())
-            r2 = float((ref ** 2).sum())
+        for r, idx in zip(refs, idxs):
+            d2 = float(((r - res[idx]) ** 2).sum())
+            r2 = float((r ** 2).sum())
             num += d2
             den += r2
             worst = max(worst, math.sqrt(d2 / r2))
         return math.sqrt(num / den), worst
 
-    E_all, worst = errors(out.cpu().numpy())
-    # the same forest at its fastest (n, MAC) point with E <= 1e-6 over all systems
-    at1e6 = None
-    for mac_name, mac_v in (("batch", K.MAC_BATCH), ("particle", K.MAC_PARTICLE), ("all", K.MAC_ALL)):
-        for nd in (8, 9, 10, 11):
-            p6 = K.Params(theta=0.7, degree=nd, leaf_size=tuned.leaf_size, eps=EPS, precision=K.MIXED,
-                          mac=mac_v, target_batch=tuned.target_batch)
-            step(p6, out)
+    def run(p, n_steps, n_warm):
+        ms, st = timed(stream, flush, lambda: step(p, out), n_steps, n_warm)
+        e_all, worst = errors(out.cpu().numpy())
+        m = float(np.mean(ms))
+        return {"value": ntot / (m / 1e3), "ms_per_step": m, "steps": n_steps, "warmup": n_warm,
+                "E_all": e_all, "E_worst_system": worst, "theta": p.theta, "degree": p.degree,
+                "mac": MAC_NAMES[p.mac], "leaf_size": p.leaf_size, "target_batch": p.target_batch}, st
+
+    l0 = K.kitc_launch_count()
+    cfg, st = run(P(**point), steps, warmup)
+    peak = measure_peaks(K, dev)["fp32_tflops"] if tune_it else None
+    # the fastest (MAC, n) at theta = 0.7 with E <= 1e-6 over all systems
+    at = None
+    for mac_name, degrees in BATCHED_1E6_SEARCH:
+        for nd in degrees:
+            q = P(**dict(point, degree=nd, mac=mac_name))
+            step(q, out)
             torch.cuda.synchronize()
-            e6, w6 = errors(out.cpu().numpy())
-            if e6 <= 1e-6:
-                ms6 = []
-                for _ in range(args.steps):
-                    flush.zero_()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    step(p6, out)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    ms6.append(e0.elapsed_time(e1))
-                m6 = reduce_max(sum(ms6), ws) / args.steps
-                cand = {"degree": nd, "mac": mac_name, "theta": 0.7, "E_all": e6, "E_worst_system": w6,
-                        "ms": m6, "value": ws * ntot / (m6 / 1e3)}
-                if at1e6 is None or cand["ms"] < at1e6["ms"]:
-                    at1e6 = cand
+            if errors(out.cpu().numpy())[0] <= TARGET_E:
+                cand, cst = run(q, steps, 1)
+                if at is None or cand["ms_per_step"] < at[0]["ms_per_step"]:
+                    at = (cand, cst)
                 break
-    line = {"metric": "batched Stokeslet targets/sec, 256 systems", "value": value,
-            "unit": "targets/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
-            "config": {"workload": "256 systems, N_s = round(exp(U[ln 1e3, ln 2e5])), uniform in "
-                                   "boxes of side U[0.5, 2], total %d targets" % ntot,
-                       "eps": EPS, "theta": 0.7, "degree": 6, "mac": MAC_NAMES[tuned.mac],
-                       "leaf_size": tuned.leaf_size, "target_batch": tuned.target_batch,
+    res = {"workload": "256 systems, N_s = round(exp(U[ln 1e3, ln 2e5])), uniform in boxes of side "
+                       "U[0.5, 2], total %d targets (seed %d)" % (ntot, BATCHED_SEED + rank),
+           "config_point": cfg, "at_1e-6": at[0] if at else None,
+           "stage_ms": {k: st[k] for k in ("ms_tree", "ms_weights", "ms_lists", "ms_evaluate")},
+           "gpu_launches": int(K.kitc_launch_count() - l0)}
+    if at:
+        a2 = algorithm2_counts(K, xd, P(**dict(point, degree=at[0]["degree"], mac=at[0]["mac"])), counts)
+        cst = at[1]
+        pk = peak or measure_peaks(K, dev)["fp32_tflops"]
+        res["roofline"] = eval_roofline("k_eval<Stokeslet, mixed> (one launch over all systems)",
+                                        FLOPS_PER_INTERACTION, a2["near_pairs"] + a2["far_points"],
+                                        cst["near_exec"] + cst["far_exec"], cst["ms_evaluate"], pk,
+                                        "measured FP32 FMA micro-benchmark")
+        res["value"] = at[0]["value"]
+        res["E"] = at[0]["E_all"]
+        res["ms_per_step"] = at[0]["ms_per_step"]
+        res["steps"] = at[0]["steps"]
+    # repeated products with the same geometry: CUDA-graph replay of weights + evaluator
+    t = K.kitc_build_forest(xd, counts, P(**point))
+    try:
+        K.kitc_modified_weights(t, fd)
+        K.kitc_evaluate_forest(t, xd, counts, out)
+        gs = torch.cuda.Stream()
+        out2 = torch.empty_like(out)
+        with torch.cuda.stream(gs):
+            K.kitc_apply(t, fd, out2)
+            gs.synchronize()
+            a0, a1 = event_pair()
+            a0.record(gs)
+            for _ in range(steps):
+                K.kitc_apply(t, fd, out2)
+            a1.record(gs)
+            gs.synchronize()
+        apply_ms = a0.elapsed_time(a1) / steps
+        res["apply_graph"] = {"value": ntot / (apply_ms / 1e3), "unit": "targets/s", "ms": apply_ms,
+                              "what": "kitc_apply at the config point: new weights, same geometry, "
+                                      "CUDA-graph replay"}
+    finally:
+        t.free()
+    if fp64 and at:
+        q = P(prec=K.FP64, **dict(point, degree=at[0]["degree"], mac=at[0]["mac"]))
+        r64, _ = run(q, 1, 0)
+        r64["point"] = "the mixed form's E <= 1e-6 point (the FP64 error is at most the mixed one there)"
+        res["plain_fp64"] = r64
+        res["speedup_vs_plain_fp64"] = at[0]["value"] / r64["value"]
+    return res
+
+
+def run_batched(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    clocks = Clocks(local)
+    clocks.start()
+    r = form_batched(args, rank, dev, args.steps, args.warmup, tune_it=True,
+                     fp64=not args.no_fp64 and ws == 1)
+    clk = clocks.stop()
+    value = r.get("value") or r["config_point"]["value"]
+    line = {"metric": "batched Stokeslet targets/sec at E <= 1e-6 over all systems, 256 systems",
+            "value": ws * value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": reduce_max(r.get("ms_per_step") or
+                                                             r["config_point"]["ms_per_step"], ws),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
+            "config": {"workload": r["workload"], "eps": EPS,
                        "tuning": "N0 in {500,1000,2000,4000,8000} x batch in {32,64} x MAC in "
-                                 "{particle, batch, all}, fastest step",
+                                 "{particle, batch, all} at theta = 0.7, n = 6, fastest step",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "E_all": E_all, "E_worst_system": worst, "stage_ms": stage_ms, "roofline": roof,
-            "at_1e-6": at1e6,
-            "apply_graph": {"value": ntot / (apply_ms / 1e3), "unit": "targets/s",
-                            "ms": apply_ms,
-                            "what": "kitc_apply: new weights, same geometry, CUDA-graph replay"},
-            "gpu_launches": int(launches), "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_fp64:
-        pf = K.Params(theta=0.7, degree=6, eps=EPS, precision=K.FP64, mac=tuned.mac,
-                      leaf_size=tuned.leaf_size, target_batch=tuned.target_batch)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(pf, torch.empty_like(out))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        line["plain_fp64"] = {"value": ntot / (e0.elapsed_time(e1) / 1e3), "unit": "targets/s",
-                              "ms_per_step": e0.elapsed_time(e1)}
-        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+            "clocks": clk}
+    line.update({k: v for k, v in r.items() if k not in ("workload", "value", "ms_per_step", "steps")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-# Learned-degree workload: 8M Plummer system (7.2M Plummer, a = 0.1, truncated at
-# r = 2, plus 0.8M uniform in [-2,2]^3), Stokeslet, eps = 1e-3, theta = 0.7,
-# batch MAC, mixed, N0 = 2000.  The selector is trained on another system of
-# the same recipe (seed 15); the label budget is the largest of LEARNED_BUDGETS
-# whose learned run on the training system stays within LEARNED_TRAIN_E of the
-# direct sum, so that the whole error stays under 1e-6.
+# ------------------------------------------------------- learned-degree form
+# Plummer system (90% Plummer, a = 0.1, truncated at r = 2, plus 10% uniform in
+# [-2,2]^3), Stokeslet, eps = 1e-3, theta = 0.7, batch MAC, mixed, N0 = 2000.
+# The selector is trained on another system of the same recipe (seed 15); the
+# label budget is the largest of LEARNED_BUDGETS whose learned run on the
+# training system stays within LEARNED_TRAIN_E of the direct sum, so that the
+# whole error stays under 1e-6.  --workload learned runs N = 8M; the default
+# line's learned form runs a 2M system of the same recipe.
 LEARNED_N = 8_000_000
+LEARNED_FORM_N = 2_000_000
 LEARNED_SEED, LEARNED_TRAIN_SEED = 5, 15
 LEARNED_LEAF = 2000
 LEARNED_BUDGETS = (0.25e-6, 0.35e-6, 0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6)
 LEARNED_TRAIN_E = 0.8e-6     # the training system's learned run must stay within this
-LEARNED_TARGET_E = 1e-6
 LEARNED_MAC = 1              # the box rule (KITC_MAC_BATCH), for both forms
 
 
-def run_learned(args, ws, rank, local):
-    """Learned per-cluster degree vs the fixed-degree treecode at matched error."""
+def form_learned(args, rank, dev, n, steps, warmup, fp64=True):
+    """Learned per-cluster degree against the fixed degree at matched error
+    (E <= 1e-6 against the FP64 direct sum on sampled targets), and the plain
+    FP64 treecode at the fixed degree."""
     import torch
     from paper_1902_02250_gb300 import kitc as K, learned as LD, workloads as wl
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
     def P(**kw):
@@ -659,7 +829,7 @@ def run_learned(args, ws, rank, local):
 
     # training: the treecode measures per-cluster far-field errors on another system
     t0 = time.perf_counter()
-    xt, ft = wl.plummer_with_background(LEARNED_N, LEARNED_TRAIN_SEED + rank)
+    xt, ft = wl.plummer_with_background(n, LEARNED_TRAIN_SEED + rank)
     xtd, ftd = torch.from_numpy(xt).to(dev), torch.from_numpy(ft).to(dev)
     meas = LD.measure(xtd, ftd, P())
     calib = []
@@ -676,8 +846,8 @@ def run_learned(args, ws, rank, local):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del xtd, ftd, meas
+    torch.cuda.empty_cache()
 
-    n = LEARNED_N
     x, f = wl.plummer_with_background(n, LEARNED_SEED + rank)
     xd, fd = torch.from_numpy(x).to(dev), torch.from_numpy(f).to(dev)
     out = torch.empty((n, 3), dtype=torch.float64, device=dev)
@@ -686,133 +856,115 @@ def run_learned(args, ws, rank, local):
     ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd, fd,
                         K.Params(eps=EPS, precision=K.FP64)).cpu().numpy()
 
-    def fixed_step(p, o):
+    def fixed_step(p):
         t = K.kitc_build_tree(xd, p)
         try:
             K.kitc_modified_weights(t, fd)
-            K.kitc_evaluate(t, xd, o)
+            K.kitc_evaluate(t, xd, out)
             return t.stats()
         finally:
             t.free()
 
-    def learned_step(p, o):
-        return LD.learned_step(xd, fd, p, params, o)
-
-    def timed(fn, p, steps, warmup):
-        for _ in range(warmup):
-            flush.zero_()
-            fn(p, out)
-        torch.cuda.synchronize()
-        barrier(ws)
-        ms, st = [], None
-        for _ in range(steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = fn(p, out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return reduce_max(sum(ms), ws) / steps, st
-
     # the fixed degree: the smallest n with E <= 1e-6 (work grows with n)
-    fixed = []
-    best = None
-    for nd in range(7, 14):
-        ms, st = timed(fixed_step, P(degree=nd), 1, 1)
+    search, best = [], None
+    for nd in range(7, 15):
+        st = fixed_step(P(degree=nd))
+        torch.cuda.synchronize()
         E = rel_l2(ref, out.cpu().numpy()[idx])
-        fixed.append({"degree": nd, "ms": ms, "E": E, "far_points": st["far_points"]})
-        if E <= LEARNED_TARGET_E:
+        search.append({"degree": nd, "E": E, "far_points": st["far_points"]})
+        if E <= TARGET_E:
             best = nd
             break
-    # timed comparison: learned, then the fixed degree, same protocol
+    l0 = K.kitc_launch_count()
+    ms_l, st_l = timed(stream, flush, lambda: LD.learned_step(xd, fd, P(), params, out), steps, warmup)
+    launches = K.kitc_launch_count() - l0
+    E_l = rel_l2(ref, out.cpu().numpy()[idx])
+    value_l = n / (np.mean(ms_l) / 1e3)
+    res = {"workload": "Plummer a = 0.1 truncated at r = 2 (90%%) + U[-2,2]^3 (10%%), N = %d, "
+                       "seed %d; f ~ U[-1,1]^3; eps = %g, theta = 0.7, N0 = %d, %s MAC"
+                       % (n, LEARNED_SEED + rank, EPS, LEARNED_LEAF, MAC_NAMES[LEARNED_MAC]),
+           "learned": {"value": value_l, "ms_per_step": float(np.mean(ms_l)), "steps": steps,
+                       "warmup": warmup, "E": E_l, "far_points": st_l["far_points"],
+                       "near_pairs": st_l["near_pairs"],
+                       "stage_ms": {k: st_l[k] for k in ("ms_tree", "ms_weights", "ms_lists",
+                                                         "ms_evaluate")}},
+           "degree_classes": list(LD.CLASSES),
+           "training": {"seconds": train_s, "system_seed": LEARNED_TRAIN_SEED + rank,
+                        "clusters": int(valid.sum()), "tau": tau, "budget": budget,
+                        "calibration": calib,
+                        "label_hist": np.bincount(lab[valid], minlength=len(LD.CLASSES)).tolist()},
+           "gpu_launches": int(launches)}
+    fallback = E_l > TARGET_E
+    if best:
+        ms_f, st_f = timed(stream, flush, lambda: fixed_step(P(degree=best)), steps, 1)
+        E_f = rel_l2(ref, out.cpu().numpy()[idx])
+        value_f = n / (np.mean(ms_f) / 1e3)
+        res["fixed"] = {"degree": best, "value": value_f, "ms_per_step": float(np.mean(ms_f)),
+                        "steps": steps, "E": E_f, "far_points": st_f["far_points"], "search": search}
+        res["speedup_vs_fixed"] = None if fallback else value_l / value_f
+    res["fallback_to_fixed"] = bool(fallback)
+    chosen = res["fixed"] if (fallback and best) else res["learned"]
+    res.update(value=chosen["value"], E=chosen["E"], ms_per_step=chosen["ms_per_step"], steps=steps)
+    pk = measure_peaks(K, dev)["fp32_tflops"]
+    res["roofline"] = eval_roofline("k_eval<Stokeslet, mixed> (learned degrees)", FLOPS_PER_INTERACTION,
+                                    st_l["near_pairs"] + st_l["far_points"],
+                                    st_l["near_exec"] + st_l["far_exec"], st_l["ms_evaluate"], pk,
+                                    "measured FP32 FMA micro-benchmark")
+    res["roofline"]["useful_work"] = "batch-MAC interactions under the learned degree map"
+    if fp64 and best:
+        ms64, _ = timed(stream, flush, lambda: fixed_step(P(degree=best, precision=K.FP64)), 1, 0)
+        res["plain_fp64"] = {"value": n / (ms64[0] / 1e3), "ms_per_step": ms64[0], "steps": 1,
+                             "degree": best, "E": rel_l2(ref, out.cpu().numpy()[idx]),
+                             "point": "the fixed degree with E <= 1e-6 (mixed search)"}
+        res["speedup_vs_plain_fp64"] = res["value"] / res["plain_fp64"]["value"]
+    return res
+
+
+def run_learned(args, ws, rank, local):
+    """Learned per-cluster degree vs the fixed-degree treecode at matched error, N = 8M."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     clocks = Clocks(local)
     clocks.start()
-    l0 = K.kitc_launch_count()
-    ms_l, st_l = timed(learned_step, P(), args.steps, args.warmup)
-    launches = K.kitc_launch_count() - l0
+    r = form_learned(args, rank, dev, LEARNED_N, args.steps, args.warmup,
+                     fp64=not args.no_fp64 and ws == 1)
     clk = clocks.stop()
-    E_l = rel_l2(ref, out.cpu().numpy()[idx])
-    ms_f, st_f = timed(fixed_step, P(degree=best), args.steps, 1) if best else (None, None)
-    E_f = rel_l2(ref, out.cpu().numpy()[idx]) if best else None
-    fallback = E_l > LEARNED_TARGET_E
-    value_l = ws * n / (ms_l / 1e3)
-    value_f = ws * n / (ms_f / 1e3) if best else None
-    value = value_f if (fallback and best) else value_l
-    flops = FLOPS_PER_INTERACTION * (st_l["near_pairs"] + st_l["far_points"])
-    achieved = flops / (st_l["ms_evaluate"] / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     line = {"metric": "Stokeslet targets/sec at 1e-6 rel. L2 error, N=8M Plummer, learned "
                       "per-cluster degree vs fixed degree",
-            "value": value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_f if (fallback and best) else ms_l,
+            "value": ws * r["value"], "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": reduce_max(r["ms_per_step"], ws),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
-            "config": {"workload": "Plummer a = 0.1 truncated at r = 2 (7.2M) + U[-2,2]^3 (0.8M), "
-                                   "seed %d + rank; f ~ U[-1,1]^3" % LEARNED_SEED,
-                       "eps": EPS, "theta": 0.7, "leaf_size": LEARNED_LEAF, "target_batch": BATCH,
-                       "mac": MAC_NAMES[LEARNED_MAC], "precision": "mixed",
-                       "degree_classes": list(LD.CLASSES),
-                       "training": "selector trained on seed %d (same recipe), label budget "
-                                   "%.1e calibrated to E <= %.1e on the training system"
-                                   % (LEARNED_TRAIN_SEED, budget, LEARNED_TRAIN_E),
+            "config": {"workload": r["workload"],
                        "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "learned": {"value": value_l, "ms": ms_l, "E": E_l, "far_points": st_l["far_points"],
-                        "near_pairs": st_l["near_pairs"],
-                        "stage_ms": {k: st_l[k] for k in ("ms_tree", "ms_weights", "ms_lists",
-                                                          "ms_evaluate")}},
-            "fixed": {"degree": best, "value": value_f, "ms": ms_f, "E": E_f,
-                      "far_points": st_f["far_points"] if st_f else None, "search": fixed},
-            "fallback_to_fixed": bool(fallback),
-            "speedup_vs_fixed": (value_l / value_f) if (best and not fallback) else None,
-            "training": {"seconds": train_s, "clusters": int(valid.sum()), "tau": tau,
-                         "budget": budget, "calibration": calib,
-                         "label_hist": np.bincount(lab[valid], minlength=len(LD.CLASSES)).tolist()},
-            "roofline": {"kernel": "k_eval<Stokeslet, mixed> (learned degrees)", "bound": "alu",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "flops_per_interaction": FLOPS_PER_INTERACTION,
-                         "useful_work": "batch-MAC interactions under the learned degree map "
-                                        "(all executed)",
-                         "launch_ms": st_l["ms_evaluate"], "traffic": None},
-            "gpu_launches": int(launches), "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_fp64 and best:
-        pf = P(degree=best, precision=K.FP64)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fixed_step(pf, out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        line["plain_fp64"] = {"value": n / (ms64 / 1e3), "unit": "targets/s", "ms_per_step": ms64,
-                              "degree": best, "E": rel_l2(ref, out.cpu().numpy()[idx])}
-        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+            "clocks": clk}
+    line.update({k: v for k, v in r.items() if k not in ("workload", "value", "ms_per_step", "steps")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-# Rotlet sweep workload: N = 1M points on the unit sphere surface (x = g/|g|,
-# g ~ N(0, I3)), torque weights N(0,1), regularized rotlet (output u and w),
-# eps = 0.005, N0 = 2000, per-target MAC; theta x n grid, FP64 and mixed.
+# ------------------------------------------------------------- sphere rotlet
+# N = 1M points on the unit sphere surface (x = g/|g|, g ~ N(0, I3)), torque
+# weights N(0,1), regularized rotlet (output u and w), eps = 0.005, N0 = 2000.
 SPHERE_N, SPHERE_SEED, SPHERE_EPS, SPHERE_LEAF = 1_000_000, 3, 0.005, 2000
 SPHERE_THETAS, SPHERE_DEGREES = (0.5, 0.7, 0.9), (2, 4, 6, 8, 10)
+# the sweep's fastest mixed point with E <= 1e-6, and the FP64 candidates in
+# order of their time in the sweep (the first with E <= 1e-6 is taken)
+SPHERE_BEST = (0.7, 6, "all")
+SPHERE_FP64 = ((0.7, 6, "all"), (0.5, 4, "particle"), (0.7, 8, "particle"))
 
 
-def run_sphere(args, ws, rank, local):
-    """E and time of the rotlet treecode over the theta x n grid: both precisions
-    under the per-target MAC, and the mixed form under the all-targets MAC."""
+def _sphere_setup(K, dev, rank):
     import torch
-    from paper_1902_02250_gb300 import kitc as K, workloads as wl
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
+    from paper_1902_02250_gb300 import workloads as wl
     x, f = wl.sphere_surface(SPHERE_N, SPHERE_SEED + rank)
     xd, fd = torch.from_numpy(x).to(dev), torch.from_numpy(f).to(dev)
     idx = wl.sample_indices(SPHERE_N, N_SAMPLE, SAMPLE_SEED)
     ref = K.kitc_direct(xd[torch.from_numpy(idx).to(dev)].contiguous(), xd, fd,
                         K.Params(eps=SPHERE_EPS, kernel=K.ROTLET, precision=K.FP64)).cpu().numpy()
     out = torch.empty((SPHERE_N, 6), dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step(p):
         t = K.kitc_build_tree(xd, p)
@@ -823,58 +975,94 @@ def run_sphere(args, ws, rank, local):
         finally:
             t.free()
 
+    def P(theta, n, mac, prec):
+        return K.Params(theta=theta, degree=n, leaf_size=SPHERE_LEAF, eps=SPHERE_EPS, kernel=K.ROTLET,
+                        precision=prec, mac=MAC_IDS[mac], target_batch=BATCH)
+    return xd, fd, idx, ref, out, step, P
+
+
+def form_sphere(args, rank, dev, steps, warmup, fp64=True):
+    """The rotlet on the sphere at the sweep's fastest mixed point with
+    E <= 1e-6 and the plain FP64 treecode at its own fastest such point."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    xd, fd, idx, ref, out, step, P = _sphere_setup(K, dev, rank)
+    th, n, mac = SPHERE_BEST
+    p = P(th, n, mac, K.MIXED)
+    ms, st = timed(stream, flush, lambda: step(p), steps, warmup)
+    E = rel_l2(ref, out.cpu().numpy()[idx])
+    m = float(np.mean(ms))
+    a2 = algorithm2_counts(K, xd, P(th, n, "particle", K.MIXED))
+    pk = measure_peaks(K, dev)["fp32_tflops"]
+    res = {"workload": "unit sphere surface, N = 1,000,000 (seed %d), torques N(0,1), rotlet "
+                       "(u and w), eps = %g, N0 = %d" % (SPHERE_SEED + rank, SPHERE_EPS, SPHERE_LEAF),
+           "value": SPHERE_N / (m / 1e3), "ms_per_step": m, "steps": steps, "warmup": warmup, "E": E,
+           "point": {"theta": th, "degree": n, "mac": mac},
+           "roofline": eval_roofline("k_eval<rotlet, mixed> (FP32x2 evaluator)",
+                                     ROTLET_FLOPS_PER_INTERACTION, a2["near_pairs"] + a2["far_points"],
+                                     st["near_exec"] + st["far_exec"], st["ms_evaluate"], pk,
+                                     "measured FP32 FMA micro-benchmark",
+                                     traffic_per_launch("rotlet"))}
+    if fp64:
+        tried = []
+        for th64, n64, mac64 in SPHERE_FP64:
+            ms64, _ = timed(stream, flush, lambda: step(P(th64, n64, mac64, K.FP64)), 1, 0)
+            E64 = rel_l2(ref, out.cpu().numpy()[idx])
+            tried.append({"theta": th64, "degree": n64, "mac": mac64, "ms": ms64[0], "E": E64})
+            if E64 <= TARGET_E:
+                res["plain_fp64"] = {"value": SPHERE_N / (ms64[0] / 1e3), "ms_per_step": ms64[0],
+                                     "steps": 1, "E": E64,
+                                     "point": {"theta": th64, "degree": n64, "mac": mac64}}
+                res["speedup_vs_plain_fp64"] = res["value"] / res["plain_fp64"]["value"]
+                break
+        res["fp64_tried"] = tried
+    return res
+
+
+def run_sphere(args, ws, rank, local):
+    """E and time of the rotlet treecode over the theta x n grid: both precisions
+    under the per-target MAC, and the mixed form under the all-targets MAC."""
+    import torch
+    from paper_1902_02250_gb300 import kitc as K
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    xd, fd, idx, ref, out, step, P = _sphere_setup(K, dev, rank)
     precisions = [("mixed", K.MIXED)] + ([] if args.no_fp64 else [("fp64", K.FP64)])
     rows = []
     l0 = K.kitc_launch_count()
     clocks = Clocks(local)
     clocks.start()
-    # the mixed form also runs with the all-targets MAC (one decision per batch,
-    # taken only when every target of the batch passes Eq. MAC)
     sweep = [(pn, pr, mac) for pn, pr in precisions
-             for mac in ((K.MAC_PARTICLE, K.MAC_ALL) if pr == K.MIXED else (K.MAC_PARTICLE,))]
+             for mac in (("particle", "all") if pr == K.MIXED else ("particle",))]
     for pname, prec, mac in sweep:
         for th in SPHERE_THETAS:
             for n in SPHERE_DEGREES:
-                p = K.Params(theta=th, degree=n, leaf_size=SPHERE_LEAF, eps=SPHERE_EPS,
-                             kernel=K.ROTLET, precision=prec, mac=mac, target_batch=BATCH)
-                if not rows:
-                    step(p)  # warm-up
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                st = step(p)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms = reduce_max(e0.elapsed_time(e1), ws)
-                rows.append({"precision": pname, "mac": MAC_NAMES[mac], "theta": th, "degree": n, "ms": ms,
-                             "targets_per_s": ws * SPHERE_N / (ms / 1e3),
+                p = P(th, n, mac, prec)
+                ms, st = timed(stream, flush, lambda: step(p), 1, 0 if rows else 1)
+                msr = reduce_max(ms[0], ws)
+                rows.append({"precision": pname, "mac": mac, "theta": th, "degree": n, "ms": msr,
+                             "targets_per_s": ws * SPHERE_N / (msr / 1e3),
                              "E": rel_l2(ref, out.cpu().numpy()[idx]),
                              "far_points": st["far_points"], "near_pairs": st["near_pairs"],
                              "far_exec": st["far_exec"], "near_exec": st["near_exec"],
                              "ms_evaluate": st["ms_evaluate"]})
     clk = clocks.stop()
     launches = K.kitc_launch_count() - l0
-    ok = [r for r in rows if r["precision"] == "mixed" and r["E"] <= 1e-6]
+    ok = [r for r in rows if r["precision"] == "mixed" and r["E"] <= TARGET_E]
     best = max(ok, key=lambda r: r["targets_per_s"]) if ok else None
     roof = None
     if best:
-        # useful work: Algorithm 2's (per-target MAC) interactions at the same theta,
-        # n, N0; the evaluations of masked lanes are the executed overhead
-        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        sec = best["ms_evaluate"] / 1e3
-        a2 = best if best["mac"] == "particle" else algorithm2_counts(
-            K, xd, K.Params(theta=best["theta"], degree=best["degree"], leaf_size=SPHERE_LEAF,
-                            eps=SPHERE_EPS, kernel=K.ROTLET, precision=K.MIXED, target_batch=BATCH))
-        achieved = ROTLET_FLOPS_PER_INTERACTION * (a2["near_pairs"] + a2["far_points"]) / sec / 1e12
-        executed = ROTLET_FLOPS_PER_INTERACTION * (best["near_exec"] + best["far_exec"]) / sec / 1e12
-        roof = {"kernel": "k_eval<rotlet, mixed> (FP32x2 evaluator)", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "flops_per_interaction": ROTLET_FLOPS_PER_INTERACTION,
-                "useful_work": "Algorithm 2 (per-target MAC) interactions",
-                "executed_tflops": executed, "executed_frac": executed / peak,
-                "launch_ms": best["ms_evaluate"],
-                "traffic": traffic_per_launch("rotlet")
-                if (best["theta"], best["degree"], best["mac"]) == (0.7, 6, "all") else None}
+        a2 = algorithm2_counts(K, xd, P(best["theta"], best["degree"], "particle", K.MIXED))
+        roof = eval_roofline("k_eval<rotlet, mixed> (FP32x2 evaluator)", ROTLET_FLOPS_PER_INTERACTION,
+                             a2["near_pairs"] + a2["far_points"], best["near_exec"] + best["far_exec"],
+                             best["ms_evaluate"], measure_peaks(K, dev)["fp32_tflops"],
+                             "measured FP32 FMA micro-benchmark",
+                             traffic_per_launch("rotlet")
+                             if (best["theta"], best["degree"], best["mac"]) == SPHERE_BEST else None)
     line = {"metric": "regularized rotlet targets/sec on the unit sphere, N=1M (theta x n sweep)",
             "value": best["targets_per_s"] if best else None, "unit": "targets/s", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": best["ms"] if best else None,
@@ -883,8 +1071,7 @@ def run_sphere(args, ws, rank, local):
             "config": {"workload": "unit sphere surface, N = 1,000,000 (seed 3 + rank), torque "
                                    "weights N(0,1), regularized rotlet (u and w)",
                        "eps": SPHERE_EPS, "leaf_size": SPHERE_LEAF,
-                       "mac": best["mac"] if best else None,
-                       "target_batch": BATCH,
+                       "mac": best["mac"] if best else None, "target_batch": BATCH,
                        "value": "fastest mixed point (theta, n, MAC in {particle, all}) with E <= 1e-6",
                        "error": "rel. L2 of (u, w) vs FP64 direct sum on %d sampled targets"
                                 % N_SAMPLE,
@@ -895,6 +1082,7 @@ def run_sphere(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- paper workloads
 # The paper's own workloads (theta = 0.7, n = 7).  Example 1 (Sec. 8.1):
 # organisms in a cube of side 10, eps = l = 0.02 (Table CaseI_new) and eps = l in
 # 0.005..0.08 at N = 640K (Table CaseI_DiffEps), N0 = 2000, Stokeslet.  Example 2
@@ -930,21 +1118,17 @@ def run_paper(args, ws, rank, local):
                 continue
             p = K.Params(theta=0.7, degree=7, leaf_size=leaf, eps=eps, kernel=kernel,
                          precision=prec, mac=K.MAC_PARTICLE, target_batch=BATCH)
-            ms = []
-            for i in range(2 if prec == K.MIXED else 1):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+
+            def one():
                 t = K.kitc_build_tree(xd, p)
-                K.kitc_modified_weights(t, fd)
-                K.kitc_evaluate(t, xd, out)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                st = t.stats()
-                t.free()
-                ms.append(e0.elapsed_time(e1))
-            m = ms[-1]
-            res[pname] = {"ms": m, "targets_per_s": n / (m / 1e3),
+                try:
+                    K.kitc_modified_weights(t, fd)
+                    K.kitc_evaluate(t, xd, out)
+                    return t.stats()
+                finally:
+                    t.free()
+            ms, st = timed(stream, flush, one, 1, 1 if prec == K.MIXED else 0)
+            res[pname] = {"ms": ms[-1], "targets_per_s": n / (ms[-1] / 1e3),
                           "E": rel_l2(ref, out.cpu().numpy()[idx]),
                           "far_points": st["far_points"], "near_pairs": st["near_pairs"]}
         del xd, fd, out
