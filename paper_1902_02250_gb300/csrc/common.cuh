@@ -245,6 +245,10 @@ struct EvalArgs {
     const int64_t *roff;
     const double *chebt;
     double eps;
+    // set by evaluate_launch from eps: eps^2, eps^4 in FP64 and the FP32 kernel
+    // coefficients eps^2, eps^4, 1.5 eps^2, 3.75 eps^2, 3.75 eps^4, -0.75 eps^2
+    double e2d, e4d;
+    float ecf[6];
     double *out;                 // caller order, n x wout
     int *queue;                  // work counter, zero at launch
     int *err;                    // error flag (nonzero on a timed-out wait)

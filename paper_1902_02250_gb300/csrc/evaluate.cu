@@ -63,6 +63,9 @@ struct TileMeta {
     int np;          // far: grid points per dimension of the cluster (n_c + 1)
     uint64_t mask;   // targets of the batch that use this entry
     dvec4 lo, hi;    // far: the cluster's box (read ahead by the producer)
+    // far, FP32x2 path: cluster centre minus batch centre and half widths of
+    // the box, formed in FP64 by the producer and rounded once
+    float goff[3], ghw[3];
 };
 
 // ---------------------------------------------------------------------------
@@ -187,6 +190,14 @@ template <bool MIXED, int WIN> struct Rec {
 #endif
 constexpr int RPR = KITC_RPR, NPB = KITC_NPB;
 
+// FP32x2 path: the producer forms each far cluster's offset from the batch
+// centre and its half widths (FP64, rounded to FP32) once per entry, and the
+// consumers map the FP32 Chebyshev table with one FMA per grid coordinate
+// (KITC_FAR_PROD=0: every consumer warp maps the points in FP64).
+#ifndef KITC_FAR_PROD
+#define KITC_FAR_PROD 1
+#endif
+
 // FP32x2 rotlet: FP64 sums and third FP32 level in shared memory (they change
 // every 8 / 64 runs), which leaves the registers to the six-component run sums.
 #ifndef KITC_ROT_SACC
@@ -202,7 +213,9 @@ template <int K> struct Smem {
     // KITC_SMEM_ACC: the FP64 sums and the third FP32 level of the mixed path
     static constexpr bool SA = KITC_SMEM_ACC || (KITC_ROT_SACC && K == KITC_ROTLET);
     static constexpr size_t ACCS = SA ? (size_t)NCW * KITC_MAX_BATCH * WOUT * 12 : 0;
-    static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID + ACCS;
+    // FP32 Chebyshev table cos(k pi / n) [n][k] of the FP32x2 far field
+    static constexpr size_t CHEBF = (size_t)(KITC_MAX_DEGREE + 1) * (KITC_MAX_DEGREE + 1) * sizeof(float);
+    static constexpr size_t TOTAL = (size_t)STAGES * TILE + RED + META + BARS + GRID + ACCS + CHEBF;
 };
 
 // Weight components of a record as R values.
@@ -282,6 +295,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                                                                       SM::GRID) +
                                            (size_t)NCW * KITC_MAX_BATCH * WOUT) +
                  (size_t)warp * KITC_MAX_BATCH * WOUT;
+    float *chebf = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(gridc) + SM::GRID +
+                                             SM::ACCS);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
     const uint32_t rbw = smem_u32(bars + 2 * STAGES), rbr = smem_u32(bars + 2 * STAGES + 1);
     if (threadIdx.x == 0) {
@@ -292,6 +307,16 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
         mbar_init(rbw, NCW);
         mbar_init(rbr, NCW);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if constexpr (PAIR && KITC_FAR_PROD) {
+        constexpr int NC = KITC_MAX_DEGREE + 1;
+        for (int q = threadIdx.x; q < NC * NC; q += blockDim.x) {
+            const int n = q / NC, k = q % NC;  // row n: degree n (cos(k pi / n), k <= n)
+            double v = 0.0;
+            if (a.chebt) v = a.chebt[q];
+            else if (n == a.degree) v = a.cheb[k];
+            chebf[q] = (float)v;
+        }
     }
     __syncthreads();
     const int np0 = a.degree + 1;                                 // uniform degree
@@ -324,6 +349,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
         for (;;) {
             int b = atomicAdd(a.queue, 1);
             if (b >= a.nb) break;
+            dvec4 pcB = zero4;
+            if (PAIR && KITC_FAR_PROD && a.bctr && a.near_off) pcB = a.bctr[b];
             bool have = false, first = true;
             TileMeta pend{};
             const unsigned char *psrc = nullptr;
@@ -361,6 +388,14 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         int k2 = min(np, k1 + planes_max);
                         TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
                                    b, c, k1, k2, 0, np, mk, lo, hi};
+                        if (PAIR && KITC_FAR_PROD && k1 == 0) {
+                            m.goff[0] = (float)(0.5 * (lo.x + hi.x) - pcB.x);
+                            m.goff[1] = (float)(0.5 * (lo.y + hi.y) - pcB.y);
+                            m.goff[2] = (float)(0.5 * (lo.z + hi.z) - pcB.z);
+                            m.ghw[0] = (float)(0.5 * (hi.x - lo.x));
+                            m.ghw[1] = (float)(0.5 * (hi.y - lo.y));
+                            m.ghw[2] = (float)(0.5 * (hi.z - lo.z));
+                        }
                         ok = push(m, cb + (size_t)k1 * plane_bytes, (uint32_t)((k2 - k1) * plane_bytes));
                     }
                 }
@@ -412,7 +447,9 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     // Per target: a1 sums one run (a grid row of n+1 points or a block of <= 8
     // sources) and is added to a2 only if the target uses the entry; a2 holds
     // <= 8 runs, a3 <= 8 a2's, and every 64 runs a3 goes into the FP64 sum.
-    const R e2 = (R)(a.eps * a.eps), e4 = (R)(a.eps * a.eps * a.eps * a.eps);
+    // eps-derived constants come precomputed in the kernel parameters: rebuilt
+    // from eps inside the loops they would cost FP64 multiplies and conversions
+    const R e2 = MIXED ? (R)a.ecf[0] : (R)a.e2d, e4 = MIXED ? (R)a.ecf[1] : (R)a.e4d;
     R X[TPL][3], XL[TPL][3], XO[TPL][3];
     double acc[TPL][WOUT];
     R a1[TPL][WOUT], a2[TPL][WOUT], a3[TPL][WOUT];
@@ -424,12 +461,12 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     R *gs = reinterpret_cast<R *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
     float *gsf = reinterpret_cast<float *>(gridc + (size_t)warp * 3 * (KITC_MAX_DEGREE + 1));
     float2 Xh2[TPL][3], Xl2[TPL][3];
-    const float2 e22 = bc2((float)(a.eps * a.eps));
+    const float2 e22 = bc2(a.ecf[0]);
     // rotlet (times 8 pi): Q/2 = ri3 + 1.5 eps^2 ri5, D2/4 = ri5 (1.5 + 3.75 eps^2 ri2),
     // D1/4 = ri3 (-0.5 + ri2 (-0.75 eps^2 + 3.75 eps^4 ri2))
-    const float2 cq = bc2((float)(1.5 * a.eps * a.eps)), cd2a = bc2((float)(3.75 * a.eps * a.eps));
-    const float2 cd1a = bc2((float)(3.75 * a.eps * a.eps * a.eps * a.eps));
-    const float2 cd1b = bc2((float)(-0.75 * a.eps * a.eps));
+    const float2 cq = bc2(a.ecf[2]), cd2a = bc2(a.ecf[3]);
+    const float2 cd1a = bc2(a.ecf[4]);
+    const float2 cd1b = bc2(a.ecf[5]);
     const float2 c15 = bc2(1.5f), cm05 = bc2(-0.5f), m1 = bc2(-1.f);
     uint32_t it = 0, nbd = 0;
     int64_t bslot = 0;
@@ -596,6 +633,14 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 if (flags & F_FIRST_ENTRY) {
                     // grid points relative to the batch centre: x at gsf[0..], y at
                     // gsf[18..], -z at gsf[36..] (a missing odd point lies far away)
+                    if constexpr (KITC_FAR_PROD) {
+                        const float *cr = chebf + (np - 1) * (KITC_MAX_DEGREE + 1);
+                        for (int q = lane; q < 3 * np; q += 32) {
+                            const int l = q / np, k = q % np;
+                            const float v = fmaf(mr.ghw[l], cr[k], mr.goff[l]);
+                            gsf[18 * l + k] = l == 2 ? -v : v;
+                        }
+                    } else
                     for (int q = lane; q < 3 * np; q += 32) {
                         int l = q / np, k = q % np;
                         double lo_l = l == 0 ? mr.lo.x : (l == 1 ? mr.lo.y : mr.lo.z);
@@ -1120,8 +1165,18 @@ kitc_status evaluate_preload(size_t *lmem)
     return preload_k<KITC_TEST_POLY, false, false>(lmem);
 }
 
-kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s)
+kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a0, cudaStream_t s)
 {
+    EvalArgs a = a0;
+    const double e2 = a.eps * a.eps;
+    a.e2d = e2;
+    a.e4d = e2 * e2;
+    a.ecf[0] = (float)e2;
+    a.ecf[1] = (float)(e2 * e2);
+    a.ecf[2] = (float)(1.5 * e2);
+    a.ecf[3] = (float)(3.75 * e2);
+    a.ecf[4] = (float)(3.75 * e2 * e2);
+    a.ecf[5] = (float)(-0.75 * e2);
     switch (kernel) {
     case KITC_STOKESLET:
         return mixed ? launch_eps<KITC_STOKESLET, true>(a, s) : launch_eps<KITC_STOKESLET, false>(a, s);
