@@ -128,9 +128,15 @@ typedef struct {
 
 /* Sec. 6 tree build.  src_xyz: device, n_src x 3.  Copies the sources into
  * tree order inside the handle, so src_xyz may be reused once the stream has
- * passed this call.  Synchronizes `stream` once per tree level (the cluster
- * count of the next level is read back).  On success *out holds a new
- * handle; free it with kitc_free_tree. */
+ * passed this call.  The levels run on the device, each reading the cluster
+ * range the previous one wrote; the host queues them in rounds and
+ * synchronizes `stream` once per round to read the cluster count back.  One
+ * round covers the depth of a uniform tree with leaves of N0 plus four
+ * levels, so the usual trees take one synchronization; deeper trees (strongly
+ * clustered points, coincident points) take one per further round, and a tree
+ * with more clusters than the room first reserved (16 per N0 + 1 particles)
+ * is built again with twice the room.  On success *out holds a new handle;
+ * free it with kitc_free_tree. */
 kitc_status kitc_build_tree(const double *src_xyz, int64_t n_src, const kitc_params *p,
                             void *stream, kitc_tree *out);
 
@@ -150,8 +156,9 @@ kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream);
 
 /* Algorithm 2: u at n_tgt targets.  tgt_xyz: device, n_tgt x 3; out: device,
  * n_tgt x w_out, overwritten.  Builds the target order, the interaction
- * lists and runs the fused near/far evaluator.  Synchronizes `stream` once
- * per level of the target tree and once to size the lists.
+ * lists and runs the fused near/far evaluator.  Synchronizes `stream` for the
+ * target tree (as kitc_build_tree), once to size the lists and once to read
+ * the evaluator's error flag.
  * KITC_ERR_STATE if kitc_modified_weights was not called. */
 kitc_status kitc_evaluate(kitc_tree t, const double *tgt_xyz, int64_t n_tgt, double *out,
                           void *stream);

@@ -10,6 +10,13 @@
 // sqrt(2), midpoint, x >= mid) uses round-to-nearest operations with no
 // contraction, so any IEEE implementation of the same expressions takes the
 // same decisions.
+//
+// The level loop runs on the device: each level's kernels read the level's
+// cluster range from a small state block that the previous level wrote, so the
+// host queues several levels without waiting and reads the state back once
+// (once per round of levels; one round covers the trees of the usual inputs).
+// Cluster arrays are sized from a host bound; a tree that would exceed it sets
+// an overflow flag, and the build is repeated with a larger bound.
 #include <algorithm>
 
 #include "common.cuh"
@@ -24,6 +31,22 @@ struct SplitInfo {
     double mid[3];
     int mask;   // bit l set: axis l is bisected; 0: the cluster is a leaf
     int pad;
+};
+
+// Clusters [lb, lb + nl) of one level.
+struct LevelState {
+    int lb, nl;
+};
+
+// State of the device-side level loop.  Level l reads st[l & 1]; its
+// k_children writes st[(l + 1) & 1].  Slots, permutation and cluster ids of
+// the slots live in the A buffers while cur = 0 and in the B buffers while
+// cur = 1; a level that scatters sets flip, and the next level's k_split
+// applies it (after the scatter has read cur).
+struct BuildState {
+    LevelState st[2];
+    int nclus, depth, nleaves, overflow, cur, flip;
+    int level_start[KITC_MAX_LEVEL + 2];
 };
 
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
@@ -107,15 +130,21 @@ __global__ void k_root_final(int nsys, const int32_t *__restrict__ c0, const int
     parent[sys] = -1;
 }
 
-// Split decision of each cluster of the level [lb, lb + nl).
-__global__ void k_split(int lb, int nl, int leaf, const dvec4 *__restrict__ lo,
+// Split decision of each cluster of level lvl; clears the level's counts.
+__global__ void k_split(BuildState *bs, int lvl, int leaf, const dvec4 *__restrict__ lo,
                         const dvec4 *__restrict__ hi, const int32_t *__restrict__ begin,
                         const int32_t *__restrict__ end, const int32_t *__restrict__ level,
-                        SplitInfo *__restrict__ info)
+                        SplitInfo *__restrict__ info, int32_t *__restrict__ ccount)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && bs->flip) {  // the previous level scattered
+        bs->cur ^= 1;
+        bs->flip = 0;
+    }
+    const LevelState L = bs->st[lvl & 1];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nl) return;
-    int c = lb + i;
+    if (i >= L.nl) return;
+    int c = L.lb + i;
+    for (int k = 0; k < 8; ++k) ccount[i * 8 + k] = 0;
     SplitInfo s;
     s.mask = 0;
     s.pad = 0;
@@ -152,10 +181,18 @@ __device__ __forceinline__ int slot_key(int64_t p, int64_t n, int lb, int nl,
 }
 
 // Per (cluster, code) counts and per (code, block) counts of the level.
-__global__ void k_count(int64_t n, int lb, int nl, const double *__restrict__ xs,
-                        const int32_t *__restrict__ node, const SplitInfo *__restrict__ info,
-                        int32_t *__restrict__ ccount, int32_t *__restrict__ bcount, int nblk)
+__global__ void k_count(int64_t n, const BuildState *__restrict__ bs, int lvl,
+                        const double *__restrict__ xsA, const double *__restrict__ xsB,
+                        const int32_t *__restrict__ nodeA, const int32_t *__restrict__ nodeB,
+                        const SplitInfo *__restrict__ info, int32_t *__restrict__ ccount,
+                        int32_t *__restrict__ bcount, int nblk)
 {
+    const LevelState L = bs->st[lvl & 1];
+    if (L.nl == 0) return;
+    const int lb = L.lb, nl = L.nl;
+    const bool cur = bs->cur != 0;
+    const double *__restrict__ xs = cur ? xsB : xsA;
+    const int32_t *__restrict__ node = cur ? nodeB : nodeA;
     __shared__ int sb[8];
     __shared__ int sc[8];
     __shared__ int c0s;
@@ -226,13 +263,20 @@ __device__ void block_scan_strided(int32_t *a, int m, int stride, int *tot_out)
     __syncthreads();
 }
 
-// Scans of the level and creation of the children clusters.  Single block.
+// Scans of the level and creation of the children clusters, which become the
+// next level (at most cap clusters in all).  Single block.
 __global__ void __launch_bounds__(BT) k_children(
-    int lb, int nl, int nclus, const SplitInfo *__restrict__ info, int32_t *ccount,
+    BuildState *bs, int lvl, int cap, const SplitInfo *__restrict__ info, int32_t *ccount,
     int32_t *cprefix, int32_t *childoff, int32_t *childidx, int32_t *bcount, int nblk,
     int32_t *nchild_scan, dvec4 *lo, dvec4 *hi, int32_t *begin, int32_t *end,
-    int32_t *first_child, int32_t *n_child, int32_t *level, int32_t *parent, int32_t *out2)
+    int32_t *first_child, int32_t *n_child, int32_t *level, int32_t *parent)
 {
+    const LevelState L = bs->st[lvl & 1];
+    const int lb = L.lb, nl = L.nl, nclus = bs->nclus;
+    if (nl == 0) {
+        if (threadIdx.x == 0) bs->st[(lvl + 1) & 1] = LevelState{lb, 0};
+        return;
+    }
     // per code: exclusive scan of the block counts, and of the cluster counts
     for (int k = 0; k < 8; ++k) block_scan_strided(bcount + k * nblk, nblk, 1, nullptr);
     for (int i = threadIdx.x; i < nl * 8; i += blockDim.x) cprefix[i] = ccount[i];
@@ -253,6 +297,13 @@ __global__ void __launch_bounds__(BT) k_children(
     __shared__ int total, nsplit;
     if (threadIdx.x == 0) nsplit = 0;
     block_scan_strided(nchild_scan, nl, 1, &total);
+    if ((int64_t)nclus + total > (int64_t)cap) {  // no room: stop the build, the host retries
+        if (threadIdx.x == 0) {
+            bs->overflow = 1;
+            bs->st[(lvl + 1) & 1] = LevelState{nclus, 0};
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
         int c = lb + i;
         int m = info[i].mask;
@@ -285,20 +336,35 @@ __global__ void __launch_bounds__(BT) k_children(
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        out2[0] = total;
-        out2[1] = nsplit;
+        bs->st[(lvl + 1) & 1] = LevelState{nclus, total};
+        bs->nclus = nclus + total;
+        bs->nleaves += nl - nsplit;
+        bs->depth += 1;
+        if (total > 0) bs->level_start[bs->depth] = nclus;
+        bs->flip = total > 0;  // this level's scatter runs, then the next level flips cur
     }
 }
 
-// Stable scatter of the level's participating slots into their children.
+// Stable scatter of the level's participating slots into their children,
+// from the current buffers into the other ones.  Runs only when the level
+// created children.
 __global__ void __launch_bounds__(BT) k_scatter(
-    int64_t n, int lb, int nl, const double *__restrict__ xs, const int32_t *__restrict__ perm,
-    const int32_t *__restrict__ node, const SplitInfo *__restrict__ info,
+    int64_t n, const BuildState *__restrict__ bs, int lvl, double *xsA, double *xsB, int32_t *permA,
+    int32_t *permB, int32_t *nodeA, int32_t *nodeB, const SplitInfo *__restrict__ info,
     const int32_t *__restrict__ begin, const int32_t *__restrict__ cprefix,
     const int32_t *__restrict__ childoff, const int32_t *__restrict__ childidx,
-    const int32_t *__restrict__ bprefix, int nblk, double *__restrict__ xs2,
-    int32_t *__restrict__ perm2, int32_t *__restrict__ node2)
+    const int32_t *__restrict__ bprefix, int nblk)
 {
+    const LevelState L = bs->st[lvl & 1];
+    if (L.nl == 0 || !bs->flip) return;
+    const int lb = L.lb, nl = L.nl;
+    const bool cur = bs->cur != 0;
+    const double *__restrict__ xs = cur ? xsB : xsA;
+    const int32_t *__restrict__ perm = cur ? permB : permA;
+    const int32_t *__restrict__ node = cur ? nodeB : nodeA;
+    double *__restrict__ xs2 = cur ? xsA : xsB;
+    int32_t *__restrict__ perm2 = cur ? permA : permB;
+    int32_t *__restrict__ node2 = cur ? nodeA : nodeB;
     __shared__ int wcnt[BT / 32][8];
     __shared__ int run[8];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -363,18 +429,13 @@ __global__ void k_geometry(int m, const dvec4 *__restrict__ lo, const dvec4 *__r
                                   __double2float_rn(g.z - (double)hz), 0.f);
 }
 
-kitc_status grow_clusters(TreeDev &t, int need, cudaStream_t s)
+// Cluster arrays for cap clusters (contents not kept).
+kitc_status alloc_clusters(TreeDev &t, int cap, cudaStream_t s)
 {
-    if (need <= t.cap) return KITC_OK;
-    int cap = std::max(need, std::max(64, 2 * t.cap));
-    KITC_TRY(t.lo.reserve(sizeof(dvec4) * cap, s, true));
-    KITC_TRY(t.hi.reserve(sizeof(dvec4) * cap, s, true));
-    KITC_TRY(t.begin.reserve(sizeof(int32_t) * cap, s, true));
-    KITC_TRY(t.end.reserve(sizeof(int32_t) * cap, s, true));
-    KITC_TRY(t.first_child.reserve(sizeof(int32_t) * cap, s, true));
-    KITC_TRY(t.n_child.reserve(sizeof(int32_t) * cap, s, true));
-    KITC_TRY(t.level.reserve(sizeof(int32_t) * cap, s, true));
-    KITC_TRY(t.parent.reserve(sizeof(int32_t) * cap, s, true));
+    for (DevBuf *d : {&t.lo, &t.hi})
+        KITC_TRY(d->reserve(sizeof(dvec4) * cap, s));
+    for (DevBuf *d : {&t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
+        KITC_TRY(d->reserve(sizeof(int32_t) * cap, s));
     t.cap = cap;
     return KITC_OK;
 }
@@ -401,10 +462,12 @@ size_t TreeDev::bytes() const
     return b;
 }
 
-kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t,
-                       const int64_t *counts, int nsys)
+// One attempt at the build with room for cap clusters; *needed > cap on
+// return means the tree did not fit (nothing else of t is valid then).
+static kitc_status tree_build_cap(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t,
+                                  const int64_t *counts, int nsys, int cap, int64_t *needed)
 {
-    if (!counts) nsys = 1;
+    *needed = 0;
     t.release(s);
     t.n = n;
     t.leaf = leaf;
@@ -446,11 +509,26 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
     double *dpart = reinterpret_cast<double *>(offs.as<char>() + ((sizeof(int64_t) * h64.size() +
                                                                    sizeof(int32_t) * h32.size() + 15) / 16) * 16);
     KITC_TRY(bcount.reserve(sizeof(int32_t) * 8 * nblk, s));
-    KITC_TRY(grow_clusters(t, std::max(64, nsys), s));
+    KITC_TRY(alloc_clusters(t, cap, s));
+    // level scratch for the largest level: info | ccount | cprefix | childoff | childidx | nchild_scan
+    const int64_t max_nl = std::min<int64_t>(cap, n + nsys);
+    const size_t per = (size_t)max_nl * 8;
+    KITC_TRY(lvl.reserve(sizeof(SplitInfo) * max_nl + sizeof(int32_t) * (4 * per + max_nl + 2) +
+                         sizeof(BuildState) + 512, s));
+    char *q = lvl.as<char>();
+    BuildState *bs = reinterpret_cast<BuildState *>(q);
+    SplitInfo *info = reinterpret_cast<SplitInfo *>(q + ((sizeof(BuildState) + 255) / 256) * 256);
+    int32_t *ccount = reinterpret_cast<int32_t *>(info + max_nl);
+    int32_t *cprefix = ccount + per, *childoff = cprefix + per, *childidx = childoff + per;
+    int32_t *nchs = childidx + per;
     // every buffer the kernels below write must exist before any launch
-    for (const DevBuf *b : {&t.perm, &perm2, &t.xs, &xs2, &node, &node2, &offs, &bcount, &t.lo, &t.hi,
-                            &t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
+    for (const DevBuf *b : {&t.perm, &perm2, &t.xs, &xs2, &node, &node2, &offs, &bcount, &lvl, &t.lo,
+                            &t.hi, &t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
         if (!b->ptr) return KITC_ERR_OOM;
+    BuildState h0{};
+    h0.st[0] = LevelState{0, nsys};
+    h0.nclus = nsys;
+    KITC_CUDA(cudaMemcpyAsync(bs, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
     KITC_CUDA(cudaMemcpyAsync(d64, h64.data(), sizeof(int64_t) * h64.size(), cudaMemcpyHostToDevice, s));
     KITC_CUDA(cudaMemcpyAsync(d32, h32.data(), sizeof(int32_t) * h32.size(), cudaMemcpyHostToDevice, s));
     kitc_count_launch();
@@ -467,79 +545,92 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
                                                     t.n_child.as<int32_t>(), t.level.as<int32_t>(),
                                                     t.parent.as<int32_t>());
     KITC_CUDA(cudaGetLastError());
-    int32_t *h2 = nullptr;
-    KITC_TRY(host_readback_buffer(reinterpret_cast<void **>(&h2)));
-    int lb = 0, nl = nsys, nclus = nsys, depth = 0, nleaves = 0;
-    t.nsys = nsys;
-    t.sys_off = hoff;
-    t.level_start.assign(1, 0);
+    // Levels are queued in rounds: the depth of a roughly uniform tree plus a
+    // few levels of slack, then the state is read back once; a deeper tree
+    // takes further rounds.  Levels after the last one exit at once.
+    int round = 4;
+    for (int64_t m = std::max<int64_t>(1, n / std::max(1, nsys)); m > leaf; m = (m + 7) / 8) ++round;
+    BuildState hs{};
+    int lv = 0;
+    for (;;) {
+        const int lv_end = std::min(KITC_MAX_LEVEL + 1, lv + round);
+        for (; lv < lv_end; ++lv) {
+            int64_t cap_l = std::min<int64_t>(max_nl, nsys);
+            for (int k = 0; k < lv && cap_l < max_nl; ++k) cap_l = std::min<int64_t>(max_nl, 8 * cap_l);
+            kitc_count_launch();
+            k_split<<<(unsigned)((cap_l + 255) / 256), 256, 0, s>>>(
+                bs, lv, leaf, t.lo.as<dvec4>(), t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                t.end.as<int32_t>(), t.level.as<int32_t>(), info, ccount);
+            kitc_count_launch();
+            k_count<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
+                                        node.as<int32_t>(), node2.as<int32_t>(), info, ccount,
+                                        bcount.as<int32_t>(), nblk);
+            kitc_count_launch();
+            k_children<<<1, BT, 0, s>>>(bs, lv, cap, info, ccount, cprefix, childoff, childidx,
+                                        bcount.as<int32_t>(), nblk, nchs, t.lo.as<dvec4>(),
+                                        t.hi.as<dvec4>(), t.begin.as<int32_t>(), t.end.as<int32_t>(),
+                                        t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                                        t.level.as<int32_t>(), t.parent.as<int32_t>());
+            kitc_count_launch();
+            k_scatter<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
+                                          t.perm.as<int32_t>(), perm2.as<int32_t>(), node.as<int32_t>(),
+                                          node2.as<int32_t>(), info, t.begin.as<int32_t>(), cprefix,
+                                          childoff, childidx, bcount.as<int32_t>(), nblk);
+            KITC_CUDA(cudaGetLastError());
+        }
+        // the one read-back of the round (it also ends the life of the host
+        // arrays copied above)
+        KITC_CUDA(cudaMemcpyAsync(&hs, bs, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        KITC_CUDA(cudaStreamSynchronize(s));
+        if (hs.overflow || hs.st[lv & 1].nl == 0 || lv > KITC_MAX_LEVEL) break;
+    }
     kitc_status st = KITC_OK;
-    while (nl > 0) {
-        if ((st = grow_clusters(t, nclus + 8 * nl, s)) != KITC_OK) break;
-        size_t per = (size_t)nl * 8;
-        // level scratch: info | ccount | cprefix | childoff | childidx | nchild_scan | out2
-        size_t need = sizeof(SplitInfo) * nl + sizeof(int32_t) * (4 * per + nl + 2) + 256;
-        if ((st = lvl.reserve(need, s)) != KITC_OK) break;
-        char *q = lvl.as<char>();
-        SplitInfo *info = reinterpret_cast<SplitInfo *>(q);
-        int32_t *ccount = reinterpret_cast<int32_t *>(q + sizeof(SplitInfo) * nl);
-        int32_t *cprefix = ccount + per, *childoff = cprefix + per, *childidx = childoff + per;
-        int32_t *nchs = childidx + per, *out2 = nchs + nl;
-        if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * per, s) != cudaSuccess) {
-            st = KITC_ERR_CUDA;
-            break;
-        }
-        kitc_count_launch();
-        k_split<<<(nl + 255) / 256, 256, 0, s>>>(lb, nl, leaf, t.lo.as<dvec4>(),
-                                                t.hi.as<dvec4>(), t.begin.as<int32_t>(),
-                                                t.end.as<int32_t>(), t.level.as<int32_t>(), info);
-        kitc_count_launch();
-        k_count<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), node.as<int32_t>(), info, ccount,
-                                    bcount.as<int32_t>(), nblk);
-        kitc_count_launch();
-        k_children<<<1, BT, 0, s>>>(lb, nl, nclus, info, ccount, cprefix, childoff, childidx,
-                                    bcount.as<int32_t>(), nblk, nchs, t.lo.as<dvec4>(),
-                                    t.hi.as<dvec4>(), t.begin.as<int32_t>(),
-                                    t.end.as<int32_t>(), t.first_child.as<int32_t>(),
-                                    t.n_child.as<int32_t>(), t.level.as<int32_t>(),
-                                    t.parent.as<int32_t>(), out2);
-        kitc_count_launch();
-        k_scatter<<<nblk, BT, 0, s>>>(n, lb, nl, t.xs.as<double>(), t.perm.as<int32_t>(),
-                                      node.as<int32_t>(), info, t.begin.as<int32_t>(), cprefix,
-                                      childoff, childidx, bcount.as<int32_t>(), nblk,
-                                      xs2.as<double>(), perm2.as<int32_t>(), node2.as<int32_t>());
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h2, out2, 2 * sizeof(int32_t),
-                                                  cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            st = kitc_from_cuda(e);
-            break;
-        }
+    if (hs.overflow) {
+        *needed = 2 * (int64_t)cap;
+        st = KITC_OK;
+    } else if (hs.st[lv & 1].nl != 0) {
+        st = KITC_ERR_CUDA;  // cannot happen: a level past KITC_MAX_LEVEL splits nothing
+    }
+    for (DevBuf *b : {&node, &node2, &offs, &bcount, &lvl}) b->release(s);
+    if (st != KITC_OK || hs.overflow) {
+        perm2.release(s);
+        xs2.release(s);
+        return st;
+    }
+    if ((hs.cur ^ hs.flip) != 0) {  // the final order is in the B buffers
         std::swap(t.xs, xs2);
         std::swap(t.perm, perm2);
-        std::swap(node, node2);
-        int nch = h2[0], nsplit = h2[1];
-        nleaves += nl - nsplit;
-        depth++;
-        lb = nclus;
-        nclus += nch;
-        nl = nch;
-        if (nl > 0) t.level_start.push_back(lb);
     }
-    // the host offsets must outlive the copy above
-    cudaError_t se = cudaStreamSynchronize(s);
-    for (DevBuf *b : {&perm2, &xs2, &node, &node2, &offs, &bcount, &lvl}) b->release(s);
-    if (st == KITC_OK && se != cudaSuccess) st = kitc_from_cuda(se);
-    if (st != KITC_OK) return st;
-    t.nclus = nclus;
-    t.depth = depth;
-    t.nleaves = nleaves;
+    perm2.release(s);
+    xs2.release(s);
+    t.nclus = hs.nclus;
+    t.depth = hs.depth;
+    t.nleaves = hs.nleaves;
+    t.nsys = nsys;
+    t.sys_off = hoff;
+    t.level_start.assign(hs.level_start, hs.level_start + hs.depth);
     KITC_TRY(t.ctr.reserve(sizeof(dvec4) * t.cap, s));
     KITC_TRY(t.ctrf.reserve(2 * sizeof(float4) * t.cap, s));
     kitc_count_launch();
-    k_geometry<<<(nclus + 255) / 256, 256, 0, s>>>(nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+    k_geometry<<<(t.nclus + 255) / 256, 256, 0, s>>>(t.nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
                                                    t.ctr.as<dvec4>(), t.ctrf.as<float4>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
+}
+
+kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, TreeDev &t,
+                       const int64_t *counts, int nsys)
+{
+    if (!counts) nsys = 1;
+    // room for the clusters of a tree whose levels each split at most
+    // n / (N0 + 1) clusters into 8, over 16 levels' worth; a tree that does not
+    // fit is built again with twice the room
+    int64_t cap = (int64_t)nsys + 16 * ((n + leaf) / (leaf + 1)) + 64;
+    for (;;) {
+        if (cap > (int64_t)INT32_MAX / 2) return KITC_ERR_OOM;
+        int64_t needed = 0;
+        KITC_TRY(tree_build_cap(xyz, n, leaf, s, t, counts, nsys, (int)cap, &needed));
+        if (needed == 0) return KITC_OK;
+        cap = needed;
+    }
 }

@@ -56,6 +56,10 @@ TREE_CASES = {
     "one": lambda: (np.array([[0.25, -0.5, 1.0]]), 4),
     "root_leaf": lambda: (wl.uniform_cube(500, 34)[0], 500),
     "duplicates": lambda: (np.vstack([np.full((300, 3), 0.125), wl.uniform_cube(700, 35)[0]]), 50),
+    # ten groups of 200 coincident points, N0 = 100: ten chains down to the
+    # depth limit, more clusters than the first room the build reserves (the
+    # build is repeated with more room) and several rounds of levels
+    "chains": lambda: (np.repeat(wl.uniform_cube(10, 36)[0], 200, axis=0), 100),
 }
 
 
