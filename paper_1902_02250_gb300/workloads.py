@@ -74,14 +74,21 @@ def batched_systems(num, seed, nmin=1000, nmax=200000, side=(0.5, 2.0), origin=1
     return out
 
 
-def organisms(n_pairs, seed, length=10.0, ell=0.02):
-    """Example 1 shape: n_pairs organisms with uniform centres in [0, length]^3
-    and uniform directions on the sphere; each is two particles ell apart
-    carrying unit forces of opposite sign along the organism axis."""
+def organisms(n_pairs, seed, length=10.0, ell=0.02, orientation="random"):
+    """Example 1 shape: n_pairs organisms with uniform centres in [0, length]^3;
+    each is two particles ell apart carrying unit forces of opposite sign along
+    the organism axis.  The paper does not state the orientations:
+    "random" draws each axis uniformly on the sphere, "aligned" gives every
+    organism the axis z (the draws of the centres are the same)."""
     g = rng(seed)
     c = g.uniform(0.0, length, size=(n_pairs, 3))
     d = g.standard_normal(size=(n_pairs, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
+    if orientation == "aligned":
+        d = np.zeros((n_pairs, 3))
+        d[:, 2] = 1.0
+    elif orientation != "random":
+        raise ValueError("orientation must be 'random' or 'aligned'")
     x = np.empty((2 * n_pairs, 3))
     f = np.empty((2 * n_pairs, 3))
     x[0::2] = c + 0.5 * ell * d

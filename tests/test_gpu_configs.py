@@ -19,7 +19,7 @@
   Example 1 (organisms, N = 640,000, eps = 0.02, theta = 0.7, n = 7, N0 = 2000,
   per-target MAC) and Example 2 (helical rods, N = 966,400, Stokeslet +
   rotlet, eps = 0.3, theta = 0.7, n = 7, N0 = 1000), sampled targets against the
-  oracle's Algorithm 2.
+  oracle's Algorithm 2; and Example 1 at N = 5.12M in FP64.
 Every mixed comparison also bounds the error of every single target
 (mixed_parity.check_mixed).
 """
@@ -134,6 +134,23 @@ def _paper_case(K, orc, x, f, kernel, eps, leaf, what):
 def test_config_paper_example1_640k(K, orc):
     x, f = wl.organisms(320_000, 31)
     _paper_case(K, orc, x, f, orc.STOKESLET, 0.02, 2000, "Example 1 N=640K")
+
+
+def test_config_paper_example1_5m_fp64(K, orc):
+    """Example 1 at N = 5.12M (the size where our error departs most from the
+    paper's table): the FP64 treecode against the oracle's Algorithm 2 on
+    sampled targets."""
+    x, f = wl.organisms(2_560_000, 31)
+    xd, fd = dev(x), dev(f)
+    sel = wl.sample_indices(len(x), 200, 2028)
+    o = orc.Tree(x, 2000)
+    ref, _ = o.treecode(f, o.modified_weights(f, 7), 7, orc.STOKESLET, 0.02, 0.7, x[sel])
+    p = K.Params(theta=0.7, degree=7, leaf_size=2000, eps=0.02, precision=K.FP64,
+                 mac=K.MAC_PARTICLE, target_batch=64)
+    out, st = K.treecode(xd, fd, p)
+    e = orc.rel_l2(ref, out.cpu().numpy()[sel])
+    print("Example 1 N=5.12M FP64 rel_l2 vs oracle on 200 samples: %.3e" % e)
+    assert e <= FP64_TOL
 
 
 def test_config_paper_example2_rods(K, orc):
