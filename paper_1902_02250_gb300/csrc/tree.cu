@@ -39,7 +39,7 @@ struct LevelState {
 };
 
 // State of the device-side level loop.  Level l reads st[l & 1]; its
-// k_children writes st[(l + 1) & 1].  Slots, permutation and cluster ids of
+// k_children_scan writes st[(l + 1) & 1].  Slots, permutation and cluster ids of
 // the slots live in the A buffers while cur = 0 and in the B buffers while
 // cur = 1; a level that scatters sets flip, and the next level's k_split
 // applies it (after the scatter has read cur).
@@ -263,13 +263,75 @@ __device__ void block_scan_strided(int32_t *a, int m, int stride, int *tot_out)
     __syncthreads();
 }
 
-// Scans of the level and creation of the children clusters, which become the
-// next level (at most cap clusters in all).  Single block.
-__global__ void __launch_bounds__(BT) k_children(
-    BuildState *bs, int lvl, int cap, const SplitInfo *__restrict__ info, int32_t *ccount,
-    int32_t *cprefix, int32_t *childoff, int32_t *childidx, int32_t *bcount, int nblk,
-    int32_t *nchild_scan, dvec4 *lo, dvec4 *hi, int32_t *begin, int32_t *end,
-    int32_t *first_child, int32_t *n_child, int32_t *level, int32_t *parent)
+// Children of the level's clusters, in three kernels (a level can hold
+// hundreds of thousands of clusters): a block-local pass over the clusters, one
+// block that scans the block totals and advances the level state, and a wide
+// pass that applies the block offsets and creates the children.
+constexpr int CB = 256;  // clusters per block of the children kernels
+constexpr int NT = 10;   // block totals: 8 code counts, children, splitting clusters
+
+// Per cluster i of the level: the offset of each of its 8 codes inside it
+// (childoff), and block-local exclusive prefixes over the clusters of the code
+// counts (cprefix) and of the children counts (nchs); block totals to btot.
+__global__ void __launch_bounds__(CB) k_children_local(
+    const BuildState *__restrict__ bs, int lvl, const SplitInfo *__restrict__ info,
+    const int32_t *__restrict__ ccount, int32_t *__restrict__ cprefix, int32_t *__restrict__ childoff,
+    int32_t *__restrict__ nchs, int32_t *__restrict__ btot)
+{
+    const int nl = bs->st[lvl & 1].nl;
+    if ((int64_t)blockIdx.x * CB >= nl) return;
+    const int i = blockIdx.x * CB + threadIdx.x;
+    int v[NT];
+    if (i < nl) {
+        const bool split = info[i].mask != 0;
+        int off = 0, nch = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int c = ccount[i * 8 + k];
+            childoff[i * 8 + k] = off;
+            off += c;
+            v[k] = c;
+            if (split && c > 0) nch++;
+        }
+        v[8] = nch;
+        v[9] = nch > 0;
+    } else {
+        for (int k = 0; k < NT; ++k) v[k] = 0;
+    }
+    __shared__ int ws[CB / 32][NT];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl[NT];
+    for (int k = 0; k < NT; ++k) {
+        int x = v[k];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        incl[k] = x;
+        if (lane == 31) ws[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NT) {
+        int run = 0;
+        for (int q = 0; q < CB / 32; ++q) {
+            const int t = ws[q][threadIdx.x];
+            ws[q][threadIdx.x] = run;
+            run += t;
+        }
+        btot[(int64_t)blockIdx.x * NT + threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (i < nl) {
+        for (int k = 0; k < 8; ++k) cprefix[i * 8 + k] = ws[w][k] + incl[k] - v[k];
+        nchs[i] = ws[w][8] + incl[8] - v[8];
+    }
+}
+
+// Single block: exclusive scans of the per-block code counts of the slots
+// (bcount) and of the cluster-block totals; then the capacity check and the
+// next level's state (the new level holds the children, at most cap clusters
+// in all).
+__global__ void __launch_bounds__(BT) k_children_scan(BuildState *bs, int lvl, int cap,
+                                                      int32_t *bcount, int nblk, int32_t *btot)
 {
     const LevelState L = bs->st[lvl & 1];
     const int lb = L.lb, nl = L.nl, nclus = bs->nclus;
@@ -277,72 +339,70 @@ __global__ void __launch_bounds__(BT) k_children(
         if (threadIdx.x == 0) bs->st[(lvl + 1) & 1] = LevelState{lb, 0};
         return;
     }
-    // per code: exclusive scan of the block counts, and of the cluster counts
     for (int k = 0; k < 8; ++k) block_scan_strided(bcount + k * nblk, nblk, 1, nullptr);
-    for (int i = threadIdx.x; i < nl * 8; i += blockDim.x) cprefix[i] = ccount[i];
+    __shared__ int tot[NT];
+    const int nb = (nl + CB - 1) / CB;
+    for (int k = 0; k < NT; ++k) block_scan_strided(btot + k, nb, NT, &tot[k]);
     __syncthreads();
-    for (int k = 0; k < 8; ++k) block_scan_strided(cprefix + k, nl, 8, nullptr);
-    // children per cluster and offsets of each code inside the cluster
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-        int nch = 0, off = 0;
-        for (int k = 0; k < 8; ++k) {
-            int v = ccount[i * 8 + k];
-            childoff[i * 8 + k] = off;
-            off += v;
-            if (info[i].mask != 0 && v > 0) nch++;
-        }
-        nchild_scan[i] = nch;
-    }
-    __syncthreads();
-    __shared__ int total, nsplit;
-    if (threadIdx.x == 0) nsplit = 0;
-    block_scan_strided(nchild_scan, nl, 1, &total);
+    if (threadIdx.x != 0) return;
+    const int total = tot[8], nsplit = tot[9];
     if ((int64_t)nclus + total > (int64_t)cap) {  // no room: stop the build, the host retries
-        if (threadIdx.x == 0) {
-            bs->overflow = 1;
-            bs->st[(lvl + 1) & 1] = LevelState{nclus, 0};
-        }
+        bs->overflow = 1;
+        bs->st[(lvl + 1) & 1] = LevelState{nclus, 0};
         return;
     }
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-        int c = lb + i;
-        int m = info[i].mask;
-        int fc = nclus + nchild_scan[i];
-        int j = 0;
-        for (int k = 0; k < 8; ++k) {
-            int v = ccount[i * 8 + k];
-            childidx[i * 8 + k] = -1;
-            if (m == 0 || v == 0) continue;
-            int id = fc + j++;
-            childidx[i * 8 + k] = id;
-            double l[3] = {lo[c].x, lo[c].y, lo[c].z}, h[3] = {hi[c].x, hi[c].y, hi[c].z};
-            for (int a = 0; a < 3; ++a)
-                if ((m >> a) & 1) {
-                    if ((k >> a) & 1) l[a] = info[i].mid[a];
-                    else h[a] = info[i].mid[a];
-                }
-            lo[id] = make_dvec4(l[0], l[1], l[2], 0.0);
-            hi[id] = make_dvec4(h[0], h[1], h[2], 0.0);
-            begin[id] = begin[c] + childoff[i * 8 + k];
-            end[id] = begin[id] + v;
-            first_child[id] = -1;
-            n_child[id] = 0;
-            level[id] = level[c] + 1;
-            parent[id] = c;
-        }
-        first_child[c] = j > 0 ? fc : -1;
-        n_child[c] = j;
-        if (j > 0) atomicAdd(&nsplit, 1);
+    bs->st[(lvl + 1) & 1] = LevelState{nclus, total};
+    bs->nclus = nclus + total;
+    bs->nleaves += nl - nsplit;
+    bs->depth += 1;
+    if (total > 0) bs->level_start[bs->depth] = nclus;
+    bs->flip = total > 0;  // this level's scatter runs, then the next level flips cur
+}
+
+// Block offsets applied to the prefixes; children created: boxes (geometric
+// halves of the parent), slot ranges, links.
+__global__ void __launch_bounds__(CB) k_children_make(
+    const BuildState *__restrict__ bs, int lvl, const SplitInfo *__restrict__ info,
+    const int32_t *__restrict__ ccount, int32_t *__restrict__ cprefix,
+    const int32_t *__restrict__ childoff, int32_t *__restrict__ childidx,
+    const int32_t *__restrict__ nchs, const int32_t *__restrict__ btot, dvec4 *lo, dvec4 *hi,
+    int32_t *begin, int32_t *end, int32_t *first_child, int32_t *n_child, int32_t *level,
+    int32_t *parent)
+{
+    const LevelState L = bs->st[lvl & 1];
+    const int lb = L.lb, nl = L.nl;
+    if (nl == 0 || bs->overflow) return;
+    const int i = blockIdx.x * CB + threadIdx.x;
+    if (i >= nl) return;
+    const int32_t *bt = btot + (int64_t)blockIdx.x * NT;  // exclusive over the blocks
+    for (int k = 0; k < 8; ++k) cprefix[i * 8 + k] += bt[k];
+    const int c = lb + i;
+    const int m = info[i].mask;
+    const int fc = bs->st[(lvl + 1) & 1].lb + bt[8] + nchs[i];
+    int j = 0;
+    for (int k = 0; k < 8; ++k) {
+        const int v = ccount[i * 8 + k];
+        childidx[i * 8 + k] = -1;
+        if (m == 0 || v == 0) continue;
+        const int id = fc + j++;
+        childidx[i * 8 + k] = id;
+        double l[3] = {lo[c].x, lo[c].y, lo[c].z}, h[3] = {hi[c].x, hi[c].y, hi[c].z};
+        for (int a = 0; a < 3; ++a)
+            if ((m >> a) & 1) {
+                if ((k >> a) & 1) l[a] = info[i].mid[a];
+                else h[a] = info[i].mid[a];
+            }
+        lo[id] = make_dvec4(l[0], l[1], l[2], 0.0);
+        hi[id] = make_dvec4(h[0], h[1], h[2], 0.0);
+        begin[id] = begin[c] + childoff[i * 8 + k];
+        end[id] = begin[id] + v;
+        first_child[id] = -1;
+        n_child[id] = 0;
+        level[id] = level[c] + 1;
+        parent[id] = c;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        bs->st[(lvl + 1) & 1] = LevelState{nclus, total};
-        bs->nclus = nclus + total;
-        bs->nleaves += nl - nsplit;
-        bs->depth += 1;
-        if (total > 0) bs->level_start[bs->depth] = nclus;
-        bs->flip = total > 0;  // this level's scatter runs, then the next level flips cur
-    }
+    first_child[c] = j > 0 ? fc : -1;
+    n_child[c] = j;
 }
 
 // Stable scatter of the level's participating slots into their children,
@@ -513,14 +573,15 @@ static kitc_status tree_build_cap(const double *xyz, int64_t n, int leaf, cudaSt
     // level scratch for the largest level: info | ccount | cprefix | childoff | childidx | nchild_scan
     const int64_t max_nl = std::min<int64_t>(cap, n + nsys);
     const size_t per = (size_t)max_nl * 8;
-    KITC_TRY(lvl.reserve(sizeof(SplitInfo) * max_nl + sizeof(int32_t) * (4 * per + max_nl + 2) +
+    const size_t nbt = (size_t)((max_nl + CB - 1) / CB) * NT;  // block totals of the children kernels
+    KITC_TRY(lvl.reserve(sizeof(SplitInfo) * max_nl + sizeof(int32_t) * (4 * per + max_nl + nbt + 2) +
                          sizeof(BuildState) + 512, s));
     char *q = lvl.as<char>();
     BuildState *bs = reinterpret_cast<BuildState *>(q);
     SplitInfo *info = reinterpret_cast<SplitInfo *>(q + ((sizeof(BuildState) + 255) / 256) * 256);
     int32_t *ccount = reinterpret_cast<int32_t *>(info + max_nl);
     int32_t *cprefix = ccount + per, *childoff = cprefix + per, *childidx = childoff + per;
-    int32_t *nchs = childidx + per;
+    int32_t *nchs = childidx + per, *btot = nchs + max_nl;
     // every buffer the kernels below write must exist before any launch
     for (const DevBuf *b : {&t.perm, &perm2, &t.xs, &xs2, &node, &node2, &offs, &bcount, &lvl, &t.lo,
                             &t.hi, &t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
@@ -565,12 +626,17 @@ static kitc_status tree_build_cap(const double *xyz, int64_t n, int leaf, cudaSt
             k_count<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
                                         node.as<int32_t>(), node2.as<int32_t>(), info, ccount,
                                         bcount.as<int32_t>(), nblk);
+            const unsigned gc = (unsigned)((cap_l + CB - 1) / CB);
             kitc_count_launch();
-            k_children<<<1, BT, 0, s>>>(bs, lv, cap, info, ccount, cprefix, childoff, childidx,
-                                        bcount.as<int32_t>(), nblk, nchs, t.lo.as<dvec4>(),
-                                        t.hi.as<dvec4>(), t.begin.as<int32_t>(), t.end.as<int32_t>(),
-                                        t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
-                                        t.level.as<int32_t>(), t.parent.as<int32_t>());
+            k_children_local<<<gc, CB, 0, s>>>(bs, lv, info, ccount, cprefix, childoff, nchs, btot);
+            kitc_count_launch();
+            k_children_scan<<<1, BT, 0, s>>>(bs, lv, cap, bcount.as<int32_t>(), nblk, btot);
+            kitc_count_launch();
+            k_children_make<<<gc, CB, 0, s>>>(bs, lv, info, ccount, cprefix, childoff, childidx, nchs,
+                                              btot, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                              t.begin.as<int32_t>(), t.end.as<int32_t>(),
+                                              t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                                              t.level.as<int32_t>(), t.parent.as<int32_t>());
             kitc_count_launch();
             k_scatter<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
                                           t.perm.as<int32_t>(), perm2.as<int32_t>(), node.as<int32_t>(),
