@@ -3,10 +3,11 @@
 * N = 10,000 uniform in [-1,1]^3 (seed 1), f ~ U[-1,1]^3, Stokeslet, eps = 0.01,
   theta = 0.7, n = 4, N0 = 500: the GPU treecode (FP64 and mixed) against the
   oracle's Algorithm 2, and both against the full FP64 direct sum (10^8 pairs).
-* N = 1,000,000 uniform (seed 2), eps = 1e-3, the bench point (batch MAC,
-  theta = 0.7, n = 9, N0 = 4000) in the launch configuration the bench times:
-  sampled targets against the oracle's batch-MAC treecode computed one by one,
-  and the relative L2 error against the FP64 direct sum within 1e-6.
+* N = 1,000,000 uniform (seed 2), eps = 1e-3, the bench point (all-targets
+  MAC, theta = 0.68, n = 9, N0 = 4000) in the launch configuration the bench
+  times: sampled targets against the oracle's treecode with the same MAC rule
+  computed one by one, and the relative L2 error against the FP64 direct sum
+  within 1e-6.
 * N = 1,000,000 on the unit sphere (seed 3), torques N(0,1), rotlet, eps = 0.005:
   the sphere sweep's fastest point with E <= 1e-6 (all-targets MAC, theta = 0.7,
   n = 6, N0 = 2000) and the per-target MAC at theta = 0.5, n = 4, each on the
@@ -69,21 +70,26 @@ def test_config_n10k(K, orc):
 
 
 def test_config_bench_point_1m(K, orc):
+    """The mixed treecode where the bench times it, against the oracle's
+    treecode with the same MAC rule on sampled targets (exact counts)."""
     import torch
-    x, f = wl.uniform_cube(1_000_000, 2)
+    import bench
+    x, f = wl.uniform_cube(bench.N, bench.SEED)
     xd, fd = dev(x), dev(f)
-    p = K.Params(theta=0.7, degree=9, leaf_size=4000, eps=1e-3, precision=K.MIXED,
-                 mac=K.MAC_BATCH, target_batch=64)
+    mac = bench.MAC_IDS[bench.MAC]
+    p = K.Params(theta=bench.THETA, degree=bench.DEGREE, leaf_size=bench.LEAF, eps=bench.EPS,
+                 precision=K.MIXED, mac=mac, target_batch=bench.BATCH)
     out, st = K.treecode(xd, fd, p)
     got = out.cpu().numpy()
     sel = wl.sample_indices(len(x), 300, 2024)
-    o = orc.Tree(x, 4000)
-    ref = o.treecode_batch(f, o.modified_weights(f, 9), 9, orc.STOKESLET, 1e-3, 0.7, x, 64, 64,
-                           select=sel)
+    o = orc.Tree(x, bench.LEAF)
+    ref = o.treecode_batch(f, o.modified_weights(f, bench.DEGREE), bench.DEGREE, orc.STOKESLET,
+                           bench.EPS, bench.THETA, x, bench.BATCH, bench.BATCH, select=sel,
+                           all_targets=(mac == K.MAC_ALL))
     check_mixed(ref["out"][sel], got[sel], "bench point N=10^6")
     assert st["far_points"] == ref["counts"][1] and st["near_pairs"] == ref["counts"][0]
     idx = torch.from_numpy(wl.sample_indices(len(x), 2000, 102)).cuda()
-    d = K.kitc_direct(xd[idx].contiguous(), xd, fd, K.Params(eps=1e-3, precision=K.FP64)).cpu().numpy()
+    d = K.kitc_direct(xd[idx].contiguous(), xd, fd, K.Params(eps=bench.EPS, precision=K.FP64)).cpu().numpy()
     e = orc.rel_l2(d, got[idx.cpu().numpy()])
     print("bench point E vs direct on 2000 samples: %.3e" % e)
     assert e <= 1e-6
