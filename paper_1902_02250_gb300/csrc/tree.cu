@@ -18,6 +18,7 @@
 // Cluster arrays are sized from a host bound; a tree that would exceed it sets
 // an overflow flag, and the build is repeated with a larger bound.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 
@@ -52,6 +53,20 @@ struct BuildState {
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
+// Finite doubles as 64-bit integers of the same order (negative values have
+// their magnitude bits flipped; -0 becomes +0), so that the root box's minima
+// and maxima run on the integer ALU instead of the FP64 pipe.
+__device__ __forceinline__ long long order_key(double v)
+{
+    long long k = __double_as_longlong(v);
+    if (k == (long long)0x8000000000000000ull) return 0;
+    return k < 0 ? k ^ 0x7fffffffffffffffll : k;
+}
+__device__ __forceinline__ double key_value(long long k)
+{
+    return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffll : k);
+}
+
 // Gathers the caller's n x 3 coordinates into SoA and sets the identity order.
 __global__ void k_init(const double *__restrict__ xyz, int64_t n, double *__restrict__ xs,
                        int32_t *__restrict__ perm)
@@ -69,29 +84,29 @@ __global__ void k_init(const double *__restrict__ xyz, int64_t n, double *__rest
 // Bounding box of one chunk of one system's slots (chunk c covers
 // [cb[c], ce[c]) of system cs[c]); also marks those slots as belonging to the
 // system's root.
-__global__ void __launch_bounds__(BT) k_root_partial(const int32_t *__restrict__ cs,
+__global__ void __launch_bounds__(BT, 2) k_root_partial(const int32_t *__restrict__ cs,
                                                      const int64_t *__restrict__ cb,
                                                      const int64_t *__restrict__ ce, int64_t n,
                                                      const double *__restrict__ xs,
                                                      int32_t *__restrict__ node,
                                                      double *__restrict__ part)
 {
-    __shared__ double red[6][BT / 32];
+    __shared__ long long red[6][BT / 32];
     const int c = blockIdx.x, sys = cs[c];
-    double l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+    long long l[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, h[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     for (int64_t i = cb[c] + threadIdx.x; i < ce[c]; i += BT) {
         node[i] = sys;
         for (int a = 0; a < 3; ++a) {
-            double v = xs[a * n + i];
-            l[a] = dmin(l[a], v);
-            h[a] = dmax(h[a], v);
+            const long long v = order_key(xs[a * n + i]);
+            l[a] = min(l[a], v);
+            h[a] = max(h[a], v);
         }
     }
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
         for (int o = 16; o > 0; o >>= 1) {
-            l[a] = dmin(l[a], __shfl_xor_sync(0xffffffffu, l[a], o));
-            h[a] = dmax(h[a], __shfl_xor_sync(0xffffffffu, h[a], o));
+            l[a] = min(l[a], __shfl_xor_sync(0xffffffffu, l[a], o));
+            h[a] = max(h[a], __shfl_xor_sync(0xffffffffu, h[a], o));
         }
         if (lane == 0) {
             red[a][w] = l[a];
@@ -101,9 +116,9 @@ __global__ void __launch_bounds__(BT) k_root_partial(const int32_t *__restrict__
     __syncthreads();
     if (threadIdx.x < 6) {
         int q = threadIdx.x;
-        double v = red[q][0];
-        for (int k = 1; k < BT / 32; ++k) v = q < 3 ? dmin(v, red[q][k]) : dmax(v, red[q][k]);
-        part[6 * c + q] = v;
+        long long v = red[q][0];
+        for (int k = 1; k < BT / 32; ++k) v = q < 3 ? min(v, red[q][k]) : max(v, red[q][k]);
+        part[6 * c + q] = key_value(v);
     }
 }
 
@@ -408,7 +423,7 @@ __global__ void __launch_bounds__(CB) k_children_make(
 // Stable scatter of the level's participating slots into their children,
 // from the current buffers into the other ones.  Runs only when the level
 // created children.
-__global__ void __launch_bounds__(BT) k_scatter(
+__global__ void __launch_bounds__(BT, 2) k_scatter(
     int64_t n, const BuildState *__restrict__ bs, int lvl, double *xsA, double *xsB, int32_t *permA,
     int32_t *permB, int32_t *nodeA, int32_t *nodeB, const SplitInfo *__restrict__ info,
     const int32_t *__restrict__ begin, const int32_t *__restrict__ cprefix,
@@ -425,8 +440,13 @@ __global__ void __launch_bounds__(BT) k_scatter(
     double *__restrict__ xs2 = cur ? xsA : xsB;
     int32_t *__restrict__ perm2 = cur ? permA : permB;
     int32_t *__restrict__ node2 = cur ? nodeA : nodeB;
-    __shared__ int wcnt[BT / 32][8];
-    __shared__ int run[8];
+    // Each round of BT slots is staged in shared memory in the order of its
+    // destinations (by code, then slot), so that consecutive threads write
+    // consecutive addresses of the children's ranges.
+    __shared__ int wcnt[BT / 32][9];
+    __shared__ int run[8], rbase[10];
+    __shared__ double sx[3][BT];
+    __shared__ int32_t sperm[BT], snode[BT], sdst[BT];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x < 8) run[threadIdx.x] = 0;
     __syncthreads();
@@ -435,35 +455,55 @@ __global__ void __launch_bounds__(BT) k_scatter(
         int64_t p = base + r * BT + threadIdx.x;
         int c = -1, k = 8;
         if (p < n) k = slot_key(p, n, lb, nl, xs, node, info, &c);
-        unsigned grp = __match_any_sync(0xffffffffu, k);
+        const int kk = p < n ? k : 9;  // 0..7 split codes, 8 slots that stay, 9 past the end
+        unsigned grp = __match_any_sync(0xffffffffu, kk);
         int rank = __popc(grp & ((1u << lane) - 1u));
-        if (lane < 8) wcnt[w][lane] = 0;
+        if (lane < 9) wcnt[w][lane] = 0;
         __syncwarp();
-        if (k < 8 && rank == 0) wcnt[w][k] = __popc(grp);
+        if (kk < 9 && rank == 0) wcnt[w][kk] = __popc(grp);
         __syncthreads();
-        if (threadIdx.x < 8) {  // exclusive prefix over warps, per code
-            int s = run[threadIdx.x];
+        if (threadIdx.x < 9) {  // exclusive prefix over warps, per code (and per "stays")
+            int t = 0;
             for (int q = 0; q < BT / 32; ++q) {
                 int v = wcnt[q][threadIdx.x];
-                wcnt[q][threadIdx.x] = s;
-                s += v;
+                wcnt[q][threadIdx.x] = t;
+                t += v;
             }
-            run[threadIdx.x] = s;
+            rbase[threadIdx.x] = t;  // round totals, turned into offsets below
         }
         __syncthreads();
-        if (p < n) {
-            if (k < 8) {
-                int g = bprefix[k * nblk + blockIdx.x] + wcnt[w][k] + rank;
-                int64_t np_ = (int64_t)begin[lb + c] + childoff[c * 8 + k] + g - cprefix[c * 8 + k];
-                perm2[np_] = perm[p];
-                node2[np_] = childidx[c * 8 + k];
-                for (int a = 0; a < 3; ++a) xs2[a * n + np_] = xs[a * n + p];
-            } else {
-                perm2[p] = perm[p];
-                node2[p] = node[p];
-                for (int a = 0; a < 3; ++a) xs2[a * n + p] = xs[a * n + p];
+        if (threadIdx.x == 0) {  // offsets of the codes in the round's staged order
+            int t = 0;
+            for (int q = 0; q < 9; ++q) {
+                int v = rbase[q];
+                rbase[q] = t;
+                t += v;
             }
+            rbase[9] = t;  // staged slots of the round
         }
+        __syncthreads();
+        if (kk < 9) {
+            int64_t dst;
+            if (k < 8) {
+                int g = bprefix[k * nblk + blockIdx.x] + run[k] + wcnt[w][k] + rank;
+                dst = (int64_t)begin[lb + c] + childoff[c * 8 + k] + g - cprefix[c * 8 + k];
+            } else {
+                dst = p;
+            }
+            const int pos = rbase[kk] + wcnt[w][kk] + rank;
+            for (int a = 0; a < 3; ++a) sx[a][pos] = xs[a * n + p];
+            sperm[pos] = perm[p];
+            snode[pos] = k < 8 ? childidx[c * 8 + k] : node[p];
+            sdst[pos] = (int32_t)dst;
+        }
+        __syncthreads();
+        if (threadIdx.x < rbase[9]) {
+            const int64_t d = sdst[threadIdx.x];
+            for (int a = 0; a < 3; ++a) xs2[a * n + d] = sx[a][threadIdx.x];
+            perm2[d] = sperm[threadIdx.x];
+            node2[d] = snode[threadIdx.x];
+        }
+        if (threadIdx.x < 8) run[threadIdx.x] += rbase[threadIdx.x + 1] - rbase[threadIdx.x];
         __syncthreads();
     }
 }
