@@ -388,7 +388,7 @@ def weights_roofline(st, n, win, ms, peaks, split):
     flops = st["n_sources"] * per_src + upward
     achieved = flops / (ms / 1e3) / 1e12
     peak = peaks["fp32_tflops"] if split else peaks["fp64_tflops"]
-    return {"kernel": "k_weights_chunk + k_weights_reduce + k_upward (+ record packing)",
+    return {"kernel": "k_weights_chunk + k_weights_reduce + k_upward_child/_sum (+ record packing)",
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "peak_source": ("measured FP32 FMA rate: the products run in split FP32 arithmetic "

@@ -40,6 +40,12 @@ constexpr size_t UP_SMEM_MAX = 200 * 1024;
 constexpr size_t CHUNK_SMEM_MAX = 96 * 1024;  // dynamic shared memory of k_weights_chunk
 kitc_status allow_up_smem();  // shared-memory attribute of the upward kernels
 
+// Particles staged per round of k_weights_chunk (at most; fewer when the
+// round's shared memory would exceed CHUNK_SMEM_MAX).
+#ifndef KITC_WEIGHTS_SB
+#define KITC_WEIGHTS_SB 64
+#endif
+
 struct Cheb {
     double t[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
     double w[KITC_MAX_DEGREE + 1];  // (-1)^k delta_k
@@ -239,62 +245,74 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
 // children therefore gives
 //   fhat_P[k1,k2,k3] = sum_c sum_k' L^P_k1(s^c_k1') L^P_k2(s^c_k2') L^P_k3(s^c_k3') fhat_c[k'],
 // three 1D contractions per child instead of (n+1)^3 work per particle.
-__global__ void __launch_bounds__(WT) k_upward(Cheb cb, int lb, const dvec4 *__restrict__ lo,
-                                               const dvec4 *__restrict__ hi,
-                                               const int32_t *__restrict__ first_child,
-                                               const int32_t *__restrict__ n_child, int win,
-                                               double *__restrict__ fhat)
+// One CTA per child (a level holds few parents but eight times as many
+// children): child c writes its contribution, three 1D contractions, to
+// contrib[c - cb0], and k_upward_sum adds each parent's children in child
+// order.
+__global__ void __launch_bounds__(WT) k_upward_child(Cheb cb, int cb0, const dvec4 *__restrict__ lo,
+                                                     const dvec4 *__restrict__ hi,
+                                                     const int32_t *__restrict__ parent, int win,
+                                                     const double *__restrict__ fhat,
+                                                     double *__restrict__ contrib)
 {
     extern __shared__ double sm[];
-    const int p = lb + blockIdx.x;
-    const int nch = n_child[p];
-    if (nch == 0) return;
+    const int c = cb0 + blockIdx.x, p = parent[c];
     const int np = cb.n + 1, np2 = np * np, pw = np2 * np * win;
-    double *T1 = sm, *T2 = T1 + pw, *A = T2 + pw, *M = A + pw;  // M[l][k'][k] = L^P_k(s^c_k')
-    for (int i = threadIdx.x; i < pw; i += WT) A[i] = 0.0;
-    const dvec4 plo = lo[p], phi = hi[p];
-    for (int ci = 0; ci < nch; ++ci) {
-        const int c = first_child[p] + ci;
-        const dvec4 clo = lo[c], chi = hi[c];
-        __syncthreads();
-        for (int q = threadIdx.x; q < 3 * np; q += WT) {
-            int l = q / np, kp = q % np;
-            double ca = l == 0 ? clo.x : (l == 1 ? clo.y : clo.z);
-            double cb_ = l == 0 ? chi.x : (l == 1 ? chi.y : chi.z);
-            double pa = l == 0 ? plo.x : (l == 1 ? plo.y : plo.z);
-            double pb = l == 0 ? phi.x : (l == 1 ? phi.y : phi.z);
-            double y = __dmul_rn(0.5, __dadd_rn(__dadd_rn(ca, cb_), __dmul_rn(cb.t[kp], __dsub_rn(cb_, ca))));
-            double L[KITC_MAX_DEGREE + 1];
-            bary_basis(cb, pa, pb, y, L);
-            for (int k = 0; k < np; ++k) M[(l * np + kp) * np + k] = L[k];
-        }
-        __syncthreads();
-        const double *F = fhat + (size_t)c * pw;
-        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k3
-            int q = o % win, k3 = (o / win) % np, r = o / (win * np);
-            double v = 0.0;
-            for (int kp = 0; kp < np; ++kp) v = fma(M[(2 * np + kp) * np + k3], F[(r * np + kp) * win + q], v);
-            T1[o] = v;
-        }
-        __syncthreads();
-        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k2
-            int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
-            double v = 0.0;
-            for (int kp = 0; kp < np; ++kp)
-                v = fma(M[(np + kp) * np + k2], T1[((k1 * np + kp) * np + k3) * win + q], v);
-            T2[o] = v;
-        }
-        __syncthreads();
-        for (int o = threadIdx.x; o < pw; o += WT) {  // contract k1, accumulate over children
-            int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
-            double v = 0.0;
-            for (int kp = 0; kp < np; ++kp)
-                v = fma(M[kp * np + k1], T2[((kp * np + k2) * np + k3) * win + q], v);
-            A[o] += v;
-        }
+    double *T1 = sm, *T2 = T1 + pw, *M = T2 + pw;  // M[l][k'][k] = L^P_k(s^c_k')
+    const dvec4 plo = lo[p], phi = hi[p], clo = lo[c], chi = hi[c];
+    for (int q = threadIdx.x; q < 3 * np; q += WT) {
+        int l = q / np, kp = q % np;
+        double ca = l == 0 ? clo.x : (l == 1 ? clo.y : clo.z);
+        double cb_ = l == 0 ? chi.x : (l == 1 ? chi.y : chi.z);
+        double pa = l == 0 ? plo.x : (l == 1 ? plo.y : plo.z);
+        double pb = l == 0 ? phi.x : (l == 1 ? phi.y : phi.z);
+        double y = __dmul_rn(0.5, __dadd_rn(__dadd_rn(ca, cb_), __dmul_rn(cb.t[kp], __dsub_rn(cb_, ca))));
+        double L[KITC_MAX_DEGREE + 1];
+        bary_basis(cb, pa, pb, y, L);
+        for (int k = 0; k < np; ++k) M[(l * np + kp) * np + k] = L[k];
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < pw; o += WT) fhat[(size_t)p * pw + o] = A[o];
+    const double *F = fhat + (size_t)c * pw;
+    for (int o = threadIdx.x; o < pw; o += WT) {  // contract k3
+        int q = o % win, k3 = (o / win) % np, r = o / (win * np);
+        double v = 0.0;
+        for (int kp = 0; kp < np; ++kp) v = fma(M[(2 * np + kp) * np + k3], F[(r * np + kp) * win + q], v);
+        T1[o] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < pw; o += WT) {  // contract k2
+        int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
+        double v = 0.0;
+        for (int kp = 0; kp < np; ++kp)
+            v = fma(M[(np + kp) * np + k2], T1[((k1 * np + kp) * np + k3) * win + q], v);
+        T2[o] = v;
+    }
+    __syncthreads();
+    double *C = contrib + (size_t)blockIdx.x * pw;
+    for (int o = threadIdx.x; o < pw; o += WT) {  // contract k1
+        int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
+        double v = 0.0;
+        for (int kp = 0; kp < np; ++kp)
+            v = fma(M[kp * np + k1], T2[((kp * np + k2) * np + k3) * win + q], v);
+        C[o] = v;
+    }
+}
+
+// fhat of every parent [lb, le) with children: the sum of its children's
+// contributions (children are contiguous, contrib indexed from cb0).
+__global__ void k_upward_sum(int lb, int le, int cb0, int pw, const int32_t *__restrict__ first_child,
+                             const int32_t *__restrict__ n_child, const double *__restrict__ contrib,
+                             double *__restrict__ fhat)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = lb + (int)(i / pw), o = (int)(i % pw);
+    if (p >= le) return;
+    const int nch = n_child[p];
+    if (nch == 0) return;
+    const int fc = first_child[p];
+    double a = 0.0;
+    for (int ci = 0; ci < nch; ++ci) a += contrib[(size_t)(fc + ci - cb0) * pw + o];
+    fhat[(size_t)p * pw + o] = a;
 }
 
 // fhat[c] = sum of the partials of c's work items, in item order.
@@ -525,11 +543,12 @@ const ChunkLauncher *chunk_table(bool split)
     return split ? t32 : t64;
 }
 
-size_t upward_smem(int np, int win)
+size_t upward_child_smem(int np, int win)
 {
     size_t pw = (size_t)np * np * np * win;
-    return sizeof(double) * (3 * pw + 3 * (size_t)np * np);
+    return sizeof(double) * (2 * pw + 3 * (size_t)np * np);
 }
+
 
 // Host-side plan of the weights pass for one tree: work items, buffer sizes and
 // launch shapes.  Done once per tree; weights_launch then only launches kernels
@@ -542,7 +561,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     wd.planned = false;
     const int np = degree + 1;
     const int pwin = np * np * np * win;
-    const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_smem(np, win) <= UP_SMEM_MAX;
+    const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_child_smem(np, win) <= UP_SMEM_MAX;
     // work items: chunks of the slot range of every cluster (of every leaf only,
     // when the parents come from the upward pass), in cluster order
     std::vector<int32_t> hb(t.nclus), he(t.nclus), hn(t.nclus);
@@ -571,12 +590,18 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
                               cudaMemcpyHostToDevice, s));
     KITC_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (t.nclus + 1),
                               cudaMemcpyHostToDevice, s));
-    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * std::max<size_t>(nitems, 1), s));
+    size_t rows = std::max<size_t>(nitems, 1);  // item partials, then the upward contributions
+    if (upward)
+        for (size_t L = 1; L < t.level_start.size(); ++L) {
+            const int e = L + 1 < t.level_start.size() ? t.level_start[L + 1] : t.nclus;
+            rows = std::max<size_t>(rows, (size_t)(e - t.level_start[L]));
+        }
+    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * rows, s));
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
     // the host vectors must outlive the copies above
     KITC_CUDA(cudaStreamSynchronize(s));
     size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
-    int sb = 64;
+    int sb = KITC_WEIGHTS_SB;
     while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
     wd.sb = sb;
     wd.smem = per * sb;
@@ -611,14 +636,22 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
                                              wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
     if (wd.upward) {
-        size_t us = upward_smem(np, win);
-        // deepest parents first: level L needs every child at level L + 1
-        for (int L = (int)t.level_start.size() - 2; L >= 0; --L) {
-            int lb = t.level_start[L], le = t.level_start[L + 1];
+        const size_t us = upward_child_smem(np, win);
+        const int nlev = (int)t.level_start.size();
+        // deepest parents first: level L needs every child at level L + 1; the
+        // children's contributions go to the (now free) item partials
+        for (int L = nlev - 2; L >= 0; --L) {
+            const int lb = t.level_start[L], le = t.level_start[L + 1];
+            const int cb0 = t.level_start[L + 1], ce = L + 2 < nlev ? t.level_start[L + 2] : t.nclus;
             kitc_count_launch();
-            k_upward<<<le - lb, WT, us, s>>>(cb, lb, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
-                                             t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
-                                             win, wd.fhat.as<double>());
+            k_upward_child<<<ce - cb0, WT, us, s>>>(cb, cb0, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                                    t.parent.as<int32_t>(), win, wd.fhat.as<double>(),
+                                                    wd.partial.as<double>());
+            kitc_count_launch();
+            const int64_t tot = (int64_t)(le - lb) * pwin;
+            k_upward_sum<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+                lb, le, cb0, pwin, t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
+                wd.partial.as<double>(), wd.fhat.as<double>());
             KITC_CUDA(cudaGetLastError());
         }
     }
@@ -954,7 +987,8 @@ kitc_status allow_up_smem()
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && done[dev].load()) return KITC_OK;
-    KITC_CUDA(cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UP_SMEM_MAX));
+    KITC_CUDA(cudaFuncSetAttribute(k_upward_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)UP_SMEM_MAX));
     KITC_CUDA(cudaFuncSetAttribute(k_transfer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)UP_SMEM_MAX));
     KITC_CUDA(cudaFuncSetAttribute(k_transfer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
