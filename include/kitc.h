@@ -45,7 +45,8 @@ typedef enum {
     KITC_ERR_OOM = 3,         /* device memory could not be allocated             */
     KITC_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out               */
     KITC_ERR_STATE = 5,       /* call out of order (e.g. evaluate before weights) */
-    KITC_ERR_TOO_LARGE = 6    /* size beyond the fixed scratch of kitc_direct_noalloc */
+    KITC_ERR_TOO_LARGE = 6    /* size beyond the fixed scratch of kitc_direct_noalloc,
+                                 or beyond the room of a kitc_pipeline handle      */
 } kitc_status;
 
 /* Kernels of Sec. 7.  d = x - y, r = |d|, H1, H2, Q, D1, D2 of Eq. MRS_kernels. */

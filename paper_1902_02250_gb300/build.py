@@ -14,10 +14,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkitc.so")
 SOURCES = ["api.cu", "tree.cu", "weights.cu", "lists.cu", "evaluate.cu", "noalloc.cu", "learn.cu",
-           "mlp.cu", "peak.cu"]
+           "mlp.cu", "peak.cu", "pipeline.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "kmath.cuh"),
            os.path.join(ROOT, "include", "kitc.h"),
-           os.path.join(ROOT, "include", "kitc_peak.h")]
+           os.path.join(ROOT, "include", "kitc_peak.h"),
+           os.path.join(ROOT, "include", "kitc_pipeline.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -149,8 +149,6 @@ bool valid_direct_params(const kitc_params *p)
            !(p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED);
 }
 
-namespace {
-
 bool valid_params(const kitc_params *p)
 {
     if (!p) return false;
@@ -170,10 +168,17 @@ bool valid_params(const kitc_params *p)
 
 int batch_of(const kitc_params &p) { return p.target_batch == 0 ? KITC_MAX_BATCH : p.target_batch; }
 
-void record(kitc_tree t, int i, cudaStream_t s)
+void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
 {
-    if (t->ev_ok) cudaEventRecord(t->ev[i], s);
+    a.degree = p.degree;
+    cheb_cos_table(p.degree, a.cheb);
+    a.eps = p.eps;
+    a.queue = flags;
+    a.err = flags + 1;
+    a.wait_ns = (unsigned long long)g_wait_limit_ms * 1000000ull;
 }
+
+bool weights_split_enabled() { return g_weights_split; }
 
 kitc_status read_error_flag(int *d_err, cudaStream_t s)
 {
@@ -184,15 +189,13 @@ kitc_status read_error_flag(int *d_err, cudaStream_t s)
     return h[0] ? KITC_ERR_TIMEOUT : KITC_OK;
 }
 
-void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
+namespace {
+
+void record(kitc_tree t, int i, cudaStream_t s)
 {
-    a.degree = p.degree;
-    cheb_cos_table(p.degree, a.cheb);
-    a.eps = p.eps;
-    a.queue = flags;
-    a.err = flags + 1;
-    a.wait_ns = (unsigned long long)g_wait_limit_ms * 1000000ull;
+    if (t->ev_ok) cudaEventRecord(t->ev[i], s);
 }
+
 
 void free_handle(kitc_tree t)
 {
@@ -243,7 +246,7 @@ const char *kitc_status_string(kitc_status s)
     case KITC_ERR_OOM: return "out of device memory";
     case KITC_ERR_TIMEOUT: return "device-side wait timed out";
     case KITC_ERR_STATE: return "call out of order";
-    case KITC_ERR_TOO_LARGE: return "size exceeds the fixed scratch of kitc_direct_noalloc";
+    case KITC_ERR_TOO_LARGE: return "size exceeds the room reserved by the call";
     default: return "unknown status";
     }
 }

@@ -89,6 +89,60 @@ struct TreeDev {
     size_t bytes() const;
 };
 
+// State of the device-side level loop of the tree build.  Level l reads
+// st[l & 1]; its children kernels write st[(l + 1) & 1].  Slots, permutation
+// and cluster ids of the slots live in the first buffers while cur = 0 and in
+// the second ones while cur = 1; a level that scatters sets flip, and the next
+// level's split kernel applies it (after the scatter has read cur).
+// level_start[d] is the first cluster of level d for d < depth; nclus ends the
+// last level.  overflow: a level's children did not fit the cluster capacity
+// (the tree then stops there, its clusters of that level staying leaves).
+struct LevelState {
+    int lb, nl;  // clusters [lb, lb + nl) of one level
+};
+struct BuildState {
+    LevelState st[2];
+    int nclus, depth, nleaves, overflow, cur, flip;
+    int level_start[KITC_MAX_LEVEL + 2];
+};
+
+// Scratch of one tree build: the second buffers of the slot arrays, the
+// per-block and per-level scratch, the root chunks and the state block.
+struct TreeScratch {
+    DevBuf perm2, xs2, node, node2, offs, bcount, lvl;
+    int nblk = 0, nc = 0, nsys = 1, cap = 0;
+    int64_t max_nl = 0;
+    size_t n64 = 0, n32 = 0;       // int64 and int32 entries at the start of offs
+    std::vector<int64_t> hoff;     // first slot of each system (+ n)
+    BuildState *state() const;
+    void release(cudaStream_t s);
+};
+
+// A tree whose build runs without any host read-back, so that it can be
+// captured in a CUDA graph: buffers for cap clusters and `levels` levels are
+// reserved once (tree_async_reserve); tree_async_launch queues the whole
+// build.  The host never learns nclus, depth or the level starts: kernels
+// downstream read them from state().  If the tree needs more clusters than cap
+// or more levels than `levels`, bit ASYNC_TREE_OVERFLOW is set in *err; the
+// arrays still hold a valid (coarser) tree, so every later kernel stays in
+// bounds.
+struct TreeAsync {
+    TreeDev t;
+    TreeScratch sc;
+    int levels = 0;
+    const BuildState *state() const { return sc.state(); }
+    void release(cudaStream_t s);
+    size_t bytes() const;
+};
+constexpr int ASYNC_TREE_OVERFLOW = 1;   // bits of the pipeline's error word
+constexpr int ASYNC_LIST_OVERFLOW = 2;
+constexpr int ASYNC_RECORD_OVERFLOW = 4;
+constexpr int ASYNC_TRAVERSAL = 8;       // a traversal stack overflowed (lists)
+
+kitc_status tree_async_reserve(TreeAsync &a, int64_t n, int leaf, const int64_t *counts, int nsys,
+                               int cap, int levels, cudaStream_t s);
+kitc_status tree_async_launch(TreeAsync &a, const double *xyz, int *err, cudaStream_t s);
+
 // Builds the tree of the n points xyz (device, n x 3 row-major), or a forest
 // with one tree per system when counts (host, nsys entries summing to n) is
 // given: system k owns rows [sum_{j<k} counts[j], ...).  Reads back the child
@@ -119,6 +173,8 @@ struct WeightsDev {
     bool var_upward = false;  // degree map: upward form (else Algorithm 1 on every cluster)
     int var_pmax = 0;         // degree map: largest grid size of the upward form
     int64_t fhat_len = 0;     // doubles of fhat in use
+    bool async = false;       // device-planned (weights_async_reserve): nitems is the item capacity
+    int64_t paircap = 0;      // device-planned paired records: capacity in pairs
     DevBuf fhat;      // double [nclus][P][win]
     DevBuf proxy;     // evaluator records of fhat (FP32 or FP64, padded)
     DevBuf src;       // evaluator records of the sources in tree order
@@ -159,6 +215,16 @@ int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed,
                           std::vector<int64_t> &roff);
 kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,
                              const int64_t *d_roff, bool mixed, bool pairs, cudaStream_t s);
+// Weights pass and evaluator records of an asynchronously built tree, planned
+// on the device (no read-back, no allocation in the launch).  Reserve once;
+// each launch recomputes everything from the tree's state block.  Bits of
+// *err: ASYNC_RECORD_OVERFLOW (cannot happen for a valid tree; the records
+// then stay in bounds but are not the weights).
+int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode);
+kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
+                                  bool mixed, bool pairs, cudaStream_t s, WeightsDev &wd);
+kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, WeightsDev &wd,
+                                 bool mixed, bool pairs, int *err, cudaStream_t s);
 // Paired FP32 records of the FP32x2 evaluator (pack_pairs_plan once per tree,
 // then pack_pairs_launch); pbegin receives the first pair of every leaf (-1
 // for other clusters), followed by the ranges of the packing launch.
@@ -203,12 +269,23 @@ struct ListsDev {
     DevBuf counts;               // int64 scratch [nb*2] + totals
     DevBuf totals;               // int64 [8]
     int64_t near_pairs = 0, far_points = 0, near_exec = 0, far_exec = 0;
+    bool async = false;                  // capacity-sized (lists_async_reserve)
+    int64_t cap_far = 0, cap_near = 0;   // its room for far and near entries
     void release(cudaStream_t s);
     size_t bytes() const;
 };
 
 kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
                         int degree, const int32_t *cdeg, int mac, cudaStream_t s, ListsDev &L);
+// Lists of two asynchronously built trees in buffers sized once for cap_far
+// and cap_near entries (forests: batches from the target systems' sizes).
+// The launch reads nothing back; lists that exceed their room are not written,
+// every batch's lists are emptied and ASYNC_LIST_OVERFLOW is set in *err.
+// Totals (as in lists_build) stay in L.totals on the device.
+kitc_status lists_async_reserve(const TreeAsync &src, const TreeAsync &tgt, int batch, int64_t cap_far,
+                                int64_t cap_near, cudaStream_t s, ListsDev &L);
+kitc_status lists_async_launch(const TreeAsync &src, const TreeAsync &tgt, double theta, int degree,
+                               int mac, int *err, cudaStream_t s, ListsDev &L);
 // Far-field point counts of existing lists under the degree map cdeg;
 // KITC_ERR_INVALID_ARG if an accepted cluster has degree 0.
 kitc_status lists_recount(const int32_t *cdeg, cudaStream_t s, ListsDev &L);
@@ -256,6 +333,16 @@ struct EvalArgs {
 };
 
 kitc_status evaluate_launch(int kernel, bool mixed, const EvalArgs &a, cudaStream_t s);
+// Evaluator arguments common to every call: degree, Chebyshev table, eps, the
+// work counter (flags[0]), the error flag (flags[1]) and the wait bound.
+void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags);
+// kitc_params checks of the treecode entry points; the target batch in use.
+bool valid_params(const kitc_params *p);
+int batch_of(const kitc_params &p);
+// Split-precision weight products in the mixed form (a build-time choice).
+bool weights_split_enabled();
+// Reads the evaluator's error flag (synchronizes s): KITC_ERR_TIMEOUT if set.
+kitc_status read_error_flag(int *d_err, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Per-cluster degree selection: features and measured far-field errors.

@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(LW * 32) k_lists(
     int64_t *__restrict__ counts, dvec4 *__restrict__ bctr, int64_t *__restrict__ totals,
     const int64_t *__restrict__ far_off, const int64_t *__restrict__ near_off,
     int32_t *__restrict__ far_id, uint64_t *__restrict__ far_mask, int32_t *__restrict__ near_id,
-    uint64_t *__restrict__ near_mask, int *__restrict__ err)
+    uint64_t *__restrict__ near_mask, int *__restrict__ err, const int *__restrict__ skip)
 {
+    if (skip && *skip) return;  // lists over capacity: nothing is written
     __shared__ int32_t sid[LW][STK];
     __shared__ uint64_t smask[LW][STK];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -265,6 +266,25 @@ __global__ void k_far_recount(int64_t nt, int batch, int64_t nb, const int32_t *
     }
 }
 
+// After the scans of a capacity-sized build: if the lists exceed the room
+// reserved for them, the writing pass is skipped (*skip) and every batch's
+// offsets are zeroed, so that the evaluator finds empty lists; the error word
+// records the overflow and a traversal stack overflow of the counting pass.
+__global__ void k_lists_guard(int64_t nb, const int64_t *__restrict__ tot, int64_t cap_far,
+                              int64_t cap_near, int64_t *__restrict__ far_off,
+                              int64_t *__restrict__ near_off, int *__restrict__ skip,
+                              int *__restrict__ err)
+{
+    const bool over = tot[2] > cap_far || tot[3] > cap_near;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *skip = over ? 1 : 0;
+        if (over) atomicOr(err, ASYNC_LIST_OVERFLOW);
+        if (reinterpret_cast<const int *>(tot + 6)[0] != 0) atomicOr(err, ASYNC_TRAVERSAL);
+    }
+    if (over && i <= nb) far_off[i] = near_off[i] = 0;
+}
+
 }  // namespace
 
 kitc_status lists_recount(const int32_t *cdeg, cudaStream_t s, ListsDev &L)
@@ -298,6 +318,8 @@ void ListsDev::release(cudaStream_t s)
                       &counts, &totals})
         b->release(s);
     nb = nt = nfar = nnear = 0;
+    async = false;
+    cap_far = cap_near = 0;
 }
 
 size_t ListsDev::bytes() const
@@ -309,6 +331,22 @@ size_t ListsDev::bytes() const
     return b;
 }
 
+// Per-system batches of a forest's target order: batch b covers slots
+// [st[b], st[b] + sz[b]) of system rt[b]; never two systems in one batch.
+static void forest_batches(const std::vector<int64_t> &off, int nsys, int batch, std::vector<int32_t> &all)
+{
+    std::vector<int32_t> st, sz, rt;
+    for (int k = 0; k < nsys; ++k)
+        for (int64_t p = off[k]; p < off[k + 1]; p += batch) {
+            st.push_back((int32_t)p);
+            sz.push_back((int32_t)std::min<int64_t>(batch, off[k + 1] - p));
+            rt.push_back(k);
+        }
+    all = st;
+    all.insert(all.end(), sz.begin(), sz.end());
+    all.insert(all.end(), rt.begin(), rt.end());
+}
+
 kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, double theta,
                         int degree, const int32_t *cdeg, int mac, cudaStream_t s, ListsDev &L)
 {
@@ -317,18 +355,10 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
     const int32_t *bdesc = nullptr;
     if (tgt.nsys > 1) {  // per-system batches: target system k meets source system k
         if (src.nsys != tgt.nsys) return KITC_ERR_INVALID_ARG;
-        std::vector<int32_t> st, sz, rt;
-        for (int k = 0; k < tgt.nsys; ++k)
-            for (int64_t p = tgt.sys_off[k]; p < tgt.sys_off[k + 1]; p += batch) {
-                st.push_back((int32_t)p);
-                sz.push_back((int32_t)std::min<int64_t>(batch, tgt.sys_off[k + 1] - p));
-                rt.push_back(k);
-            }
-        nb = (int64_t)st.size();
+        std::vector<int32_t> all;
+        forest_batches(tgt.sys_off, tgt.nsys, batch, all);
+        nb = (int64_t)all.size() / 3;
         KITC_TRY(L.bdesc.reserve(sizeof(int32_t) * 3 * nb, s));
-        std::vector<int32_t> all(st);
-        all.insert(all.end(), sz.begin(), sz.end());
-        all.insert(all.end(), rt.begin(), rt.end());
         KITC_CUDA(cudaMemcpyAsync(L.bdesc.ptr, all.data(), sizeof(int32_t) * all.size(),
                                   cudaMemcpyHostToDevice, s));
         KITC_CUDA(cudaStreamSynchronize(s));  // the host vector must outlive the copy
@@ -354,7 +384,7 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
                                         src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
                                         theta, np3, cdeg, mac, L.counts.as<int64_t>(),
                                         L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
-                                        nullptr, nullptr, nullptr, err);
+                                        nullptr, nullptr, nullptr, err, nullptr);
     KITC_CUDA(cudaGetLastError());
     kitc_count_launch();
     k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>(), nb, L.far_off.as<int64_t>(), tot + 2);
@@ -383,7 +413,86 @@ kitc_status lists_build(const TreeDev &src, const TreeDev &tgt, int batch, doubl
                                         theta, np3, cdeg, mac, nullptr, nullptr, nullptr,
                                         L.far_off.as<int64_t>(), L.near_off.as<int64_t>(),
                                         L.far_id.as<int32_t>(), L.far_mask.as<uint64_t>(),
-                                        L.near_id.as<int32_t>(), L.near_mask.as<uint64_t>(), err);
+                                        L.near_id.as<int32_t>(), L.near_mask.as<uint64_t>(), err,
+                                        nullptr);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+kitc_status lists_async_reserve(const TreeAsync &src, const TreeAsync &tgt, int batch, int64_t cap_far,
+                                int64_t cap_near, cudaStream_t s, ListsDev &L)
+{
+    L.release(s);
+    const TreeDev &tt = tgt.t;
+    int64_t nt = tt.n;
+    int64_t nb = (nt + batch - 1) / batch;
+    L.forest = tt.nsys > 1;
+    if (L.forest) {
+        if (src.t.nsys != tt.nsys) return KITC_ERR_INVALID_ARG;
+        std::vector<int32_t> all;
+        forest_batches(tt.sys_off, tt.nsys, batch, all);
+        nb = (int64_t)all.size() / 3;
+        KITC_TRY(L.bdesc.reserve(sizeof(int32_t) * all.size(), s));
+        KITC_CUDA(cudaMemcpyAsync(L.bdesc.ptr, all.data(), sizeof(int32_t) * all.size(),
+                                  cudaMemcpyHostToDevice, s));
+        KITC_CUDA(cudaStreamSynchronize(s));  // the host vector must outlive the copy
+    }
+    L.nt = nt;
+    L.nb = nb;
+    L.batch = batch;
+    KITC_TRY(L.bctr.reserve(sizeof(dvec4) * nb, s));
+    KITC_TRY(L.counts.reserve(sizeof(int64_t) * 2 * nb, s));
+    KITC_TRY(L.far_off.reserve(sizeof(int64_t) * (nb + 1), s));
+    KITC_TRY(L.near_off.reserve(sizeof(int64_t) * (nb + 1), s));
+    KITC_TRY(L.totals.reserve(sizeof(int64_t) * 10, s));  // 8 totals | skip flag
+    KITC_TRY(L.far_id.reserve(sizeof(int32_t) * (cap_far + 1), s));
+    KITC_TRY(L.far_mask.reserve(sizeof(uint64_t) * (cap_far + 1), s));
+    KITC_TRY(L.near_id.reserve(sizeof(int32_t) * (cap_near + 1), s));
+    KITC_TRY(L.near_mask.reserve(sizeof(uint64_t) * (cap_near + 1), s));
+    L.cap_far = cap_far;
+    L.cap_near = cap_near;
+    L.nfar = L.nnear = -1;  // known on the device only
+    L.async = true;
+    return KITC_OK;
+}
+
+kitc_status lists_async_launch(const TreeAsync &srcA, const TreeAsync &tgtA, double theta, int degree,
+                               int mac, int *perr, cudaStream_t s, ListsDev &L)
+{
+    if (!L.async) return KITC_ERR_STATE;
+    const TreeDev &src = srcA.t, &tgt = tgtA.t;
+    const int64_t nt = L.nt, nb = L.nb;
+    const int batch = L.batch;
+    const int32_t *bdesc = L.forest ? L.bdesc.as<int32_t>() : nullptr;
+    const int np = degree + 1, np3 = np * np * np;
+    int64_t *tot = L.totals.as<int64_t>();
+    int *err = reinterpret_cast<int *>(tot + 6);
+    int *skip = reinterpret_cast<int *>(tot + 8);
+    KITC_CUDA(cudaMemsetAsync(tot, 0, sizeof(int64_t) * 8, s));
+    const unsigned grid = (unsigned)((nb + LW - 1) / LW);
+    kitc_count_launch();
+    k_lists<0><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+                                        src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
+                                        theta, np3, nullptr, mac, L.counts.as<int64_t>(),
+                                        L.bctr.as<dvec4>(), tot, nullptr, nullptr, nullptr,
+                                        nullptr, nullptr, nullptr, err, nullptr);
+    KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
+    k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>(), nb, L.far_off.as<int64_t>(), tot + 2);
+    kitc_count_launch();
+    k_scan64<<<1, 1024, 0, s>>>(L.counts.as<int64_t>() + nb, nb, L.near_off.as<int64_t>(), tot + 3);
+    kitc_count_launch();
+    k_lists_guard<<<(unsigned)((nb + 1 + 255) / 256), 256, 0, s>>>(
+        nb, tot, L.cap_far, L.cap_near, L.far_off.as<int64_t>(), L.near_off.as<int64_t>(), skip, perr);
+    kitc_count_launch();
+    k_lists<1><<<grid, LW * 32, 0, s>>>(nt, batch, nb, bdesc, tgt.xs.as<double>(), src.ctr.as<dvec4>(),
+                                        src.ctrf.as<float4>(), src.begin.as<int32_t>(), src.end.as<int32_t>(),
+                                        src.first_child.as<int32_t>(), src.n_child.as<int32_t>(),
+                                        theta, np3, nullptr, mac, nullptr, nullptr, nullptr,
+                                        L.far_off.as<int64_t>(), L.near_off.as<int64_t>(),
+                                        L.far_id.as<int32_t>(), L.far_mask.as<uint64_t>(),
+                                        L.near_id.as<int32_t>(), L.near_mask.as<uint64_t>(), err, skip);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }

@@ -34,22 +34,6 @@ struct SplitInfo {
     int pad;
 };
 
-// Clusters [lb, lb + nl) of one level.
-struct LevelState {
-    int lb, nl;
-};
-
-// State of the device-side level loop.  Level l reads st[l & 1]; its
-// k_children_scan writes st[(l + 1) & 1].  Slots, permutation and cluster ids of
-// the slots live in the A buffers while cur = 0 and in the B buffers while
-// cur = 1; a level that scatters sets flip, and the next level's k_split
-// applies it (after the scatter has read cur).
-struct BuildState {
-    LevelState st[2];
-    int nclus, depth, nleaves, overflow, cur, flip;
-    int level_start[KITC_MAX_LEVEL + 2];
-};
-
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
@@ -512,10 +496,13 @@ __global__ void __launch_bounds__(BT, 2) k_scatter(
 // Also writes the centre as FP32 hi/lo pairs and the radius in FP32
 // (ctrf[2c] = hi xyz + radius, ctrf[2c+1] = lo xyz) for the list builder's
 // FP32 pre-test of the MAC.
-__global__ void k_geometry(int m, const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi,
-                           dvec4 *__restrict__ ctr, float4 *__restrict__ ctrf)
+// With bs given, the clusters are bs->nclus (<= m).
+__global__ void k_geometry(int m, const BuildState *__restrict__ bs, const dvec4 *__restrict__ lo,
+                           const dvec4 *__restrict__ hi, dvec4 *__restrict__ ctr,
+                           float4 *__restrict__ ctrf)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bs) m = min(m, bs->nclus);
     if (c >= m) return;
     dvec4 a = lo[c], b = hi[c];
     double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
@@ -529,6 +516,39 @@ __global__ void k_geometry(int m, const dvec4 *__restrict__ lo, const dvec4 *__r
                                   __double2float_rn(g.z - (double)hz), 0.f);
 }
 
+// Initial state: one root per system, nothing split yet.
+__global__ void k_state_init(BuildState *bs, int nsys)
+{
+    int *w = reinterpret_cast<int *>(bs);
+    for (int i = threadIdx.x; i < (int)(sizeof(BuildState) / sizeof(int)); i += blockDim.x) w[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bs->st[0] = LevelState{0, nsys};
+        bs->nclus = nsys;
+    }
+}
+
+// End of a build whose state the host never reads: brings the final slot
+// order into the first buffers (when the last scattering level left it in the
+// second ones) and flags a tree that ran out of clusters or of levels.
+__global__ void k_tree_finish(int64_t n, const BuildState *__restrict__ bs, int levels,
+                              double *__restrict__ xsA, const double *__restrict__ xsB,
+                              int32_t *__restrict__ permA, const int32_t *__restrict__ permB,
+                              int *__restrict__ err)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (bs->overflow || bs->st[levels & 1].nl != 0))
+        atomicOr(err, ASYNC_TREE_OVERFLOW);
+    if ((bs->cur ^ bs->flip) == 0) return;
+    int64_t base = (int64_t)blockIdx.x * SPB;
+    for (int r = 0; r < RPB; ++r) {
+        int64_t i = base + r * BT + threadIdx.x;
+        if (i < n) {
+            for (int l = 0; l < 3; ++l) xsA[l * n + i] = xsB[l * n + i];
+            permA[i] = permB[i];
+        }
+    }
+}
+
 // Cluster arrays for cap clusters (contents not kept).
 kitc_status alloc_clusters(TreeDev &t, int cap, cudaStream_t s)
 {
@@ -540,7 +560,209 @@ kitc_status alloc_clusters(TreeDev &t, int cap, cudaStream_t s)
     return KITC_OK;
 }
 
+// Pointers into the level scratch: the state block, then per cluster of the
+// largest level: split info | ccount | cprefix | childoff | childidx (8 each)
+// | children prefix | block totals of the children kernels.
+struct LevelPtrs {
+    BuildState *bs;
+    SplitInfo *info;
+    int32_t *ccount, *cprefix, *childoff, *childidx, *nchs, *btot;
+};
+
+size_t level_scratch_bytes(int64_t max_nl)
+{
+    const size_t per = (size_t)max_nl * 8;
+    const size_t nbt = (size_t)((max_nl + CB - 1) / CB) * NT;
+    return ((sizeof(BuildState) + 255) / 256) * 256 + sizeof(SplitInfo) * max_nl +
+           sizeof(int32_t) * (4 * per + max_nl + nbt + 2) + 256;
+}
+
+LevelPtrs level_ptrs(const TreeScratch &sc)
+{
+    LevelPtrs q;
+    char *b = sc.lvl.as<char>();
+    const size_t per = (size_t)sc.max_nl * 8;
+    q.bs = reinterpret_cast<BuildState *>(b);
+    q.info = reinterpret_cast<SplitInfo *>(b + ((sizeof(BuildState) + 255) / 256) * 256);
+    q.ccount = reinterpret_cast<int32_t *>(q.info + sc.max_nl);
+    q.cprefix = q.ccount + per;
+    q.childoff = q.cprefix + per;
+    q.childidx = q.childoff + per;
+    q.nchs = q.childidx + per;
+    q.btot = q.nchs + sc.max_nl;
+    return q;
+}
+
+// Root-box chunks of at most 64K slots, packed in offs as
+// [off (nsys+1) | cb (nc) | ce (nc)] int64, then [c0 (nsys+1) | cs (nc)] int32,
+// then the chunks' partial boxes (6 doubles each, 16-byte aligned).
+struct RootPtrs {
+    int64_t *d64;
+    int32_t *d32;
+    double *part;
+};
+
+RootPtrs root_ptrs(const TreeScratch &sc)
+{
+    RootPtrs r;
+    r.d64 = sc.offs.as<int64_t>();
+    r.d32 = reinterpret_cast<int32_t *>(r.d64 + sc.n64);
+    r.part = reinterpret_cast<double *>(
+        sc.offs.as<char>() + ((sizeof(int64_t) * sc.n64 + sizeof(int32_t) * sc.n32 + 15) / 16) * 16);
+    return r;
+}
+
+// Slot arrays, cluster arrays for cap clusters and the scratch of one build of
+// the n points (a forest of nsys systems when counts is given); uploads the
+// root chunks.  The host copies of the chunks stay in hchunks until the
+// scratch is released, so they outlive the upload.
+kitc_status build_reserve(TreeDev &t, TreeScratch &sc, std::vector<int64_t> &h64,
+                          std::vector<int32_t> &h32, int64_t n, int leaf, const int64_t *counts,
+                          int nsys, int cap, cudaStream_t s)
+{
+    t.release(s);
+    sc.release(s);
+    t.n = n;
+    t.leaf = leaf;
+    sc.nsys = nsys;
+    sc.cap = cap;
+    sc.nblk = (int)((n + SPB - 1) / SPB);
+    KITC_TRY(t.perm.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(sc.perm2.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(t.xs.reserve(sizeof(double) * 3 * n, s));
+    KITC_TRY(sc.xs2.reserve(sizeof(double) * 3 * n, s));
+    KITC_TRY(sc.node.reserve(sizeof(int32_t) * n, s));
+    KITC_TRY(sc.node2.reserve(sizeof(int32_t) * n, s));
+    sc.hoff.assign(nsys + 1, 0);
+    for (int k = 0; k < nsys; ++k) sc.hoff[k + 1] = sc.hoff[k] + (counts ? counts[k] : n);
+    if (sc.hoff[nsys] != n) return KITC_ERR_INVALID_ARG;
+    const int64_t CH = 65536;
+    std::vector<int64_t> cbv, cev;
+    std::vector<int32_t> c0v(nsys + 1, 0), csv;
+    for (int k = 0; k < nsys; ++k) {
+        c0v[k] = (int32_t)cbv.size();
+        for (int64_t p = sc.hoff[k]; p < sc.hoff[k + 1]; p += CH) {
+            cbv.push_back(p);
+            cev.push_back(std::min(sc.hoff[k + 1], p + CH));
+            csv.push_back(k);
+        }
+    }
+    sc.nc = (int)cbv.size();
+    c0v[nsys] = sc.nc;
+    h64 = sc.hoff;
+    h64.insert(h64.end(), cbv.begin(), cbv.end());
+    h64.insert(h64.end(), cev.begin(), cev.end());
+    h32 = c0v;
+    h32.insert(h32.end(), csv.begin(), csv.end());
+    sc.n64 = h64.size();
+    sc.n32 = h32.size();
+    KITC_TRY(sc.offs.reserve(sizeof(int64_t) * sc.n64 + sizeof(int32_t) * sc.n32 +
+                             sizeof(double) * 6 * sc.nc + 64, s));
+    KITC_TRY(sc.bcount.reserve(sizeof(int32_t) * 8 * sc.nblk, s));
+    KITC_TRY(alloc_clusters(t, cap, s));
+    sc.max_nl = std::min<int64_t>(cap, n + nsys);  // the largest level
+    KITC_TRY(sc.lvl.reserve(level_scratch_bytes(sc.max_nl), s));
+    // every buffer the kernels write must exist before any launch
+    for (const DevBuf *b : {&t.perm, &sc.perm2, &t.xs, &sc.xs2, &sc.node, &sc.node2, &sc.offs,
+                            &sc.bcount, &sc.lvl, &t.lo, &t.hi, &t.begin, &t.end, &t.first_child,
+                            &t.n_child, &t.level, &t.parent})
+        if (!b->ptr) return KITC_ERR_OOM;
+    const RootPtrs r = root_ptrs(sc);
+    KITC_CUDA(cudaMemcpyAsync(r.d64, h64.data(), sizeof(int64_t) * h64.size(), cudaMemcpyHostToDevice, s));
+    KITC_CUDA(cudaMemcpyAsync(r.d32, h32.data(), sizeof(int32_t) * h32.size(), cudaMemcpyHostToDevice, s));
+    return KITC_OK;
+}
+
+// State, slot order and root boxes.
+kitc_status queue_root(TreeDev &t, const TreeScratch &sc, const double *xyz, cudaStream_t s)
+{
+    const LevelPtrs q = level_ptrs(sc);
+    const RootPtrs r = root_ptrs(sc);
+    const int nsys = sc.nsys, nc = sc.nc;
+    kitc_count_launch();
+    k_state_init<<<1, 128, 0, s>>>(q.bs, nsys);
+    kitc_count_launch();
+    k_init<<<sc.nblk, BT, 0, s>>>(xyz, t.n, t.xs.as<double>(), t.perm.as<int32_t>());
+    KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
+    k_root_partial<<<nc, BT, 0, s>>>(r.d32 + nsys + 1, r.d64 + nsys + 1, r.d64 + nsys + 1 + nc, t.n,
+                                     t.xs.as<double>(), sc.node.as<int32_t>(), r.part);
+    KITC_CUDA(cudaGetLastError());
+    kitc_count_launch();
+    k_root_final<<<(nsys + 127) / 128, 128, 0, s>>>(nsys, r.d32, r.d64, r.part, t.lo.as<dvec4>(),
+                                                    t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                                                    t.end.as<int32_t>(), t.first_child.as<int32_t>(),
+                                                    t.n_child.as<int32_t>(), t.level.as<int32_t>(),
+                                                    t.parent.as<int32_t>());
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+// Levels [lv0, lv1).  Grids are sized from a host bound of each level's size
+// (nsys 8^lv, at most the largest level); kernels of a level with no clusters
+// exit at once.
+kitc_status queue_levels(TreeDev &t, TreeScratch &sc, int leaf, int lv0, int lv1, cudaStream_t s)
+{
+    const LevelPtrs q = level_ptrs(sc);
+    const int64_t n = t.n;
+    const int nblk = sc.nblk;
+    for (int lv = lv0; lv < lv1; ++lv) {
+        int64_t cap_l = std::min<int64_t>(sc.max_nl, sc.nsys);
+        for (int k = 0; k < lv && cap_l < sc.max_nl; ++k) cap_l = std::min<int64_t>(sc.max_nl, 8 * cap_l);
+        kitc_count_launch();
+        k_split<<<(unsigned)((cap_l + 255) / 256), 256, 0, s>>>(
+            q.bs, lv, leaf, t.lo.as<dvec4>(), t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+            t.end.as<int32_t>(), t.level.as<int32_t>(), q.info, q.ccount);
+        kitc_count_launch();
+        k_count<<<nblk, BT, 0, s>>>(n, q.bs, lv, t.xs.as<double>(), sc.xs2.as<double>(),
+                                    sc.node.as<int32_t>(), sc.node2.as<int32_t>(), q.info, q.ccount,
+                                    sc.bcount.as<int32_t>(), nblk);
+        const unsigned gc = (unsigned)((cap_l + CB - 1) / CB);
+        kitc_count_launch();
+        k_children_local<<<gc, CB, 0, s>>>(q.bs, lv, q.info, q.ccount, q.cprefix, q.childoff, q.nchs,
+                                           q.btot);
+        kitc_count_launch();
+        k_children_scan<<<1, BT, 0, s>>>(q.bs, lv, sc.cap, sc.bcount.as<int32_t>(), nblk, q.btot);
+        kitc_count_launch();
+        k_children_make<<<gc, CB, 0, s>>>(q.bs, lv, q.info, q.ccount, q.cprefix, q.childoff,
+                                          q.childidx, q.nchs, q.btot, t.lo.as<dvec4>(),
+                                          t.hi.as<dvec4>(), t.begin.as<int32_t>(),
+                                          t.end.as<int32_t>(), t.first_child.as<int32_t>(),
+                                          t.n_child.as<int32_t>(), t.level.as<int32_t>(),
+                                          t.parent.as<int32_t>());
+        kitc_count_launch();
+        k_scatter<<<nblk, BT, 0, s>>>(n, q.bs, lv, t.xs.as<double>(), sc.xs2.as<double>(),
+                                      t.perm.as<int32_t>(), sc.perm2.as<int32_t>(),
+                                      sc.node.as<int32_t>(), sc.node2.as<int32_t>(), q.info,
+                                      t.begin.as<int32_t>(), q.cprefix, q.childoff, q.childidx,
+                                      sc.bcount.as<int32_t>(), nblk);
+        KITC_CUDA(cudaGetLastError());
+    }
+    return KITC_OK;
+}
+
+// Levels queued per round: the depth of a roughly uniform tree plus a few
+// levels of slack.
+int round_levels(int64_t n, int leaf, int nsys)
+{
+    int round = 4;
+    for (int64_t m = std::max<int64_t>(1, n / std::max(1, nsys)); m > leaf; m = (m + 7) / 8) ++round;
+    return round;
+}
+
 }  // namespace
+
+BuildState *TreeScratch::state() const { return level_ptrs(*this).bs; }
+
+void TreeScratch::release(cudaStream_t s)
+{
+    for (DevBuf *b : {&perm2, &xs2, &node, &node2, &offs, &bcount, &lvl}) b->release(s);
+    nblk = nc = cap = 0;
+    nsys = 1;
+    max_nl = 0;
+    n64 = n32 = 0;
+    hoff.clear();
+}
 
 void TreeDev::release(cudaStream_t s)
 {
@@ -568,157 +790,54 @@ static kitc_status tree_build_cap(const double *xyz, int64_t n, int leaf, cudaSt
                                   const int64_t *counts, int nsys, int cap, int64_t *needed)
 {
     *needed = 0;
-    t.release(s);
-    t.n = n;
-    t.leaf = leaf;
-    int nblk = (int)((n + SPB - 1) / SPB);
-    DevBuf perm2, xs2, node, node2, offs, bcount, lvl;
-    KITC_TRY(t.perm.reserve(sizeof(int32_t) * n, s));
-    KITC_TRY(perm2.reserve(sizeof(int32_t) * n, s));
-    KITC_TRY(t.xs.reserve(sizeof(double) * 3 * n, s));
-    KITC_TRY(xs2.reserve(sizeof(double) * 3 * n, s));
-    KITC_TRY(node.reserve(sizeof(int32_t) * n, s));
-    KITC_TRY(node2.reserve(sizeof(int32_t) * n, s));
-    std::vector<int64_t> hoff(nsys + 1, 0);
-    for (int k = 0; k < nsys; ++k) hoff[k + 1] = hoff[k] + (counts ? counts[k] : n);
-    if (hoff[nsys] != n) return KITC_ERR_INVALID_ARG;
-    // chunks of at most 64K slots for the root boxes; packed as
-    // [off (nsys+1) | cb (nc) | ce (nc)] int64 and [c0 (nsys+1) | cs (nc)] int32
-    const int64_t CH = 65536;
-    std::vector<int64_t> cbv, cev;
-    std::vector<int32_t> c0v(nsys + 1, 0), csv;
-    for (int k = 0; k < nsys; ++k) {
-        c0v[k] = (int32_t)cbv.size();
-        for (int64_t p = hoff[k]; p < hoff[k + 1]; p += CH) {
-            cbv.push_back(p);
-            cev.push_back(std::min(hoff[k + 1], p + CH));
-            csv.push_back(k);
-        }
-    }
-    const int nc = (int)cbv.size();
-    c0v[nsys] = nc;
-    std::vector<int64_t> h64(hoff);
-    h64.insert(h64.end(), cbv.begin(), cbv.end());
-    h64.insert(h64.end(), cev.begin(), cev.end());
-    std::vector<int32_t> h32(c0v);
-    h32.insert(h32.end(), csv.begin(), csv.end());
-    KITC_TRY(offs.reserve(sizeof(int64_t) * h64.size() + sizeof(int32_t) * h32.size() +
-                          sizeof(double) * 6 * nc + 64, s));
-    int64_t *d64 = offs.as<int64_t>();
-    int32_t *d32 = reinterpret_cast<int32_t *>(d64 + h64.size());
-    double *dpart = reinterpret_cast<double *>(offs.as<char>() + ((sizeof(int64_t) * h64.size() +
-                                                                   sizeof(int32_t) * h32.size() + 15) / 16) * 16);
-    KITC_TRY(bcount.reserve(sizeof(int32_t) * 8 * nblk, s));
-    KITC_TRY(alloc_clusters(t, cap, s));
-    // level scratch for the largest level: info | ccount | cprefix | childoff | childidx | nchild_scan
-    const int64_t max_nl = std::min<int64_t>(cap, n + nsys);
-    const size_t per = (size_t)max_nl * 8;
-    const size_t nbt = (size_t)((max_nl + CB - 1) / CB) * NT;  // block totals of the children kernels
-    KITC_TRY(lvl.reserve(sizeof(SplitInfo) * max_nl + sizeof(int32_t) * (4 * per + max_nl + nbt + 2) +
-                         sizeof(BuildState) + 512, s));
-    char *q = lvl.as<char>();
-    BuildState *bs = reinterpret_cast<BuildState *>(q);
-    SplitInfo *info = reinterpret_cast<SplitInfo *>(q + ((sizeof(BuildState) + 255) / 256) * 256);
-    int32_t *ccount = reinterpret_cast<int32_t *>(info + max_nl);
-    int32_t *cprefix = ccount + per, *childoff = cprefix + per, *childidx = childoff + per;
-    int32_t *nchs = childidx + per, *btot = nchs + max_nl;
-    // every buffer the kernels below write must exist before any launch
-    for (const DevBuf *b : {&t.perm, &perm2, &t.xs, &xs2, &node, &node2, &offs, &bcount, &lvl, &t.lo,
-                            &t.hi, &t.begin, &t.end, &t.first_child, &t.n_child, &t.level, &t.parent})
-        if (!b->ptr) return KITC_ERR_OOM;
-    BuildState h0{};
-    h0.st[0] = LevelState{0, nsys};
-    h0.nclus = nsys;
-    KITC_CUDA(cudaMemcpyAsync(bs, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d64, h64.data(), sizeof(int64_t) * h64.size(), cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d32, h32.data(), sizeof(int32_t) * h32.size(), cudaMemcpyHostToDevice, s));
-    kitc_count_launch();
-    k_init<<<nblk, BT, 0, s>>>(xyz, n, t.xs.as<double>(), t.perm.as<int32_t>());
-    KITC_CUDA(cudaGetLastError());
-    kitc_count_launch();
-    k_root_partial<<<nc, BT, 0, s>>>(d32 + nsys + 1, d64 + nsys + 1, d64 + nsys + 1 + nc, n,
-                                     t.xs.as<double>(), node.as<int32_t>(), dpart);
-    KITC_CUDA(cudaGetLastError());
-    kitc_count_launch();
-    k_root_final<<<(nsys + 127) / 128, 128, 0, s>>>(nsys, d32, d64, dpart, t.lo.as<dvec4>(),
-                                                    t.hi.as<dvec4>(), t.begin.as<int32_t>(),
-                                                    t.end.as<int32_t>(), t.first_child.as<int32_t>(),
-                                                    t.n_child.as<int32_t>(), t.level.as<int32_t>(),
-                                                    t.parent.as<int32_t>());
-    KITC_CUDA(cudaGetLastError());
-    // Levels are queued in rounds: the depth of a roughly uniform tree plus a
-    // few levels of slack, then the state is read back once; a deeper tree
-    // takes further rounds.  Levels after the last one exit at once.
-    int round = 4;
-    for (int64_t m = std::max<int64_t>(1, n / std::max(1, nsys)); m > leaf; m = (m + 7) / 8) ++round;
+    TreeScratch sc;
+    std::vector<int64_t> h64;
+    std::vector<int32_t> h32;
+    auto fail = [&](kitc_status st) {
+        sc.release(s);
+        return st;
+    };
+    kitc_status st = build_reserve(t, sc, h64, h32, n, leaf, counts, nsys, cap, s);
+    if (st == KITC_OK) st = queue_root(t, sc, xyz, s);
+    if (st != KITC_OK) return fail(st);
+    // Levels are queued in rounds, then the state is read back once; a deeper
+    // tree takes further rounds.  Levels after the last one exit at once.
+    const int round = round_levels(n, leaf, nsys);
+    const BuildState *bs = sc.state();
     BuildState hs{};
     int lv = 0;
     for (;;) {
         const int lv_end = std::min(KITC_MAX_LEVEL + 1, lv + round);
-        for (; lv < lv_end; ++lv) {
-            int64_t cap_l = std::min<int64_t>(max_nl, nsys);
-            for (int k = 0; k < lv && cap_l < max_nl; ++k) cap_l = std::min<int64_t>(max_nl, 8 * cap_l);
-            kitc_count_launch();
-            k_split<<<(unsigned)((cap_l + 255) / 256), 256, 0, s>>>(
-                bs, lv, leaf, t.lo.as<dvec4>(), t.hi.as<dvec4>(), t.begin.as<int32_t>(),
-                t.end.as<int32_t>(), t.level.as<int32_t>(), info, ccount);
-            kitc_count_launch();
-            k_count<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
-                                        node.as<int32_t>(), node2.as<int32_t>(), info, ccount,
-                                        bcount.as<int32_t>(), nblk);
-            const unsigned gc = (unsigned)((cap_l + CB - 1) / CB);
-            kitc_count_launch();
-            k_children_local<<<gc, CB, 0, s>>>(bs, lv, info, ccount, cprefix, childoff, nchs, btot);
-            kitc_count_launch();
-            k_children_scan<<<1, BT, 0, s>>>(bs, lv, cap, bcount.as<int32_t>(), nblk, btot);
-            kitc_count_launch();
-            k_children_make<<<gc, CB, 0, s>>>(bs, lv, info, ccount, cprefix, childoff, childidx, nchs,
-                                              btot, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
-                                              t.begin.as<int32_t>(), t.end.as<int32_t>(),
-                                              t.first_child.as<int32_t>(), t.n_child.as<int32_t>(),
-                                              t.level.as<int32_t>(), t.parent.as<int32_t>());
-            kitc_count_launch();
-            k_scatter<<<nblk, BT, 0, s>>>(n, bs, lv, t.xs.as<double>(), xs2.as<double>(),
-                                          t.perm.as<int32_t>(), perm2.as<int32_t>(), node.as<int32_t>(),
-                                          node2.as<int32_t>(), info, t.begin.as<int32_t>(), cprefix,
-                                          childoff, childidx, bcount.as<int32_t>(), nblk);
-            KITC_CUDA(cudaGetLastError());
-        }
+        st = queue_levels(t, sc, leaf, lv, lv_end, s);
+        if (st != KITC_OK) return fail(st);
+        lv = lv_end;
         // the one read-back of the round (it also ends the life of the host
-        // arrays copied above)
-        KITC_CUDA(cudaMemcpyAsync(&hs, bs, sizeof(hs), cudaMemcpyDeviceToHost, s));
-        KITC_CUDA(cudaStreamSynchronize(s));
+        // arrays uploaded by build_reserve)
+        st = kitc_from_cuda(cudaMemcpyAsync(&hs, bs, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        if (st == KITC_OK) st = kitc_from_cuda(cudaStreamSynchronize(s));
+        if (st != KITC_OK) return fail(st);
         if (hs.overflow || hs.st[lv & 1].nl == 0 || lv > KITC_MAX_LEVEL) break;
     }
-    kitc_status st = KITC_OK;
     if (hs.overflow) {
         *needed = 2 * (int64_t)cap;
-        st = KITC_OK;
-    } else if (hs.st[lv & 1].nl != 0) {
-        st = KITC_ERR_CUDA;  // cannot happen: a level past KITC_MAX_LEVEL splits nothing
+        return fail(KITC_OK);
     }
-    for (DevBuf *b : {&node, &node2, &offs, &bcount, &lvl}) b->release(s);
-    if (st != KITC_OK || hs.overflow) {
-        perm2.release(s);
-        xs2.release(s);
-        return st;
+    if (hs.st[lv & 1].nl != 0) return fail(KITC_ERR_CUDA);  // cannot happen: a level past KITC_MAX_LEVEL splits nothing
+    if ((hs.cur ^ hs.flip) != 0) {  // the final order is in the second buffers
+        std::swap(t.xs, sc.xs2);
+        std::swap(t.perm, sc.perm2);
     }
-    if ((hs.cur ^ hs.flip) != 0) {  // the final order is in the B buffers
-        std::swap(t.xs, xs2);
-        std::swap(t.perm, perm2);
-    }
-    perm2.release(s);
-    xs2.release(s);
+    sc.release(s);
     t.nclus = hs.nclus;
     t.depth = hs.depth;
     t.nleaves = hs.nleaves;
     t.nsys = nsys;
-    t.sys_off = hoff;
+    t.sys_off.assign(h64.begin(), h64.begin() + nsys + 1);
     t.level_start.assign(hs.level_start, hs.level_start + hs.depth);
     KITC_TRY(t.ctr.reserve(sizeof(dvec4) * t.cap, s));
     KITC_TRY(t.ctrf.reserve(2 * sizeof(float4) * t.cap, s));
     kitc_count_launch();
-    k_geometry<<<(t.nclus + 255) / 256, 256, 0, s>>>(t.nclus, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+    k_geometry<<<(t.nclus + 255) / 256, 256, 0, s>>>(t.nclus, nullptr, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
                                                    t.ctr.as<dvec4>(), t.ctrf.as<float4>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
@@ -739,4 +858,58 @@ kitc_status tree_build(const double *xyz, int64_t n, int leaf, cudaStream_t s, T
         if (needed == 0) return KITC_OK;
         cap = needed;
     }
+}
+
+void TreeAsync::release(cudaStream_t s)
+{
+    t.release(s);
+    sc.release(s);
+    levels = 0;
+}
+
+size_t TreeAsync::bytes() const
+{
+    size_t b = t.bytes();
+    for (const DevBuf *d : {&sc.perm2, &sc.xs2, &sc.node, &sc.node2, &sc.offs, &sc.bcount, &sc.lvl})
+        b += d->bytes;
+    return b;
+}
+
+kitc_status tree_async_reserve(TreeAsync &a, int64_t n, int leaf, const int64_t *counts, int nsys,
+                               int cap, int levels, cudaStream_t s)
+{
+    if (!counts) nsys = 1;
+    if (levels < 1 || levels > KITC_MAX_LEVEL + 1 || cap < nsys) return KITC_ERR_INVALID_ARG;
+    std::vector<int64_t> h64;
+    std::vector<int32_t> h32;
+    kitc_status st = build_reserve(a.t, a.sc, h64, h32, n, leaf, counts, nsys, cap, s);
+    if (st == KITC_OK) st = a.t.ctr.reserve(sizeof(dvec4) * cap, s);
+    if (st == KITC_OK) st = a.t.ctrf.reserve(2 * sizeof(float4) * cap, s);
+    if (st == KITC_OK) st = kitc_from_cuda(cudaStreamSynchronize(s));  // h64, h32 end here
+    if (st != KITC_OK) {
+        a.release(s);
+        return st;
+    }
+    a.t.nsys = nsys;
+    a.t.sys_off.assign(h64.begin(), h64.begin() + nsys + 1);
+    a.t.nclus = -1;  // known on the device only
+    a.levels = levels;
+    return KITC_OK;
+}
+
+kitc_status tree_async_launch(TreeAsync &a, const double *xyz, int *err, cudaStream_t s)
+{
+    TreeDev &t = a.t;
+    if (a.levels < 1 || !t.ctr.ptr || !t.ctrf.ptr) return KITC_ERR_STATE;
+    KITC_TRY(queue_root(t, a.sc, xyz, s));
+    KITC_TRY(queue_levels(t, a.sc, t.leaf, 0, a.levels, s));
+    const BuildState *bs = a.state();
+    kitc_count_launch();
+    k_tree_finish<<<a.sc.nblk, BT, 0, s>>>(t.n, bs, a.levels, t.xs.as<double>(), a.sc.xs2.as<double>(),
+                                           t.perm.as<int32_t>(), a.sc.perm2.as<int32_t>(), err);
+    kitc_count_launch();
+    k_geometry<<<(t.cap + 255) / 256, 256, 0, s>>>(t.cap, bs, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                                 t.ctr.as<dvec4>(), t.ctrf.as<float4>());
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
 }

@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
     Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
     const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
     const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi, int sb,
-    double *__restrict__ partial)
+    double *__restrict__ partial, const int *__restrict__ nitems_dev)
 {
+    if (nitems_dev && (int)blockIdx.x >= *nitems_dev) return;  // device-planned items: past the end
     extern __shared__ double sm[];
     const int np = cb.n + 1;
     const int np2 = np * np, nw = np * win;
@@ -249,14 +250,12 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
 // children): child c writes its contribution, three 1D contractions, to
 // contrib[c - cb0], and k_upward_sum adds each parent's children in child
 // order.
-__global__ void __launch_bounds__(WT) k_upward_child(Cheb cb, int cb0, const dvec4 *__restrict__ lo,
-                                                     const dvec4 *__restrict__ hi,
-                                                     const int32_t *__restrict__ parent, int win,
-                                                     const double *__restrict__ fhat,
-                                                     double *__restrict__ contrib)
+__device__ void upward_child(const Cheb &cb, int c, const dvec4 *__restrict__ lo,
+                             const dvec4 *__restrict__ hi, const int32_t *__restrict__ parent,
+                             int win, const double *__restrict__ fhat, double *__restrict__ C,
+                             double *sm)
 {
-    extern __shared__ double sm[];
-    const int c = cb0 + blockIdx.x, p = parent[c];
+    const int p = parent[c];
     const int np = cb.n + 1, np2 = np * np, pw = np2 * np * win;
     double *T1 = sm, *T2 = T1 + pw, *M = T2 + pw;  // M[l][k'][k] = L^P_k(s^c_k')
     const dvec4 plo = lo[p], phi = hi[p], clo = lo[c], chi = hi[c];
@@ -288,13 +287,53 @@ __global__ void __launch_bounds__(WT) k_upward_child(Cheb cb, int cb0, const dve
         T2[o] = v;
     }
     __syncthreads();
-    double *C = contrib + (size_t)blockIdx.x * pw;
     for (int o = threadIdx.x; o < pw; o += WT) {  // contract k1
         int q = o % win, k3 = (o / win) % np, k2 = (o / (win * np)) % np, k1 = o / (win * np2);
         double v = 0.0;
         for (int kp = 0; kp < np; ++kp)
             v = fma(M[kp * np + k1], T2[((kp * np + k2) * np + k3) * win + q], v);
         C[o] = v;
+    }
+}
+
+__global__ void __launch_bounds__(WT) k_upward_child(Cheb cb, int cb0, const dvec4 *__restrict__ lo,
+                                                     const dvec4 *__restrict__ hi,
+                                                     const int32_t *__restrict__ parent, int win,
+                                                     const double *__restrict__ fhat,
+                                                     double *__restrict__ contrib)
+{
+    extern __shared__ double sm[];
+    const int pw = (cb.n + 1) * (cb.n + 1) * (cb.n + 1) * win;
+    upward_child(cb, cb0 + blockIdx.x, lo, hi, parent, win, fhat, contrib + (size_t)blockIdx.x * pw, sm);
+}
+
+// Level bounds from a tree's state block: the clusters of level L are
+// [*lb, *le); false when the tree has no level L.
+__device__ __forceinline__ bool level_range(const BuildState *bs, int L, int *lb, int *le)
+{
+    const int D = bs->depth;
+    if (L >= D) return false;
+    *lb = bs->level_start[L];
+    *le = L + 1 < D ? bs->level_start[L + 1] : bs->nclus;
+    return true;
+}
+
+// k_upward_child for a tree known only on the device: the children at level
+// L + 1, CTAs striding over them.
+__global__ void __launch_bounds__(WT) k_upward_child_dev(Cheb cb, const BuildState *__restrict__ bs,
+                                                         int L, const dvec4 *__restrict__ lo,
+                                                         const dvec4 *__restrict__ hi,
+                                                         const int32_t *__restrict__ parent, int win,
+                                                         const double *__restrict__ fhat,
+                                                         double *__restrict__ contrib)
+{
+    extern __shared__ double sm[];
+    int cb0, ce;
+    if (!level_range(bs, L + 1, &cb0, &ce)) return;
+    const int pw = (cb.n + 1) * (cb.n + 1) * (cb.n + 1) * win;
+    for (int c = cb0 + blockIdx.x; c < ce; c += gridDim.x) {
+        upward_child(cb, c, lo, hi, parent, win, fhat, contrib + (size_t)(c - cb0) * pw, sm);
+        __syncthreads();  // the shared tables are rewritten for the next child
     }
 }
 
@@ -315,6 +354,28 @@ __global__ void k_upward_sum(int lb, int le, int cb0, int pw, const int32_t *__r
     fhat[(size_t)p * pw + o] = a;
 }
 
+// k_upward_sum for a tree known only on the device: the parents at level L.
+__global__ void k_upward_sum_dev(const BuildState *__restrict__ bs, int L, int pw,
+                                 const int32_t *__restrict__ first_child,
+                                 const int32_t *__restrict__ n_child,
+                                 const double *__restrict__ contrib, double *__restrict__ fhat)
+{
+    int lb, le, cb0, ce;
+    if (!level_range(bs, L + 1, &cb0, &ce)) return;
+    level_range(bs, L, &lb, &le);
+    const int64_t tot = (int64_t)(le - lb) * pw;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = lb + (int)(i / pw), o = (int)(i % pw);
+        const int nch = n_child[p];
+        if (nch == 0) continue;
+        const int fc = first_child[p];
+        double a = 0.0;
+        for (int ci = 0; ci < nch; ++ci) a += contrib[(size_t)(fc + ci - cb0) * pw + o];
+        fhat[(size_t)p * pw + o] = a;
+    }
+}
+
 // fhat[c] = sum of the partials of c's work items, in item order.
 __global__ void k_weights_reduce(const int32_t *__restrict__ first_item, int pwin,
                                  const double *__restrict__ partial, double *__restrict__ fhat)
@@ -329,11 +390,13 @@ __global__ void k_weights_reduce(const int32_t *__restrict__ first_item, int pwi
     }
 }
 
+// nclus_dev given: the records of the first *nclus_dev clusters only (np3 each).
 template <bool MIXED>
 __global__ void k_pack_proxies(int64_t nrec, int win, const double *__restrict__ fhat,
-                               void *__restrict__ out)
+                               void *__restrict__ out, const int *__restrict__ nclus_dev, int np3)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (nclus_dev) nrec = min(nrec, (int64_t)*nclus_dev * np3);
     if (r >= nrec) return;
     const double *f = fhat + r * win;
     if (MIXED) {
@@ -460,10 +523,11 @@ __global__ void k_pack_pairs_flat(int64_t n, const double *__restrict__ xyz,
 // pairs of consecutive k3 points, [fx_k fx_k+1 fy_k fy_k+1][fz_k fz_k+1 0 0];
 // a missing last point has zero weight.
 __global__ void k_pack_proxy_pairs(int64_t nrows, int np, const double *__restrict__ fhat,
-                                   float4 *__restrict__ out)
+                                   float4 *__restrict__ out, const int *__restrict__ nclus_dev)
 {
     const int npair = (np + 1) / 2;
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (nclus_dev) nrows = min(nrows, (int64_t)*nclus_dev * np * np);
     if (q >= nrows * npair) return;
     int64_t r = q / npair;
     int k = (int)(q % npair) * 2;
@@ -499,7 +563,8 @@ size_t WeightsDev::bytes() const
 
 template <int ACC, bool SPLIT>
 kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
-                          const TreeDev &t, const double *w, int win, int sb, double *partial)
+                          const TreeDev &t, const double *w, int win, int sb, double *partial,
+                          const int *nitems_dev)
 {
     // every plan keeps a chunk's shared memory within CHUNK_SMEM_MAX, so one
     // attribute value per device serves all launches (no race between threads)
@@ -515,13 +580,14 @@ kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb
     kitc_count_launch();
     k_weights_chunk<ACC, SPLIT><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
                                                 t.perm.as<int32_t>(), w, win, t.lo.as<dvec4>(),
-                                                t.hi.as<dvec4>(), sb, partial);
+                                                t.hi.as<dvec4>(), sb, partial, nitems_dev);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
 
 using ChunkLauncher = kitc_status (*)(dim3, size_t, cudaStream_t, const Cheb &, const Item *,
-                                      const TreeDev &, const double *, int, int, double *);
+                                      const TreeDev &, const double *, int, int, double *,
+                                      const int *);
 
 // Launchers of k_weights_chunk<1..16, split>.
 const ChunkLauncher *chunk_table(bool split)
@@ -630,7 +696,7 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
     const ChunkLauncher *table = chunk_table(wd.split);
     if (wd.nitems > 0)
         KITC_TRY(table[wd.acc - 1](dim3((unsigned)wd.nitems, (unsigned)wd.npass), wd.smem, s, cb,
-                                   d_items, t, w_user, win, wd.sb, wd.partial.as<double>()));
+                                   d_items, t, w_user, win, wd.sb, wd.partial.as<double>(), nullptr));
     kitc_count_launch();
     k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
                                              wd.fhat.as<double>());
@@ -673,9 +739,11 @@ kitc_status pack_proxies(const TreeDev &t, WeightsDev &wd, bool mixed, cudaStrea
     unsigned g = (unsigned)((nrec + 255) / 256);
     kitc_count_launch();
     if (mixed)
-        k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
+        k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr,
+                                               nullptr, 0);
     else
-        k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr);
+        k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, wd.win, wd.fhat.as<double>(), wd.proxy.ptr,
+                                                nullptr, 0);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -765,7 +833,8 @@ kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)
     KITC_TRY(wd.proxy.reserve((size_t)32 * nrows * npair, s));
     unsigned g = (unsigned)((nrows * npair + 255) / 256);
     kitc_count_launch();
-    k_pack_proxy_pairs<<<g, 256, 0, s>>>(nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>());
+    k_pack_proxy_pairs<<<g, 256, 0, s>>>(nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>(),
+                                         nullptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -989,6 +1058,8 @@ kitc_status allow_up_smem()
     if (dev >= 0 && dev < 64 && done[dev].load()) return KITC_OK;
     KITC_CUDA(cudaFuncSetAttribute(k_upward_child, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)UP_SMEM_MAX));
+    KITC_CUDA(cudaFuncSetAttribute(k_upward_child_dev, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)UP_SMEM_MAX));
     KITC_CUDA(cudaFuncSetAttribute(k_transfer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)UP_SMEM_MAX));
     KITC_CUDA(cudaFuncSetAttribute(k_transfer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1120,7 +1191,7 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDe
         int npass = (pwin + acc * WT - 1) / (acc * WT);
         KITC_TRY(table[acc - 1](dim3((unsigned)g.nitems, (unsigned)npass), per * sb, s,
                                 make_cheb(g.degree), d_items + g.item0, t, w_user, win, sb,
-                                wd.partial.as<double>() + g.pofs));
+                                wd.partial.as<double>() + g.pofs, nullptr));
     }
     kitc_count_launch();
     k_weights_reduce_var<<<m, 256, 0, s>>>(d_r, win, d_p, d_c, wd.var_upward ? d_g : d_f,
@@ -1186,4 +1257,264 @@ const int64_t *weights_foff(const TreeDev &t, const WeightsDev &wd)
     if (!wd.planned || !wd.var) return nullptr;
     const Item *d_items = reinterpret_cast<const Item *>(wd.items.ptr);
     return reinterpret_cast<const int64_t *>(d_items + wd.nitems) + t.nclus;
+}
+
+// ---------------------------------------------------------------------------
+// Device-planned weights pass for a tree known only on the device (the
+// graph-capturable pipeline).  The plan that weights_plan and pack_pairs_plan
+// make on the host (work items in cluster order, the first pair of every leaf)
+// is made by single-block scans over the cluster capacity, with the same
+// order, so the results are bit-identical to the host-planned pass.  Every
+// buffer is sized from bounds that hold for any tree of at most cap clusters:
+//   items <= cap + (levels counted per slot) * ceil(n / CHUNK)
+//   pairs <= (n + cap) / 2 + 1   (each leaf adds at most half a pair)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Exclusive prefix of one value per thread over a block of 1024 threads;
+// *total receives the block's sum (every thread).
+__device__ int64_t block_prefix(int64_t v, int64_t *total)
+{
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+        int64_t u = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        ws[lane] = u - t;
+        if (lane == 31) tot = u;
+    }
+    __syncthreads();
+    const int64_t r = ws[w] + x - v;
+    *total = tot;
+    __syncthreads();  // ws and tot are reused by the next call
+    return r;
+}
+
+__device__ __forceinline__ int items_of(int c, int m, bool upward, const int32_t *begin,
+                                        const int32_t *end, const int32_t *n_child)
+{
+    if (c >= m || (upward && n_child[c] > 0)) return 0;
+    return (end[c] - begin[c] + CHUNK - 1) / CHUNK;
+}
+
+// first[c] (c <= cap): the first work item of cluster c, items in cluster
+// order, chunks of CHUNK slots; clamped to itemcap.  One block of 1024.
+__global__ void __launch_bounds__(1024) k_items_plan(const BuildState *__restrict__ bs, int cap,
+                                                     bool upward, const int32_t *__restrict__ begin,
+                                                     const int32_t *__restrict__ end,
+                                                     const int32_t *__restrict__ n_child,
+                                                     int32_t *__restrict__ first, int itemcap,
+                                                     int *__restrict__ nitems, int *__restrict__ err)
+{
+    const int m = min(bs->nclus, cap);
+    const int per = (cap + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
+    int64_t loc = 0;
+    for (int c = c0; c < c1; ++c) loc += items_of(c, m, upward, begin, end, n_child);
+    int64_t total = 0;
+    int64_t run = block_prefix(loc, &total);
+    for (int c = c0; c < c1; ++c) {
+        first[c] = (int32_t)min(run, (int64_t)itemcap);
+        run += items_of(c, m, upward, begin, end, n_child);
+    }
+    if (threadIdx.x == 0) {
+        first[cap] = (int32_t)min(total, (int64_t)itemcap);
+        *nitems = (int)min(total, (int64_t)itemcap);
+        if (total > itemcap) atomicOr(err, ASYNC_RECORD_OVERFLOW);
+    }
+}
+
+__global__ void k_items_fill(const BuildState *__restrict__ bs, int cap,
+                             const int32_t *__restrict__ first, const int32_t *__restrict__ begin,
+                             const int32_t *__restrict__ end, Item *__restrict__ items)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= min(bs->nclus, cap)) return;
+    const int32_t b = begin[c], e = end[c];
+    for (int i = first[c]; i < first[c + 1]; ++i) {
+        const int32_t p = b + (i - first[c]) * CHUNK;
+        items[i] = Item{c, p, min(e, p + CHUNK), 0};
+    }
+}
+
+// Paired-record plan: pb_all = [first pair per cluster (cap, -1 off the
+// leaves) | range begin (cap) | range end (cap) | first pair (cap)], one range
+// per leaf in cluster order, empty ranges after the last leaf.  One block.
+__global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restrict__ bs, int cap,
+                                                     const int32_t *__restrict__ begin,
+                                                     const int32_t *__restrict__ end,
+                                                     const int32_t *__restrict__ n_child,
+                                                     int32_t *__restrict__ pb_all, int64_t paircap,
+                                                     int *__restrict__ err)
+{
+    const int m = min(bs->nclus, cap);
+    int32_t *cpb = pb_all, *rb = pb_all + cap, *re = rb + cap, *pb = re + cap;
+    const int per = (cap + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
+    int64_t nl = 0, np = 0;
+    for (int c = c0; c < c1; ++c)
+        if (c < m && n_child[c] == 0) {
+            nl++;
+            np += (end[c] - begin[c] + 1) / 2;
+        }
+    int64_t nleaves = 0, npairs = 0;
+    int64_t r = block_prefix(nl, &nleaves);
+    int64_t q = block_prefix(np, &npairs);
+    const bool over = npairs > paircap;  // cannot happen for a valid tree (bound above)
+    for (int c = c0; c < c1; ++c) {
+        if (c < m && n_child[c] == 0) {
+            cpb[c] = over ? 0 : (int32_t)q;
+            rb[r] = begin[c];
+            re[r] = over ? begin[c] : end[c];
+            pb[r] = over ? 0 : (int32_t)q;
+            r++;
+            q += (end[c] - begin[c] + 1) / 2;
+        } else {
+            cpb[c] = -1;
+        }
+    }
+    for (int64_t k = nleaves + threadIdx.x; k < cap; k += blockDim.x) rb[k] = re[k] = pb[k] = 0;
+    if (threadIdx.x == 0 && over) atomicOr(err, ASYNC_RECORD_OVERFLOW);
+}
+
+}  // namespace
+
+int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode)
+{
+    const int64_t per = (n + CHUNK - 1) / CHUNK;
+    return (int64_t)cap + (mode == KITC_WEIGHTS_UPWARD ? 1 : levels) * per + 1;
+}
+
+kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
+                                  bool mixed, bool pairs, cudaStream_t s, WeightsDev &wd)
+{
+    const TreeDev &t = a.t;
+    const int cap = t.cap;
+    wd.release(s);
+    wd.planned = false;
+    const int np = degree + 1, np3 = np * np * np;
+    const int pwin = np3 * win;
+    const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_child_smem(np, win) <= UP_SMEM_MAX;
+    const int64_t itemcap = weights_async_itemcap(cap, a.levels, t.n,
+                                                  upward ? KITC_WEIGHTS_UPWARD : KITC_WEIGHTS_ALGORITHM1);
+    if (itemcap > INT32_MAX / 2) return KITC_ERR_OOM;
+    // items (itemcap) | first (cap + 1) | item count
+    KITC_TRY(wd.items.reserve(sizeof(Item) * itemcap + sizeof(int32_t) * (cap + 2) + 64, s));
+    const int64_t rows = std::max<int64_t>(itemcap, cap);  // item partials, then upward contributions
+    KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * rows, s));
+    KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * cap, s));
+    if (pairs) {
+        const int64_t paircap = (t.n + cap) / 2 + 1;
+        KITC_TRY(wd.proxy.reserve((size_t)32 * cap * np * np * ((np + 1) / 2), s));
+        KITC_TRY(wd.src.reserve((size_t)80 * paircap + 16, s));
+        KITC_TRY(wd.pbegin.reserve(sizeof(int32_t) * 4 * (size_t)cap + 16, s));
+        wd.paircap = paircap;
+    } else {
+        KITC_TRY(wd.proxy.reserve((size_t)proxy_record_bytes(win, mixed) * cap * np3, s));
+        KITC_TRY(wd.src.reserve((size_t)source_record_bytes(win, mixed) * t.n, s));
+        wd.paircap = 0;
+    }
+    size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
+    int sb = KITC_WEIGHTS_SB;
+    while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
+    wd.sb = sb;
+    wd.smem = per * sb;
+    wd.acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
+    wd.npass = (pwin + wd.acc * WT - 1) / (wd.acc * WT);
+    wd.nitems = (size_t)itemcap;
+    wd.upward = upward;
+    if (upward) KITC_TRY(allow_up_smem());
+    wd.split = split;
+    wd.degree = degree;
+    wd.win = win;
+    wd.mode = mode;
+    wd.var = false;
+    wd.async = true;
+    wd.planned = true;
+    return KITC_OK;
+}
+
+kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, WeightsDev &wd,
+                                 bool mixed, bool pairs, int *err, cudaStream_t s)
+{
+    if (!wd.planned || !wd.async) return KITC_ERR_STATE;
+    const TreeDev &t = a.t;
+    const BuildState *bs = a.state();
+    const int cap = t.cap, np = wd.degree + 1, win = wd.win;
+    const int np3 = np * np * np, pwin = np3 * win;
+    const int itemcap = (int)wd.nitems;
+    Item *d_items = wd.items.as<Item>();
+    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + itemcap);
+    int *d_nitems = d_first + cap + 1;
+    const Cheb cb = make_cheb(wd.degree);
+    kitc_count_launch();
+    k_items_plan<<<1, 1024, 0, s>>>(bs, cap, wd.upward, t.begin.as<int32_t>(), t.end.as<int32_t>(),
+                                    t.n_child.as<int32_t>(), d_first, itemcap, d_nitems, err);
+    kitc_count_launch();
+    k_items_fill<<<(cap + 255) / 256, 256, 0, s>>>(bs, cap, d_first, t.begin.as<int32_t>(),
+                                                   t.end.as<int32_t>(), d_items);
+    KITC_CUDA(cudaGetLastError());
+    KITC_TRY(chunk_table(wd.split)[wd.acc - 1](dim3((unsigned)itemcap, (unsigned)wd.npass), wd.smem, s,
+                                               cb, d_items, t, w_user, win, wd.sb,
+                                               wd.partial.as<double>(), d_nitems));
+    kitc_count_launch();
+    k_weights_reduce<<<cap, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(), wd.fhat.as<double>());
+    KITC_CUDA(cudaGetLastError());
+    if (wd.upward) {
+        const size_t us = upward_child_smem(np, win);
+        const unsigned gch = (unsigned)std::min(cap, 4096);
+        const unsigned gsum = (unsigned)std::min<int64_t>(((int64_t)cap * pwin + 255) / 256, 8192);
+        for (int L = a.levels - 2; L >= 0; --L) {  // deepest parents first
+            kitc_count_launch();
+            k_upward_child_dev<<<gch, WT, us, s>>>(cb, bs, L, t.lo.as<dvec4>(), t.hi.as<dvec4>(),
+                                                   t.parent.as<int32_t>(), win, wd.fhat.as<double>(),
+                                                   wd.partial.as<double>());
+            kitc_count_launch();
+            k_upward_sum_dev<<<gsum, 256, 0, s>>>(bs, L, pwin, t.first_child.as<int32_t>(),
+                                                  t.n_child.as<int32_t>(), wd.partial.as<double>(),
+                                                  wd.fhat.as<double>());
+            KITC_CUDA(cudaGetLastError());
+        }
+    }
+    const int *nclus_dev = &bs->nclus;
+    if (pairs) {
+        const int64_t nrows = (int64_t)cap * np * np, npair = (np + 1) / 2;
+        kitc_count_launch();
+        k_pack_proxy_pairs<<<(unsigned)((nrows * npair + 255) / 256), 256, 0, s>>>(
+            nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>(), nclus_dev);
+        int32_t *d = wd.pbegin.as<int32_t>();
+        kitc_count_launch();
+        k_pairs_plan<<<1, 1024, 0, s>>>(bs, cap, t.begin.as<int32_t>(), t.end.as<int32_t>(),
+                                        t.n_child.as<int32_t>(), d, wd.paircap, err);
+        kitc_count_launch();
+        k_pack_pairs<<<(unsigned)cap, 256, 0, s>>>(d + cap, d + 2 * cap, d + 3 * cap, t.n,
+                                                   t.xs.as<double>(), t.perm.as<int32_t>(), nullptr,
+                                                   w_user, wd.src.as<float>());
+    } else {
+        const int64_t nrec = (int64_t)cap * np3;
+        const unsigned g = (unsigned)((nrec + 255) / 256);
+        kitc_count_launch();
+        if (mixed)
+            k_pack_proxies<true><<<g, 256, 0, s>>>(nrec, win, wd.fhat.as<double>(), wd.proxy.ptr,
+                                                   nclus_dev, np3);
+        else
+            k_pack_proxies<false><<<g, 256, 0, s>>>(nrec, win, wd.fhat.as<double>(), wd.proxy.ptr,
+                                                    nclus_dev, np3);
+        KITC_CUDA(cudaGetLastError());
+        KITC_TRY(pack_sources(&t, nullptr, w_user, t.n, win, mixed, s, wd.src));
+    }
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
 }

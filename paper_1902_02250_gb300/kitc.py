@@ -20,7 +20,7 @@ WEIGHTS_UPWARD, WEIGHTS_ALGORITHM1 = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
            4: "device-side wait timed out", 5: "call out of order",
-           6: "size exceeds the fixed scratch of kitc_direct_noalloc"}
+           6: "size exceeds the room reserved by the call"}
 
 
 class KitcError(RuntimeError):
@@ -82,7 +82,9 @@ SYMBOLS = ["kitc_build_tree", "kitc_build_forest", "kitc_modified_weights", "kit
            "kitc_cluster_far_errors",
            "kitc_mlp_workspace_bytes",
            "kitc_mlp_forward", "kitc_mlp_loss_grad", "kitc_mlp_adam_step",
-           "kitc_peak_launch", "kitc_peak_ops_per_launch"]
+           "kitc_peak_launch", "kitc_peak_ops_per_launch",
+           "kitc_pipeline_create", "kitc_pipeline_run", "kitc_pipeline_replay",
+           "kitc_pipeline_status", "kitc_pipeline_graph_launches", "kitc_pipeline_free"]
 
 
 def library_path():
@@ -137,6 +139,13 @@ def lib():
         L.kitc_peak_launch.argtypes = [I, I, I, I, P, P]
         L.kitc_peak_ops_per_launch.argtypes = [I, I, I, I]
         L.kitc_peak_ops_per_launch.restype = ctypes.c_double
+        L.kitc_pipeline_create.argtypes = [P, P, P, P, I, PP, ctypes.c_double, P, ctypes.POINTER(P)]
+        L.kitc_pipeline_run.argtypes = [P, P, P, P, P, P]
+        L.kitc_pipeline_replay.argtypes = [P, P, P, P, P, P]
+        L.kitc_pipeline_status.argtypes = [P, ctypes.POINTER(Stats), P]
+        L.kitc_pipeline_graph_launches.argtypes = [P]
+        L.kitc_pipeline_graph_launches.restype = I64
+        L.kitc_pipeline_free.argtypes = [P]
         for name in ("kitc_build_tree", "kitc_build_forest", "kitc_evaluate_forest", "kitc_apply",
                      "kitc_modified_weights", "kitc_evaluate", "kitc_direct",
                      "kitc_direct_noalloc",
@@ -146,7 +155,9 @@ def lib():
                      "kitc_plan_targets_forest",
                      "kitc_cluster_features",
                      "kitc_cluster_far_errors", "kitc_mlp_forward", "kitc_mlp_loss_grad",
-                     "kitc_mlp_adam_step", "kitc_peak_launch"):
+                     "kitc_mlp_adam_step", "kitc_peak_launch", "kitc_pipeline_create",
+                     "kitc_pipeline_run", "kitc_pipeline_replay", "kitc_pipeline_status",
+                     "kitc_pipeline_free"):
             getattr(L, name).restype = I
         _lib = L
     return _lib
@@ -465,6 +476,88 @@ def treecode(src_xyz, w, params, tgt_xyz=None, stream=None):
         return out, t.stats()
     finally:
         t.free()
+
+
+class Pipeline:
+    """A kitc_pipeline handle (include/kitc_pipeline.h): the whole treecode
+    queued without host synchronization or allocation, sized once from
+    example inputs; run() queues it, replay() goes through the handle's CUDA
+    graph, status() waits and reports the last run."""
+
+    def __init__(self, src_xyz, params, src_counts=None, tgt_xyz=None, tgt_counts=None,
+                 slack=1.25, stream=None):
+        ns = src_xyz.shape[0]
+        sc = np.ascontiguousarray([ns] if src_counts is None else src_counts, np.int64)
+        self.self_targets = tgt_xyz is None
+        nt = ns if tgt_xyz is None else tgt_xyz.shape[0]
+        tc = None
+        if tgt_xyz is not None:
+            tc = np.ascontiguousarray([nt] if tgt_counts is None else tgt_counts, np.int64)
+            if len(tc) != len(sc):
+                raise ValueError("tgt_counts must have one entry per system")
+        self.params = params
+        self.n_src, self.n_tgt = ns, nt
+        self.num_systems = len(sc)
+        h = ctypes.c_void_p()
+        p = params.c()
+        _check(lib().kitc_pipeline_create(
+            _dptr(src_xyz, 3, "src_xyz"), _np(sc),
+            None if tgt_xyz is None else _dptr(tgt_xyz, 3, "tgt_xyz"),
+            None if tc is None else _np(tc), len(sc), ctypes.byref(p), float(slack),
+            _stream(stream), ctypes.byref(h)), "kitc_pipeline_create")
+        self._h = h.value
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("pipeline already freed")
+        return self._h
+
+    def _args(self, src_xyz, w, tgt_xyz, out):
+        import torch
+        wout = kernel_wout(self.params.kernel)
+        if out is None:
+            out = torch.empty((self.n_tgt, wout), dtype=torch.float64, device=src_xyz.device)
+        if src_xyz.shape[0] != self.n_src or (tgt_xyz is not None and tgt_xyz.shape[0] != self.n_tgt):
+            raise ValueError("sizes differ from the ones the pipeline was created for")
+        t = None if tgt_xyz is None else _dptr(tgt_xyz, 3, "tgt_xyz")
+        return (_dptr(src_xyz, 3, "src_xyz"), _dptr(w, kernel_win(self.params.kernel), "w"), t,
+                _dptr(out, wout, "out")), out
+
+    def run(self, src_xyz, w, tgt_xyz=None, out=None, stream=None):
+        a, out = self._args(src_xyz, w, tgt_xyz, out)
+        _check(lib().kitc_pipeline_run(self.handle, *a, _stream(stream)), "kitc_pipeline_run")
+        return out
+
+    def replay(self, src_xyz, w, tgt_xyz=None, out=None, stream=None):
+        a, out = self._args(src_xyz, w, tgt_xyz, out)
+        _check(lib().kitc_pipeline_replay(self.handle, *a, _stream(stream)), "kitc_pipeline_replay")
+        return out
+
+    def status(self, stream=None):
+        """(status code, stats dict) of the last run; waits for the stream."""
+        s = Stats()
+        code = lib().kitc_pipeline_status(self.handle, ctypes.byref(s), _stream(stream))
+        return code, s.as_dict()
+
+    def check(self, stream=None):
+        code, st = self.status(stream)
+        _check(code, "kitc_pipeline_status")
+        return st
+
+    def graph_launches(self):
+        return lib().kitc_pipeline_graph_launches(self.handle)
+
+    def free(self):
+        if self._h:
+            lib().kitc_pipeline_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------- degree selection

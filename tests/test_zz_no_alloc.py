@@ -9,20 +9,19 @@ allocator, nor the device's free memory change across it.  Collected last so
 that a failure here stops a run only after every other test has run; it also
 passes alone in a fresh process.
 """
-import ctypes
+import gc
 
 import numpy as np
 import pytest
 
 from paper_1902_02250_gb300 import workloads as wl
 
+from devpool import USED_MEM_HIGH, Pool
+
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 MIXED_TOL = 1e-6
-
-# CUmemPool_attribute values of the CUDA driver API (cuda.h)
-_RESERVED_MEM_CURRENT, _USED_MEM_CURRENT, _USED_MEM_HIGH = 5, 7, 8
 
 
 @pytest.fixture(scope="module")
@@ -72,27 +71,6 @@ def test_noalloc_refuses_sizes_beyond_its_scratch(K):
     assert e.value.status == 6
 
 
-class _Pool:
-    """The device's default memory pool (where cudaMallocAsync draws from),
-    read through the CUDA driver API."""
-
-    def __init__(self, ordinal):
-        self.cu = ctypes.CDLL("libcuda.so.1")
-        dev = ctypes.c_int()
-        assert self.cu.cuDeviceGet(ctypes.byref(dev), ordinal) == 0
-        self.pool = ctypes.c_void_p()
-        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
-
-    def get(self, attr):
-        v = ctypes.c_uint64()
-        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
-        return v.value
-
-    def reset_high(self):
-        zero = ctypes.c_uint64(0)  # resets the high-water mark to the current use
-        assert self.cu.cuMemPoolSetAttribute(self.pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
-
-
 def test_noalloc_allocates_nothing_after_setup(K):
     """The first call on the device is the set-up (the scratch array and the
     kernels are loaded).  Every later call -- any kernel, either precision --
@@ -109,21 +87,22 @@ def test_noalloc_allocates_nothing_after_setup(K):
             for k in (0, 1, 2)}
     calls = [(0, 1, f3), (1, 1, f3), (2, 1, f6), (0, 0, f3), (1, 0, f3), (2, 0, f6)]
     K.kitc_direct_noalloc(yd, xd, f3, K.Params(kernel=0, precision=1, eps=0.004), outs[0])
-    torch.cuda.synchronize()
-    pool = _Pool(torch.cuda.current_device())
-    before = (pool.get(_RESERVED_MEM_CURRENT), pool.get(_USED_MEM_CURRENT),
-              torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
-              torch.cuda.mem_get_info()[0])
-    pool.reset_high()
-    for kernel, prec, w in calls:
-        K.kitc_direct_noalloc(yd, xd, w, K.Params(kernel=kernel, precision=prec, eps=0.004),
-                              outs[kernel])
-    torch.cuda.synchronize()
-    after = (pool.get(_RESERVED_MEM_CURRENT), pool.get(_USED_MEM_CURRENT),
-             torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
-             torch.cuda.mem_get_info()[0])
+    pool = Pool(torch.cuda.current_device())
+    gc.collect()  # no collection inside the window: it frees test temporaries
+    gc.disable()
+    try:
+        torch.cuda.synchronize()
+        before = pool.snapshot()
+        pool.reset_high()
+        for kernel, prec, w in calls:
+            K.kitc_direct_noalloc(yd, xd, w, K.Params(kernel=kernel, precision=prec, eps=0.004),
+                                  outs[kernel])
+        torch.cuda.synchronize()
+        after = pool.snapshot()
+    finally:
+        gc.enable()
     assert after == before, (before, after)
-    assert pool.get(_USED_MEM_HIGH) == before[1]
+    assert pool.get(USED_MEM_HIGH) == before[1]
     # and the last call's result is the direct sum
     ref = K.kitc_direct(yd, xd, f6, K.Params(kernel=2, precision=0, eps=0.004)).cpu().numpy()
     assert _rel(ref, outs[2].cpu().numpy()) <= FP64_TOL
