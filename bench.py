@@ -564,6 +564,23 @@ def run_kitc(args, ws, rank, local):
             "peaks": peaks,
             "gpu_launches": int(launches), "clocks": clk}
 
+    # the same step as one CUDA graph (kitc_pipeline_replay): trees, weights, lists and
+    # evaluator with no host synchronization inside; must equal the eager result bit for bit
+    pipe = K.Pipeline(xd, p)
+    try:
+        og = torch.empty_like(out)
+        gms, _ = timed(stream, flush, lambda: pipe.replay(xd, fd, out=og), args.steps,
+                       max(3, args.warmup))
+        pipe.check()
+        gm = float(np.mean(gms))
+        line["graph"] = {"value": N / (gm / 1e3), "unit": "targets/s (this GPU)", "ms_per_step": gm,
+                         "steps": args.steps, "identical_to_eager": bool(torch.equal(og, out)),
+                         "launches_per_replay": int(pipe.graph_launches()),
+                         "what": "the whole step captured once and replayed (kitc_pipeline_replay)"}
+        del og
+    finally:
+        pipe.free()
+
     if rank == 0 and ws == 1 and not args.no_fp64:
         th64, n64, leaf64, mac64 = FP64_POINT
         pf = K.Params(theta=th64, degree=n64, leaf_size=leaf64, eps=EPS, precision=K.FP64,
@@ -764,12 +781,114 @@ def form_batched(args, rank, dev, steps, warmup, tune_it=False, fp64=True):
                                       "CUDA-graph replay"}
     finally:
         t.free()
+    gp = P(**dict(point, degree=at[0]["degree"], mac=at[0]["mac"])) if at else P(**point)
+    res["graph"] = batched_graph(K, xd, fd, x, f, counts, gp, out, flush, steps, errors)
     if fp64 and at:
         q = P(prec=K.FP64, **dict(point, degree=at[0]["degree"], mac=at[0]["mac"]))
         r64, _ = run(q, 1, 0)
         r64["point"] = "the mixed form's E <= 1e-6 point (the FP64 error is at most the mixed one there)"
         res["plain_fp64"] = r64
         res["speedup_vs_plain_fp64"] = at[0]["value"] / r64["value"]
+    return res
+
+
+# size buckets of the batched systems: (name, smallest N_s, largest N_s + 1)
+BUCKETS = (("small", 0, 8_000), ("mid", 8_000, 50_000), ("large", 50_000, 1 << 62))
+
+
+def batched_graph(K, xd, fd, x, f, counts, p, out, flush, steps, errors):
+    """The whole pipeline (forest build, weights, lists, evaluator) captured in
+    CUDA graphs (kitc_pipeline_replay): one graph for the whole forest, and
+    one per size bucket with the three replayed back to back as the step.
+    Device-resident timings with CUDA events, and end to end per bucket: the
+    bucket's pinned host inputs copied in, the replay, its result copied out,
+    timed on the host clock around synchronized steps."""
+    import torch
+    dev = xd.device
+    stream = torch.cuda.current_stream()
+    ntot = len(x)
+    res = {"point": {"theta": p.theta, "degree": p.degree, "leaf_size": p.leaf_size,
+                     "target_batch": p.target_batch, "mac": MAC_NAMES[p.mac]}}
+    # the eager forest at the same point: every graph result must equal it bit for bit
+    t = K.kitc_build_forest(xd, counts, p)
+    try:
+        K.kitc_modified_weights(t, fd)
+        out_ref = K.kitc_evaluate_forest(t, xd, counts, torch.empty_like(out))
+    finally:
+        t.free()
+    # whole forest, one graph
+    pipe = K.Pipeline(xd, p, src_counts=counts)
+    try:
+        o = torch.empty_like(out_ref)
+        l0 = K.kitc_launch_count()
+        ms, _ = timed(stream, flush, lambda: pipe.replay(xd, fd, out=o), steps, 2)
+        st = pipe.check()
+        m = float(np.mean(ms))
+        e_all, worst = errors(o.cpu().numpy())
+        res["forest"] = {"value": ntot / (m / 1e3), "ms_per_step": m, "steps": steps, "warmup": 2,
+                         "E_all": e_all, "E_worst_system": worst,
+                         "identical_to_eager": bool(torch.equal(o, out_ref)),
+                         "launches_per_replay": int(pipe.graph_launches()),
+                         "kernels_launched": int(K.kitc_launch_count() - l0),
+                         "far_points": int(st["far_points"]), "near_pairs": int(st["near_pairs"])}
+    finally:
+        pipe.free()
+    # one graph per size bucket; each bucket's systems gathered into their own arrays
+    off = np.concatenate([[0], np.cumsum(counts)])
+    buckets, full = [], torch.empty_like(out_ref)
+    for name, lo, hi in BUCKETS:
+        ks = [k for k in range(len(counts)) if lo <= counts[k] < hi]
+        if not ks:
+            continue
+        rows = np.concatenate([np.arange(off[k], off[k + 1]) for k in ks])
+        ridx = torch.from_numpy(rows).to(dev)
+        bx, bf = xd[ridx].contiguous(), fd[ridx].contiguous()
+        bo = torch.empty((len(rows), 3), dtype=torch.float64, device=dev)
+        bp = K.Pipeline(bx, p, src_counts=counts[ks])
+        buckets.append(dict(name=name, systems=len(ks), n=len(rows), ridx=ridx, x=bx, f=bf, o=bo,
+                            pipe=bp, hx=torch.from_numpy(x[rows]).pin_memory(),
+                            hf=torch.from_numpy(f[rows]).pin_memory(),
+                            ho=torch.empty((len(rows), 3), dtype=torch.float64).pin_memory()))
+    try:
+        per = []
+        for b in buckets:
+            ms, _ = timed(stream, flush, lambda b=b: b["pipe"].replay(b["x"], b["f"], out=b["o"]), steps, 2)
+            b["pipe"].check()
+            full.index_copy_(0, b["ridx"], b["o"])
+            m = float(np.mean(ms))
+            # end to end: pinned host inputs in, replay, result out, every step
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                b["x"].copy_(b["hx"], non_blocking=True)
+                b["f"].copy_(b["hf"], non_blocking=True)
+                b["pipe"].replay(b["x"], b["f"], out=b["o"])
+                b["ho"].copy_(b["o"], non_blocking=True)
+                torch.cuda.synchronize()
+            e2e = (time.perf_counter() - t0) / steps
+            b["pipe"].check()
+            per.append({"bucket": b["name"], "systems": b["systems"], "targets": b["n"],
+                        "ms_per_step": m, "value": b["n"] / (m / 1e3),
+                        "e2e": {"value": b["n"] / e2e, "unit": "targets/s", "ms_per_step": e2e * 1e3,
+                                "h2d_bytes_per_step": int(b["hx"].numel() * 8 + b["hf"].numel() * 8),
+                                "d2h_bytes_per_step": int(b["ho"].numel() * 8)},
+                        "launches_per_replay": int(b["pipe"].graph_launches())})
+
+        def all_buckets():
+            for b in buckets:
+                b["pipe"].replay(b["x"], b["f"], out=b["o"])
+
+        ms, _ = timed(stream, flush, all_buckets, steps, 1)
+        m = float(np.mean(ms))
+        e_all, worst = errors(full.cpu().numpy())
+        res["buckets"] = per
+        res["bucket_step"] = {"value": ntot / (m / 1e3), "ms_per_step": m, "steps": steps,
+                              "E_all": e_all, "E_worst_system": worst,
+                              "identical_to_eager": bool(torch.equal(full, out_ref)),
+                              "what": "the three bucket graphs replayed back to back on one stream"}
+    finally:
+        for b in buckets:
+            b["pipe"].free()
     return res
 
 
