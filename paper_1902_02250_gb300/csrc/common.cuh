@@ -158,8 +158,7 @@ struct WeightsDev {
     int degree = 0, win = 0, mode = 0;
     // plan of the weights pass (weights_plan), reused by weights_launch
     bool planned = false, upward = false;
-    size_t nitems = 0, smem = 0;
-    int acc = 1, npass = 1, sb = 8;
+    size_t nitems = 0;
     int pair_ranges = 0;  // ranges of the paired records (pack_pairs_plan)
     // degree per cluster (weights_plan_var): one Algorithm 1 launch per degree
     struct Group {

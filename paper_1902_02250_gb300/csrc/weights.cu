@@ -16,13 +16,14 @@
 // one FP64 FMA per particle.  Chunks of one cluster write partial sums that a
 // second kernel adds in a fixed order, so the result is deterministic.
 //
-// Split-precision products (SPLIT, used by the mixed-precision form): the FP64
-// basis values L and the weights f are held as FP32 pairs hi + lo (lo the
-// rounded remainder); h = L1 L2 and g = L3 f and then each product h g are
+// Split-precision products (the mixed-precision form, k_weights_split): the
+// FP64 basis values L and the weights f are held as FP32 pairs hi + lo (lo
+// the rounded remainder); h = L1 L2 and g = L3 f and then each product h g are
 // formed from pairs (the exact product of the high parts by FMA, TwoProduct,
 // plus the cross terms); runs of up to 256 particles are summed in FP32 pairs
-// with TwoSum, and each run's value is added to the FP64 accumulator.  Products carry about 2^-47 relative error; the barycentric
-// denominators and the accumulation stay FP64.
+// with TwoSum, and each run's value is added to the FP64 sum.  Products carry
+// about 2^-47 relative error; the barycentric basis and the accumulation
+// across runs stay FP64.
 #include <float.h>
 
 #include <algorithm>
@@ -116,7 +117,7 @@ __device__ __forceinline__ float2 mul_f2(float2 a, float2 b)
     return make_float2(hi, c - (hi - p));
 }
 
-template <int ACC, bool SPLIT>
+template <int ACC>
 __global__ void __launch_bounds__(WT) k_weights_chunk(
     Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
     const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
@@ -131,7 +132,6 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
     double *Ls = sm;                        // [sb][3][np]
     double *hs = Ls + (size_t)sb * 3 * np;  // [sb][np2]
     double *gs = hs + (size_t)sb * np2;     // [sb][nw]
-    float2 *wsf = reinterpret_cast<float2 *>(gs + (size_t)sb * nw);  // SPLIT: [sb][win]
     Item it = items[blockIdx.x];
     int obase = blockIdx.y * ACC * WT;
     dvec4 blo = lo[it.c], bhi = hi[it.c];
@@ -145,89 +145,28 @@ __global__ void __launch_bounds__(WT) k_weights_chunk(
         rowoff[i] = o < pwin ? o / nw : 0;
         coloff[i] = o < pwin ? o % nw : 0;
     }
-    // SPLIT: FP32-pair run sums of up to FLUSH chunks (<= FLUSH * 64 particles)
-    constexpr int FLUSH = 4;
-    float sh[ACC], sl[ACC];
-#pragma unroll
-    for (int i = 0; i < ACC; ++i) sh[i] = sl[i] = 0.f;
-    int nrun = 0;
     for (int j0 = it.p0; j0 < it.p1; j0 += sb) {
         int cnt = min(sb, it.p1 - j0);
         for (int q = threadIdx.x; q < cnt * 3; q += WT) {
             int j = q / 3, l = q % 3;
             double a = l == 0 ? blo.x : (l == 1 ? blo.y : blo.z);
             double b = l == 0 ? bhi.x : (l == 1 ? bhi.y : bhi.z);
-            double L[KITC_MAX_DEGREE + 1];
-            bary_basis(cb, a, b, xs[l * n + j0 + j], L);
-            if (SPLIT) {  // the FP64 basis as FP32 hi/lo pairs
-                float2 *Lf = reinterpret_cast<float2 *>(Ls);
-                for (int k = 0; k < np; ++k) Lf[(j * 3 + l) * np + k] = split_f2(L[k]);
-            } else {
-                for (int k = 0; k < np; ++k) Ls[(j * 3 + l) * np + k] = L[k];
-            }
+            bary_basis(cb, a, b, xs[l * n + j0 + j], Ls + (j * 3 + l) * np);
         }
-        if (SPLIT) {
-            for (int q = threadIdx.x; q < cnt * win; q += WT)
-                wsf[q] = split_f2(w[(int64_t)perm[j0 + q / win] * win + q % win]);
-            __syncthreads();
-            // h = L1 L2 and g = L3 f as FP32 pairs: products of pairs (TwoProduct)
-            const float2 *Lf = reinterpret_cast<const float2 *>(Ls);
-            for (int q = threadIdx.x; q < cnt * np2; q += WT) {
-                int j = q / np2, r = q % np2;
-                reinterpret_cast<float2 *>(hs)[j * np2 + r] =
-                    mul_f2(Lf[(j * 3 + 0) * np + r / np], Lf[(j * 3 + 1) * np + r % np]);
-            }
-            for (int q = threadIdx.x; q < cnt * nw; q += WT) {
-                int j = q / nw, r = q % nw;
-                reinterpret_cast<float2 *>(gs)[j * nw + r] =
-                    mul_f2(Lf[(j * 3 + 2) * np + r / win], wsf[j * win + r % win]);
-            }
-            __syncthreads();
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt * np2; q += WT) {
+            int j = q / np2, r = q % np2;
+            hs[j * np2 + r] = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
         }
-        if (!SPLIT) {
-            __syncthreads();
-            for (int q = threadIdx.x; q < cnt * np2; q += WT) {
-                int j = q / np2, r = q % np2;
-                hs[j * np2 + r] = Ls[(j * 3 + 0) * np + r / np] * Ls[(j * 3 + 1) * np + r % np];
-            }
-            for (int q = threadIdx.x; q < cnt * nw; q += WT) {
-                int j = q / nw, r = q % nw;
-                gs[j * nw + r] = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
-            }
-            __syncthreads();
+        for (int q = threadIdx.x; q < cnt * nw; q += WT) {
+            int j = q / nw, r = q % nw;
+            gs[j * nw + r] = Ls[(j * 3 + 2) * np + r / win] * w[(int64_t)perm[j0 + j] * win + r % win];
         }
-        if constexpr (SPLIT) {
-            const float2 *h2 = reinterpret_cast<const float2 *>(hs);
-            const float2 *g2 = reinterpret_cast<const float2 *>(gs);
-            for (int j = 0; j < cnt; ++j) {
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const double *h = hs + j * np2, *g = gs + j * nw;
 #pragma unroll
-                for (int i = 0; i < ACC; ++i) {
-                    const float2 a = h2[j * np2 + rowoff[i]], b = g2[j * nw + coloff[i]];
-                    const float p = a.x * b.x;
-                    const float e = __fmaf_rn(a.x, b.x, -p);                       // a.x b.x = p + e
-                    const float c = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));  // + cross terms
-                    const float t = sh[i] + p;                                     // TwoSum(sh, p)
-                    const float bb = t - sh[i];
-                    const float err = (sh[i] - (t - bb)) + (p - bb);
-                    sh[i] = t;
-                    sl[i] += err + c;
-                }
-            }
-            // into the FP64 sums every FLUSH chunks and at the item's end
-            if (++nrun == FLUSH || j0 + sb >= it.p1) {
-#pragma unroll
-                for (int i = 0; i < ACC; ++i) {
-                    acc[i] += (double)sh[i] + (double)sl[i];
-                    sh[i] = sl[i] = 0.f;
-                }
-                nrun = 0;
-            }
-        } else {
-            for (int j = 0; j < cnt; ++j) {
-                const double *h = hs + j * np2, *g = gs + j * nw;
-#pragma unroll
-                for (int i = 0; i < ACC; ++i) acc[i] = fma(h[rowoff[i]], g[coloff[i]], acc[i]);
-            }
+            for (int i = 0; i < ACC; ++i) acc[i] = fma(h[rowoff[i]], g[coloff[i]], acc[i]);
         }
         __syncthreads();
     }
@@ -561,7 +500,7 @@ size_t WeightsDev::bytes() const
     return fhat.bytes + proxy.bytes + src.bytes + pbegin.bytes + partial.bytes + items.bytes;
 }
 
-template <int ACC, bool SPLIT>
+template <int ACC>
 kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb, const Item *items,
                           const TreeDev &t, const double *w, int win, int sb, double *partial,
                           const int *nitems_dev)
@@ -573,14 +512,14 @@ kitc_status launch_chunks(dim3 grid, size_t smem, cudaStream_t s, const Cheb &cb
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !configured[dev].load()) {
-        KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC, SPLIT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SMEM_MAX));
+        KITC_CUDA(cudaFuncSetAttribute(k_weights_chunk<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CHUNK_SMEM_MAX));
         if (dev >= 0 && dev < 64) configured[dev].store(1);
     }
     kitc_count_launch();
-    k_weights_chunk<ACC, SPLIT><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(),
-                                                t.perm.as<int32_t>(), w, win, t.lo.as<dvec4>(),
-                                                t.hi.as<dvec4>(), sb, partial, nitems_dev);
+    k_weights_chunk<ACC><<<grid, WT, smem, s>>>(cb, items, t.n, t.xs.as<double>(), t.perm.as<int32_t>(), w,
+                                                win, t.lo.as<dvec4>(), t.hi.as<dvec4>(), sb, partial,
+                                                nitems_dev);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -589,25 +528,348 @@ using ChunkLauncher = kitc_status (*)(dim3, size_t, cudaStream_t, const Cheb &, 
                                       const TreeDev &, const double *, int, int, double *,
                                       const int *);
 
-// Launchers of k_weights_chunk<1..16, split>.
-const ChunkLauncher *chunk_table(bool split)
+// Launchers of k_weights_chunk<1..16>.
+const ChunkLauncher *chunk_table()
 {
     static constexpr ChunkLauncher t64[ACC_MAX] = {
-        &launch_chunks<1, false>, &launch_chunks<2, false>, &launch_chunks<3, false>,
-        &launch_chunks<4, false>, &launch_chunks<5, false>, &launch_chunks<6, false>,
-        &launch_chunks<7, false>, &launch_chunks<8, false>, &launch_chunks<9, false>,
-        &launch_chunks<10, false>, &launch_chunks<11, false>, &launch_chunks<12, false>,
-        &launch_chunks<13, false>, &launch_chunks<14, false>, &launch_chunks<15, false>,
-        &launch_chunks<16, false>};
-    static constexpr ChunkLauncher t32[ACC_MAX] = {
-        &launch_chunks<1, true>, &launch_chunks<2, true>, &launch_chunks<3, true>,
-        &launch_chunks<4, true>, &launch_chunks<5, true>, &launch_chunks<6, true>,
-        &launch_chunks<7, true>, &launch_chunks<8, true>, &launch_chunks<9, true>,
-        &launch_chunks<10, true>, &launch_chunks<11, true>, &launch_chunks<12, true>,
-        &launch_chunks<13, true>, &launch_chunks<14, true>, &launch_chunks<15, true>,
-        &launch_chunks<16, true>};
-    return split ? t32 : t64;
+        &launch_chunks<1>, &launch_chunks<2>, &launch_chunks<3>, &launch_chunks<4>,
+        &launch_chunks<5>, &launch_chunks<6>, &launch_chunks<7>, &launch_chunks<8>,
+        &launch_chunks<9>, &launch_chunks<10>, &launch_chunks<11>, &launch_chunks<12>,
+        &launch_chunks<13>, &launch_chunks<14>, &launch_chunks<15>, &launch_chunks<16>};
+    return t64;
 }
+
+// ---------------------------------------------------------------------------
+// Split-precision Algorithm 1 with register tiles (the mixed form's weights).
+// * The two FP32 lanes of a packed FP32x2 instruction carry two consecutive
+//   particles: h = L1 L2 and g = L3 f are stored pair-interleaved,
+//   [hi_j hi_j+1 lo_j lo_j+1] per row (column), so one 128-bit shared load
+//   gives a row's (column's) values for both particles.
+// * Each thread owns an R x C tile of outputs (rows (k1, k2), columns
+//   (k3, q)) and loads R + C values per particle pair for R C products.
+// * Per product the arithmetic is TwoProduct of the high parts (by FMA), the
+//   cross terms, TwoSum into the running FP32 pair; each lane sums every other
+//   particle of a run, and the two lanes are added (TwoSum) when the run is
+//   folded into the FP64 sum.
+// * The FP64 basis takes the grid points once per item and one reciprocal per
+//   axis (bary_basis_split).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SplitPlan {
+    int R = 0, C = 0, TR = 0, TC = 0, np2pad = 0, nwpad = 0, sb = 0, npass = 0;
+    size_t smem = 0;
+};
+
+// a - b on both lanes (PTX sub.rn.f32x2)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long ra = *reinterpret_cast<const unsigned long long *>(&a);
+    unsigned long long rb = *reinterpret_cast<const unsigned long long *>(&b);
+    unsigned long long rd;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<const float2 *>(&rd);
+}
+
+// Barycentric basis of the coordinate y at the grid points s[0..n] of an
+// interval of width 1/iw, written to Lj as FP32 hi/lo pairs.  The same
+// values as bary_basis (the second barycentric form, Eq. Barycentric-1D)
+// with the same coincident-point rule: numerator and denominator multiplied
+// by prod_j (y - s_j) iw, so that
+//   L_k = w_k P_k / sum_j w_j P_j,   P_k = prod_{j != k} (y - s_j) iw,
+// from prefix and suffix products and one reciprocal instead of one per
+// point.  iw keeps every factor in [-1, 1]; the factors other than the
+// nearest point's are at least half a Chebyshev spacing, so the largest P_k
+// cannot underflow.  The FP64 values are formed in the 8-byte slots of Lj and
+// split in place.
+__device__ __forceinline__ void bary_basis_split(const Cheb &cb, const double *__restrict__ s, double iw,
+                                                 double y, float2 *Lj)
+{
+    const int np = cb.n + 1;
+    double *Ld = reinterpret_cast<double *>(Lj);
+    int flag = -1;
+    double pre = 1.0;
+    for (int k = 0; k < np; ++k) {
+        const double d = y - s[k];
+        // |d| <= DBL_MIN, tested on the bits (d is finite)
+        if ((__double_as_longlong(d) & 0x7fffffffffffffffll) <= 0x0010000000000000ll) flag = k;
+        Ld[k] = pre;
+        pre *= d * iw;
+    }
+    if (flag >= 0) {
+        for (int k = 0; k < np; ++k) Lj[k] = make_float2(k == flag ? 1.f : 0.f, 0.f);
+        return;
+    }
+    double suf = 1.0, D = 0.0;
+    for (int k = np - 1; k >= 0; --k) {
+        const double pk = Ld[k] * suf;
+        Ld[k] = pk;
+        D = fma(cb.w[k], pk, D);
+        suf *= (y - s[k]) * iw;
+    }
+    const double rD = __drcp_rn(D);
+    for (int k = 0; k < np; ++k) Lj[k] = split_f2(Ld[k] * (cb.w[k] * rD));
+}
+
+template <int R, int C>
+__global__ void __launch_bounds__(WT, 2) k_weights_split(
+    Cheb cb, const Item *__restrict__ items, int64_t n, const double *__restrict__ xs,
+    const int32_t *__restrict__ perm, const double *__restrict__ w, int win,
+    const dvec4 *__restrict__ lo, const dvec4 *__restrict__ hi, SplitPlan sp,
+    double *__restrict__ partial, const int *__restrict__ nitems_dev)
+{
+    if (nitems_dev && (int)blockIdx.x >= *nitems_dev) return;  // device-planned items: past the end
+    extern __shared__ float4 smf4[];
+    const int np = cb.n + 1, np2 = np * np, nw = np * win, pwin = np2 * nw;
+    const int sb = sp.sb, np2pad = sp.np2pad, nwpad = sp.nwpad;
+    float4 *h4 = smf4;                                            // [sb/2][np2pad]
+    float4 *g4 = h4 + (size_t)(sb / 2) * np2pad;                  // [sb/2][nwpad]
+    float2 *Lf = reinterpret_cast<float2 *>(g4 + (size_t)(sb / 2) * nwpad);  // [sb][3][np]
+    float2 *wsf = Lf + (size_t)sb * 3 * np;                       // [sb][win]
+    double *sg = reinterpret_cast<double *>(wsf + (size_t)sb * win);  // [3][np] grid points
+    double *siw = sg + 3 * np;                                    // [3] 1 / box width
+    uint8_t *tk1 = reinterpret_cast<uint8_t *>(siw + 3);          // row r = (k1, k2)
+    uint8_t *tk2 = tk1 + np2pad;
+    uint8_t *tk3 = tk2 + np2pad;                                  // column c = (k3, q)
+    uint8_t *tq = tk3 + nwpad;
+    const Item it = items[blockIdx.x];
+    const dvec4 blo = lo[it.c], bhi = hi[it.c];
+    // the item's grid points (the expression of bary_basis) and index tables
+    for (int t = threadIdx.x; t < 3 * np; t += WT) {
+        const int l = t / np, k = t % np;
+        const double a = l == 0 ? blo.x : (l == 1 ? blo.y : blo.z);
+        const double b = l == 0 ? bhi.x : (l == 1 ? bhi.y : bhi.z);
+        sg[t] = __dmul_rn(0.5, __dadd_rn(__dadd_rn(a, b), __dmul_rn(cb.t[k], __dsub_rn(b, a))));
+    }
+    if (threadIdx.x < 3) {
+        const int l = threadIdx.x;
+        const double a = l == 0 ? blo.x : (l == 1 ? blo.y : blo.z);
+        const double b = l == 0 ? bhi.x : (l == 1 ? bhi.y : bhi.z);
+        siw[l] = b > a ? __drcp_rn(__dsub_rn(b, a)) : 0.0;  // a flat axis: every point coincides
+    }
+    for (int t = threadIdx.x; t < np2pad; t += WT) {
+        tk1[t] = (uint8_t)(t < np2 ? t / np : 0);
+        tk2[t] = (uint8_t)(t < np2 ? t % np : 0);
+    }
+    for (int t = threadIdx.x; t < nwpad; t += WT) {
+        tk3[t] = (uint8_t)(t < nw ? t / win : 0);
+        tq[t] = (uint8_t)(t < nw ? t % win : 0);
+    }
+    // this thread's start and stride in the (particle, row), (particle, column)
+    // and (particle, component) loops of a round: no division inside them
+    const int jh0 = threadIdx.x / np2pad, rh0 = threadIdx.x % np2pad;
+    const int djh = WT / np2pad, drh = WT % np2pad;
+    const int jg0 = threadIdx.x / nwpad, cg0 = threadIdx.x % nwpad;
+    const int djg = WT / nwpad, dcg = WT % nwpad;
+    const int jw0 = threadIdx.x / win, qw0 = threadIdx.x % win;
+    const int djw = WT / win, dqw = WT % win;
+    const int q = blockIdx.y * WT + threadIdx.x;
+    const bool active = q < sp.TR * sp.TC;
+    const int r0 = active ? (q / sp.TC) * R : 0, c0 = active ? (q % sp.TC) * C : 0;
+    // the FP64 sums live in this item's partial row (each output has one
+    // owner thread), touched once per run; the FP32 pairs in registers
+    double *dst = partial + (size_t)blockIdx.x * pwin;
+    float2 SH[R][C], SL[R][C];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int k = 0; k < C; ++k) SH[i][k] = SL[i][k] = make_float2(0.f, 0.f);
+    constexpr int FLUSH = 4;  // chunks per FP32 run
+    int nrun = 0;
+    bool first = true;
+    __syncthreads();
+    for (int j0 = it.p0; j0 < it.p1; j0 += sb) {
+        const int cnt = min(sb, it.p1 - j0), cnt2 = (cnt + 1) & ~1;
+        for (int t = threadIdx.x; t < cnt * 3; t += WT) {
+            const int j = t / 3, l = t % 3;
+            bary_basis_split(cb, sg + l * np, siw[l], xs[l * n + j0 + j], Lf + (j * 3 + l) * np);
+        }
+        for (int j = jw0, qq = qw0; j < cnt;) {
+            wsf[j * win + qq] = split_f2(w[(int64_t)perm[j0 + j] * win + qq]);
+            j += djw;
+            qq += dqw;
+            if (qq >= win) {
+                qq -= win;
+                ++j;
+            }
+        }
+        __syncthreads();
+        // h and g of the round, pair-interleaved; padding rows, columns and the
+        // missing partner of an odd last particle are zero
+        for (int j = jh0, r = rh0; j < cnt2;) {
+            float2 v = make_float2(0.f, 0.f);
+            if (j < cnt && r < np2) v = mul_f2(Lf[(j * 3 + 0) * np + tk1[r]], Lf[(j * 3 + 1) * np + tk2[r]]);
+            float *d = reinterpret_cast<float *>(h4 + (size_t)(j >> 1) * np2pad + r);
+            d[j & 1] = v.x;
+            d[2 + (j & 1)] = v.y;
+            j += djh;
+            r += drh;
+            if (r >= np2pad) {
+                r -= np2pad;
+                ++j;
+            }
+        }
+        for (int j = jg0, c = cg0; j < cnt2;) {
+            float2 v = make_float2(0.f, 0.f);
+            if (j < cnt && c < nw) v = mul_f2(Lf[(j * 3 + 2) * np + tk3[c]], wsf[j * win + tq[c]]);
+            float *d = reinterpret_cast<float *>(g4 + (size_t)(j >> 1) * nwpad + c);
+            d[j & 1] = v.x;
+            d[2 + (j & 1)] = v.y;
+            j += djg;
+            c += dcg;
+            if (c >= nwpad) {
+                c -= nwpad;
+                ++j;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            const float4 *hp = h4 + r0, *gp = g4 + c0;
+            for (int jp = 0; jp < cnt2 / 2; ++jp, hp += np2pad, gp += nwpad) {
+                float4 B[C];
+                float2 nbh[C];
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    B[k] = gp[k];
+                    nbh[k] = sub2(make_float2(0.f, 0.f), make_float2(B[k].x, B[k].y));
+                }
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float4 A = hp[i];
+                    const float2 ah = make_float2(A.x, A.y), al = make_float2(A.z, A.w);
+#pragma unroll
+                    for (int k = 0; k < C; ++k) {
+                        const float2 bh = make_float2(B[k].x, B[k].y), bl = make_float2(B[k].z, B[k].w);
+                        const float2 p = __fmul2_rn(ah, bh);
+                        const float2 en = __ffma2_rn(ah, nbh[k], p);  // p - ah bh, exact (= -e)
+                        const float2 c = sub2(__ffma2_rn(ah, bl, __fmul2_rn(al, bh)), en);
+                        const float2 t = __fadd2_rn(SH[i][k], p);      // TwoSum(SH, p)
+                        const float2 bb = sub2(t, SH[i][k]);
+                        const float2 er = __fadd2_rn(sub2(SH[i][k], sub2(t, bb)), sub2(p, bb));
+                        SH[i][k] = t;
+                        SL[i][k] = __fadd2_rn(SL[i][k], __fadd2_rn(er, c));
+                    }
+                }
+            }
+        }
+        // into the FP64 sums every FLUSH chunks and at the item's end: the two
+        // lanes added by TwoSum first
+        if (++nrun == FLUSH || j0 + sb >= it.p1) {
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    const float a = SH[i][k].x, b = SH[i][k].y;
+                    const float s = a + b, bb = s - a;
+                    const float e = (a - (s - bb)) + (b - bb);
+                    const double run = (double)s + (double)((SL[i][k].x + SL[i][k].y) + e);
+                    if (active && r0 + i < np2 && c0 + k < nw) {
+                        double *o = dst + (r0 + i) * nw + c0 + k;
+                        *o = first ? run : *o + run;
+                    }
+                    SH[i][k] = SL[i][k] = make_float2(0.f, 0.f);
+                }
+            nrun = 0;
+            first = false;
+        }
+        __syncthreads();
+    }
+}
+
+// Tile shape of the split kernel for degree np - 1: among R, C in 2..4 with
+// R C <= 12 (two CTAs of 256 threads per SM at <= 128 registers), the fewest
+// passes over the particles (each pass stages the bases again), then the
+// least work per thread, then the fewest tiles.
+SplitPlan split_plan(int np, int win)
+{
+    const int np2 = np * np, nw = np * win;
+    SplitPlan best;
+    int64_t best_cost = -1;
+    for (int R = 2; R <= 4; ++R)
+        for (int C = 2; C <= 4; ++C) {
+            if (R * C > 12) continue;
+            const int TR = (np2 + R - 1) / R, TC = (nw + C - 1) / C, tiles = TR * TC;
+            const int passes = (tiles + WT - 1) / WT;
+            const int64_t cost = ((int64_t)passes * (R * C + 6)) * 1000000 + tiles;
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                best.R = R;
+                best.C = C;
+                best.TR = TR;
+                best.TC = TC;
+                best.npass = passes;
+            }
+        }
+    best.np2pad = best.TR * best.R;
+    best.nwpad = best.TC * best.C;
+    const size_t per = 8 * ((size_t)best.np2pad + best.nwpad + 3 * (size_t)np + win);  // bytes per particle
+    // grid points, box widths and the index tables
+    const size_t fixed = 8 * (3 * (size_t)np + 3) + 2 * ((size_t)best.np2pad + best.nwpad) + 16;
+    int sb = KITC_WEIGHTS_SB;
+    while (sb > 8 && per * sb + fixed > CHUNK_SMEM_MAX) sb /= 2;
+    best.sb = sb;
+    best.smem = per * sb + fixed;
+    return best;
+}
+
+template <int R, int C>
+kitc_status launch_split_rc(dim3 grid, const SplitPlan &sp, cudaStream_t s, const Cheb &cb,
+                            const Item *items, const TreeDev &t, const double *w, int win,
+                            double *partial, const int *nitems_dev)
+{
+    static std::atomic<int> configured[64] = {};  // one attribute value per device, never changed
+    int dev = 0;
+    KITC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !configured[dev].load()) {
+        KITC_CUDA(cudaFuncSetAttribute(k_weights_split<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)CHUNK_SMEM_MAX));
+        if (dev >= 0 && dev < 64) configured[dev].store(1);
+    }
+    kitc_count_launch();
+    k_weights_split<R, C><<<grid, WT, sp.smem, s>>>(cb, items, t.n, t.xs.as<double>(), t.perm.as<int32_t>(),
+                                                    w, win, t.lo.as<dvec4>(), t.hi.as<dvec4>(), sp, partial,
+                                                    nitems_dev);
+    KITC_CUDA(cudaGetLastError());
+    return KITC_OK;
+}
+
+// Algorithm 1 over nitems work items (grid.x; with nitems_dev, items past
+// *nitems_dev exit): the tiled split kernel for the mixed form, else the FP64
+// k_weights_chunk with the fewest accumulators per thread that cover the
+// outputs in one pass.
+kitc_status launch_items(bool split, int degree, int win, int64_t nitems, const Item *items,
+                         const TreeDev &t, const double *w, double *partial, const int *nitems_dev,
+                         cudaStream_t s)
+{
+    if (nitems <= 0) return KITC_OK;
+    const int np = degree + 1, pwin = np * np * np * win;
+    const Cheb cb = make_cheb(degree);
+    if (split) {
+        const SplitPlan sp = split_plan(np, win);
+        if (sp.smem > CHUNK_SMEM_MAX) return KITC_ERR_INVALID_ARG;
+        const dim3 grid((unsigned)nitems, (unsigned)sp.npass);
+        switch (sp.R * 10 + sp.C) {
+        case 22: return launch_split_rc<2, 2>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 23: return launch_split_rc<2, 3>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 24: return launch_split_rc<2, 4>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 32: return launch_split_rc<3, 2>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 33: return launch_split_rc<3, 3>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 34: return launch_split_rc<3, 4>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 42: return launch_split_rc<4, 2>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        case 43: return launch_split_rc<4, 3>(grid, sp, s, cb, items, t, w, win, partial, nitems_dev);
+        default: return KITC_ERR_INVALID_ARG;
+        }
+    }
+    const size_t per = sizeof(double) * (3 * np + np * np + np * win);
+    int sb = KITC_WEIGHTS_SB;
+    while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
+    const int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
+    const int npass = (pwin + acc * WT - 1) / (acc * WT);
+    return chunk_table()[acc - 1](dim3((unsigned)nitems, (unsigned)npass), per * sb, s, cb, items, t, w,
+                                  win, sb, partial, nitems_dev);
+}
+
+}  // namespace
 
 size_t upward_child_smem(int np, int win)
 {
@@ -666,14 +928,6 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
     // the host vectors must outlive the copies above
     KITC_CUDA(cudaStreamSynchronize(s));
-    size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
-    int sb = KITC_WEIGHTS_SB;
-    while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
-    wd.sb = sb;
-    wd.smem = per * sb;
-    // the fewest accumulators per thread that cover the outputs in one pass
-    wd.acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
-    wd.npass = (pwin + wd.acc * WT - 1) / (wd.acc * WT);
     wd.nitems = nitems;
     wd.upward = upward;
     if (upward) KITC_TRY(allow_up_smem());
@@ -693,10 +947,8 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
     Item *d_items = wd.items.as<Item>();
     int32_t *d_first = reinterpret_cast<int32_t *>(d_items + wd.nitems);
     const Cheb cb = make_cheb(wd.degree);
-    const ChunkLauncher *table = chunk_table(wd.split);
-    if (wd.nitems > 0)
-        KITC_TRY(table[wd.acc - 1](dim3((unsigned)wd.nitems, (unsigned)wd.npass), wd.smem, s, cb,
-                                   d_items, t, w_user, win, wd.sb, wd.partial.as<double>(), nullptr));
+    KITC_TRY(launch_items(wd.split, wd.degree, win, (int64_t)wd.nitems, d_items, t, w_user,
+                          wd.partial.as<double>(), nullptr, s));
     kitc_count_launch();
     k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
                                              wd.fhat.as<double>());
@@ -1181,18 +1433,9 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDe
     int32_t *d_r = d_c + m, *d_a = d_r + m, *d_d = d_a + m;
     const Cheb *d_cheb = reinterpret_cast<const Cheb *>(
         (reinterpret_cast<uintptr_t>(d_d + m) + 15) & ~static_cast<uintptr_t>(15));
-    const ChunkLauncher *table = chunk_table(wd.split);
-    for (const auto &g : wd.groups) {
-        int np = g.degree + 1, pwin = np * np * np * win;
-        size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
-        int sb = 64;
-        while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
-        int acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
-        int npass = (pwin + acc * WT - 1) / (acc * WT);
-        KITC_TRY(table[acc - 1](dim3((unsigned)g.nitems, (unsigned)npass), per * sb, s,
-                                make_cheb(g.degree), d_items + g.item0, t, w_user, win, sb,
-                                wd.partial.as<double>() + g.pofs, nullptr));
-    }
+    for (const auto &g : wd.groups)
+        KITC_TRY(launch_items(wd.split, g.degree, win, (int64_t)g.nitems, d_items + g.item0, t, w_user,
+                              wd.partial.as<double>() + g.pofs, nullptr, s));
     kitc_count_launch();
     k_weights_reduce_var<<<m, 256, 0, s>>>(d_r, win, d_p, d_c, wd.var_upward ? d_g : d_f,
                                            wd.partial.as<double>(), wd.fhat.as<double>());
@@ -1426,13 +1669,6 @@ kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int m
         KITC_TRY(wd.src.reserve((size_t)source_record_bytes(win, mixed) * t.n, s));
         wd.paircap = 0;
     }
-    size_t per = sizeof(double) * (3 * np + np * np + np * win + win);
-    int sb = KITC_WEIGHTS_SB;
-    while (sb > 8 && per * sb > CHUNK_SMEM_MAX) sb /= 2;
-    wd.sb = sb;
-    wd.smem = per * sb;
-    wd.acc = std::min(ACC_MAX, (pwin + WT - 1) / WT);
-    wd.npass = (pwin + wd.acc * WT - 1) / (wd.acc * WT);
     wd.nitems = (size_t)itemcap;
     wd.upward = upward;
     if (upward) KITC_TRY(allow_up_smem());
@@ -1466,9 +1702,8 @@ kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, Weigh
     k_items_fill<<<(cap + 255) / 256, 256, 0, s>>>(bs, cap, d_first, t.begin.as<int32_t>(),
                                                    t.end.as<int32_t>(), d_items);
     KITC_CUDA(cudaGetLastError());
-    KITC_TRY(chunk_table(wd.split)[wd.acc - 1](dim3((unsigned)itemcap, (unsigned)wd.npass), wd.smem, s,
-                                               cb, d_items, t, w_user, win, wd.sb,
-                                               wd.partial.as<double>(), d_nitems));
+    KITC_TRY(launch_items(wd.split, wd.degree, win, itemcap, d_items, t, w_user, wd.partial.as<double>(),
+                          d_nitems, s));
     kitc_count_launch();
     k_weights_reduce<<<cap, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(), wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
