@@ -379,22 +379,35 @@ def eval_roofline(kernel, flops_per, useful, executed, ms, peak, peak_source, tr
 
 
 def weights_roofline(st, n, win, ms, peaks, split):
-    """Modified weights (Algorithm 1 on the leaves, upward pass to the parents):
-    FP64-equivalent flops per source: (n+1)^3 w_in FMAs, (n+1)^2 + (n+1)^3
-    basis products; per child cluster 3 (n+1)^4 w_in FMAs of the upward pass."""
+    """Modified weights (Algorithm 1 on the leaves, upward pass to the parents).
+    FP64 form: FP64-equivalent flops per source, (n+1)^3 w_in FMAs plus
+    (n+1)^2 + (n+1)^3 basis products, and per child cluster 3 (n+1)^4 w_in
+    FMAs of the upward pass, against the measured FP64 FMA rate.  Mixed form
+    (k_weights_split): the FP32 lane operations of its split arithmetic, 13 per
+    (source, output) -- TwoProduct by FMA, the cross terms, TwoSum and the
+    low-part sum, two particles per packed FP32x2 instruction -- against the
+    measured FP32 FMA rate in lane operations (half its flop rate)."""
     p1 = n + 1
     per_src = 2 * p1 ** 3 * win + p1 ** 2 + p1 ** 3
     upward = 2 * 3 * p1 ** 4 * win * max(st["n_clusters"] - 1, 0)
     flops = st["n_sources"] * per_src + upward
-    achieved = flops / (ms / 1e3) / 1e12
-    peak = peaks["fp32_tflops"] if split else peaks["fp64_tflops"]
-    return {"kernel": "k_weights_chunk + k_weights_reduce + k_upward_child/_sum (+ record packing)",
-            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    fp64_eq = flops / (ms / 1e3) / 1e12
+    if not split:
+        peak = peaks["fp64_tflops"]
+        return {"kernel": "k_weights_chunk + k_weights_reduce + k_upward_child/_sum (+ record packing)",
+                "bound": "alu", "achieved": fp64_eq, "peak": peak, "unit": "TFLOP/s",
+                "frac": fp64_eq / peak, "peak_source": "measured FP64 FMA rate",
+                "flops": flops, "stage_ms": ms, "traffic": None}
+    lane_ops = 13.0 * st["n_sources"] * p1 ** 3 * win
+    achieved = lane_ops / (ms / 1e3) / 1e12
+    peak = peaks["fp32_tflops"] / 2
+    return {"kernel": "k_weights_split + k_weights_reduce + k_upward_child/_sum (+ record packing)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-ops/s",
             "frac": achieved / peak,
-            "peak_source": ("measured FP32 FMA rate: the products run in split FP32 arithmetic "
-                            "(FP64-equivalent flops counted)" if split else "measured FP64 FMA rate"),
-            "vs_fp64_pipe": achieved / peaks["fp64_tflops"],
-            "flops": flops, "stage_ms": ms, "traffic": None}
+            "peak_source": "measured FP32 FMA rate (max of scalar and packed FP32x2), in lane operations",
+            "work": "13 FP32 lane operations per (source, output) of the split arithmetic",
+            "lane_ops": lane_ops, "fp64_equivalent_tflops": fp64_eq,
+            "vs_fp64_pipe": fp64_eq / peaks["fp64_tflops"], "stage_ms": ms, "traffic": None}
 
 
 def tree_roofline(n, depth, ms):
