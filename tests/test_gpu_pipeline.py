@@ -14,6 +14,8 @@ with the oracle):
 * a forest of 12 systems through the handle's CUDA graph, replayed on new
   values written into the same buffers, with exact interaction counts and no
   allocation across replays;
+* a forest whose systems have target sets of their own (rotlet, per-target
+  MAC, batches of 48), through run() and the graph;
 * an input that needs more levels and entries than reserved: the run stays in
   bounds, reports KITC_ERR_TOO_LARGE, and the next run that fits is exact again.
 """
@@ -141,6 +143,40 @@ def test_pipeline_forest_graph_replay_bit_for_bit(K):
             assert torch.equal(out, ref), (step, float((out - ref).abs().max()))
             same_counts(st, rst)
         assert pipe.graph_launches() > 20
+    finally:
+        pipe.free()
+
+
+def test_pipeline_forest_with_own_targets(K):
+    """A forest whose systems have target sets of their own, of other sizes than
+    their sources (rotlet, per-target MAC, batches of 48), through run() and
+    replay(): bit-identical to the eager forest, exact counts."""
+    import torch
+    systems = wl.batched_systems(7, 87, nmin=1500, nmax=25_000)
+    sc = np.array([len(s[0]) for s in systems], np.int64)
+    g = wl.rng(88)
+    tgts = []
+    for xs, _ in systems:
+        lo, hi = xs.min(0), xs.max(0)
+        tgts.append(lo + (hi - lo) * g.uniform(0.0, 1.0, size=(int(g.integers(100, 9000)), 3)))
+    tc = np.array([len(t) for t in tgts], np.int64)
+    x = np.concatenate([s[0] for s in systems])
+    f = np.concatenate([s[1] for s in systems])
+    y = np.concatenate(tgts)
+    p = K.Params(theta=0.65, degree=6, leaf_size=800, eps=2e-3, kernel=K.ROTLET, precision=K.MIXED,
+                 mac=K.MAC_PARTICLE, target_batch=48)
+    xd, fd, yd = dev(x), dev(f), dev(y)
+    pipe = K.Pipeline(xd, p, src_counts=sc, tgt_xyz=yd, tgt_counts=tc)
+    try:
+        ref, rst = eager(K, xd, fd, p, y=yd, sc=sc, tc=tc)
+        out = pipe.run(xd, fd, yd)
+        same_counts(pipe.check(), rst)
+        assert torch.equal(out, ref), float((out - ref).abs().max())
+        out2 = torch.empty_like(ref)
+        for _ in range(2):  # capture, then a launch of the graph
+            pipe.replay(xd, fd, yd, out=out2)
+            same_counts(pipe.check(), rst)
+            assert torch.equal(out2, ref)
     finally:
         pipe.free()
 
