@@ -80,8 +80,8 @@ kitc_status kitc_pipeline_status(kitc_pipeline h, kitc_stats *st, void *stream);
 /* Launches captured in the handle's graph (0 before the first replay). */
 int64_t kitc_pipeline_graph_launches(kitc_pipeline h);
 
-/* Frees the handle (waits for nothing: the caller's stream must be done with
- * it). */
+/* Frees the handle.  Waits for the handle's own second stream only: every
+ * stream the caller ran or replayed the handle on must be done with it. */
 kitc_status kitc_pipeline_free(kitc_pipeline h);
 
 #ifdef __cplusplus
