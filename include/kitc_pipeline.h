@@ -21,7 +21,9 @@
  * All pointers given to a run are device pointers (n x 3 row-major
  * coordinates, n x w_in weights, n_tgt x w_out output in the caller's target
  * order); the library copies what it needs, and they may be reused once the
- * stream has passed the run.  Handles are not thread-safe. */
+ * stream has passed the run.  Handles are not thread-safe, and belong to the
+ * device that was current at creation: a run, replay or status call made with
+ * another device current returns KITC_ERR_STATE. */
 #pragma once
 #include "kitc.h"
 
@@ -68,7 +70,8 @@ kitc_status kitc_pipeline_run(kitc_pipeline h, const double *src_xyz, const doub
 kitc_status kitc_pipeline_replay(kitc_pipeline h, const double *src_xyz, const double *w,
                                  const double *tgt_xyz, double *out, void *stream);
 
-/* Waits for `stream` and reports the last run: KITC_ERR_TOO_LARGE if the
+/* Waits for `stream` and reports the last run (before any run: KITC_OK and
+ * zero counts): KITC_ERR_TOO_LARGE if the
  * trees, the work items or the lists needed more room than the handle holds
  * (create the handle again from inputs like these, or with more slack),
  * KITC_ERR_INVALID_ARG if a traversal stack overflowed (as kitc_evaluate),

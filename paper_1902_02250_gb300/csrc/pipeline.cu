@@ -96,6 +96,13 @@ kitc_status run_impl(kitc_pipeline h, const double *src_xyz, const double *w, co
     return evaluate_launch(p.kernel, mixed, a, s);
 }
 
+// The handle's buffers live on the device that was current at creation.
+bool on_device(kitc_pipeline h)
+{
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess && d == h->device;
+}
+
 }  // namespace
 
 extern "C" {
@@ -170,6 +177,10 @@ kitc_status kitc_pipeline_create(const double *src_xyz, const int64_t *src_count
     for (auto &row : h->ev)
         for (cudaEvent_t &e : row)
             if (st == KITC_OK) st = kitc_from_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // a status read before any run finds no error and zero counts
+    if (st == KITC_OK) st = kitc_from_cuda(cudaMemsetAsync(h->flags.ptr, 0, 4 * sizeof(int), s));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaMemsetAsync(h->lists.totals.ptr, 0, h->lists.totals.bytes, s));
+    if (st == KITC_OK) st = kitc_from_cuda(cudaMemsetAsync(h->src.sc.state(), 0, sizeof(BuildState), s));
     if (st == KITC_OK) st = kitc_from_cuda(cudaStreamSynchronize(s));
     if (st != KITC_OK) return fail(st);
     // evaluator arguments: every pointer is fixed but the output
@@ -212,6 +223,7 @@ kitc_status kitc_pipeline_run(kitc_pipeline h, const double *src_xyz, const doub
 {
     if (!h || !src_xyz || !w || !out || (tgt_xyz != nullptr) == h->self_targets)
         return KITC_ERR_INVALID_ARG;
+    if (!on_device(h)) return KITC_ERR_STATE;
     return run_impl(h, src_xyz, w, tgt_xyz, out, reinterpret_cast<cudaStream_t>(stream), 0);
 }
 
@@ -220,6 +232,7 @@ kitc_status kitc_pipeline_replay(kitc_pipeline h, const double *src_xyz, const d
 {
     if (!h || !src_xyz || !w || !out || (tgt_xyz != nullptr) == h->self_targets)
         return KITC_ERR_INVALID_ARG;
+    if (!on_device(h)) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (h->graph && h->g_src == src_xyz && h->g_w == w && h->g_tgt == tgt_xyz && h->g_out == out) {
         for (int64_t i = 0; i < h->graph_launches; ++i) kitc_count_launch();
@@ -261,6 +274,7 @@ kitc_status kitc_pipeline_replay(kitc_pipeline h, const double *src_xyz, const d
 kitc_status kitc_pipeline_status(kitc_pipeline h, kitc_stats *st, void *stream)
 {
     if (!h) return KITC_ERR_INVALID_ARG;
+    if (!on_device(h)) return KITC_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int hf[4] = {0, 0, 0, 0};
     BuildState bs{};

@@ -218,6 +218,8 @@ def test_pipeline_argument_checks(K):
     assert e.value.status == 1
     pipe = K.Pipeline(xd, K.Params(leaf_size=300))
     try:
+        code, st = pipe.status()  # before any run: no error, no counts
+        assert code == 0 and st["far_points"] == 0 and st["near_pairs"] == 0 and st["n_clusters"] == 0
         with pytest.raises(K.KitcError) as e:  # created with the sources as targets
             pipe.run(xd, fd, tgt_xyz=xd)
         assert e.value.status == 1
