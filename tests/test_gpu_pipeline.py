@@ -16,6 +16,8 @@ with the oracle):
   allocation across replays;
 * a forest whose systems have target sets of their own (rotlet, per-target
   MAC, batches of 48), through run() and the graph;
+* the degenerate trees of the eager tree tests (one particle, a root leaf,
+  coincident points, chains to the depth limit, a slab);
 * an input that needs more levels and entries than reserved: the run stays in
   bounds, reports KITC_ERR_TOO_LARGE, and the next run that fits is exact again.
 """
@@ -177,6 +179,40 @@ def test_pipeline_forest_with_own_targets(K):
             pipe.replay(xd, fd, yd, out=out2)
             same_counts(pipe.check(), rst)
             assert torch.equal(out2, ref)
+    finally:
+        pipe.free()
+
+
+DEGENERATE = {
+    # one particle; a root that is already a leaf; 300 coincident points among
+    # 700 others; ten groups of 200 coincident points with N0 = 100, whose
+    # chains run to the depth limit (41 levels queued, 40 upward levels); a slab
+    "one": lambda: (np.array([[0.25, -0.5, 1.0]]), 4),
+    "root_leaf": lambda: (wl.uniform_cube(500, 34)[0], 500),
+    "duplicates": lambda: (np.vstack([np.full((300, 3), 0.125), wl.uniform_cube(700, 35)[0]]), 50),
+    "chains": lambda: (np.repeat(wl.uniform_cube(10, 36)[0], 200, axis=0), 100),
+    "slab": lambda: (np.column_stack([wl.rng(1).uniform(0, 16, 30000), wl.rng(2).uniform(0, 16, 30000),
+                                      wl.rng(3).uniform(0, 9, 30000)]), 400),
+}
+
+
+@pytest.mark.parametrize("case", sorted(DEGENERATE))
+def test_pipeline_degenerate_trees(K, case):
+    """The trees of the eager tree tests, through the whole pipeline (mixed
+    Stokeslet, all-targets MAC): bit-identical to the eager calls."""
+    import torch
+    x, N0 = DEGENERATE[case]()
+    f = wl.rng(89).uniform(-1.0, 1.0, size=(len(x), 3))
+    p = K.Params(theta=0.7, degree=4, leaf_size=N0, eps=0.01, precision=K.MIXED, mac=K.MAC_ALL,
+                 target_batch=64)
+    xd, fd = dev(x), dev(f)
+    pipe = K.Pipeline(xd, p)
+    try:
+        out = pipe.run(xd, fd)
+        st = pipe.check()
+        ref, rst = eager(K, xd, fd, p)
+        assert torch.equal(out, ref), (case, float((out - ref).abs().max()))
+        same_counts(st, rst)
     finally:
         pipe.free()
 
