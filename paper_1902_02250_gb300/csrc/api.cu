@@ -314,6 +314,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 {
     const bool mixed = t->p.precision == KITC_MIXED;
     const bool pairs = uses_pair_records(t->p.kernel, mixed);
+    t->wts.rowpairs = pairs && uses_row_pairs(t->p.kernel);
     if (t->var) {
         KITC_TRY(weights_launch_var(t->src, w, t->wts, s));
         KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
@@ -820,7 +821,7 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream)
     const bool mixed = t->p.precision == KITC_MIXED;
     const bool pairs = uses_pair_records(t->p.kernel, mixed);
     std::vector<int64_t> ro;
-    t->proxy_bytes = proxy_offsets_var(h, t->win, mixed, pairs, ro);
+    t->proxy_bytes = proxy_offsets_var(h, t->win, mixed, pairs, pairs && uses_row_pairs(t->p.kernel), ro);
     std::vector<double> tab((KITC_MAX_DEGREE + 1) * (KITC_MAX_DEGREE + 1), 0.0);
     for (int d = 1; d <= KITC_MAX_DEGREE; ++d) cheb_cos_table(d, &tab[(size_t)d * (KITC_MAX_DEGREE + 1)]);
     KITC_TRY(t->cdeg.reserve(sizeof(int32_t) * m, s));

@@ -172,6 +172,7 @@ struct WeightsDev {
     bool var_upward = false;  // degree map: upward form (else Algorithm 1 on every cluster)
     int var_pmax = 0;         // degree map: largest grid size of the upward form
     int64_t fhat_len = 0;     // doubles of fhat in use
+    bool rowpairs = false;    // paired grid records in the row-pair form (uses_row_pairs)
     bool async = false;       // device-planned (weights_async_reserve): nitems is the item capacity
     int64_t paircap = 0;      // device-planned paired records: capacity in pairs
     DevBuf fhat;      // double [nclus][P][win]
@@ -206,12 +207,24 @@ constexpr bool uses_pair_records(int kernel, bool mixed)
 }
 // Paired FP32x2 grid records of the modified weights.
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
+// Paired grid records of one cluster with np points per axis, 32 bytes each.
+// Each grid row (k1, k2) holds ceil(np / 2) records of consecutive k3 points,
+// a missing last point with zero weight.  With row pairs (the rotlet's form)
+// and odd np, each record instead holds one k3 point of two consecutive grid
+// rows (row index k1 np + k2), the last row of the odd count paired with a
+// zero-weight row.
+constexpr bool uses_row_pairs(int kernel) { return kernel == KITC_ROTLET; }
+__host__ __device__ inline int64_t pair_records(int np, bool rowpairs)
+{
+    return (rowpairs && (np & 1)) ? (int64_t)((np * np + 1) / 2) * np
+                                  : (int64_t)np * np * ((np + 1) / 2);
+}
 kitc_status weights_plan_var(const TreeDev &t, int win, const std::vector<int32_t> &hdeg,
                              cudaStream_t s, WeightsDev &wd);
 kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDev &wd,
                                cudaStream_t s);
 int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed, bool pairs,
-                          std::vector<int64_t> &roff);
+                          bool rowpairs, std::vector<int64_t> &roff);
 kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_deg,
                              const int64_t *d_roff, bool mixed, bool pairs, cudaStream_t s);
 // Weights pass and evaluator records of an asynchronously built tree, planned
@@ -221,7 +234,8 @@ kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_
 // then stay in bounds but are not the weights).
 int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode);
 kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
-                                  bool mixed, bool pairs, cudaStream_t s, WeightsDev &wd);
+                                  bool mixed, bool pairs, bool rowpairs, cudaStream_t s,
+                                  WeightsDev &wd);
 kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, WeightsDev &wd,
                                  bool mixed, bool pairs, int *err, cudaStream_t s);
 // Paired FP32 records of the FP32x2 evaluator (pack_pairs_plan once per tree,

@@ -379,14 +379,17 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     // grid of cluster c: (n_c+1)^3 records from its offset
                     const int np = a.cdeg ? a.cdeg[c] + 1 : np0;
                     if (np < 2 || np > KITC_MAX_DEGREE + 1) { ok = false; break; }
-                    const int row_bytes = PAIR ? (np + 1) / 2 * 32 : np * PREC;
-                    const int plane_bytes = np * row_bytes;
-                    const int planes_max = TILE / plane_bytes;
+                    // a tile holds whole units: planes k1 of np grid rows, or
+                    // (paired rotlet records, odd np) pairs of consecutive grid rows
+                    const bool rowpairs = PAIR && ROT && (np & 1);
+                    const int unit_bytes = rowpairs ? np * 32 : np * (PAIR ? (np + 1) / 2 * 32 : np * PREC);
+                    const int nunits = rowpairs ? (np * np + 1) / 2 : np;
+                    const int units_max = TILE / unit_bytes;
                     const unsigned char *cb = pxb + (a.roff ? (size_t)a.roff[c]
-                                                            : (size_t)c * np * plane_bytes);
-                    for (int k1 = 0; k1 < np && ok; k1 += planes_max) {
-                        int k2 = min(np, k1 + planes_max);
-                        TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == np ? F_LAST_ENTRY : 0),
+                                                            : (size_t)c * nunits * unit_bytes);
+                    for (int k1 = 0; k1 < nunits && ok; k1 += units_max) {
+                        int k2 = min(nunits, k1 + units_max);
+                        TileMeta m{K_FAR, (k1 == 0 ? F_FIRST_ENTRY : 0) | (k2 == nunits ? F_LAST_ENTRY : 0),
                                    b, c, k1, k2, 0, np, mk, lo, hi};
                         if (PAIR && KITC_FAR_PROD && k1 == 0) {
                             m.goff[0] = (float)(0.5 * (lo.x + hi.x) - pcB.x);
@@ -396,7 +399,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                             m.ghw[1] = (float)(0.5 * (hi.y - lo.y));
                             m.ghw[2] = (float)(0.5 * (hi.z - lo.z));
                         }
-                        ok = push(m, cb + (size_t)k1 * plane_bytes, (uint32_t)((k2 - k1) * plane_bytes));
+                        ok = push(m, cb + (size_t)k1 * unit_bytes, (uint32_t)((k2 - k1) * unit_bytes));
                     }
                 }
                 int64_t n0 = a.near_off[b], n1 = a.near_off[b + 1];
@@ -653,6 +656,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                     }
                     if (lane == 0 && (np & 1)) gsf[36 + np] = -1e18f;
                     __syncwarp();
+                    if (ROT && (np & 1)) {  // row pairs: -z of each point on both lanes
+                        for (int k = lane; k < np; k += 32) gsf[54 + 2 * k] = gsf[55 + 2 * k] = gsf[36 + k];
+                        __syncwarp();
+                    }
                 }
                 const int rows = (tb - ta) * np;
                 // rows of the tile, split over the warps; the loop over the point
@@ -807,10 +814,110 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         }
                     }
                 };
+                // Rotlet, odd n + 1: a record holds one k3 point of two
+                // consecutive grid rows (row index k1 np + k2) on the two lanes,
+                // the last row of the odd count paired with a zero-weight row
+                // placed far away, instead of a padding point in every row.
+                // Along a unit dx and dy stay constant per lane, so the row sums
+                // fold per lane as above.  Unit u of the tile is rows 2 (ta + u)
+                // and 2 (ta + u) + 1; a warp's units advance by NCW, its rows by
+                // 2 NCW.  (The Stokeslet keeps its padded rows: at its
+                // 96-register budget the second loop made the whole kernel slower.)
+                auto unit_rows = [&](int k1, int k2, int t, float2 &dx2, float2 &dy2) {
+                    int k2b = k2 + 1, k1b = k1;
+                    if (k2b == np) {
+                        k2b = 0;
+                        ++k1b;
+                    }
+                    const bool pad = k1b >= np;
+                    dx2 = make_float2(XO[t][0] - gsf[k1], pad ? 1e18f : XO[t][0] - gsf[k1b]);
+                    dy2 = make_float2(XO[t][1] - gsf[18 + k2], pad ? 0.f : XO[t][1] - gsf[18 + k2b]);
+                };
+                auto far_rowpairs_rot = [&](auto npc) {
+                    constexpr int NP = decltype(npc)::value;
+                    const int units = tb - ta;
+                    int u = (warp + rot) % NCW;
+                    int k1 = (2 * (ta + u)) / NP, k2 = 2 * (ta + u) - k1 * NP;
+                    for (; u < units; u += NCW) {
+                        const unsigned char *row = tile + (size_t)u * (NP * 32);
+                        float2 v[TPL][WOUT];
+                        float2 dx2[TPL], dy2[TPL], rxy2[TPL], z2[TPL];
+                        float2 S0[TPL], S1[TPL], S2[TPL], B0[TPL], B1[TPL], W0[TPL], W1[TPL], W2[TPL], T[TPL], Z[TPL];
+#pragma unroll
+                        for (int t = 0; t < TPL; ++t) {
+                            unit_rows(k1, k2, t, dx2[t], dy2[t]);
+                            rxy2[t] = fma2(dx2[t], dx2[t], fma2(dy2[t], dy2[t], e22));
+                            z2[t] = bc2(XO[t][2]);
+                            S0[t] = S1[t] = S2[t] = B0[t] = B1[t] = make_float2(0.f, 0.f);
+                            W0[t] = W1[t] = W2[t] = T[t] = Z[t] = make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const float4 A = *reinterpret_cast<const float4 *>(row + q * 32);
+                            const float4 B = *reinterpret_cast<const float4 *>(row + q * 32 + 16);
+                            const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w);
+                            const float2 nz = make_float2(B.x, B.y);
+                            const float2 ngzq = *reinterpret_cast<const float2 *>(gsf + 54 + 2 * q);
+#pragma unroll
+                            for (int t = 0; t < TPL; ++t) {
+                                const float2 dz = add2(z2[t], ngzq);
+                                float2 hQ, qD1, qD2;
+                                rot_factors(fma2(dz, dz, rxy2[t]), hQ, qD1, qD2);
+                                const float2 nd = fma2(nx, dx2[t], fma2(ny, dy2[t], mul2(nz, dz)));
+                                const float2 tt = mul2(nd, qD2);
+                                S0[t] = fma2(hQ, nx, S0[t]);
+                                S1[t] = fma2(hQ, ny, S1[t]);
+                                S2[t] = fma2(hQ, nz, S2[t]);
+                                const float2 hz = mul2(hQ, dz);
+                                B0[t] = fma2(hz, nx, B0[t]);
+                                B1[t] = fma2(hz, ny, B1[t]);
+                                W0[t] = fma2(nx, qD1, W0[t]);
+                                W1[t] = fma2(ny, qD1, W1[t]);
+                                W2[t] = fma2(nz, qD1, W2[t]);
+                                T[t] = add2(T[t], tt);
+                                Z[t] = fma2(dz, tt, Z[t]);
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < TPL; ++t) {
+                            v[t][0] = fma2(mul2(m1, dy2[t]), S2[t], B1[t]);
+                            v[t][1] = fma2(dx2[t], S2[t], mul2(m1, B0[t]));
+                            v[t][2] = fma2(dy2[t], S0[t], mul2(mul2(m1, dx2[t]), S1[t]));
+                            if constexpr (WOUT == 6) {
+                                v[t][3] = fma2(dx2[t], T[t], W0[t]);
+                                v[t][4] = fma2(dy2[t], T[t], W1[t]);
+                                v[t][5] = add2(W2[t], Z[t]);
+                            }
+                        }
+                        step2(u0, u1, v[0], v[TPL - 1]);
+                        k2 += 2 * NCW;
+                        while (k2 >= NP) {
+                            k2 -= NP;
+                            ++k1;
+                        }
+                    }
+                };
                 auto far_any = [&](auto npc) {
                     if constexpr (ROT) far_rows_rot(npc);
                     else far_rows(npc);
                 };
+                bool done = false;
+                if constexpr (ROT) {
+                    if (np & 1) {
+                        switch (np) {
+                        case 3: far_rowpairs_rot(std::integral_constant<int, 3>{}); break;
+                        case 5: far_rowpairs_rot(std::integral_constant<int, 5>{}); break;
+                        case 7: far_rowpairs_rot(std::integral_constant<int, 7>{}); break;
+                        case 9: far_rowpairs_rot(std::integral_constant<int, 9>{}); break;
+                        case 11: far_rowpairs_rot(std::integral_constant<int, 11>{}); break;
+                        case 13: far_rowpairs_rot(std::integral_constant<int, 13>{}); break;
+                        case 15: far_rowpairs_rot(std::integral_constant<int, 15>{}); break;
+                        default: far_rowpairs_rot(std::integral_constant<int, 17>{}); break;
+                        }
+                        done = true;
+                    }
+                }
+                if (!done)
                 switch (npair) {
                 case 1: far_any(std::integral_constant<int, 1>{}); break;
                 case 2: far_any(std::integral_constant<int, 2>{}); break;

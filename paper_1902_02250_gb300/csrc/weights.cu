@@ -458,24 +458,43 @@ __global__ void k_pack_pairs_flat(int64_t n, const double *__restrict__ xyz,
     put_pair_half(out + (i / 2) * 20, (int)(i & 1), x, f);
 }
 
-// Paired modified-weight records: each grid row (k1, k2) holds ceil((n+1)/2)
-// pairs of consecutive k3 points, [fx_k fx_k+1 fy_k fy_k+1][fz_k fz_k+1 0 0];
-// a missing last point has zero weight.
-__global__ void k_pack_proxy_pairs(int64_t nrows, int np, const double *__restrict__ fhat,
+// Record q of a cluster's paired grid records (pair_records): fh is the
+// cluster's FP64 weights [k1][k2][k3][3]; the record is
+// [fx_a fx_b fy_a fy_b][fz_a fz_b 0 0] for its two points a, b (a missing b
+// has zero weight).
+__device__ __forceinline__ void pack_pair_record(const double *__restrict__ fh, int np, bool rowpairs,
+                                                 int64_t q, float4 *__restrict__ o)
+{
+    const double *a, *b = nullptr;
+    if (rowpairs && (np & 1)) {  // point k3 of rows 2P and 2P + 1
+        const int64_t P = q / np, ra = 2 * P;
+        const int k3 = (int)(q - P * np);
+        a = fh + (ra * np + k3) * 3;
+        if (ra + 1 < (int64_t)np * np) b = fh + ((ra + 1) * np + k3) * 3;
+    } else {                     // points k, k + 1 of row r
+        const int h = (np + 1) / 2;
+        const int64_t r = q / h;
+        const int k = (int)(q - r * h) * 2;
+        a = fh + (r * np + k) * 3;
+        if (k + 1 < np) b = a + 3;
+    }
+    double g[3] = {0.0, 0.0, 0.0};
+    if (b)
+        for (int l = 0; l < 3; ++l) g[l] = b[l];
+    o[0] = make_float4((float)a[0], (float)g[0], (float)a[1], (float)g[1]);
+    o[1] = make_float4((float)a[2], (float)g[2], 0.f, 0.f);
+}
+
+// Paired records of every cluster (of the first *nclus_dev when given).
+__global__ void k_pack_proxy_pairs(int64_t nclus, int np, bool rowpairs, const double *__restrict__ fhat,
                                    float4 *__restrict__ out, const int *__restrict__ nclus_dev)
 {
-    const int npair = (np + 1) / 2;
+    const int64_t R = pair_records(np, rowpairs);
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (nclus_dev) nrows = min(nrows, (int64_t)*nclus_dev * np * np);
-    if (q >= nrows * npair) return;
-    int64_t r = q / npair;
-    int k = (int)(q % npair) * 2;
-    const double *f0 = fhat + (r * np + k) * 3;
-    double g[3] = {0.0, 0.0, 0.0};
-    if (k + 1 < np)
-        for (int l = 0; l < 3; ++l) g[l] = f0[3 + l];
-    out[2 * q] = make_float4((float)f0[0], (float)g[0], (float)f0[1], (float)g[1]);
-    out[2 * q + 1] = make_float4((float)f0[2], (float)g[2], 0.f, 0.f);
+    if (nclus_dev) nclus = min(nclus, (int64_t)*nclus_dev);
+    if (q >= nclus * R) return;
+    const int64_t c = q / R;
+    pack_pair_record(fhat + c * np * np * np * 3, np, rowpairs, q - c * R, out + 2 * q);
 }
 
 }  // namespace
@@ -1080,13 +1099,13 @@ kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const do
 
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s)
 {
-    int np = wd.degree + 1, npair = (np + 1) / 2;
-    int64_t nrows = (int64_t)t.nclus * np * np;
-    KITC_TRY(wd.proxy.reserve((size_t)32 * nrows * npair, s));
-    unsigned g = (unsigned)((nrows * npair + 255) / 256);
+    const int np = wd.degree + 1;
+    const int64_t nrec = (int64_t)t.nclus * pair_records(np, wd.rowpairs);
+    KITC_TRY(wd.proxy.reserve((size_t)32 * nrec, s));
+    unsigned g = (unsigned)((nrec + 255) / 256);
     kitc_count_launch();
-    k_pack_proxy_pairs<<<g, 256, 0, s>>>(nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>(),
-                                         nullptr);
+    k_pack_proxy_pairs<<<g, 256, 0, s>>>(t.nclus, np, wd.rowpairs, wd.fhat.as<double>(),
+                                         wd.proxy.as<float4>(), nullptr);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -1255,7 +1274,7 @@ template <int FORM>  // 0: pairs, 1: FP32 float4 per point, 2: FP64 per point
 __global__ void k_pack_proxies_var(const int32_t *__restrict__ deg, int win,
                                    const int64_t *__restrict__ foff,
                                    const int64_t *__restrict__ roff, const double *__restrict__ fhat,
-                                   unsigned char *__restrict__ proxy)
+                                   unsigned char *__restrict__ proxy, bool rowpairs)
 {
     int c = blockIdx.x;
     int d = deg[c];
@@ -1264,17 +1283,9 @@ __global__ void k_pack_proxies_var(const int32_t *__restrict__ deg, int win,
     const double *fh = fhat + foff[c];
     unsigned char *out = proxy + roff[c];
     if (FORM == 0) {
-        int npair = (np + 1) / 2;
-        for (int q = threadIdx.x; q < np * np * npair; q += blockDim.x) {
-            int r = q / npair, k = (q % npair) * 2;
-            const double *f0 = fh + ((size_t)r * np + k) * 3;
-            double g[3] = {0.0, 0.0, 0.0};
-            if (k + 1 < np)
-                for (int l = 0; l < 3; ++l) g[l] = f0[3 + l];
-            float4 *o = reinterpret_cast<float4 *>(out) + 2 * q;
-            o[0] = make_float4((float)f0[0], (float)g[0], (float)f0[1], (float)g[1]);
-            o[1] = make_float4((float)f0[2], (float)g[2], 0.f, 0.f);
-        }
+        const int64_t R = pair_records(np, rowpairs);
+        for (int64_t q = threadIdx.x; q < R; q += blockDim.x)
+            pack_pair_record(fh, np, rowpairs, q, reinterpret_cast<float4 *>(out) + 2 * q);
     } else {
         int P = np * np * np;
         for (int r = threadIdx.x; r < P; r += blockDim.x) {
@@ -1462,7 +1473,7 @@ kitc_status weights_launch_var(const TreeDev &t, const double *w_user, WeightsDe
 
 // Record offsets (bytes) of each cluster's grid records in the given form.
 int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed, bool pairs,
-                          std::vector<int64_t> &roff)
+                          bool rowpairs, std::vector<int64_t> &roff)
 {
     roff.assign(hdeg.size(), 0);
     int64_t o = 0;
@@ -1471,7 +1482,7 @@ int64_t proxy_offsets_var(const std::vector<int32_t> &hdeg, int win, bool mixed,
         int d = hdeg[c];
         if (d <= 0) continue;
         int64_t np = d + 1;
-        o += pairs ? np * np * ((np + 1) / 2) * 32 : np * np * np * proxy_record_bytes(win, mixed);
+        o += pairs ? pair_records((int)np, rowpairs) * 32 : np * np * np * proxy_record_bytes(win, mixed);
     }
     return o;
 }
@@ -1484,13 +1495,13 @@ kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_
     kitc_count_launch();
     if (pairs)
         k_pack_proxies_var<0><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
-                                                     wd.proxy.as<unsigned char>());
+                                                     wd.proxy.as<unsigned char>(), wd.rowpairs);
     else if (mixed)
         k_pack_proxies_var<1><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
-                                                     wd.proxy.as<unsigned char>());
+                                                     wd.proxy.as<unsigned char>(), false);
     else
         k_pack_proxies_var<2><<<t.nclus, 128, 0, s>>>(d_deg, wd.win, d_f, d_roff, wd.fhat.as<double>(),
-                                                     wd.proxy.as<unsigned char>());
+                                                     wd.proxy.as<unsigned char>(), false);
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -1641,7 +1652,8 @@ int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode)
 }
 
 kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
-                                  bool mixed, bool pairs, cudaStream_t s, WeightsDev &wd)
+                                  bool mixed, bool pairs, bool rowpairs, cudaStream_t s,
+                                  WeightsDev &wd)
 {
     const TreeDev &t = a.t;
     const int cap = t.cap;
@@ -1660,7 +1672,7 @@ kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int m
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * cap, s));
     if (pairs) {
         const int64_t paircap = (t.n + cap) / 2 + 1;
-        KITC_TRY(wd.proxy.reserve((size_t)32 * cap * np * np * ((np + 1) / 2), s));
+        KITC_TRY(wd.proxy.reserve((size_t)32 * cap * pair_records(np, rowpairs), s));
         KITC_TRY(wd.src.reserve((size_t)80 * paircap + 16, s));
         KITC_TRY(wd.pbegin.reserve(sizeof(int32_t) * 4 * (size_t)cap + 16, s));
         wd.paircap = paircap;
@@ -1673,6 +1685,7 @@ kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int m
     wd.upward = upward;
     if (upward) KITC_TRY(allow_up_smem());
     wd.split = split;
+    wd.rowpairs = pairs && rowpairs;
     wd.degree = degree;
     wd.win = win;
     wd.mode = mode;
@@ -1725,10 +1738,10 @@ kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, Weigh
     }
     const int *nclus_dev = &bs->nclus;
     if (pairs) {
-        const int64_t nrows = (int64_t)cap * np * np, npair = (np + 1) / 2;
+        const int64_t nrec = (int64_t)cap * pair_records(np, wd.rowpairs);
         kitc_count_launch();
-        k_pack_proxy_pairs<<<(unsigned)((nrows * npair + 255) / 256), 256, 0, s>>>(
-            nrows, np, wd.fhat.as<double>(), wd.proxy.as<float4>(), nclus_dev);
+        k_pack_proxy_pairs<<<(unsigned)((nrec + 255) / 256), 256, 0, s>>>(
+            cap, np, wd.rowpairs, wd.fhat.as<double>(), wd.proxy.as<float4>(), nclus_dev);
         int32_t *d = wd.pbegin.as<int32_t>();
         kitc_count_launch();
         k_pairs_plan<<<1, 1024, 0, s>>>(bs, cap, t.begin.as<int32_t>(), t.end.as<int32_t>(),
