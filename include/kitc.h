@@ -152,7 +152,10 @@ kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int 
 
 /* Eq. modified_weights (Algorithm 1) for every cluster of the tree, in
  * FP64.  w: device, n_src x w_in, in the order of src_xyz.  Replaces any
- * weights set before; stream-ordered, no synchronization. */
+ * weights set before.  Stream-ordered and without host synchronization: the
+ * work items and the evaluator's record ranges are planned on the device.
+ * With a degree map (kitc_set_degrees), the first call after it plans the
+ * degree groups on the host and synchronizes `stream` once. */
 kitc_status kitc_modified_weights(kitc_tree t, const double *w, void *stream);
 
 /* Algorithm 2: u at n_tgt targets.  tgt_xyz: device, n_tgt x 3; out: device,

@@ -897,9 +897,144 @@ size_t upward_child_smem(int np, int win)
 }
 
 
-// Host-side plan of the weights pass for one tree: work items, buffer sizes and
-// launch shapes.  Done once per tree; weights_launch then only launches kernels
-// (so that it can be captured in a CUDA graph).
+namespace {
+
+// ---------------------------------------------------------------------------
+// Plans made on the device: the work items of Algorithm 1 in cluster order
+// (chunks of CHUNK slots) and the ranges of the paired source records (one
+// per leaf, in cluster order), by single-block scans over the clusters.  The
+// cluster count comes from a tree's device state block (bs), or from the host
+// (m_fixed) for a tree built by tree_build.  Every buffer is sized from bounds
+// that hold for any tree of at most cap clusters:
+//   items <= cap + (levels counted per slot) * ceil(n / CHUNK)
+//   pairs <= (n + cap) / 2 + 1   (each leaf adds at most half a pair)
+// ---------------------------------------------------------------------------
+// Exclusive prefix of one value per thread over a block of 1024 threads;
+// *total receives the block's sum (every thread).
+__device__ int64_t block_prefix(int64_t v, int64_t *total)
+{
+    __shared__ int64_t ws[32];
+    __shared__ int64_t tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+        int64_t u = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        ws[lane] = u - t;
+        if (lane == 31) tot = u;
+    }
+    __syncthreads();
+    const int64_t r = ws[w] + x - v;
+    *total = tot;
+    __syncthreads();  // ws and tot are reused by the next call
+    return r;
+}
+
+__device__ __forceinline__ int items_of(int c, int m, bool upward, const int32_t *begin,
+                                        const int32_t *end, const int32_t *n_child)
+{
+    if (c >= m || (upward && n_child[c] > 0)) return 0;
+    return (end[c] - begin[c] + CHUNK - 1) / CHUNK;
+}
+
+// first[c] (c <= cap): the first work item of cluster c, items in cluster
+// order, chunks of CHUNK slots; clamped to itemcap.  One block of 1024.
+__global__ void __launch_bounds__(1024) k_items_plan(const BuildState *__restrict__ bs, int m_fixed,
+                                                     int cap, bool upward,
+                                                     const int32_t *__restrict__ begin,
+                                                     const int32_t *__restrict__ end,
+                                                     const int32_t *__restrict__ n_child,
+                                                     int32_t *__restrict__ first, int itemcap,
+                                                     int *__restrict__ nitems, int *__restrict__ err)
+{
+    const int m = min(bs ? bs->nclus : m_fixed, cap);
+    const int per = (cap + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
+    int64_t loc = 0;
+    for (int c = c0; c < c1; ++c) loc += items_of(c, m, upward, begin, end, n_child);
+    int64_t total = 0;
+    int64_t run = block_prefix(loc, &total);
+    for (int c = c0; c < c1; ++c) {
+        first[c] = (int32_t)min(run, (int64_t)itemcap);
+        run += items_of(c, m, upward, begin, end, n_child);
+    }
+    if (threadIdx.x == 0) {
+        first[cap] = (int32_t)min(total, (int64_t)itemcap);
+        *nitems = (int)min(total, (int64_t)itemcap);
+        if (total > itemcap) atomicOr(err, ASYNC_RECORD_OVERFLOW);
+    }
+}
+
+__global__ void k_items_fill(const BuildState *__restrict__ bs, int m_fixed, int cap,
+                             const int32_t *__restrict__ first, const int32_t *__restrict__ begin,
+                             const int32_t *__restrict__ end, Item *__restrict__ items)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= min(bs ? bs->nclus : m_fixed, cap)) return;
+    const int32_t b = begin[c], e = end[c];
+    for (int i = first[c]; i < first[c + 1]; ++i) {
+        const int32_t p = b + (i - first[c]) * CHUNK;
+        items[i] = Item{c, p, min(e, p + CHUNK), 0};
+    }
+}
+
+// Paired-record plan: pb_all = [first pair per cluster (cap, -1 off the
+// leaves) | range begin (cap) | range end (cap) | first pair (cap)], one range
+// per leaf in cluster order, empty ranges after the last leaf.  One block.
+__global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restrict__ bs, int m_fixed,
+                                                     int cap, const int32_t *__restrict__ begin,
+                                                     const int32_t *__restrict__ end,
+                                                     const int32_t *__restrict__ n_child,
+                                                     int32_t *__restrict__ pb_all, int64_t paircap,
+                                                     int *__restrict__ err)
+{
+    const int m = min(bs ? bs->nclus : m_fixed, cap);
+    int32_t *cpb = pb_all, *rb = pb_all + cap, *re = rb + cap, *pb = re + cap;
+    const int per = (cap + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
+    int64_t nl = 0, np = 0;
+    for (int c = c0; c < c1; ++c)
+        if (c < m && n_child[c] == 0) {
+            nl++;
+            np += (end[c] - begin[c] + 1) / 2;
+        }
+    int64_t nleaves = 0, npairs = 0;
+    int64_t r = block_prefix(nl, &nleaves);
+    int64_t q = block_prefix(np, &npairs);
+    const bool over = npairs > paircap;  // cannot happen for a valid tree (bound above)
+    for (int c = c0; c < c1; ++c) {
+        if (c < m && n_child[c] == 0) {
+            cpb[c] = over ? 0 : (int32_t)q;
+            rb[r] = begin[c];
+            re[r] = over ? begin[c] : end[c];
+            pb[r] = over ? 0 : (int32_t)q;
+            r++;
+            q += (end[c] - begin[c] + 1) / 2;
+        } else {
+            cpb[c] = -1;
+        }
+    }
+    for (int64_t k = nleaves + threadIdx.x; k < cap; k += blockDim.x) rb[k] = re[k] = pb[k] = 0;
+    if (threadIdx.x == 0 && over) atomicOr(err, ASYNC_RECORD_OVERFLOW);
+}
+
+}  // namespace
+
+// Plan of the weights pass for one tree: buffer sizes and launch shapes.  The
+// work items themselves are planned on the device by each launch (k_items_plan,
+// in cluster order), in room that bounds the items of a tree of these clusters
+// and levels, so neither the plan nor the launch reads anything back and the
+// launch can be captured in a CUDA graph.
 kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaStream_t s,
                          WeightsDev &wd)
 {
@@ -909,35 +1044,12 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
     const int np = degree + 1;
     const int pwin = np * np * np * win;
     const bool upward = mode == KITC_WEIGHTS_UPWARD && upward_child_smem(np, win) <= UP_SMEM_MAX;
-    // work items: chunks of the slot range of every cluster (of every leaf only,
-    // when the parents come from the upward pass), in cluster order
-    std::vector<int32_t> hb(t.nclus), he(t.nclus), hn(t.nclus);
-    KITC_CUDA(cudaMemcpyAsync(hb.data(), t.begin.ptr, sizeof(int32_t) * t.nclus,
-                              cudaMemcpyDeviceToHost, s));
-    KITC_CUDA(cudaMemcpyAsync(he.data(), t.end.ptr, sizeof(int32_t) * t.nclus,
-                              cudaMemcpyDeviceToHost, s));
-    KITC_CUDA(cudaMemcpyAsync(hn.data(), t.n_child.ptr, sizeof(int32_t) * t.nclus,
-                              cudaMemcpyDeviceToHost, s));
-    KITC_CUDA(cudaStreamSynchronize(s));
-    std::vector<Item> items;
-    std::vector<int32_t> first(t.nclus + 1);
-    for (int c = 0; c < t.nclus; ++c) {
-        first[c] = (int32_t)items.size();
-        if (upward && hn[c] > 0) continue;
-        for (int32_t p = hb[c]; p < he[c]; p += CHUNK)
-            items.push_back(Item{c, p, std::min(he[c], p + CHUNK), 0});
-    }
-    first[t.nclus] = (int32_t)items.size();
-    size_t nitems = items.size();
-    size_t ibytes = sizeof(Item) * nitems + sizeof(int32_t) * (t.nclus + 1) + 64;
-    KITC_TRY(wd.items.reserve(ibytes, s));
-    Item *d_items = wd.items.as<Item>();
-    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + nitems);
-    KITC_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(Item) * nitems,
-                              cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int32_t) * (t.nclus + 1),
-                              cudaMemcpyHostToDevice, s));
-    size_t rows = std::max<size_t>(nitems, 1);  // item partials, then the upward contributions
+    const int64_t itemcap = weights_async_itemcap(t.nclus, std::max(1, t.depth), t.n,
+                                                  upward ? KITC_WEIGHTS_UPWARD : KITC_WEIGHTS_ALGORITHM1);
+    if (itemcap > INT32_MAX / 2) return KITC_ERR_OOM;
+    // items (itemcap) | first item of each cluster (nclus + 1) | item count | error word
+    KITC_TRY(wd.items.reserve(sizeof(Item) * itemcap + sizeof(int32_t) * ((size_t)t.nclus + 3) + 64, s));
+    size_t rows = (size_t)itemcap;  // item partials, then the upward contributions
     if (upward)
         for (size_t L = 1; L < t.level_start.size(); ++L) {
             const int e = L + 1 < t.level_start.size() ? t.level_start[L + 1] : t.nclus;
@@ -945,9 +1057,7 @@ kitc_status weights_plan(const TreeDev &t, int win, int degree, int mode, cudaSt
         }
     KITC_TRY(wd.partial.reserve(sizeof(double) * pwin * rows, s));
     KITC_TRY(wd.fhat.reserve(sizeof(double) * pwin * t.nclus, s));
-    // the host vectors must outlive the copies above
-    KITC_CUDA(cudaStreamSynchronize(s));
-    wd.nitems = nitems;
+    wd.nitems = (size_t)itemcap;
     wd.upward = upward;
     if (upward) KITC_TRY(allow_up_smem());
     wd.degree = degree;
@@ -963,14 +1073,24 @@ kitc_status weights_launch(const TreeDev &t, const double *w_user, WeightsDev &w
     if (!wd.planned) return KITC_ERR_STATE;
     const int np = wd.degree + 1, win = wd.win;
     const int pwin = np * np * np * win;
+    const int nclus = t.nclus, itemcap = (int)wd.nitems;
     Item *d_items = wd.items.as<Item>();
-    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + wd.nitems);
+    int32_t *d_first = reinterpret_cast<int32_t *>(d_items + itemcap);
+    int *d_nitems = d_first + nclus + 1;
     const Cheb cb = make_cheb(wd.degree);
-    KITC_TRY(launch_items(wd.split, wd.degree, win, (int64_t)wd.nitems, d_items, t, w_user,
-                          wd.partial.as<double>(), nullptr, s));
     kitc_count_launch();
-    k_weights_reduce<<<t.nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
-                                             wd.fhat.as<double>());
+    k_items_plan<<<1, 1024, 0, s>>>(nullptr, nclus, nclus, wd.upward, t.begin.as<int32_t>(),
+                                    t.end.as<int32_t>(), t.n_child.as<int32_t>(), d_first, itemcap,
+                                    d_nitems, d_nitems + 1);
+    kitc_count_launch();
+    k_items_fill<<<(nclus + 255) / 256, 256, 0, s>>>(nullptr, nclus, nclus, d_first, t.begin.as<int32_t>(),
+                                                     t.end.as<int32_t>(), d_items);
+    KITC_CUDA(cudaGetLastError());
+    KITC_TRY(launch_items(wd.split, wd.degree, win, itemcap, d_items, t, w_user,
+                          wd.partial.as<double>(), d_nitems, s));
+    kitc_count_launch();
+    k_weights_reduce<<<nclus, 256, 0, s>>>(d_first, pwin, wd.partial.as<double>(),
+                                           wd.fhat.as<double>());
     KITC_CUDA(cudaGetLastError());
     if (wd.upward) {
         const size_t us = upward_child_smem(np, win);
@@ -1035,50 +1155,26 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
     return KITC_OK;
 }
 
-// Host-side plan of the paired records: one range per leaf (or one for a
-// direct sum), the first pair of each range, uploaded once into pbegin as
-// [cluster -> first pair (nclus) | range begin | range end | first pair].
+// Plan of the paired records, made on the device (k_pairs_plan): one range per
+// leaf in cluster order, in room for any leaf sizes of this tree; pbegin
+// receives [first pair of each cluster (nclus, -1 off the leaves) | range
+// begin | range end | first pair (nclus each; empty ranges after the last
+// leaf) | an error word].  Reads nothing back.
 kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
                             DevBuf &pbegin, int *nranges)
 {
-    std::vector<int32_t> rb, re, pb;
-    int nclus = t ? t->nclus : 1;
-    std::vector<int32_t> cpb(nclus, -1);
-    if (t) {
-        std::vector<int32_t> hb(nclus), he(nclus), hn(nclus);
-        KITC_CUDA(cudaMemcpyAsync(hb.data(), t->begin.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
-        KITC_CUDA(cudaMemcpyAsync(he.data(), t->end.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
-        KITC_CUDA(cudaMemcpyAsync(hn.data(), t->n_child.ptr, sizeof(int32_t) * nclus, cudaMemcpyDeviceToHost, s));
-        KITC_CUDA(cudaStreamSynchronize(s));
-        int32_t next = 0;
-        for (int c = 0; c < nclus; ++c) {
-            if (hn[c] != 0) continue;
-            rb.push_back(hb[c]);
-            re.push_back(he[c]);
-            pb.push_back(next);
-            cpb[c] = next;
-            next += (he[c] - hb[c] + 1) / 2;
-        }
-    } else {
-        rb.push_back(0);
-        re.push_back((int32_t)n);
-        pb.push_back(0);
-        cpb[0] = 0;
-    }
-    int64_t npairs = 0;
-    for (size_t i = 0; i < rb.size(); ++i) npairs += (re[i] - rb[i] + 1) / 2;
-    size_t nr = rb.size();
-    KITC_TRY(out.reserve((size_t)80 * npairs + 16, s));
-    KITC_TRY(pbegin.reserve(sizeof(int32_t) * (3 * nr + nclus) + 16, s));
-    std::vector<int32_t> all;
-    all.insert(all.end(), cpb.begin(), cpb.end());
-    all.insert(all.end(), rb.begin(), rb.end());
-    all.insert(all.end(), re.begin(), re.end());
-    all.insert(all.end(), pb.begin(), pb.end());
-    KITC_CUDA(cudaMemcpyAsync(pbegin.ptr, all.data(), sizeof(int32_t) * all.size(),
-                              cudaMemcpyHostToDevice, s));
-    KITC_CUDA(cudaStreamSynchronize(s));  // the host vector must outlive the copy
-    *nranges = (int)nr;
+    if (!t) return KITC_ERR_INVALID_ARG;
+    const int nclus = t->nclus;
+    const int64_t paircap = (n + nclus) / 2 + 1;
+    KITC_TRY(out.reserve((size_t)80 * paircap + 16, s));
+    KITC_TRY(pbegin.reserve(sizeof(int32_t) * (4 * (size_t)nclus + 1) + 16, s));
+    int32_t *d = pbegin.as<int32_t>();
+    kitc_count_launch();
+    k_pairs_plan<<<1, 1024, 0, s>>>(nullptr, nclus, nclus, t->begin.as<int32_t>(), t->end.as<int32_t>(),
+                                    t->n_child.as<int32_t>(), d, paircap,
+                                    reinterpret_cast<int *>(d + 4 * (size_t)nclus));
+    KITC_CUDA(cudaGetLastError());
+    *nranges = nclus;
     return KITC_OK;
 }
 
@@ -1514,137 +1610,10 @@ const int64_t *weights_foff(const TreeDev &t, const WeightsDev &wd)
 }
 
 // ---------------------------------------------------------------------------
-// Device-planned weights pass for a tree known only on the device (the
-// graph-capturable pipeline).  The plan that weights_plan and pack_pairs_plan
-// make on the host (work items in cluster order, the first pair of every leaf)
-// is made by single-block scans over the cluster capacity, with the same
-// order, so the results are bit-identical to the host-planned pass.  Every
-// buffer is sized from bounds that hold for any tree of at most cap clusters:
-//   items <= cap + (levels counted per slot) * ceil(n / CHUNK)
-//   pairs <= (n + cap) / 2 + 1   (each leaf adds at most half a pair)
+// Weights pass for a tree known only on the device (the graph-capturable
+// pipeline): the device plans above, the cluster count and the level starts
+// read from the tree's state block, buffers sized once from the capacities.
 // ---------------------------------------------------------------------------
-namespace {
-
-// Exclusive prefix of one value per thread over a block of 1024 threads;
-// *total receives the block's sum (every thread).
-__device__ int64_t block_prefix(int64_t v, int64_t *total)
-{
-    __shared__ int64_t ws[32];
-    __shared__ int64_t tot;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) ws[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        const int64_t t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
-        int64_t u = t;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, u, o);
-            if (lane >= o) u += y;
-        }
-        ws[lane] = u - t;
-        if (lane == 31) tot = u;
-    }
-    __syncthreads();
-    const int64_t r = ws[w] + x - v;
-    *total = tot;
-    __syncthreads();  // ws and tot are reused by the next call
-    return r;
-}
-
-__device__ __forceinline__ int items_of(int c, int m, bool upward, const int32_t *begin,
-                                        const int32_t *end, const int32_t *n_child)
-{
-    if (c >= m || (upward && n_child[c] > 0)) return 0;
-    return (end[c] - begin[c] + CHUNK - 1) / CHUNK;
-}
-
-// first[c] (c <= cap): the first work item of cluster c, items in cluster
-// order, chunks of CHUNK slots; clamped to itemcap.  One block of 1024.
-__global__ void __launch_bounds__(1024) k_items_plan(const BuildState *__restrict__ bs, int cap,
-                                                     bool upward, const int32_t *__restrict__ begin,
-                                                     const int32_t *__restrict__ end,
-                                                     const int32_t *__restrict__ n_child,
-                                                     int32_t *__restrict__ first, int itemcap,
-                                                     int *__restrict__ nitems, int *__restrict__ err)
-{
-    const int m = min(bs->nclus, cap);
-    const int per = (cap + blockDim.x - 1) / blockDim.x;
-    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
-    int64_t loc = 0;
-    for (int c = c0; c < c1; ++c) loc += items_of(c, m, upward, begin, end, n_child);
-    int64_t total = 0;
-    int64_t run = block_prefix(loc, &total);
-    for (int c = c0; c < c1; ++c) {
-        first[c] = (int32_t)min(run, (int64_t)itemcap);
-        run += items_of(c, m, upward, begin, end, n_child);
-    }
-    if (threadIdx.x == 0) {
-        first[cap] = (int32_t)min(total, (int64_t)itemcap);
-        *nitems = (int)min(total, (int64_t)itemcap);
-        if (total > itemcap) atomicOr(err, ASYNC_RECORD_OVERFLOW);
-    }
-}
-
-__global__ void k_items_fill(const BuildState *__restrict__ bs, int cap,
-                             const int32_t *__restrict__ first, const int32_t *__restrict__ begin,
-                             const int32_t *__restrict__ end, Item *__restrict__ items)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= min(bs->nclus, cap)) return;
-    const int32_t b = begin[c], e = end[c];
-    for (int i = first[c]; i < first[c + 1]; ++i) {
-        const int32_t p = b + (i - first[c]) * CHUNK;
-        items[i] = Item{c, p, min(e, p + CHUNK), 0};
-    }
-}
-
-// Paired-record plan: pb_all = [first pair per cluster (cap, -1 off the
-// leaves) | range begin (cap) | range end (cap) | first pair (cap)], one range
-// per leaf in cluster order, empty ranges after the last leaf.  One block.
-__global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restrict__ bs, int cap,
-                                                     const int32_t *__restrict__ begin,
-                                                     const int32_t *__restrict__ end,
-                                                     const int32_t *__restrict__ n_child,
-                                                     int32_t *__restrict__ pb_all, int64_t paircap,
-                                                     int *__restrict__ err)
-{
-    const int m = min(bs->nclus, cap);
-    int32_t *cpb = pb_all, *rb = pb_all + cap, *re = rb + cap, *pb = re + cap;
-    const int per = (cap + blockDim.x - 1) / blockDim.x;
-    const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
-    int64_t nl = 0, np = 0;
-    for (int c = c0; c < c1; ++c)
-        if (c < m && n_child[c] == 0) {
-            nl++;
-            np += (end[c] - begin[c] + 1) / 2;
-        }
-    int64_t nleaves = 0, npairs = 0;
-    int64_t r = block_prefix(nl, &nleaves);
-    int64_t q = block_prefix(np, &npairs);
-    const bool over = npairs > paircap;  // cannot happen for a valid tree (bound above)
-    for (int c = c0; c < c1; ++c) {
-        if (c < m && n_child[c] == 0) {
-            cpb[c] = over ? 0 : (int32_t)q;
-            rb[r] = begin[c];
-            re[r] = over ? begin[c] : end[c];
-            pb[r] = over ? 0 : (int32_t)q;
-            r++;
-            q += (end[c] - begin[c] + 1) / 2;
-        } else {
-            cpb[c] = -1;
-        }
-    }
-    for (int64_t k = nleaves + threadIdx.x; k < cap; k += blockDim.x) rb[k] = re[k] = pb[k] = 0;
-    if (threadIdx.x == 0 && over) atomicOr(err, ASYNC_RECORD_OVERFLOW);
-}
-
-}  // namespace
-
 int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode)
 {
     const int64_t per = (n + CHUNK - 1) / CHUNK;
@@ -1709,10 +1678,10 @@ kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, Weigh
     int *d_nitems = d_first + cap + 1;
     const Cheb cb = make_cheb(wd.degree);
     kitc_count_launch();
-    k_items_plan<<<1, 1024, 0, s>>>(bs, cap, wd.upward, t.begin.as<int32_t>(), t.end.as<int32_t>(),
+    k_items_plan<<<1, 1024, 0, s>>>(bs, 0, cap, wd.upward, t.begin.as<int32_t>(), t.end.as<int32_t>(),
                                     t.n_child.as<int32_t>(), d_first, itemcap, d_nitems, err);
     kitc_count_launch();
-    k_items_fill<<<(cap + 255) / 256, 256, 0, s>>>(bs, cap, d_first, t.begin.as<int32_t>(),
+    k_items_fill<<<(cap + 255) / 256, 256, 0, s>>>(bs, 0, cap, d_first, t.begin.as<int32_t>(),
                                                    t.end.as<int32_t>(), d_items);
     KITC_CUDA(cudaGetLastError());
     KITC_TRY(launch_items(wd.split, wd.degree, win, itemcap, d_items, t, w_user, wd.partial.as<double>(),
@@ -1744,7 +1713,7 @@ kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, Weigh
             cap, np, wd.rowpairs, wd.fhat.as<double>(), wd.proxy.as<float4>(), nclus_dev);
         int32_t *d = wd.pbegin.as<int32_t>();
         kitc_count_launch();
-        k_pairs_plan<<<1, 1024, 0, s>>>(bs, cap, t.begin.as<int32_t>(), t.end.as<int32_t>(),
+        k_pairs_plan<<<1, 1024, 0, s>>>(bs, 0, cap, t.begin.as<int32_t>(), t.end.as<int32_t>(),
                                         t.n_child.as<int32_t>(), d, wd.paircap, err);
         kitc_count_launch();
         k_pack_pairs<<<(unsigned)cap, 256, 0, s>>>(d + cap, d + 2 * cap, d + 3 * cap, t.n,
