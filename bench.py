@@ -43,6 +43,10 @@ sys.path.insert(0, ROOT)
 # the batch MAC needs theta = 0.70 for that margin and runs 2% slower; E is
 # re-measured every run).  The literal point theta = 0.7, n = 8, N0 = 2000
 # gives E ~ 5.5e-6 (--literal).
+# Precision: the mixed form with leaf-offset near-field differences
+# (KITC_MIXED_LEAF; E 5.34e-7 / 6.97e-7 / 6.22e-7 on the same seeds, evaluator
+# 7% faster); the hi/lo form (KITC_MIXED) at the same point is timed beside it
+# in the line ("mixed_hilo"), or is the headline with --precision mixed.
 N = 1_000_000
 SEED = 2
 EPS = 1e-3
@@ -88,6 +92,9 @@ def parse():
                     help="no overlap of the weights with the target tree and lists")
     ap.add_argument("--literal", action="store_true",
                     help="theta = 0.7, n = 8, N0 = 2000, per-target MAC (E above 1e-6)")
+    ap.add_argument("--precision", default="mixed_leaf", choices=["mixed_leaf", "mixed"],
+                    help="mixed_leaf: near-field differences from leaf offsets (KITC_MIXED_LEAF); "
+                         "mixed: from hi/lo pairs (KITC_MIXED)")
     args = ap.parse_args()
     th, n, leaf, mac = LITERAL if args.literal else (THETA, DEGREE, LEAF, MAC)
     args.theta = th if args.theta is None else args.theta
@@ -194,6 +201,8 @@ def config(args, precision):
     return {"workload": "uniform cube [-1,1]^3, N=1,000,000 (seed 2 + rank), Stokeslet, f ~ U[-1,1]^3",
             "eps": EPS, "theta": args.theta, "degree": args.degree, "leaf_size": args.leaf,
             "target_batch": BATCH, "mac": args.mac, "precision": precision,
+            "near_differences": "offsets to the leaf's box centre, rounded once to FP32"
+            if precision == "mixed_leaf" else "hi/lo FP32 pairs",
             "parameters": "fastest with E <= 8e-7 on seeds 2, 3, 4 (sweep of MAC rule, theta, n)"
             if not args.literal else "literal",
             "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
@@ -499,8 +508,9 @@ def run_kitc(args, ws, rank, local):
     x, f = wl.uniform_cube(N, SEED + rank)
     xd = torch.from_numpy(x).to(dev)
     fd = torch.from_numpy(f).to(dev)
+    prec = K.MIXED_LEAF if args.precision == "mixed_leaf" else K.MIXED
     p = K.Params(theta=args.theta, degree=args.degree, leaf_size=args.leaf, eps=EPS,
-                 kernel=K.STOKESLET, precision=K.MIXED, mac=mac, target_batch=BATCH)
+                 kernel=K.STOKESLET, precision=prec, mac=mac, target_batch=BATCH)
     out = torch.empty((N, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -564,7 +574,7 @@ def run_kitc(args, ws, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 kernel values, f64 sums", "data": "synthetic",
-            "config": config(args, "mixed"), "E": E,
+            "config": config(args, args.precision), "E": E,
             "stage_ms": stage_ms,
             "interactions_per_target": {"near": st["near_pairs"] / N, "far": st["far_points"] / N,
                                         "algorithm2_near": a2["near_pairs"] / N,
@@ -593,6 +603,21 @@ def run_kitc(args, ws, rank, local):
         del og
     finally:
         pipe.free()
+
+    if rank == 0 and ws == 1 and prec == K.MIXED_LEAF:
+        # the same point with hi/lo near-field differences (KITC_MIXED), for comparison
+        ph = K.Params(theta=args.theta, degree=args.degree, leaf_size=args.leaf, eps=EPS,
+                      kernel=K.STOKESLET, precision=K.MIXED, mac=mac, target_batch=BATCH)
+        outh = torch.empty_like(out)
+        ksh = max(1, min(args.steps, 3))
+        msh, sth = timed(stream, flush, lambda: step(ph, outh), ksh, 1)
+        line["mixed_hilo"] = {"value": N / (np.mean(msh) / 1e3), "unit": "targets/s",
+                              "ms_per_step": float(np.mean(msh)), "steps": ksh,
+                              "ms_evaluate": sth["ms_evaluate"],
+                              "E": rel_l2(ref, outh.cpu().numpy()[idx]),
+                              "what": "KITC_MIXED at the same point: near-field differences from "
+                                      "hi/lo FP32 pairs"}
+        del outh
 
     if rank == 0 and ws == 1 and not args.no_fp64:
         th64, n64, leaf64, mac64 = FP64_POINT

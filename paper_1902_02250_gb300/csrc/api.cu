@@ -144,9 +144,9 @@ bool device_accessible(const void *ptr)
 bool valid_direct_params(const kitc_params *p)
 {
     return p && kitc_kernel_win(p->kernel) >= 0 && p->eps >= 0.0 && isfinite(p->eps) &&
-           (p->precision == KITC_FP64 || p->precision == KITC_MIXED) && p->target_batch >= 0 &&
+           (p->precision == KITC_FP64 || is_mixed(p->precision)) && p->target_batch >= 0 &&
            p->target_batch <= KITC_MAX_BATCH &&
-           !(p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED);
+           !(p->kernel == KITC_TEST_POLY && is_mixed(p->precision));
 }
 
 bool valid_params(const kitc_params *p)
@@ -157,11 +157,11 @@ bool valid_params(const kitc_params *p)
     if (p->leaf_size < 1) return false;
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return false;
     if (kitc_kernel_win(p->kernel) < 0) return false;
-    if (p->precision != KITC_FP64 && p->precision != KITC_MIXED) return false;
+    if (p->precision != KITC_FP64 && !is_mixed(p->precision)) return false;
     if (p->mac != KITC_MAC_PARTICLE && p->mac != KITC_MAC_BATCH && p->mac != KITC_MAC_ALL)
         return false;
     if (p->target_batch < 0 || p->target_batch > KITC_MAX_BATCH) return false;
-    if (p->kernel == KITC_TEST_POLY && p->precision == KITC_MIXED) return false;
+    if (p->kernel == KITC_TEST_POLY && is_mixed(p->precision)) return false;
     if (p->weights != KITC_WEIGHTS_UPWARD && p->weights != KITC_WEIGHTS_ALGORITHM1) return false;
     return true;
 }
@@ -176,6 +176,7 @@ void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
     a.queue = flags;
     a.err = flags + 1;
     a.wait_ns = (unsigned long long)g_wait_limit_ms * 1000000ull;
+    a.leaf = uses_leaf_offsets(p.kernel, p.precision);
 }
 
 bool weights_split_enabled() { return g_weights_split; }
@@ -312,15 +313,16 @@ kitc_status kitc_build_forest(const double *src_xyz, const int64_t *counts, int 
 // plans must exist (prepare_weights).
 static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 {
-    const bool mixed = t->p.precision == KITC_MIXED;
+    const bool mixed = is_mixed(t->p.precision);
     const bool pairs = uses_pair_records(t->p.kernel, mixed);
     t->wts.rowpairs = pairs && uses_row_pairs(t->p.kernel);
+    const bool leaf = uses_leaf_offsets(t->p.kernel, t->p.precision);
     if (t->var) {
         KITC_TRY(weights_launch_var(t->src, w, t->wts, s));
         KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
                                   mixed, pairs, s));
         if (pairs)
-            KITC_TRY(pack_pairs_launch(&t->src, nullptr, w, t->src.n, t->wts.pair_ranges, s,
+            KITC_TRY(pack_pairs_launch(&t->src, w, t->src.n, t->wts.pair_ranges, leaf, s,
                                        t->wts.src, t->wts.pbegin));
         else
             KITC_TRY(pack_sources(&t->src, nullptr, w, t->src.n, t->win, mixed, s, t->wts.src));
@@ -329,7 +331,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
     KITC_TRY(weights_launch(t->src, w, t->wts, s));
     if (pairs) {  // FP32x2 evaluator records
         KITC_TRY(pack_proxy_pairs(t->src, t->wts, s));
-        KITC_TRY(pack_pairs_launch(&t->src, nullptr, w, t->src.n, t->wts.pair_ranges, s,
+        KITC_TRY(pack_pairs_launch(&t->src, w, t->src.n, t->wts.pair_ranges, leaf, s,
                                    t->wts.src, t->wts.pbegin));
     } else {
         KITC_TRY(pack_proxies(t->src, t->wts, mixed, s));
@@ -340,7 +342,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
 
 static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
 {
-    t->wts.split = t->p.precision == KITC_MIXED && g_weights_split;
+    t->wts.split = is_mixed(t->p.precision) && g_weights_split;
     if (t->var) {
         if (!t->wts.planned || !t->wts.var) {
             KITC_TRY(weights_plan_var(t->src, t->win, t->hdeg, s, t->wts));
@@ -349,8 +351,9 @@ static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
     } else {
         KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
     }
-    if (uses_pair_records(t->p.kernel, t->p.precision == KITC_MIXED) && !t->pairs_planned) {
-        KITC_TRY(pack_pairs_plan(&t->src, t->src.n, s, t->wts.src, t->wts.pbegin,
+    if (uses_pair_records(t->p.kernel, is_mixed(t->p.precision)) && !t->pairs_planned) {
+        KITC_TRY(pack_pairs_plan(&t->src, t->src.n, uses_leaf_offsets(t->p.kernel, t->p.precision), s,
+                                 t->wts.src, t->wts.pbegin,
                                  &t->wts.pair_ranges));
         t->pairs_planned = true;
     }
@@ -441,7 +444,7 @@ static kitc_status evaluate_impl(kitc_tree t, const double *tgt_xyz, int64_t n_t
         a.chebt = t->chebt.as<double>();
     }
     KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
-    KITC_TRY(evaluate_launch(p.kernel, p.precision == KITC_MIXED, a, s));
+    KITC_TRY(evaluate_launch(p.kernel, is_mixed(p.precision), a, s));
     record(t, 6, s);
     t->last = a;
     KITC_TRY(read_error_flag(t->flags.as<int>() + 1, s));
@@ -484,7 +487,7 @@ kitc_status kitc_direct(const double *tgt_xyz, int64_t n_tgt, const double *src_
         !device_accessible(src_xyz) || !device_accessible(w) || !device_accessible(out))
         return KITC_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    bool mixed = p->precision == KITC_MIXED;
+    bool mixed = is_mixed(p->precision);
     int win = kitc_kernel_win(p->kernel);
     int B = batch_of(*p);
     DevBuf rec, flags;
@@ -738,7 +741,7 @@ kitc_status kitc_apply(kitc_tree t, const double *w, double *out, void *stream)
     t->stream = s;
     EvalArgs a = t->last;
     a.out = out;
-    const bool mixed = t->p.precision == KITC_MIXED;
+    const bool mixed = is_mixed(t->p.precision);
     auto body = [&]() -> kitc_status {
         KITC_TRY(launch_weights(t, w, s));
         KITC_CUDA(cudaMemsetAsync(t->flags.ptr, 0, 4 * sizeof(int), s));
@@ -818,7 +821,7 @@ kitc_status kitc_set_degrees(kitc_tree t, const int32_t *degrees, void *stream)
     t->wts.planned = false;
     t->var = false;
     if (!degrees) return KITC_OK;
-    const bool mixed = t->p.precision == KITC_MIXED;
+    const bool mixed = is_mixed(t->p.precision);
     const bool pairs = uses_pair_records(t->p.kernel, mixed);
     std::vector<int64_t> ro;
     t->proxy_bytes = proxy_offsets_var(h, t->win, mixed, pairs, pairs && uses_row_pairs(t->p.kernel), ro);

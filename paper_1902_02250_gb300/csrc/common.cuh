@@ -173,6 +173,7 @@ struct WeightsDev {
     int var_pmax = 0;         // degree map: largest grid size of the upward form
     int64_t fhat_len = 0;     // doubles of fhat in use
     bool rowpairs = false;    // paired grid records in the row-pair form (uses_row_pairs)
+    bool leaf = false;        // paired source records as leaf offsets (uses_leaf_offsets)
     bool async = false;       // device-planned (weights_async_reserve): nitems is the item capacity
     int64_t paircap = 0;      // device-planned paired records: capacity in pairs
     DevBuf fhat;      // double [nclus][P][win]
@@ -205,6 +206,13 @@ constexpr bool uses_pair_records(int kernel, bool mixed)
 {
     return mixed && (kernel == KITC_STOKESLET || kernel == KITC_ROTLET);
 }
+// Both mixed forms (FP32 kernel values, FP64 sums).
+constexpr bool is_mixed(int precision) { return precision == KITC_MIXED || precision == KITC_MIXED_LEAF; }
+// A tree's paired source records hold offsets from the leaf's box centre.
+constexpr bool uses_leaf_offsets(int kernel, int precision)
+{
+    return precision == KITC_MIXED_LEAF && uses_pair_records(kernel, true);
+}
 // Paired FP32x2 grid records of the modified weights.
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);
 // Paired grid records of one cluster with np points per axis, 32 bytes each.
@@ -234,17 +242,37 @@ kitc_status pack_proxies_var(const TreeDev &t, WeightsDev &wd, const int32_t *d_
 // then stay in bounds but are not the weights).
 int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode);
 kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
-                                  bool mixed, bool pairs, bool rowpairs, cudaStream_t s,
+                                  bool mixed, bool pairs, bool rowpairs, bool leaf, cudaStream_t s,
                                   WeightsDev &wd);
 kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, WeightsDev &wd,
                                  bool mixed, bool pairs, int *err, cudaStream_t s);
-// Paired FP32 records of the FP32x2 evaluator (pack_pairs_plan once per tree,
-// then pack_pairs_launch); pbegin receives the first pair of every leaf (-1
-// for other clusters), followed by the ranges of the packing launch.
-kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
+// Paired FP32 records of a tree's leaves for the FP32x2 evaluator
+// (pack_pairs_plan once per tree, then pack_pairs_launch): hi/lo coordinates
+// (80 bytes a pair), or with leaf offsets (KITC_MIXED_LEAF) the offsets from
+// the leaf's box centre (48 bytes); pbegin receives the first pair of every
+// leaf (-1 for other clusters), followed by the ranges of the packing launch.
+constexpr int LEAF_PAIR_BYTES = 48;
+// The leaf-offset arithmetic shared by the record packing and the evaluator:
+// c = the box centre as FP32 hi/lo parts, and the FP32 offset of a point p
+// given as hi/lo parts, (ph - ch) + (pl - cl) (rounded at each step, no
+// contraction), within about 2^-23 of |p - c|.
+__host__ __device__ inline void leaf_centre(const dvec4 &lo, const dvec4 &hi, float *ch, float *cl)
+{
+    const double c[3] = {0.5 * (lo.x + hi.x), 0.5 * (lo.y + hi.y), 0.5 * (lo.z + hi.z)};
+    for (int l = 0; l < 3; ++l) {
+        ch[l] = (float)c[l];
+        cl[l] = (float)(c[l] - (double)ch[l]);
+    }
+}
+__device__ __forceinline__ float leaf_offset(float ph, float pl, float ch, float cl)
+{
+    return __fadd_rn(__fsub_rn(ph, ch), __fsub_rn(pl, cl));
+}
+constexpr size_t pair_record_bytes(bool leaf) { return leaf ? LEAF_PAIR_BYTES : 80; }
+kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, bool leaf, cudaStream_t s, DevBuf &out,
                             DevBuf &pbegin, int *nranges);
-kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
-                              int64_t n, int nranges, cudaStream_t s, DevBuf &out, DevBuf &pbegin);
+kitc_status pack_pairs_launch(const TreeDev *t, const double *w_user, int64_t n, int nranges,
+                              bool leaf, cudaStream_t s, DevBuf &out, DevBuf &pbegin);
 // Direct-sum source records in the caller's order, written to caller-provided
 // device memory of direct_record_bytes() bytes (no allocation, no host copy);
 // pairs selects the paired FP32x2 format.
@@ -327,6 +355,7 @@ struct EvalArgs {
     const dvec4 *clo, *chi;    // cluster boxes (far field grid points)
     const int32_t *cbegin, *cend;
     const int32_t *pbegin;       // paired records: first pair of each leaf
+    int leaf;                    // tree's paired records hold leaf offsets (KITC_MIXED_LEAF)
     int degree;
     double cheb[KITC_MAX_DEGREE + 1];  // cos(k pi / n)
     // degree per cluster (NULL: degree everywhere); then cluster c's grid

@@ -15,8 +15,10 @@
 //    formed; the per-point work is one rsqrt and a few FMAs.
 //  * KITC_MIXED: coordinate differences of near pairs come from hi/lo FP32
 //    pairs (d = (xh - yh) + (xl - yl), relative error ~1e-7 at any distance);
-//    far-field points are taken relative to the batch centre in FP64 and then
-//    rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
+//    KITC_MIXED_LEAF (FP32x2 path): from offsets to the leaf's box centre c,
+//    each formed in FP64 and rounded once, d = (x - c) - (y - c), one packed
+//    add per coordinate instead of three.  Far-field points are taken
+//    relative to the batch centre in FP64 and then rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
 //    terms, those runs summed over at most 8, and so on one more level; the
 //    per-leaf / per-cluster sums are accumulated in FP64.
 //  * The mixed Stokeslet and rotlet run on packed FP32x2 arithmetic over pairs
@@ -63,8 +65,9 @@ struct TileMeta {
     int np;          // far: grid points per dimension of the cluster (n_c + 1)
     uint64_t mask;   // targets of the batch that use this entry
     dvec4 lo, hi;    // far: the cluster's box (read ahead by the producer)
-    // far, FP32x2 path: cluster centre minus batch centre and half widths of
-    // the box, formed in FP64 by the producer and rounded once
+    // FP32x2 path, far: cluster centre minus batch centre and half widths of
+    // the box, formed in FP64 by the producer and rounded once; near with
+    // leaf offsets: the leaf's box centre as FP32 hi (goff) and lo (ghw) parts
     float goff[3], ghw[3];
 };
 
@@ -266,7 +269,9 @@ template <int K, bool MIXED> struct MinBlocks {
     static constexpr int value = (MIXED && K == KITC_STOKESLET) ? KITC_PAIR_MINB : 1;
 };
 
-template <int K, bool MIXED, bool EPS0, int TPL>
+// LEAF: the FP32x2 near field reads leaf-offset records (KITC_MIXED_LEAF);
+// otherwise double-float records (KITC_MIXED, and every direct sum).
+template <int K, bool MIXED, bool EPS0, int TPL, bool LEAF>
 __device__ __forceinline__ void eval_body(const EvalArgs &a)
 {
     static_assert(TPL == 1 || TPL == 2, "one or two targets per lane");
@@ -277,7 +282,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     // points (see pack_pairs)
     constexpr bool PAIR = MIXED && (K == KITC_STOKESLET || K == KITC_ROTLET);
     constexpr bool ROT = K == KITC_ROTLET;
-    constexpr int PAIR_REC = 80;
+    constexpr bool OFF = PAIR && LEAF;  // near records: offsets from the leaf centre
+    constexpr int PAIR_REC = OFF ? LEAF_PAIR_BYTES : 80;
     using R = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *tiles = smem;
@@ -412,10 +418,16 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         p0 = a.pbegin[c];
                         p1 = p0 + pc;
                     }
+                    float lch[3] = {0.f, 0.f, 0.f}, lcl[3] = {0.f, 0.f, 0.f};  // OFF: leaf centre
+                    if (OFF) leaf_centre(a.clo[c], a.chi[c], lch, lcl);
                     for (int q = p0; q < p1 && ok; q += near_max) {
                         int q1 = min(p1, q + near_max);
                         TileMeta m{K_NEAR, (q == p0 ? F_FIRST_ENTRY : 0) | (q1 == p1 ? F_LAST_ENTRY : 0),
                                    b, c, q, q1, 0, 0, mk, zero4, zero4};
+                        for (int l = 0; l < 3; ++l) {
+                            m.goff[l] = lch[l];
+                            m.ghw[l] = lcl[l];
+                        }
                         ok = push(m, srcb + (size_t)q * near_unit, (uint32_t)((q1 - q) * near_unit));
                     }
                 }
@@ -622,7 +634,7 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                         a3s[(lane + 32 * t) * WOUT + c] = 0.f;
                     }
                 }
-                if constexpr (PAIR) {
+                if constexpr (PAIR && !OFF) {
 #pragma unroll
                     for (int l = 0; l < 3; ++l) {
                         Xh2[t][l] = bc2(X[t][l]);
@@ -934,23 +946,53 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 constexpr int NPBK = ROT ? NPB : KITC_NPB_S;  // source pairs per run
                 const int nb4 = (cnt + NPBK - 1) / NPBK, nfull = cnt / NPBK;
                 float2 ux[TPL], uy[TPL], uz[TPL];
-                auto body = [&](int idx) {
-                    const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
+                // OFF: the targets' offsets from the leaf centre, formed as the
+                // records' offsets are
+                float2 Xc2[TPL][3];
+                if constexpr (OFF) {
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t)
+#pragma unroll
+                        for (int l = 0; l < 3; ++l)
+                            Xc2[t][l] = bc2(leaf_offset(X[t][l], XL[t][l], mr.goff[l], mr.ghw[l]));
+                }
+                // a record's source pair: the negated coordinates as they enter
+                // x - y (leaf offsets, or hi and lo parts), and the weights
+                auto load_pair = [&](const unsigned char *rec, float2 (&ny)[2][3], float2 (&w)[3]) {
                     const float4 A = *reinterpret_cast<const float4 *>(rec);
                     const float4 B = *reinterpret_cast<const float4 *>(rec + 16);
                     const float4 C = *reinterpret_cast<const float4 *>(rec + 32);
-                    const float4 D = *reinterpret_cast<const float4 *>(rec + 48);
-                    const float4 E = *reinterpret_cast<const float4 *>(rec + 64);
-                    const float2 hx = make_float2(A.x, A.y), hy = make_float2(A.z, A.w);
-                    const float2 hz = make_float2(B.x, B.y), lx = make_float2(B.z, B.w);
-                    const float2 ly = make_float2(C.x, C.y), lz = make_float2(C.z, C.w);
-                    const float2 fx = make_float2(D.x, D.y), fy = make_float2(D.z, D.w);
-                    const float2 fz = make_float2(E.x, E.y);
+                    ny[0][0] = make_float2(A.x, A.y);
+                    ny[0][1] = make_float2(A.z, A.w);
+                    ny[0][2] = make_float2(B.x, B.y);
+                    if constexpr (OFF) {
+                        w[0] = make_float2(B.z, B.w);
+                        w[1] = make_float2(C.x, C.y);
+                        w[2] = make_float2(C.z, C.w);
+                    } else {
+                        const float4 D = *reinterpret_cast<const float4 *>(rec + 48);
+                        const float4 E = *reinterpret_cast<const float4 *>(rec + 64);
+                        ny[1][0] = make_float2(B.z, B.w);
+                        ny[1][1] = make_float2(C.x, C.y);
+                        ny[1][2] = make_float2(C.z, C.w);
+                        w[0] = make_float2(D.x, D.y);
+                        w[1] = make_float2(D.z, D.w);
+                        w[2] = make_float2(E.x, E.y);
+                    }
+                };
+                auto diff = [&](int t, int l, const float2 (&ny)[2][3]) -> float2 {
+                    if constexpr (OFF) return add2(Xc2[t][l], ny[0][l]);
+                    else return add2(add2(Xh2[t][l], ny[0][l]), add2(Xl2[t][l], ny[1][l]));
+                };
+                auto body = [&](int idx) {
+                    float2 ny[2][3], fw[3];
+                    load_pair(tile + (size_t)idx * PAIR_REC, ny, fw);
+                    const float2 fx = fw[0], fy = fw[1], fz = fw[2];
 #pragma unroll
                     for (int t = 0; t < TPL; ++t) {
-                        float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
-                        float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
-                        float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
+                        float2 dx = diff(t, 0, ny);
+                        float2 dy = diff(t, 1, ny);
+                        float2 dz = diff(t, 2, ny);
                         float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e22)));
                         float2 ri = make_float2(rsq<EPS0>(r2.x), rsq<EPS0>(r2.y));
                         float2 ri3 = mul2(mul2(ri, ri), ri);
@@ -966,22 +1008,14 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
                 // products of the cross product, summed separately over a run
                 float2 P[TPL][3], M[TPL][3], Wr[TPL][3];
                 auto body_rot = [&](int idx) {
-                    const unsigned char *rec = tile + (size_t)idx * PAIR_REC;
-                    const float4 A = *reinterpret_cast<const float4 *>(rec);
-                    const float4 B = *reinterpret_cast<const float4 *>(rec + 16);
-                    const float4 C = *reinterpret_cast<const float4 *>(rec + 32);
-                    const float4 D = *reinterpret_cast<const float4 *>(rec + 48);
-                    const float4 E = *reinterpret_cast<const float4 *>(rec + 64);
-                    const float2 hx = make_float2(A.x, A.y), hy = make_float2(A.z, A.w);
-                    const float2 hz = make_float2(B.x, B.y), lx = make_float2(B.z, B.w);
-                    const float2 ly = make_float2(C.x, C.y), lz = make_float2(C.z, C.w);
-                    const float2 nx = make_float2(D.x, D.y), ny = make_float2(D.z, D.w);
-                    const float2 nz = make_float2(E.x, E.y);
+                    float2 nyc[2][3], nw[3];
+                    load_pair(tile + (size_t)idx * PAIR_REC, nyc, nw);
+                    const float2 nx = nw[0], ny = nw[1], nz = nw[2];
 #pragma unroll
                     for (int t = 0; t < TPL; ++t) {
-                        const float2 dx = add2(add2(Xh2[t][0], hx), add2(Xl2[t][0], lx));
-                        const float2 dy = add2(add2(Xh2[t][1], hy), add2(Xl2[t][1], ly));
-                        const float2 dz = add2(add2(Xh2[t][2], hz), add2(Xl2[t][2], lz));
+                        const float2 dx = diff(t, 0, nyc);
+                        const float2 dy = diff(t, 1, nyc);
+                        const float2 dz = diff(t, 2, nyc);
                         float2 hQ, qD1, qD2;
                         rot_factors(fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e22))), hQ, qD1, qD2);
                         const float2 nd = fma2(nx, dx, fma2(ny, dy, mul2(nz, dz)));
@@ -1165,10 +1199,10 @@ __device__ __forceinline__ void eval_body(const EvalArgs &a)
     }
 }
 
-template <int K, bool MIXED, bool EPS0, int TPL>
+template <int K, bool MIXED, bool EPS0, int TPL, bool LEAF>
 __global__ void __launch_bounds__(NTH, (MinBlocks<K, MIXED>::value)) k_eval(const EvalArgs a)
 {
-    eval_body<K, MIXED, EPS0, TPL>(a);
+    eval_body<K, MIXED, EPS0, TPL, LEAF>(a);
 }
 
 
@@ -1203,16 +1237,22 @@ kitc_status launch_k(const EvalArgs &a, cudaStream_t s)
     if (!a.src || (a.near_off && !a.proxy) || !a.out || !a.queue || !a.err)
         return KITC_ERR_INVALID_ARG;
     const size_t smem = Smem<K>::TOTAL;
-    void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0, 2>;
-    if constexpr (ONE) {
-        if (one) kern = k_eval<K, MIXED, EPS0, 1>;
+    // leaf-offset near records: a tree's near field under KITC_MIXED_LEAF
+    const bool leaf = PAIR && a.near_off && a.leaf;
+    void (*kern)(const EvalArgs) = k_eval<K, MIXED, EPS0, 2, false>;
+    if constexpr (PAIR) {
+        if (leaf) kern = k_eval<K, MIXED, EPS0, 2, true>;
     }
-    static std::atomic<int> configured[2][64] = {};  // the attribute's value never changes
+    if constexpr (ONE) {
+        if (one) kern = leaf ? k_eval<K, MIXED, EPS0, 1, true> : k_eval<K, MIXED, EPS0, 1, false>;
+    }
+    const int form = (one ? 1 : 0) + (leaf ? 2 : 0);
+    static std::atomic<int> configured[4][64] = {};  // the attribute's value never changes
     int dev = 0;
     KITC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !configured[one][dev].load()) {
+    if (dev < 0 || dev >= 64 || !configured[form][dev].load()) {
         KITC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (dev >= 0 && dev < 64) configured[one][dev].store(1);
+        if (dev >= 0 && dev < 64) configured[form][dev].store(1);
     }
     int sms = 0, occ = 0;
     KITC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1230,10 +1270,16 @@ template <int K, bool MIXED, bool EPS0>
 kitc_status preload_k(size_t *lmem)
 {
     cudaFuncAttributes at;
-    KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 2>));
+    KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 2, false>));
     *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
     if constexpr (KITC_TPL1 && MIXED && K == KITC_STOKESLET) {
-        KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 1>));
+        KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 1, false>));
+        *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
+        KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 1, true>));
+        *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
+    }
+    if constexpr (MIXED && (K == KITC_STOKESLET || K == KITC_ROTLET)) {
+        KITC_CUDA(cudaFuncGetAttributes(&at, k_eval<K, MIXED, EPS0, 2, true>));
         *lmem = std::max(*lmem, (size_t)at.localSizeBytes);
     }
     return KITC_OK;

@@ -72,7 +72,7 @@ extern "C" kitc_status kitc_direct_noalloc(const double *tgt_xyz, int64_t n_tgt,
         !device_accessible(out))
         return KITC_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const bool mixed = p->precision == KITC_MIXED;
+    const bool mixed = is_mixed(p->precision);
     const bool pairs = uses_pair_records(p->kernel, mixed);
     const int win = kitc_kernel_win(p->kernel);
     if (RECORDS_AT + direct_record_bytes(n_src, win, mixed, pairs) > SCRATCH_BYTES)

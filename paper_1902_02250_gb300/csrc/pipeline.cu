@@ -71,7 +71,7 @@ kitc_status run_impl(kitc_pipeline h, const double *src_xyz, const double *w, co
                      double *out, cudaStream_t s, int k)
 {
     const kitc_params &p = h->p;
-    const bool mixed = p.precision == KITC_MIXED;
+    const bool mixed = is_mixed(p.precision);
     const bool pairs = uses_pair_records(p.kernel, mixed);
     int *flags = h->flags.as<int>();
     int *err = flags + FLAG_ERR;
@@ -136,7 +136,7 @@ kitc_status kitc_pipeline_create(const double *src_xyz, const int64_t *src_count
     h->self_targets = tgt_xyz == nullptr;
     cudaGetDevice(&h->device);
     const int B = h->p.target_batch;
-    const bool mixed = p->precision == KITC_MIXED;
+    const bool mixed = is_mixed(p->precision);
     const bool pairs = uses_pair_records(p->kernel, mixed);
     auto fail = [&](kitc_status st) {
         destroy(h);
@@ -169,7 +169,8 @@ kitc_status kitc_pipeline_create(const double *src_xyz, const int64_t *src_count
     if (st == KITC_OK) st = tree_async_reserve(h->tgt, nt, B, tcc, nsys, cap_t, lev_t, s);
     if (st == KITC_OK)
         st = weights_async_reserve(h->src, h->win, p->degree, p->weights, mixed && weights_split_enabled(),
-                                   mixed, pairs, pairs && uses_row_pairs(p->kernel), s, h->wts);
+                                   mixed, pairs, pairs && uses_row_pairs(p->kernel),
+                                   uses_leaf_offsets(p->kernel, p->precision), s, h->wts);
     if (st == KITC_OK) st = lists_async_reserve(h->src, h->tgt, B, cap_far, cap_near, s, h->lists);
     if (st == KITC_OK) st = h->flags.reserve(4 * sizeof(int), s);
     for (cudaStream_t *q : {&h->side[0], &h->side[1], &h->cap})

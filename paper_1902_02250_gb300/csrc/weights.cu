@@ -393,14 +393,14 @@ __global__ void k_pack_sources(int64_t n, int win, const double *__restrict__ xs
     }
 }
 
-// Paired records for the FP32x2 evaluator (Stokeslet forces or rotlet torques
-// as the weights): two consecutive sources of one leaf share a 80-byte record
-// (negated hi/lo coordinates, so that the packed add forms x - y, then the
-// weights):
+// Paired records of a direct sum for the FP32x2 evaluator (Stokeslet forces or
+// rotlet torques as the weights): two consecutive sources share a 80-byte
+// record (negated hi/lo coordinates, so that the packed add forms x - y, then
+// the weights):
 //   [-yh_x0 -yh_x1 -yh_y0 -yh_y1][-yh_z0 -yh_z1 -yl_x0 -yl_x1]
 //   [-yl_y0 -yl_y1 -yl_z0 -yl_z1][f_x0 f_x1 f_y0 f_y1][f_z0 f_z1 0 0]
-// A leaf of odd size is padded with a zero-weight point at 1e18, whose term is
-// exactly zero.  put_pair_half writes half h (0 or 1) of record rec.
+// An odd source count is padded with a zero-weight point at 1e18, whose term
+// is exactly zero.  put_pair_half writes half h (0 or 1) of record rec.
 __device__ __forceinline__ void put_pair_half(float *__restrict__ rec, int h, const double *x,
                                               const double *f)
 {
@@ -414,23 +414,49 @@ __device__ __forceinline__ void put_pair_half(float *__restrict__ rec, int h, co
     rec[18 + h] = 0.f;
 }
 
-// Block r packs the slot range [rb[r], re[r]) from pair pb[r].
+// Paired records of a tree's leaves with leaf offsets (KITC_MIXED_LEAF): two
+// consecutive sources of one leaf share a 48-byte record of their offsets
+// from the centre c of the leaf's box (negated, so that the packed add forms
+// x' - y' from the target's offset x'), then the weights:
+//   [-y'_x0 -y'_x1 -y'_y0 -y'_y1][-y'_z0 -y'_z1 f_x0 f_x1][f_y0 f_y1 f_z0 f_z1]
+// The offset of a point p is leaf_offset(ph, pl, ch, cl) of the FP32 hi/lo
+// parts of p and c, the same arithmetic the evaluator applies to each target,
+// so that a target on a source gives x' - y' = 0 exactly.  A leaf of odd size
+// is padded with a zero-weight point at 1e18.
+__device__ __forceinline__ void put_leaf_pair_half(float *__restrict__ rec, int h, const double *x,
+                                                   const float *ch, const float *cl, const double *f)
+{
+    for (int l = 0; l < 3; ++l) {
+        const float xh = __double2float_rn(x[l]);
+        const float xl = __double2float_rn(x[l] - (double)xh);
+        rec[2 * l + h] = -leaf_offset(xh, xl, ch[l], cl[l]);
+        rec[6 + 2 * l + h] = (float)f[l];
+    }
+}
+
+// Block r packs the slot range [rb[r], re[r]) of leaf rc[r] from pair pb[r],
+// as hi/lo records (put_pair_half) or, LEAF, as leaf-offset records.
+template <bool LEAF>
 __global__ void k_pack_pairs(const int32_t *__restrict__ rb, const int32_t *__restrict__ re,
-                             const int32_t *__restrict__ pb, int64_t n,
-                             const double *__restrict__ xs, const int32_t *__restrict__ perm,
-                             const double *__restrict__ xyz, const double *__restrict__ w,
+                             const int32_t *__restrict__ pb, const int32_t *__restrict__ rc,
+                             int64_t n, const double *__restrict__ xs,
+                             const int32_t *__restrict__ perm, const dvec4 *__restrict__ clo,
+                             const dvec4 *__restrict__ chi, const double *__restrict__ w,
                              float *__restrict__ out)
 {
     const int r = blockIdx.x;
     const int64_t b = rb[r], e = re[r];
     const int64_t cnt2 = ((e - b + 1) / 2) * 2;
+    if (cnt2 == 0) return;
+    float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+    if (LEAF) leaf_centre(clo[rc[r]], chi[rc[r]], ch, cl);
     for (int64_t i = threadIdx.x; i < cnt2; i += blockDim.x) {
         int64_t slot = b + i;
         double x[3], f[3];
         if (slot < e) {
-            int64_t j = perm ? perm[slot] : slot;
+            int64_t j = perm[slot];
             for (int l = 0; l < 3; ++l) {
-                x[l] = perm ? xs[l * n + slot] : xyz[3 * slot + l];
+                x[l] = xs[l * n + slot];
                 f[l] = w[3 * j + l];
             }
         } else {
@@ -439,7 +465,8 @@ __global__ void k_pack_pairs(const int32_t *__restrict__ rb, const int32_t *__re
                 f[l] = 0.0;
             }
         }
-        put_pair_half(out + ((int64_t)pb[r] + i / 2) * 20, (int)(i & 1), x, f);
+        if (LEAF) put_leaf_pair_half(out + ((int64_t)pb[r] + i / 2) * 12, (int)(i & 1), x, ch, cl, f);
+        else put_pair_half(out + ((int64_t)pb[r] + i / 2) * 20, (int)(i & 1), x, f);
     }
 }
 
@@ -989,8 +1016,9 @@ __global__ void k_items_fill(const BuildState *__restrict__ bs, int m_fixed, int
 }
 
 // Paired-record plan: pb_all = [first pair per cluster (cap, -1 off the
-// leaves) | range begin (cap) | range end (cap) | first pair (cap)], one range
-// per leaf in cluster order, empty ranges after the last leaf.  One block.
+// leaves) | range begin (cap) | range end (cap) | first pair (cap) | leaf of
+// the range (cap)], one range per leaf in cluster order, empty ranges after
+// the last leaf.  One block.
 __global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restrict__ bs, int m_fixed,
                                                      int cap, const int32_t *__restrict__ begin,
                                                      const int32_t *__restrict__ end,
@@ -999,7 +1027,7 @@ __global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restric
                                                      int *__restrict__ err)
 {
     const int m = min(bs ? bs->nclus : m_fixed, cap);
-    int32_t *cpb = pb_all, *rb = pb_all + cap, *re = rb + cap, *pb = re + cap;
+    int32_t *cpb = pb_all, *rb = pb_all + cap, *re = rb + cap, *pb = re + cap, *rc = pb + cap;
     const int per = (cap + blockDim.x - 1) / blockDim.x;
     const int c0 = min(cap, (int)threadIdx.x * per), c1 = min(cap, c0 + per);
     int64_t nl = 0, np = 0;
@@ -1018,13 +1046,14 @@ __global__ void __launch_bounds__(1024) k_pairs_plan(const BuildState *__restric
             rb[r] = begin[c];
             re[r] = over ? begin[c] : end[c];
             pb[r] = over ? 0 : (int32_t)q;
+            rc[r] = c;
             r++;
             q += (end[c] - begin[c] + 1) / 2;
         } else {
             cpb[c] = -1;
         }
     }
-    for (int64_t k = nleaves + threadIdx.x; k < cap; k += blockDim.x) rb[k] = re[k] = pb[k] = 0;
+    for (int64_t k = nleaves + threadIdx.x; k < cap; k += blockDim.x) rb[k] = re[k] = pb[k] = rc[k] = 0;
     if (threadIdx.x == 0 && over) atomicOr(err, ASYNC_RECORD_OVERFLOW);
 }
 
@@ -1158,37 +1187,38 @@ kitc_status pack_sources(const TreeDev *t, const double *xyz_user, const double 
 // Plan of the paired records, made on the device (k_pairs_plan): one range per
 // leaf in cluster order, in room for any leaf sizes of this tree; pbegin
 // receives [first pair of each cluster (nclus, -1 off the leaves) | range
-// begin | range end | first pair (nclus each; empty ranges after the last
-// leaf) | an error word].  Reads nothing back.
-kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, cudaStream_t s, DevBuf &out,
+// begin | range end | first pair | leaf (nclus each; empty ranges after the
+// last leaf) | an error word].  Reads nothing back.
+kitc_status pack_pairs_plan(const TreeDev *t, int64_t n, bool leaf, cudaStream_t s, DevBuf &out,
                             DevBuf &pbegin, int *nranges)
 {
     if (!t) return KITC_ERR_INVALID_ARG;
     const int nclus = t->nclus;
     const int64_t paircap = (n + nclus) / 2 + 1;
-    KITC_TRY(out.reserve((size_t)80 * paircap + 16, s));
-    KITC_TRY(pbegin.reserve(sizeof(int32_t) * (4 * (size_t)nclus + 1) + 16, s));
+    KITC_TRY(out.reserve(pair_record_bytes(leaf) * paircap + 16, s));
+    KITC_TRY(pbegin.reserve(sizeof(int32_t) * (5 * (size_t)nclus + 1) + 16, s));
     int32_t *d = pbegin.as<int32_t>();
     kitc_count_launch();
     k_pairs_plan<<<1, 1024, 0, s>>>(nullptr, nclus, nclus, t->begin.as<int32_t>(), t->end.as<int32_t>(),
                                     t->n_child.as<int32_t>(), d, paircap,
-                                    reinterpret_cast<int *>(d + 4 * (size_t)nclus));
+                                    reinterpret_cast<int *>(d + 5 * (size_t)nclus));
     KITC_CUDA(cudaGetLastError());
     *nranges = nclus;
     return KITC_OK;
 }
 
-kitc_status pack_pairs_launch(const TreeDev *t, const double *xyz_user, const double *w_user,
-                              int64_t n, int nranges, cudaStream_t s, DevBuf &out, DevBuf &pbegin)
+kitc_status pack_pairs_launch(const TreeDev *t, const double *w_user, int64_t n, int nranges,
+                              bool leaf, cudaStream_t s, DevBuf &out, DevBuf &pbegin)
 {
-    int nclus = t ? t->nclus : 1;
+    if (!t) return KITC_ERR_INVALID_ARG;
+    const int nclus = t->nclus;
     int32_t *d = pbegin.as<int32_t>();
     kitc_count_launch();
-    k_pack_pairs<<<(unsigned)nranges, 256, 0, s>>>(d + nclus, d + nclus + nranges,
-                                                   d + nclus + 2 * nranges, n,
-                                                   t ? t->xs.as<double>() : nullptr,
-                                                   t ? t->perm.as<int32_t>() : nullptr, xyz_user,
-                                                   w_user, out.as<float>());
+    (leaf ? k_pack_pairs<true> : k_pack_pairs<false>)<<<(unsigned)nranges, 256, 0, s>>>(d + nclus, d + nclus + nranges,
+                                                   d + nclus + 2 * nranges, d + nclus + 3 * nranges, n,
+                                                   t->xs.as<double>(), t->perm.as<int32_t>(),
+                                                   t->lo.as<dvec4>(), t->hi.as<dvec4>(), w_user,
+                                                   out.as<float>());
     KITC_CUDA(cudaGetLastError());
     return KITC_OK;
 }
@@ -1621,7 +1651,7 @@ int64_t weights_async_itemcap(int cap, int levels, int64_t n, int mode)
 }
 
 kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int mode, bool split,
-                                  bool mixed, bool pairs, bool rowpairs, cudaStream_t s,
+                                  bool mixed, bool pairs, bool rowpairs, bool leaf, cudaStream_t s,
                                   WeightsDev &wd)
 {
     const TreeDev &t = a.t;
@@ -1642,8 +1672,8 @@ kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int m
     if (pairs) {
         const int64_t paircap = (t.n + cap) / 2 + 1;
         KITC_TRY(wd.proxy.reserve((size_t)32 * cap * pair_records(np, rowpairs), s));
-        KITC_TRY(wd.src.reserve((size_t)80 * paircap + 16, s));
-        KITC_TRY(wd.pbegin.reserve(sizeof(int32_t) * 4 * (size_t)cap + 16, s));
+        KITC_TRY(wd.src.reserve(pair_record_bytes(leaf) * paircap + 16, s));
+        KITC_TRY(wd.pbegin.reserve(sizeof(int32_t) * 5 * (size_t)cap + 16, s));
         wd.paircap = paircap;
     } else {
         KITC_TRY(wd.proxy.reserve((size_t)proxy_record_bytes(win, mixed) * cap * np3, s));
@@ -1655,6 +1685,7 @@ kitc_status weights_async_reserve(const TreeAsync &a, int win, int degree, int m
     if (upward) KITC_TRY(allow_up_smem());
     wd.split = split;
     wd.rowpairs = pairs && rowpairs;
+    wd.leaf = pairs && leaf;
     wd.degree = degree;
     wd.win = win;
     wd.mode = mode;
@@ -1716,9 +1747,10 @@ kitc_status weights_async_launch(const TreeAsync &a, const double *w_user, Weigh
         k_pairs_plan<<<1, 1024, 0, s>>>(bs, 0, cap, t.begin.as<int32_t>(), t.end.as<int32_t>(),
                                         t.n_child.as<int32_t>(), d, wd.paircap, err);
         kitc_count_launch();
-        k_pack_pairs<<<(unsigned)cap, 256, 0, s>>>(d + cap, d + 2 * cap, d + 3 * cap, t.n,
-                                                   t.xs.as<double>(), t.perm.as<int32_t>(), nullptr,
-                                                   w_user, wd.src.as<float>());
+        (wd.leaf ? k_pack_pairs<true> : k_pack_pairs<false>)<<<(unsigned)cap, 256, 0, s>>>(d + cap, d + 2 * cap, d + 3 * cap, d + 4 * cap, t.n,
+                                                   t.xs.as<double>(), t.perm.as<int32_t>(),
+                                                   t.lo.as<dvec4>(), t.hi.as<dvec4>(), w_user,
+                                                   wd.src.as<float>());
     } else {
         const int64_t nrec = (int64_t)cap * np3;
         const unsigned g = (unsigned)((nrec + 255) / 256);

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 STOKESLET, ROTLET, STOKESLET_ROTLET, TEST_POLY = 0, 1, 2, 99
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_LEAF = 0, 1, 2
 MAC_PARTICLE, MAC_BATCH, MAC_ALL = 0, 1, 2
 WEIGHTS_UPWARD, WEIGHTS_ALGORITHM1 = 0, 1
 

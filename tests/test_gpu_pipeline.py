@@ -8,7 +8,7 @@ path's decisions in the same order, so the output is compared bit for bit
 with kitc_build_tree / kitc_build_forest + kitc_modified_weights +
 kitc_evaluate(_forest) on the same inputs (which the parity tests compare
 with the oracle):
-* one system, four kernel / precision / MAC / weights-mode combinations,
+* one system, six kernel / precision / MAC / weights-mode combinations,
   separate and self targets, on coordinates and weights other than the
   example's;
 * a forest of 12 systems through the handle's CUDA graph, replayed on new
@@ -77,6 +77,8 @@ CASES = [  # kernel, precision, MAC, weights mode, batch, separate targets
     ("rotlet mixed per-target", 1, 1, 0, 0, 64, False),
     ("stokeslet+rotlet mixed batch", 2, 1, 1, 0, 32, True),
     ("stokeslet fp64 batch algorithm1", 0, 0, 1, 1, 64, False),
+    ("stokeslet leaf-offsets all-targets", 0, 2, 2, 0, 64, True),
+    ("rotlet leaf-offsets per-target", 1, 2, 0, 0, 64, False),
 ]
 
 
