@@ -328,9 +328,9 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------- GPU helpers
 def traffic_per_launch(kernel=None):
-    """DRAM bytes of one evaluator launch (the Stokeslet bench point, or the
-    record named kernel) from the committed ncu capture, if it was taken on the
-    current evaluator source; else None."""
+    """DRAM bytes of one evaluator launch (the Stokeslet bench point in the
+    leaf-offset form, or the record named kernel) from the committed ncu
+    capture, if it was taken on the current evaluator source; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "eval_traffic.json")
     src = os.path.join(ROOT, "paper_1902_02250_gb300", "csrc", "evaluate.cu")
@@ -564,12 +564,20 @@ def run_kitc(args, ws, rank, local):
             % peaks["fp32_tflops"]
     roof = eval_roofline("k_eval<Stokeslet, mixed> (fused near/far evaluator)", FLOPS_PER_INTERACTION,
                          a2["near_pairs"] + a2["far_points"], st["near_exec"] + st["far_exec"],
-                         ev_ms, peaks["fp32_tflops"], src32, traffic_per_launch())
+                         ev_ms, peaks["fp32_tflops"], src32,
+                         traffic_per_launch() if prec == K.MIXED_LEAF else None)
     roof["useful_work"] = ("Algorithm 2 (per-target MAC) interactions at the same theta, n, N0; "
                            "the extra interactions of the batch rule (%s MAC) are overhead" % args.mac)
     # precision floor of the mixed form: mixed direct sum vs FP64 direct sum, same samples
     mixed_direct = K.kitc_direct(yd, xd, fd, K.Params(eps=EPS, precision=K.MIXED)).cpu().numpy()
     floor_E = rel_l2(ref, mixed_direct)
+    leaf_floor_E = None
+    if prec == K.MIXED_LEAF:  # the leaf form's near field alone: theta = 0 makes every pair near
+        o0, _ = K.treecode(xd, fd, K.Params(theta=0.0, degree=1, leaf_size=args.leaf, eps=EPS,
+                                            kernel=K.STOKESLET, precision=K.MIXED_LEAF, mac=mac,
+                                            target_batch=BATCH), yd)
+        leaf_floor_E = rel_l2(ref, o0.cpu().numpy())
+        del o0
     line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -580,6 +588,7 @@ def run_kitc(args, ws, rank, local):
                                         "algorithm2_near": a2["near_pairs"] / N,
                                         "algorithm2_far": a2["far_points"] / N},
             "mixed_floor_E": floor_E,
+            "leaf_floor_E": leaf_floor_E,
             "roofline": roof,
             "rooflines": {"weights": weights_roofline(st, args.degree, 3, stage_ms["ms_weights"],
                                                       peaks, split=True),
