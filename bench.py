@@ -693,7 +693,8 @@ def run_kitc(args, ws, rank, local):
 # 256 independent Stokeslet systems.  N0, batch size and MAC of the configured
 # point (theta = 0.7, n = 6) as tune_forest picked them on a GB300 (N0 in
 # {500, ..., 8000} x batch in {32, 64} x MAC in {particle, batch, all});
-# the E <= 1e-6 point is searched over n and the MAC at theta = 0.7.
+# the E <= 1e-6 point is searched over the mixed form (hi/lo or leaf-offset
+# near-field differences), n and the MAC at theta = 0.7.
 BATCHED_SYSTEMS, BATCHED_SEED = 256, 4
 BATCHED_POINT = dict(theta=0.7, degree=6, leaf_size=4000, target_batch=64, mac="all")
 BATCHED_1E6_SEARCH = (("all", (8, 9, 10, 11)), ("batch", (8, 9, 10, 11)))
@@ -772,23 +773,25 @@ def form_batched(args, rank, dev, steps, warmup, tune_it=False, fp64=True):
         m = float(np.mean(ms))
         return {"value": ntot / (m / 1e3), "ms_per_step": m, "steps": n_steps, "warmup": n_warm,
                 "E_all": e_all, "E_worst_system": worst, "theta": p.theta, "degree": p.degree,
-                "mac": MAC_NAMES[p.mac], "leaf_size": p.leaf_size, "target_batch": p.target_batch}, st
+                "mac": MAC_NAMES[p.mac], "leaf_size": p.leaf_size, "target_batch": p.target_batch,
+                "precision": {K.MIXED: "mixed", K.MIXED_LEAF: "mixed_leaf"}.get(p.precision, "fp64")}, st
 
     l0 = K.kitc_launch_count()
     cfg, st = run(P(**point), steps, warmup)
     peak = measure_peaks(K, dev)["fp32_tflops"] if tune_it else None
-    # the fastest (MAC, n) at theta = 0.7 with E <= 1e-6 over all systems
-    at = None
-    for mac_name, degrees in BATCHED_1E6_SEARCH:
-        for nd in degrees:
-            q = P(**dict(point, degree=nd, mac=mac_name))
-            step(q, out)
-            torch.cuda.synchronize()
-            if errors(out.cpu().numpy())[0] <= TARGET_E:
-                cand, cst = run(q, steps, 1)
-                if at is None or cand["ms_per_step"] < at[0]["ms_per_step"]:
-                    at = (cand, cst)
-                break
+    # the fastest (mixed form, MAC, n) at theta = 0.7 with E <= 1e-6 over all systems
+    at, at_prec = None, K.MIXED
+    for prec in (K.MIXED_LEAF, K.MIXED):
+        for mac_name, degrees in BATCHED_1E6_SEARCH:
+            for nd in degrees:
+                q = P(prec, **dict(point, degree=nd, mac=mac_name))
+                step(q, out)
+                torch.cuda.synchronize()
+                if errors(out.cpu().numpy())[0] <= TARGET_E:
+                    cand, cst = run(q, steps, 1)
+                    if at is None or cand["ms_per_step"] < at[0]["ms_per_step"]:
+                        at, at_prec = (cand, cst), prec
+                    break
     res = {"workload": "256 systems, N_s = round(exp(U[ln 1e3, ln 2e5])), uniform in boxes of side "
                        "U[0.5, 2], total %d targets (seed %d)" % (ntot, BATCHED_SEED + rank),
            "config_point": cfg, "at_1e-6": at[0] if at else None,
@@ -828,7 +831,7 @@ def form_batched(args, rank, dev, steps, warmup, tune_it=False, fp64=True):
                                       "CUDA-graph replay"}
     finally:
         t.free()
-    gp = P(**dict(point, degree=at[0]["degree"], mac=at[0]["mac"])) if at else P(**point)
+    gp = P(at_prec, **dict(point, degree=at[0]["degree"], mac=at[0]["mac"])) if at else P(**point)
     res["graph"] = batched_graph(K, xd, fd, x, f, counts, gp, out, flush, steps, errors)
     if fp64 and at:
         q = P(prec=K.FP64, **dict(point, degree=at[0]["degree"], mac=at[0]["mac"]))
@@ -855,7 +858,8 @@ def batched_graph(K, xd, fd, x, f, counts, p, out, flush, steps, errors):
     stream = torch.cuda.current_stream()
     ntot = len(x)
     res = {"point": {"theta": p.theta, "degree": p.degree, "leaf_size": p.leaf_size,
-                     "target_batch": p.target_batch, "mac": MAC_NAMES[p.mac]}}
+                     "target_batch": p.target_batch, "mac": MAC_NAMES[p.mac],
+                     "precision": {K.MIXED: "mixed", K.MIXED_LEAF: "mixed_leaf"}.get(p.precision, "fp64")}}
     # the eager forest at the same point: every graph result must equal it bit for bit
     t = K.kitc_build_forest(xd, counts, p)
     try:
