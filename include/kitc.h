@@ -66,11 +66,12 @@ typedef enum {
  * the mixed form forms the modified-weight products in split precision
  * (FP32 hi/lo pairs, about 2^-47 relative error per product).
  * KITC_MIXED_LEAF: KITC_MIXED, except that the tree's near field of the
- * Stokeslet and the rotlet forms x - y = (x - c) - (y - c) from offsets to
- * the leaf's box centre c, each computed in FP64 and rounded once to FP32
- * (one FP32 subtraction per coordinate instead of three).  A pair's
- * difference then carries an absolute error of about 2^-24 times the
- * leaf's extent, which matters only for pairs much closer than that: on a
+ * Stokeslet and the rotlet forms x - y = (x - c) - (y - c) from FP32 offsets
+ * to the leaf's box centre c, each within about 2^-23 of its magnitude and
+ * formed by the same arithmetic for targets and sources (a target on a
+ * source gives exactly 0), one FP32 subtraction per coordinate instead of
+ * three.  A pair's difference then carries an absolute error of about 2^-24
+ * times the leaf's extent, which matters only for pairs much closer than that: on a
  * uniform cube (Stokeslet, N = 10^6, N0 = 4000) it changes the output by
  * about 1e-7 relative L2; on clustered inputs (dipole pairs, points on a
  * surface, the rotlet's 1/r^2 near field) by up to ~1e-6.  Direct sums and

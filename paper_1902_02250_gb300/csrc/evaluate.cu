@@ -15,10 +15,11 @@
 //    formed; the per-point work is one rsqrt and a few FMAs.
 //  * KITC_MIXED: coordinate differences of near pairs come from hi/lo FP32
 //    pairs (d = (xh - yh) + (xl - yl), relative error ~1e-7 at any distance);
-//    KITC_MIXED_LEAF (FP32x2 path): from offsets to the leaf's box centre c,
-//    each formed in FP64 and rounded once, d = (x - c) - (y - c), one packed
-//    add per coordinate instead of three.  Far-field points are taken
-//    relative to the batch centre in FP64 and then rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
+//    KITC_MIXED_LEAF (FP32x2 path): d = (x - c) - (y - c) from offsets to the
+//    leaf's box centre c, both formed by the same FP32 arithmetic on hi/lo
+//    parts (leaf_offset), one packed add per coordinate instead of three.
+//    Far-field points are taken relative to the batch centre in FP64 and then
+//    rounded.  Kernel values are FP32, summed in FP32 over runs of at most 8
 //    terms, those runs summed over at most 8, and so on one more level; the
 //    per-leaf / per-cluster sums are accumulated in FP64.
 //  * The mixed Stokeslet and rotlet run on packed FP32x2 arithmetic over pairs
