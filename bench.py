@@ -971,7 +971,8 @@ def run_batched(args, ws, rank, local):
 
 # ------------------------------------------------------- learned-degree form
 # Plummer system (90% Plummer, a = 0.1, truncated at r = 2, plus 10% uniform in
-# [-2,2]^3), Stokeslet, eps = 1e-3, theta = 0.7, batch MAC, mixed, N0 = 2000.
+# [-2,2]^3), Stokeslet, eps = 1e-3, theta = 0.7, batch MAC, N0 = 2000, mixed with
+# the leaf-offset near field (the training, the calibration and both forms).
 # The selector is trained on another system of the same recipe (seed 15); the
 # label budget is the largest of LEARNED_BUDGETS whose learned run on the
 # training system stays within LEARNED_TRAIN_E of the direct sum, so that the
@@ -984,6 +985,7 @@ LEARNED_LEAF = 2000
 LEARNED_BUDGETS = (0.25e-6, 0.35e-6, 0.5e-6, 0.7e-6, 1.0e-6, 1.4e-6, 2.0e-6)
 LEARNED_TRAIN_E = 0.8e-6     # the training system's learned run must stay within this
 LEARNED_MAC = 1              # the box rule (KITC_MAC_BATCH), for both forms
+LEARNED_PRECISION = 2        # KITC_MIXED_LEAF (leaf-offset near field), for both forms
 
 
 def form_learned(args, rank, dev, n, steps, warmup, fp64=True):
@@ -996,7 +998,7 @@ def form_learned(args, rank, dev, n, steps, warmup, fp64=True):
 
     def P(**kw):
         b = dict(theta=0.7, degree=8, leaf_size=LEARNED_LEAF, eps=EPS, kernel=K.STOKESLET,
-                 precision=K.MIXED, mac=LEARNED_MAC, target_batch=BATCH)
+                 precision=LEARNED_PRECISION, mac=LEARNED_MAC, target_batch=BATCH)
         b.update(kw)
         return K.Params(**b)
 
@@ -1054,8 +1056,9 @@ def form_learned(args, rank, dev, n, steps, warmup, fp64=True):
     E_l = rel_l2(ref, out.cpu().numpy()[idx])
     value_l = n / (np.mean(ms_l) / 1e3)
     res = {"workload": "Plummer a = 0.1 truncated at r = 2 (90%%) + U[-2,2]^3 (10%%), N = %d, "
-                       "seed %d; f ~ U[-1,1]^3; eps = %g, theta = 0.7, N0 = %d, %s MAC"
-                       % (n, LEARNED_SEED + rank, EPS, LEARNED_LEAF, MAC_NAMES[LEARNED_MAC]),
+                       "seed %d; f ~ U[-1,1]^3; eps = %g, theta = 0.7, N0 = %d, %s MAC, "
+                       "leaf-offset near field" % (n, LEARNED_SEED + rank, EPS, LEARNED_LEAF,
+                                                   MAC_NAMES[LEARNED_MAC]),
            "learned": {"value": value_l, "ms_per_step": float(np.mean(ms_l)), "steps": steps,
                        "warmup": warmup, "E": E_l, "far_points": st_l["far_points"],
                        "near_pairs": st_l["near_pairs"],

@@ -134,11 +134,13 @@ def test_fp64_batch_mac_per_cluster_degree_zero_where_unused(K, orc):
 
 @pytest.mark.parametrize("kernel", [ST, RO])
 @pytest.mark.parametrize("mac", [0, 1])
-def test_mixed_per_cluster_degree(K, orc, kernel, mac):
-    """FP32x2 paired records (Stokeslet) and per-point records (rotlet)."""
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_per_cluster_degree(K, orc, kernel, mac, prec):
+    """FP32x2 paired grid records of every degree, with the near field's
+    hi/lo (KITC_MIXED) or leaf-offset (KITC_MIXED_LEAF) source records."""
     x, f = wl.uniform_cube(20000, 69)
     p = K.Params(theta=0.6, degree=6, leaf_size=300, eps=0.005, kernel=kernel, mac=mac,
-                 precision=K.MIXED)
+                 precision=prec)
     t = K.kitc_build_tree(dev(x), p)
     deg = random_degrees(t.stats()["n_clusters"], 70, 2, 16)
     K.kitc_set_degrees(t, deg)
@@ -153,7 +155,7 @@ def test_mixed_per_cluster_degree(K, orc, kernel, mac):
     else:
         ref = o.treecode_batch_var(f, fh, deg, foff, kernel, 0.005, 0.6, x, 64, 64,
                                    select=sel)[0][sel]
-    check_mixed(ref, got[sel], "per-cluster degree kernel=%d mac=%d" % (kernel, mac))
+    check_mixed(ref, got[sel], "per-cluster degree kernel=%d mac=%d precision=%d" % (kernel, mac, prec))
     t.free()
 
 
