@@ -62,9 +62,10 @@ typedef enum {
  * from hi/lo FP32 pairs, far-field points taken relative to the target
  * batch's centre), FP32 partial sums over short runs, FP64 accumulation
  * of the per-leaf and per-cluster sums.  The tree, the MAC decisions, the
- * barycentric denominators and the modified-weight sums are FP64 in both;
- * the mixed form forms the modified-weight products in split precision
- * (FP32 hi/lo pairs, about 2^-47 relative error per product).
+ * differences y - s_k of the barycentric basis and the modified-weight sums
+ * are FP64 in both; the mixed form takes the basis's quotients and the
+ * modified-weight products in split precision (FP32 hi/lo pairs, about
+ * 2^-45 and 2^-47 relative error).
  * KITC_MIXED_LEAF: KITC_MIXED, except that the tree's near field of the
  * Stokeslet and the rotlet forms x - y = (x - c) - (y - c) from FP32 offsets
  * to the leaf's box centre c, each within about 2^-23 of its magnitude and

@@ -617,44 +617,70 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
     return *reinterpret_cast<const float2 *>(&rd);
 }
 
+// (a.x + a.y) + (b.x + b.y) as an FP32 pair: TwoSum of the high parts, the
+// low parts added to its error, renormalised (Fast2Sum).
+__device__ __forceinline__ float2 add_f2(float2 a, float2 b)
+{
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    const float c = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float hi = __fadd_rn(s, c);
+    return make_float2(hi, __fsub_rn(c, __fsub_rn(hi, s)));
+}
+
+// 1 / (a.x + a.y) as an FP32 pair: the correctly rounded reciprocal r of the
+// high part, then one Newton step r + r (1 - a r), the residual formed with
+// the exact product a.x r (TwoProduct by FMA); relative error about 2^-46.
+__device__ __forceinline__ float2 rcp_f2(float2 a)
+{
+    const float r = __frcp_rn(a.x);
+    const float p = __fmul_rn(a.x, r);
+    const float e = __fmaf_rn(a.x, r, -p);                       // a.x r = p + e
+    const float res = __fmaf_rn(-a.y, r, __fsub_rn(__fsub_rn(1.f, p), e));  // 1 - a r
+    const float c = __fmul_rn(r, res);
+    const float hi = __fadd_rn(r, c);
+    return make_float2(hi, __fsub_rn(c, __fsub_rn(hi, r)));
+}
+
 // Barycentric basis of the coordinate y at the grid points s[0..n] of an
-// interval of width 1/iw, written to Lj as FP32 hi/lo pairs.  The same
-// values as bary_basis (the second barycentric form, Eq. Barycentric-1D)
-// with the same coincident-point rule: numerator and denominator multiplied
-// by prod_j (y - s_j) iw, so that
-//   L_k = w_k P_k / sum_j w_j P_j,   P_k = prod_{j != k} (y - s_j) iw,
-// from prefix and suffix products and one reciprocal instead of one per
-// point.  iw keeps every factor in [-1, 1]; the factors other than the
-// nearest point's are at least half a Chebyshev spacing, so the largest P_k
-// cannot underflow.  The FP64 values are formed in the 8-byte slots of Lj and
-// split in place.
+// interval of width 1/iw, written to Lj as FP32 hi/lo pairs: the second
+// barycentric form (Eq. Barycentric-1D) with the same coincident-point rule
+// as bary_basis,
+//   L_k = (w_k / q_k) / sum_j (w_j / q_j),   q_j = (y - s_j) iw,
+// with the differences and q_j in FP64 and the reciprocals, the sum and the
+// quotients in FP32 pairs (about 2^-45 relative), which leaves the FP64 pipe
+// one subtraction, one product and the conversion of q_j per point.  iw keeps
+// every q_j in [-1, 1]; a point whose |q_j| is at most 2^-60 is taken as
+// coinciding too (its L_j is 1 to within 2^-58, beyond the pairs' range of
+// reciprocals).
 __device__ __forceinline__ void bary_basis_split(const Cheb &cb, const double *__restrict__ s, double iw,
                                                  double y, float2 *Lj)
 {
     const int np = cb.n + 1;
-    double *Ld = reinterpret_cast<double *>(Lj);
     int flag = -1;
-    double pre = 1.0;
+    float2 S = make_float2(0.f, 0.f);
     for (int k = 0; k < np; ++k) {
         const double d = y - s[k];
-        // |d| <= DBL_MIN, tested on the bits (d is finite)
-        if ((__double_as_longlong(d) & 0x7fffffffffffffffll) <= 0x0010000000000000ll) flag = k;
-        Ld[k] = pre;
-        pre *= d * iw;
+        const double q = d * iw;
+        // |d| <= DBL_MIN or |q| <= 2^-60, tested on the bits (d and q are finite)
+        if ((__double_as_longlong(d) & 0x7fffffffffffffffll) <= 0x0010000000000000ll ||
+            (__double_as_longlong(q) & 0x7fffffffffffffffll) <= 0x3c30000000000000ll)
+            flag = k;
+        // w_k = (-1)^k, halved at both ends (the weights of make_cheb): exact
+        const float wk = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == cb.n) ? 0.5f : 1.f);
+        float2 r = rcp_f2(split_f2(q));
+        r.x *= wk;
+        r.y *= wk;
+        Lj[k] = r;
+        S = add_f2(S, r);
     }
     if (flag >= 0) {
         for (int k = 0; k < np; ++k) Lj[k] = make_float2(k == flag ? 1.f : 0.f, 0.f);
         return;
     }
-    double suf = 1.0, D = 0.0;
-    for (int k = np - 1; k >= 0; --k) {
-        const double pk = Ld[k] * suf;
-        Ld[k] = pk;
-        D = fma(cb.w[k], pk, D);
-        suf *= (y - s[k]) * iw;
-    }
-    const double rD = __drcp_rn(D);
-    for (int k = 0; k < np; ++k) Lj[k] = split_f2(Ld[k] * (cb.w[k] * rD));
+    const float2 rS = rcp_f2(S);
+    for (int k = 0; k < np; ++k) Lj[k] = mul_f2(Lj[k], rS);
 }
 
 template <int R, int C>

@@ -80,3 +80,36 @@ def test_weights_of_large_and_small_magnitude(K, orc):
     ref = orc.Tree(x, 250).modified_weights(f, 5)
     for q in range(3):
         assert _maxrel(got[..., q], ref[..., q]) <= TOL, q
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_basis_at_and_near_grid_points(K, orc, n):
+    """One leaf whose box is exactly [0, 1]^3 (corner particles): particles on
+    grid points (0, 1/2 for even n, 1; Eq. Barycentric-1D's coincident case),
+    within 1e-25 and 1e-30 of the grid point 0 (taken as coinciding by the
+    FP32-pair basis, |q| <= 2^-60; by the oracle evaluated, L = 1 within 1e-25),
+    and a slab of particles on one plane of a flat second leaf's box."""
+    g = wl.rng(163)
+    x = g.uniform(0.0, 1.0, size=(1500, 3))
+    special = np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [0.0, 0.5, 1.0], [1e-25, 0.5, 1e-30],
+                        [0.5, 1e-22, 0.5], [1.0, 1e-25, 0.0]])
+    x = np.vstack([special, x])
+    f = g.uniform(-1.0, 1.0, size=(len(x), 3))
+    p = K.Params(theta=0.7, degree=n, leaf_size=len(x), eps=0.01, precision=K.MIXED)
+    t = K.kitc_build_tree(dev(x), p)
+    assert t.stats()["n_clusters"] == 1
+    K.kitc_modified_weights(t, dev(f))
+    got = t.weights()
+    t.free()
+    ref = orc.Tree(x, len(x)).modified_weights(f, n)
+    assert _maxrel(got[0], ref[0]) <= TOL
+    # a flat axis: every z equal, so every grid point of that axis coincides
+    # (the last one is taken, reading R9)
+    xs = x.copy()
+    xs[:, 2] = 0.3
+    t = K.kitc_build_tree(dev(xs), p)
+    K.kitc_modified_weights(t, dev(f))
+    got = t.weights()
+    t.free()
+    ref = orc.Tree(xs, len(xs)).modified_weights(f, n)
+    assert _maxrel(got[0], ref[0]) <= TOL
