@@ -201,8 +201,8 @@ def config(args, precision):
     return {"workload": "uniform cube [-1,1]^3, N=1,000,000 (seed 2 + rank), Stokeslet, f ~ U[-1,1]^3",
             "eps": EPS, "theta": args.theta, "degree": args.degree, "leaf_size": args.leaf,
             "target_batch": BATCH, "mac": args.mac, "precision": precision,
-            "near_differences": "offsets to the leaf's box centre, rounded once to FP32"
-            if precision == "mixed_leaf" else "hi/lo FP32 pairs",
+            "near_differences": {"mixed_leaf": "offsets to the leaf's box centre, as FP32",
+                                 "mixed": "hi/lo FP32 pairs"}.get(precision, "FP64"),
             "parameters": "fastest with E <= 8e-7 on seeds 2, 3, 4 (sweep of MAC rule, theta, n)"
             if not args.literal else "literal",
             "error": "rel. L2 vs FP64 direct sum on %d sampled targets" % N_SAMPLE,
