@@ -286,13 +286,18 @@ def test_invalid_arguments_and_state(K):
     assert L.kitc_build_tree(K._np(host), 100, ctypes.byref(p), None, ctypes.byref(h)) == 1
     assert L.kitc_build_tree(None, 100, ctypes.byref(p), None, ctypes.byref(h)) == 1
     for field, bad in (("degree", 0), ("degree", 17), ("leaf_size", 0), ("theta", -1.0),
-                       ("eps", -0.1), ("kernel", 5), ("target_batch", 65)):
+                       ("eps", -0.1), ("kernel", 5), ("target_batch", 65), ("precision", 3),
+                       ("precision", -1)):
         q = K.Params().c()
         setattr(q, field, bad)
         assert L.kitc_build_tree(ctypes.c_void_p(x.data_ptr()), 100, ctypes.byref(q), None,
                                  ctypes.byref(h)) == 1, field
     assert L.kitc_build_tree(ctypes.c_void_p(x.data_ptr()), 0, ctypes.byref(p), None,
                              ctypes.byref(h)) == 1
+    for prec in (K.MIXED, K.MIXED_LEAF):  # the test kernel is FP64 only
+        q = K.Params(kernel=K.TEST_POLY, precision=prec).c()
+        assert L.kitc_build_tree(ctypes.c_void_p(x.data_ptr()), 100, ctypes.byref(q), None,
+                                 ctypes.byref(h)) == 1, prec
     t = K.kitc_build_tree(x, K.Params())
     out = torch.empty((100, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(K.KitcError) as e:
