@@ -5,7 +5,8 @@
   oracle's Algorithm 2, and both against the full FP64 direct sum (10^8 pairs).
 * N = 1,000,000 uniform (seed 2), eps = 1e-3, the bench point (all-targets
   MAC, theta = 0.68, n = 9, N0 = 4000) in the launch configuration the bench
-  times: sampled targets against the oracle's treecode with the same MAC rule
+  times, in both mixed forms (leaf-offset and hi/lo near-field differences):
+  sampled targets against the oracle's treecode with the same MAC rule
   computed one by one, and the relative L2 error against the FP64 direct sum
   within 1e-6.
 * N = 1,000,000 on the unit sphere (seed 3), torques N(0,1), rotlet, eps = 0.005:
@@ -69,16 +70,18 @@ def test_config_n10k(K, orc):
     assert orc.rel_l2(direct, gd) <= 1e-12
 
 
-def test_config_bench_point_1m(K, orc):
-    """The mixed treecode where the bench times it, against the oracle's
-    treecode with the same MAC rule on sampled targets (exact counts)."""
+@pytest.mark.parametrize("prec", ["MIXED_LEAF", "MIXED"])
+def test_config_bench_point_1m(K, orc, prec):
+    """The mixed treecode where the bench times it (the headline's leaf-offset
+    form, and the hi/lo form timed beside it), against the oracle's treecode
+    with the same MAC rule on sampled targets (exact counts)."""
     import torch
     import bench
     x, f = wl.uniform_cube(bench.N, bench.SEED)
     xd, fd = dev(x), dev(f)
     mac = bench.MAC_IDS[bench.MAC]
     p = K.Params(theta=bench.THETA, degree=bench.DEGREE, leaf_size=bench.LEAF, eps=bench.EPS,
-                 precision=K.MIXED, mac=mac, target_batch=bench.BATCH)
+                 precision=getattr(K, prec), mac=mac, target_batch=bench.BATCH)
     out, st = K.treecode(xd, fd, p)
     got = out.cpu().numpy()
     sel = wl.sample_indices(len(x), 300, 2024)
@@ -86,7 +89,7 @@ def test_config_bench_point_1m(K, orc):
     ref = o.treecode_batch(f, o.modified_weights(f, bench.DEGREE), bench.DEGREE, orc.STOKESLET,
                            bench.EPS, bench.THETA, x, bench.BATCH, bench.BATCH, select=sel,
                            all_targets=(mac == K.MAC_ALL))
-    check_mixed(ref["out"][sel], got[sel], "bench point N=10^6")
+    check_mixed(ref["out"][sel], got[sel], "bench point N=10^6 %s" % prec)
     assert st["far_points"] == ref["counts"][1] and st["near_pairs"] == ref["counts"][0]
     idx = torch.from_numpy(wl.sample_indices(len(x), 2000, 102)).cuda()
     d = K.kitc_direct(xd[idx].contiguous(), xd, fd, K.Params(eps=bench.EPS, precision=K.FP64)).cpu().numpy()
