@@ -64,7 +64,9 @@ N_SAMPLE = 10_000        # targets of the error estimate (drawn without replacem
 CPU_SAMPLE = 30_000      # targets of one timed CPU-oracle sample (both CPU legs)
 SAMPLE_SEED = 102
 L2_FLUSH_BYTES = 256 << 20
-FLOPS_PER_INTERACTION = 32   # one Stokeslet k(x, y) f, FMA = 2 (see the design notes)
+# one Stokeslet k(x, y) f, an FMA counted as 2: d = x - y 3, rho^2 6, rsqrt 1, ri^2 and
+# ri^3 2, H1 2, f.d 5, s = (f.d) ri^3 1, u += f H1 + d s 12
+FLOPS_PER_INTERACTION = 32
 ROTLET_FLOPS_PER_INTERACTION = 57   # one rotlet (u, w) pair, counted the same way
 TARGET_E = 1e-6
 

@@ -14,8 +14,7 @@
  * tree-split and MAC predicates below must take the same IEEE decisions as
  * any other implementation that writes the same expressions.
  *
- * Readings of points the paper leaves open (each is also listed in the
- * design notes of the repository):
+ * Readings of points the paper leaves open:
  *   - leaf rule: a cluster is a leaf iff it holds <= N0 particles (Sec. 6,
  *     "maximum leaf size N0" of Algorithm 2);
  *   - l_max is the longest side of the cluster being split (Sec. 6 says

@@ -4,7 +4,7 @@ through the C ABI.
 Tolerances: integer work (tree order, boxes, list entries, interaction
 counts) must be bit-exact; FP64 results must agree to a relative L2 error of
 1e-12; the mixed form (FP32 kernel values, FP64 sums) is held to
-MIXED_TOL, derived in the design notes from FP32 rounding: a pair's value
+MIXED_TOL, derived from FP32 rounding: a pair's value
 carries a few units of 2^-24 ~ 6e-8 of relative error, and sums over runs of
 <= 8 terms, three levels deep, add about sqrt(3 * 4) units more, so the
 relative L2 error of u sits near 3e-7; the bound keeps a factor ~3 margin.
