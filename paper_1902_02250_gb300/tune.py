@@ -127,12 +127,15 @@ def main():
     ap.add_argument("--budget", type=float, default=8e-7)
     ap.add_argument("--samples", type=int, default=4000)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_leaf", "fp64"],
+                    help="mixed_leaf: near-field differences from leaf offsets")
     args = ap.parse_args()
     x, f = wl.uniform_cube(args.n, args.seed)
     xd = torch.from_numpy(x).cuda()
     fd = torch.from_numpy(f).cuda()
     idx = wl.sample_indices(args.n, args.samples, 101)
-    base = K.Params(eps=args.eps, precision=K.MIXED)
+    base = K.Params(eps=args.eps, precision={"mixed": K.MIXED, "mixed_leaf": K.MIXED_LEAF,
+                                             "fp64": K.FP64}[args.precision])
     ref = K.kitc_direct(xd[torch.from_numpy(idx).cuda()].contiguous(), xd, fd,
                         K.Params(eps=args.eps, precision=K.FP64)).cpu().numpy()
     best, recs = tune(xd, fd, base, args.budget, idx, ref, log=lambda r: print(json.dumps(r), flush=True))
