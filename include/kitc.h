@@ -72,11 +72,11 @@ typedef enum {
  * formed by the same arithmetic for targets and sources (a target on a
  * source gives exactly 0), one FP32 subtraction per coordinate instead of
  * three.  A pair's difference then carries an absolute error of about 2^-24
- * times the leaf's extent, which matters only for pairs much closer than that: on a
- * uniform cube (Stokeslet, N = 10^6, N0 = 4000) it changes the output by
- * about 1e-7 relative L2; on clustered inputs (dipole pairs, points on a
- * surface, the rotlet's 1/r^2 near field) by up to ~1e-6.  Direct sums and
- * the other kernels are the same as KITC_MIXED. */
+ * times the leaf's extent, which matters only for pairs much closer than
+ * that: on a uniform cube (Stokeslet, N = 10^6, N0 = 4000) it changes the
+ * output by about 1e-7 relative L2; on clustered inputs (dipole pairs,
+ * points on a surface, the rotlet's 1/r^2 near field) by up to ~1e-6.
+ * Direct sums and the other kernels are the same as KITC_MIXED. */
 typedef enum { KITC_FP64 = 0, KITC_MIXED = 1, KITC_MIXED_LEAF = 2 } kitc_precision;
 
 /* Traversal.  KITC_MAC_PARTICLE takes Algorithm 2's decision for every
