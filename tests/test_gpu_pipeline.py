@@ -11,9 +11,9 @@ with the oracle):
 * one system, six kernel / precision / MAC / weights-mode combinations,
   separate and self targets, on coordinates and weights other than the
   example's;
-* a forest of 12 systems through the handle's CUDA graph, replayed on new
-  values written into the same buffers, with exact interaction counts and no
-  allocation across replays;
+* a forest of 12 systems through the handle's CUDA graph (hi/lo and
+  leaf-offset near fields), replayed on new values written into the same
+  buffers, with exact interaction counts and no allocation across replays;
 * a forest whose systems have target sets of their own (rotlet, per-target
   MAC, batches of 48), through run() and the graph;
 * the degenerate trees of the eager tree tests (one particle, a root leaf,
@@ -108,7 +108,8 @@ def test_pipeline_matches_eager_bit_for_bit(K, name, kernel, prec, mac, wmode, b
         pipe.free()
 
 
-def test_pipeline_forest_graph_replay_bit_for_bit(K):
+@pytest.mark.parametrize("prec", ["MIXED", "MIXED_LEAF"])
+def test_pipeline_forest_graph_replay_bit_for_bit(K, prec):
     """A forest through the handle's CUDA graph: replayed on new coordinates
     and weights written into the captured buffers, bit-identical to the eager
     forest each time, and no device memory allocated across replays."""
@@ -117,7 +118,7 @@ def test_pipeline_forest_graph_replay_bit_for_bit(K):
     sc = np.array([len(s[0]) for s in systems], np.int64)
     x0 = np.concatenate([s[0] for s in systems])
     f0 = np.concatenate([s[1] for s in systems])
-    p = K.Params(theta=0.7, degree=7, leaf_size=1000, eps=1e-3, precision=K.MIXED,
+    p = K.Params(theta=0.7, degree=7, leaf_size=1000, eps=1e-3, precision=getattr(K, prec),
                  mac=K.MAC_ALL, target_batch=64)
     pipe = K.Pipeline(dev(x0), p, src_counts=sc)
     try:
