@@ -363,7 +363,7 @@ def test_forest_of_one_equals_tree(K):
 
 
 # ------------------------------------------------------------ kitc_apply
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_apply_replays_with_new_weights(K, precision):
     import torch
     x, f1 = wl.uniform_cube(20000, 54)
