@@ -14,6 +14,16 @@ def test_defaults(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
     assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "kitc"
+    assert a.precision == "mixed_leaf"
+    assert (a.theta, a.degree, a.leaf, a.mac) == (bench.THETA, bench.DEGREE, bench.LEAF, bench.MAC)
+
+
+def test_config_names_the_near_field_form():
+    import bench
+    monkey = type("A", (), dict(theta=0.68, degree=9, leaf=4000, mac="all", literal=False))
+    assert "leaf" in bench.config(monkey, "mixed_leaf")["near_differences"]
+    assert "hi/lo" in bench.config(monkey, "mixed")["near_differences"]
+    assert bench.config(monkey, "fp64 (CPU oracle)")["near_differences"] == "FP64"
 
 
 def test_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
