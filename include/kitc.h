@@ -76,7 +76,8 @@ typedef enum {
  * that: on a uniform cube (Stokeslet, N = 10^6, N0 = 4000) it changes the
  * output by about 1e-7 relative L2; on clustered inputs (dipole pairs,
  * points on a surface, the rotlet's 1/r^2 near field) by up to ~1e-6.
- * Direct sums and the other kernels are the same as KITC_MIXED. */
+ * Direct sums, the other kernels and eps = 0 (where nothing bounds the
+ * kernel of a close pair) are the same as KITC_MIXED. */
 typedef enum { KITC_FP64 = 0, KITC_MIXED = 1, KITC_MIXED_LEAF = 2 } kitc_precision;
 
 /* Traversal.  KITC_MAC_PARTICLE takes Algorithm 2's decision for every

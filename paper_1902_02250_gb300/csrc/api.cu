@@ -176,7 +176,7 @@ void fill_eval_common(EvalArgs &a, const kitc_params &p, int *flags)
     a.queue = flags;
     a.err = flags + 1;
     a.wait_ns = (unsigned long long)g_wait_limit_ms * 1000000ull;
-    a.leaf = uses_leaf_offsets(p.kernel, p.precision);
+    a.leaf = uses_leaf_offsets(p);
 }
 
 bool weights_split_enabled() { return g_weights_split; }
@@ -316,7 +316,7 @@ static kitc_status launch_weights(kitc_tree t, const double *w, cudaStream_t s)
     const bool mixed = is_mixed(t->p.precision);
     const bool pairs = uses_pair_records(t->p.kernel, mixed);
     t->wts.rowpairs = pairs && uses_row_pairs(t->p.kernel);
-    const bool leaf = uses_leaf_offsets(t->p.kernel, t->p.precision);
+    const bool leaf = uses_leaf_offsets(t->p);
     if (t->var) {
         KITC_TRY(weights_launch_var(t->src, w, t->wts, s));
         KITC_TRY(pack_proxies_var(t->src, t->wts, t->cdeg.as<int32_t>(), t->roff.as<int64_t>(),
@@ -352,7 +352,7 @@ static kitc_status prepare_weights(kitc_tree t, cudaStream_t s)
         KITC_TRY(weights_plan(t->src, t->win, t->p.degree, t->p.weights, s, t->wts));
     }
     if (uses_pair_records(t->p.kernel, is_mixed(t->p.precision)) && !t->pairs_planned) {
-        KITC_TRY(pack_pairs_plan(&t->src, t->src.n, uses_leaf_offsets(t->p.kernel, t->p.precision), s,
+        KITC_TRY(pack_pairs_plan(&t->src, t->src.n, uses_leaf_offsets(t->p), s,
                                  t->wts.src, t->wts.pbegin,
                                  &t->wts.pair_ranges));
         t->pairs_planned = true;

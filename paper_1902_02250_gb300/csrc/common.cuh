@@ -208,10 +208,12 @@ constexpr bool uses_pair_records(int kernel, bool mixed)
 }
 // Both mixed forms (FP32 kernel values, FP64 sums).
 constexpr bool is_mixed(int precision) { return precision == KITC_MIXED || precision == KITC_MIXED_LEAF; }
-// A tree's paired source records hold offsets from the leaf's box centre.
-constexpr bool uses_leaf_offsets(int kernel, int precision)
+// A tree's paired source records hold offsets from the leaf's box centre
+// (KITC_MIXED_LEAF with eps > 0: at eps = 0 nothing bounds the kernel of a
+// close pair, whose difference would then carry the offsets' rounding).
+inline bool uses_leaf_offsets(const kitc_params &p)
 {
-    return precision == KITC_MIXED_LEAF && uses_pair_records(kernel, true);
+    return p.precision == KITC_MIXED_LEAF && uses_pair_records(p.kernel, true) && p.eps > 0.0;
 }
 // Paired FP32x2 grid records of the modified weights.
 kitc_status pack_proxy_pairs(const TreeDev &t, WeightsDev &wd, cudaStream_t s);

@@ -170,7 +170,7 @@ kitc_status kitc_pipeline_create(const double *src_xyz, const int64_t *src_count
     if (st == KITC_OK)
         st = weights_async_reserve(h->src, h->win, p->degree, p->weights, mixed && weights_split_enabled(),
                                    mixed, pairs, pairs && uses_row_pairs(p->kernel),
-                                   uses_leaf_offsets(p->kernel, p->precision), s, h->wts);
+                                   uses_leaf_offsets(*p), s, h->wts);
     if (st == KITC_OK) st = lists_async_reserve(h->src, h->tgt, B, cap_far, cap_near, s, h->lists);
     if (st == KITC_OK) st = h->flags.reserve(4 * sizeof(int), s);
     for (cudaStream_t *q : {&h->side[0], &h->side[1], &h->cap})

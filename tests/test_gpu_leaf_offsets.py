@@ -4,8 +4,11 @@ c, each rounded once to FP32, instead of from hi/lo pairs.
 
 * against the FP64 oracle on the Stokeslet (uniform, Plummer and slab inputs,
   per-target and all-targets MAC, even and odd grids, ragged leaves and
-  batches, separate targets, batches of <= 32 with one target per lane, eps = 0
-  with coincident points) with the mixed bounds of mixed_parity;
+  batches, leaves of 1 to 7 particles, degrees 1 and 16, separate targets,
+  batches of <= 32 with one target per lane) with the mixed bounds of
+  mixed_parity;
+* eps = 0 (Stokeslet on a cube, rotlet on the sphere, coincident points):
+  the hi/lo differences, bit for bit KITC_MIXED;
 * the rotlet on the unit sphere with the leaf form's own bound (LEAF_ROT_TOL):
   its 1/r^2 near field over a surface meets pairs far closer than the leaf's
   extent, where the offsets' rounding (about 2^-24 of the extent) shows;
@@ -96,19 +99,21 @@ def test_separate_targets_and_small_batches(K, orc):
         check_mixed(ref, out.cpu().numpy(), "leaf offsets separate targets B=%d" % B)
 
 
-def test_eps0_with_coincident_points(K, orc):
-    """eps = 0: a target on a source (and 40 duplicated points) contributes
-    nothing (Sec. 1); the target's and the record's offsets are formed by the
-    same arithmetic, so x - y is exactly zero there."""
+def test_eps0_is_the_hi_lo_form(K, orc):
+    """eps = 0: nothing bounds the kernel of a close pair, so the leaf form
+    takes the hi/lo differences there; the result equals KITC_MIXED's bit for
+    bit, and a target on a source (40 duplicated points) contributes nothing
+    (Sec. 1)."""
     x, f = wl.uniform_cube(6000, 188)
     x[100:140] = x[0]
-    p = K.Params(theta=0.7, degree=5, leaf_size=200, eps=0.0, precision=K.MIXED_LEAF,
-                 mac=K.MAC_ALL)
-    out, _ = K.treecode(dev(x), dev(f), p)
-    got = out.cpu().numpy()
+    outs = []
+    for prec in (K.MIXED_LEAF, K.MIXED):
+        p = K.Params(theta=0.7, degree=5, leaf_size=200, eps=0.0, precision=prec, mac=K.MAC_ALL)
+        outs.append(K.treecode(dev(x), dev(f), p)[0].cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
     ref, _ = oracle_out(orc, x, f, ST, 0.0, 0.7, 5, 200, 2, 64)
-    assert np.all(np.isfinite(got))
-    check_mixed(ref, got, "leaf offsets eps=0")
+    assert np.all(np.isfinite(outs[0]))
+    check_mixed(ref, outs[0], "leaf offsets eps=0")
 
 
 def test_rotlet_on_the_sphere(K, orc):
@@ -163,3 +168,37 @@ def test_forest_matches_oracle_per_system(K, orc):
         xs, fs = x[off[k]:off[k + 1]], f[off[k]:off[k + 1]]
         ref, _ = oracle_out(orc, xs, fs, ST, 0.002, 0.7, 6, 300, 2, 64)
         check_mixed(ref, got[off[k]:off[k + 1]], "leaf offsets forest system %d" % k)
+
+
+@pytest.mark.parametrize("N0,n", [(1, 3), (3, 1), (7, 16)])
+def test_small_leaves_and_extreme_degrees(K, orc, N0, n):
+    """Leaves of one to seven particles (odd sizes: a padding point in most
+    leaf records) and the smallest and largest degrees, per-target MAC."""
+    x, f = wl.uniform_cube(3001, 191)
+    p = K.Params(theta=0.6, degree=n, leaf_size=N0, eps=0.02, precision=K.MIXED_LEAF,
+                 mac=K.MAC_PARTICLE)
+    out, st = K.treecode(dev(x), dev(f), p)
+    ref, cnt = oracle_out(orc, x, f, ST, 0.02, 0.6, n, N0, 0, 64)
+    assert st["near_pairs"] == cnt[0] and st["far_points"] == cnt[1]
+    check_mixed(ref, out.cpu().numpy(), "leaf offsets N0=%d n=%d" % (N0, n))
+
+
+def test_rotlet_eps0_is_the_hi_lo_form(K, orc):
+    """The rotlet at eps = 0 on the sphere with 30 duplicated points, whose
+    closest distinct pairs lie ~1e-3 apart in leaves ~0.5 wide: with leaf
+    offsets their 1/r^2 terms would carry errors of order 1e-4 of the
+    output, so the leaf form takes the hi/lo differences at eps = 0 (bit for
+    bit KITC_MIXED), within the mixed bounds of the oracle."""
+    x, f = wl.sphere_surface(5000, 192)
+    x[200:230] = x[7]
+    outs = []
+    for prec in (K.MIXED_LEAF, K.MIXED):
+        p = K.Params(theta=0.6, degree=5, leaf_size=250, eps=0.0, kernel=RO, precision=prec,
+                     mac=K.MAC_ALL)
+        out, st = K.treecode(dev(x), dev(f), p)
+        outs.append(out.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    ref, cnt = oracle_out(orc, x, f, RO, 0.0, 0.6, 5, 250, 2, 64)
+    assert st["near_pairs"] == cnt[0] and st["far_points"] == cnt[1]
+    assert np.all(np.isfinite(outs[0]))
+    check_mixed(ref, outs[0], "rotlet eps=0 (hi/lo differences)")
